@@ -1,0 +1,252 @@
+"""Pins of the oracle's time step (Secs. II-III): conservation, steady uniform equilibrium,
+mirror symmetry, a long-hand brute-force RHS on a tiny grid, and the analytic
+Navier-Stokes Couette profile u_phi = A R + B/R (Sec. II macroscopic equations)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import equilibrium as eq
+from oracle import geometry as geo
+from oracle import model
+from oracle import solver as S
+from paper_2403_15051_gb300 import workloads as wl
+
+
+def _perturbed(P, seed=1, amp=0.05):
+    return S.uniform_state(P) * wl.perturbation(P.shape, seed, amp)
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_mass_conserved_to_roundoff(g, beta):
+    # needs N_a >= 3 on every axis: the Shakhov and J1 factors are cubic in xi (A5 reading)
+    P = S.make_problem(g, 1.0, 2.5, 24, 4, 4, 5, eta0=0.15, Kn=0.1, beta=beta,
+                       T_wall=(1.0, 1.2), u_wall=((0.2, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    f = _perturbed(P)
+    m0 = S.total_mass(f, P)
+    f = S.run(f, P, 20)
+    assert abs(S.total_mass(f, P) - m0) / m0 < 1e-13
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_uniform_equilibrium_is_steady(g, beta):
+    # walls at rest at T = 1 and chi from the local density: the uniform equilibrium is an
+    # exact discrete steady state (advection, curvature force and wall terms cancel)
+    P = S.make_problem(g, 1.0, 3.0, 20, 4, 4, 4, eta0=0.2, Kn=0.1, beta=beta, chi_model=S.SET_LOCAL)
+    f = S.uniform_state(P)
+    L = S.rhs(f, P)
+    assert np.max(np.abs(L)) < 1e-12 * np.max(np.abs(f)) / P.dt * P.dt  # relative to f per unit time
+    g1 = S.run(f, P, 5)
+    assert np.max(np.abs(g1 - f)) <= 1e-13 * np.max(np.abs(f))
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+def test_collision_and_force_conserve_mass_per_cell(g):
+    P = S.make_problem(g, 1.0, 2.0, 16, 4, 4, 4, eta0=0.2, Kn=0.05, T_wall=(1.0, 1.3))
+    f = _perturbed(P, seed=3, amp=0.1)
+    _, d = S.rhs(f, P, details=True)
+    scale = np.abs(d["coll"]).sum((1, 2, 3))
+    assert np.all(np.abs(d["coll"].sum((1, 2, 3))) <= 1e-13 * scale)
+    scale = np.abs(d["force"]).sum((1, 2, 3))
+    assert np.all(np.abs(d["force"].sum((1, 2, 3))) <= 1e-13 * scale)
+
+
+def test_mirror_symmetry_of_wall_speed():
+    # u_w -> -u_w flips u_phi and q_phi and leaves n, T, q_R unchanged
+    kw = dict(eta0=0.1, Kn=0.1)
+    Pa = S.make_problem(geo.CYL, 1.0, 2.0, 16, 4, 4, 4, u_wall=(0.2, 0.0), **kw)
+    Pb = S.make_problem(geo.CYL, 1.0, 2.0, 16, 4, 4, 4, u_wall=(-0.2, 0.0), **kw)
+    fa = S.run(S.uniform_state(Pa), Pa, 30)
+    fb = S.run(S.uniform_state(Pb), Pb, 30)
+    ma, mb = S.moments(fa, Pa), S.moments(fb, Pb)
+    assert np.allclose(ma["n"], mb["n"], rtol=1e-12)
+    assert np.allclose(ma["T"], mb["T"], rtol=1e-12)
+    assert np.allclose(ma["q"][:, 0], mb["q"][:, 0], atol=1e-11 * np.abs(ma["q"]).max())
+    assert np.allclose(ma["u"][:, 1], -mb["u"][:, 1], atol=1e-13)
+    assert np.allclose(ma["q"][:, 1], -mb["q"][:, 1], atol=1e-11 * np.abs(ma["q"]).max())
+    assert np.abs(ma["u"][:, 1]).max() > 1e-3
+
+
+# ----------------------------------------------------------------------------- brute force
+def _weno_scalar(a, b, c, d, e, eps=1e-6):
+    # Jiang-Shu fifth-order reconstruction at the right face of c, upwind from the left
+    s0 = 13 / 12 * (a - 2 * b + c) ** 2 + 1 / 4 * (a - 4 * b + 3 * c) ** 2
+    s1 = 13 / 12 * (b - 2 * c + d) ** 2 + 1 / 4 * (b - d) ** 2
+    s2 = 13 / 12 * (c - 2 * d + e) ** 2 + 1 / 4 * (3 * c - 4 * d + e) ** 2
+    w = [0.1 / (eps + s0) ** 2, 0.6 / (eps + s1) ** 2, 0.3 / (eps + s2) ** 2]
+    r = [(2 * a - 7 * b + 11 * c) / 6, (-b + 5 * c + 2 * d) / 6, (2 * c + 5 * d - e) / 6]
+    return sum(wi * ri for wi, ri in zip(w, r)) / sum(w)
+
+
+def longhand_rhs(f, P):
+    """The same equations as oracle.solver.rhs, evaluated cell by cell and momentum by
+    momentum with scalar loops (no array broadcasting)."""
+    G = P.grid
+    N, nR, n2, n3 = f.shape
+    pa = [P.pR, P.p2, P.p3]
+    wgt = lambda i, j, k: P.wR[i] * P.w2[j] * P.w3[k]
+    # moments
+    n = np.zeros(N); u = np.zeros((N, 3)); T = np.zeros(N); q = np.zeros((N, 3))
+    for c in range(N):
+        s0 = 0.0; s1 = np.zeros(3); s2 = np.zeros((3, 3)); s3 = np.zeros(3)
+        for i in range(nR):
+            for j in range(n2):
+                for k in range(n3):
+                    p = np.array([pa[0][i], pa[1][j], pa[2][k]])
+                    v = f[c, i, j, k]
+                    s0 += v; s1 += v * p; s2 += v * np.outer(p, p); s3 += v * (p @ p) * p
+        n[c] = s0; u[c] = s1 / s0
+        T[c] = (np.trace(s2) - s0 * u[c] @ u[c]) / (3 * s0)
+        for i in range(nR):
+            for j in range(n2):
+                for k in range(n3):
+                    xi = np.array([pa[0][i], pa[1][j], pa[2][k]]) - u[c]
+                    q[c] += 0.5 * f[c, i, j, k] * (xi @ xi) * xi
+    # closure
+    nbar = np.array([sum(P.W[c, d] * n[d] for d in range(N)) for c in range(N)])
+    chi = np.array([model.chi_set(math.pi * P.sigma ** 3 * nb / 6) for nb in nbar])
+    br = 2 * math.pi / 3 * P.sigma ** 3 * n
+    Pr = np.array([model.prandtl(n[c], chi[c], P.sigma) for c in range(N)])
+    tau = np.array([model.relaxation_time(n[c], T[c], chi[c], P.sigma) for c in range(N)])
+    X, Y = S.d_dR(np.log(n * n * chi * T), G), S.d_dR(np.log(T), G)
+    du = [S.d_dR(u[:, a], G) for a in range(3)]
+    out = np.zeros_like(f)
+    for c in range(N):
+        R = G.R_c[c]
+        Sab = np.zeros((3, 3))
+        Sab[0, 0] = du[0][c]
+        Sab[0, 1] = Sab[1, 0] = 0.5 * (du[1][c] - u[c, 1] / R)
+        if P.geometry == geo.CYL:
+            Sab[1, 1] = u[c, 0] / R
+            Sab[0, 2] = Sab[2, 0] = 0.5 * du[2][c]
+            div = du[0][c] + u[c, 0] / R
+        else:
+            Sab[1, 1] = Sab[2, 2] = u[c, 0] / R
+            Sab[0, 2] = Sab[2, 0] = 0.5 * (du[2][c] - u[c, 2] / R)
+            div = du[0][c] + 2 * u[c, 0] / R
+        gR = eq.g_half(P.pR, P.wR, P.alphaR, P.betaR, P.NR, u[c, 0], T[c])
+        g2 = eq.g_full(P.p2, P.w2, P.N2, u[c, 1], T[c])
+        g3 = eq.g_full(P.p3, P.w3, P.N3, u[c, 2], T[c])
+        for i in range(nR):
+            for j in range(n2):
+                for k in range(n3):
+                    xi = np.array([pa[0][i], pa[1][j], pa[2][k]]) - u[c]
+                    x2 = xi @ xi
+                    fmb = n[c] * gR[i] * g2[j] * g3[k]
+                    fs = fmb * (1 + (1 - Pr[c]) / (n[c] * T[c] ** 2) * (x2 / (5 * T[c]) - 1) * (xi @ q[c]))
+                    z2 = x2 / (2 * T[c])
+                    strain = sum(xi[a] * xi[b] * Sab[a, b] for a in range(3) for b in range(3)) / T[c]
+                    j1 = -br[c] * chi[c] * fmb * (xi[0] * (X[c] + 0.6 * (z2 - 2.5) * Y[c])
+                                                   + 0.4 * (strain + (z2 - 2.5) * div))
+                    out[c, i, j, k] += -(f[c, i, j, k] - fs) / tau[c] + j1
+                    # force
+                    KRf = sum(P.KR[i, a] * f[c, a, j, k] for a in range(nR))
+                    K2f = sum(P.K2[j, b] * f[c, i, b, k] for b in range(n2))
+                    if P.geometry == geo.CYL:
+                        frc = G.kappa[c] * (pa[1][j] ** 2 * KRf - pa[0][i] * K2f)
+                    else:
+                        K3f = sum(P.K3[k, b] * f[c, i, j, b] for b in range(n3))
+                        frc = 0.5 * G.kappa[c] * ((pa[1][j] ** 2 + pa[2][k] ** 2) * KRf - pa[0][i] * (K2f + K3f))
+                    out[c, i, j, k] -= frc
+    # advection, momentum by momentum
+    gw = S.wall_maxwellians(P)
+    vhat = {}
+    for i in range(nR):
+        for j in range(n2):
+            for k in range(n3):
+                w = wgt(i, j, k)
+                v = [f[c, i, j, k] / w for c in range(N)]
+                ext = {c: v[c] for c in range(N)}
+                ext[-1] = 4 * v[0] - 6 * v[1] + 4 * v[2] - v[3]
+                ext[-2] = 10 * v[0] - 20 * v[1] + 15 * v[2] - 4 * v[3]
+                ext[N] = 4 * v[N - 1] - 6 * v[N - 2] + 4 * v[N - 3] - v[N - 4]
+                ext[N + 1] = 10 * v[N - 1] - 20 * v[N - 2] + 15 * v[N - 3] - 4 * v[N - 4]
+                vhat[(i, j, k)] = (_weno_scalar(ext[2], ext[1], ext[0], ext[-1], ext[-2]),
+                                   _weno_scalar(ext[N - 3], ext[N - 2], ext[N - 1], ext[N], ext[N + 1]), ext)
+    outL = sum(abs(pa[0][i]) * wgt(i, j, k) * vhat[(i, j, k)][0]
+               for i in range(nR) for j in range(n2) for k in range(n3) if pa[0][i] < 0)
+    inL = sum(pa[0][i] * gw[0][i, j, k] for i in range(nR) for j in range(n2) for k in range(n3) if pa[0][i] > 0)
+    outR = sum(pa[0][i] * wgt(i, j, k) * vhat[(i, j, k)][1]
+               for i in range(nR) for j in range(n2) for k in range(n3) if pa[0][i] > 0)
+    inR = sum(abs(pa[0][i]) * gw[1][i, j, k] for i in range(nR) for j in range(n2) for k in range(n3) if pa[0][i] < 0)
+    nwL, nwR = outL / inL, outR / inR
+    for i in range(nR):
+        for j in range(n2):
+            for k in range(n3):
+                w = wgt(i, j, k)
+                vl, vr, ext = vhat[(i, j, k)]
+                p = pa[0][i]
+                if p > 0:
+                    ext[-1] = ext[-2] = nwL * gw[0][i, j, k] / w
+                else:
+                    ext[N] = ext[N + 1] = nwR * gw[1][i, j, k] / w
+                F = np.zeros(N + 1)
+                for fc in range(N + 1):
+                    if fc == 0:
+                        val = nwL * gw[0][i, j, k] if p > 0 else w * vl
+                    elif fc == N:
+                        val = w * vr if p > 0 else nwR * gw[1][i, j, k]
+                    elif p > 0:
+                        val = w * _weno_scalar(ext[fc - 3], ext[fc - 2], ext[fc - 1], ext[fc], ext[fc + 1])
+                    else:
+                        val = w * _weno_scalar(ext[fc + 2], ext[fc + 1], ext[fc], ext[fc - 1], ext[fc - 2])
+                    F[fc] = G.A_f[fc] * p * val
+                for c in range(N):
+                    out[c, i, j, k] -= (F[c + 1] - F[c]) / G.V_c[c]
+    return out
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+def test_vectorised_rhs_matches_longhand_loops(g):
+    P = S.make_problem(g, 1.0, 2.0, 7, 2, 3, 2, eta0=0.2, Kn=0.3, beta=0.7, T_wall=(1.0, 1.25),
+                       u_wall=((0.15, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    f = _perturbed(P, seed=7, amp=0.1)
+    a = S.rhs(f, P)
+    b = longhand_rhs(f, P)
+    assert np.allclose(a, b, rtol=1e-11, atol=1e-12 * np.abs(b).max())
+
+
+# ----------------------------------------------------------------------------- physics
+@pytest.mark.slow
+def test_couette_profile_is_A_R_plus_B_over_R_in_the_dilute_small_Kn_limit():
+    """Navier-Stokes steady cylindrical Couette flow has u_phi = A R + B / R (Sec. II
+    macroscopic equations with the Newton stress law); a dilute gas at Kn = 0.05 must follow
+    that form in the bulk, with A and B within slip corrections of the no-slip values."""
+    R1, R2, uw = 1.0, 2.0, 0.05
+    P = S.make_problem(geo.CYL, R1, R2, 24, 4, 4, 4, eta0=0.001, Kn=0.05, u_wall=(uw, 0.0))
+    A0 = uw * R1 / (R1 ** 2 - R2 ** 2)
+    B0 = uw * R1 * R2 ** 2 / (R2 ** 2 - R1 ** 2)
+    Rc = P.grid.R_c
+    n = np.full(P.grid.N, P.n0)
+    f = S.shakhov_seed(P, n, A0 * Rc + B0 / Rc, np.ones_like(Rc), np.zeros_like(Rc))
+    steps = int(round(12.0 / P.dt))
+    f = S.run(f, P, steps)
+    last = S.profile_moments(f, P)
+    f = S.run(f, P, 100)
+    assert S.moment_residual(last, S.profile_moments(f, P), 100, (P.n0, 1, 1, P.n0)) < 1e-6
+    uphi = S.moments(f, P)["u"][:, 1]
+    bulk = slice(4, -4)
+    M = np.stack([Rc, 1 / Rc], 1)[bulk]
+    (A, B), *_ = np.linalg.lstsq(M, uphi[bulk], rcond=None)
+    fit_res = np.max(np.abs(M @ np.array([A, B]) - uphi[bulk]))
+    M1 = np.stack([Rc, np.ones_like(Rc)], 1)[bulk]
+    c1, *_ = np.linalg.lstsq(M1, uphi[bulk], rcond=None)
+    lin_res = np.max(np.abs(M1 @ c1 - uphi[bulk]))
+    assert fit_res < 2e-3 * uw
+    assert lin_res > 5 * fit_res  # the curvature of the profile is resolved
+    assert A == pytest.approx(A0, rel=0.25) and B == pytest.approx(B0, rel=0.25)
+
+
+@pytest.mark.slow
+def test_fourier_flow_radial_heat_flux_constant_times_R():
+    """Steady Fourier flow between coaxial cylinders: R q_R is constant across the gap
+    (Sec. IV.B, geometry comparison: q^R R = const)."""
+    P = S.make_problem(geo.CYL, 1.0, 2.0, 24, 4, 4, 4, eta0=0.1, Kn=0.1, T_wall=(1.1, 0.9))
+    f = S.uniform_state(P)
+    f = S.run(f, P, int(round(12.0 / P.dt)))
+    m = S.moments(f, P)
+    Rq = P.grid.R_c * m["q"][:, 0]
+    assert np.all(Rq > 0)  # heat flows outwards from the hot inner wall
+    assert (Rq.max() - Rq.min()) / Rq.mean() < 0.02
