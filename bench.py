@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 FDLB step: node-velocity updates/s (radial cells x momenta x SSP-RK3
+steps per second) on the cylindrical Fourier-flow workload (1024 stretched cells, 16 x 8 x 8 =
+1024 momenta, FP32 populations with FP64 moment sums).
+
+One timed step = one SSP-RK3 step of the whole instance (3 closure + 3 fused-stage launches,
+replayed from a one-step CUDA graph), with L2 flushed (256 MB write) before every timed step
+because the 4 MB population arrays would otherwise stay L2-resident.  Device time from CUDA
+events on the solver's stream; max over ranks (one independent replica per GPU: weak scaling).
+
+Also reported: the fused-stage kernel against the HBM roofline (algorithmic bytes per launch /
+its event-timed duration), the end-to-end rate through the C ABI with host buffers, the FP64
+CPU oracle timed on the host cores (`cpu_baseline`), SM clocks sampled during the run.
+
+--impl reference times the FP64 CPU oracle on the same workload (the comparison arm).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2403_15051_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "node-velocity updates/s"
+UNIT = "updates/s"
+L2_FLUSH_BYTES = 256 << 20
+KERNEL_SOURCES = ["paper_2403_15051_gb300/csrc/stream_kernel.cuh", "paper_2403_15051_gb300/csrc/device_common.cuh",
+                  "paper_2403_15051_gb300/csrc/kernels_decl.h"]
+
+
+def accept_kn(kn, eta0):
+    # C >= 3 with Kn = 1/(6 sqrt2 eta0 chi(eta0) C), chi the Carnahan-Starling contact value
+    chi = (2.0 - eta0) / (2.0 * (1.0 - eta0) ** 3)
+    return 1.0 / (6.0 * math.sqrt(2.0) * eta0 * chi * kn) >= 3.0
+
+
+def workload(name):
+    if name == "fourier_cyl_1024":
+        return [wl.fourier_cyl_1024()]
+    if name == "couette_cyl_64":
+        return [wl.couette_cyl_64()]
+    if name == "fourier_sph_2048":
+        return [wl.fourier_sph_2048(accept_kn)]
+    if name == "batch_512":
+        return wl.batch_instances(lambda kn, e, r: accept_kn(kn, e) and (r - 1.0) * 0 == 0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def units_per_step(ds):
+    return sum(d["n_cells"] * 2 * d["Q_R"] * d["Q_2"] * d["Q_3"] for d in ds)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name):
+    """DRAM bytes per fused-stage launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stream_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    ent = rec.get(workload_name)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                 str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(ds, budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores: whole SSP-RK3 steps of the workload
+    (the first instance for a batch) until about `budget_s` seconds of work."""
+    from oracle import solver as osolver
+
+    d = ds[0]
+    P = osolver.make_problem(d["geometry"], d["R_in"], d["R_out"], d["n_cells"], d["Q_R"], d["Q_2"], d["Q_3"],
+                             eta0=d["eta0"], Kn=d.get("Kn"), beta=d.get("beta", 0.0) or 0.0,
+                             T_wall=tuple(d["T_wall"]), u_wall=tuple(d["u_wall"]), dt=d.get("dt"))
+    f = osolver.uniform_state(P)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f = osolver.rk3_step(f, P)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 200:
+            break
+    units = d["n_cells"] * 2 * d["Q_R"] * d["Q_2"] * d["Q_3"]
+    return {"value": units * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 steps of one {d['n_cells']}-cell x {units // d['n_cells']}-momentum instance "
+                      f"({el:.1f} s, numpy FP64, one thread)"}
+
+
+def bench_config(args, ds, world, flush_needed):
+    d = ds[0]
+    units = units_per_step(ds)
+    return {"workload": args.workload, "instances": len(ds), "n_cells": sum(x["n_cells"] for x in ds),
+            "n_momenta": 2 * d["Q_R"] * d["Q_2"] * d["Q_3"], "precision": d["precision"],
+            "updates_per_step": units,
+            "l2": "flushed by a 256 MB write before every timed step" if flush_needed else "inputs larger than L2",
+            "graph": "one-step CUDA graph per timed step", "parallelism": f"{world} independent replicas"}
+
+
+def needs_flush(ds):
+    tsize = 4 if ds[0]["precision"] == "fp32" else 8
+    return 3 * units_per_step(ds) * tsize < 2 * (129 << 20)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup() if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (1, 0, 0)
+    if rank != 0:
+        return 0
+    from oracle import solver as osolver
+
+    ds = workload(args.workload)
+    d = ds[0]
+    P = osolver.make_problem(d["geometry"], d["R_in"], d["R_out"], d["n_cells"], d["Q_R"], d["Q_2"], d["Q_3"],
+                             eta0=d["eta0"], Kn=d.get("Kn"), beta=d.get("beta", 0.0) or 0.0,
+                             T_wall=tuple(d["T_wall"]), u_wall=tuple(d["u_wall"]), dt=d.get("dt"))
+    f = osolver.uniform_state(P)
+    for _ in range(args.warmup):
+        f = osolver.rk3_step(f, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = osolver.rk3_step(f, P)
+    el = time.perf_counter() - t0
+    units = d["n_cells"] * 2 * d["Q_R"] * d["Q_2"] * d["Q_3"]
+    val = units * args.steps / el
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": bench_config(args, ds, args.gpus, needs_flush(ds)),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} SSP-RK3 steps of the full instance, numpy FP64, one thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2403_15051_gb300 import build as fbuild
+    from paper_2403_15051_gb300 import fdlb
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    fbuild.build()
+    ds = workload(args.workload)
+    S = fdlb.Solver(ds)
+    S.set_graph_steps(1)
+    stream = torch.cuda.ExternalStream(S.stream_handle())
+    units = units_per_step(ds)
+    tsize = 4 if ds[0]["precision"] == "fp32" else 8
+    state_bytes = units * tsize
+    flush_needed = needs_flush(ds)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def l2_flush(k):
+        if flush_needed:
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k % 7))
+
+    if args.profile:
+        # lean run for launch lists under a profiler: warm-up and K steps, nothing else
+        for k in range(args.warmup + args.steps):
+            l2_flush(k)
+            S.step(1)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": args.workload, "steps": args.steps, "warmup": args.warmup}))
+        S.close()
+        return 0
+
+    # warm-up (also brings the clocks up before the sampler window)
+    for k in range(args.warmup):
+        l2_flush(k)
+        S.step(1)
+    torch.cuda.synchronize()
+    t_end = time.perf_counter() + 0.6
+    k = 0
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    while time.perf_counter() < t_end:
+        l2_flush(k)
+        S.step(1)
+        k += 1
+        if k % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+
+    # ---- timed region: exactly K steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    for k in range(args.steps):
+        l2_flush(k)
+        evs[k][0].record(stream)
+        S.step(1)
+        evs[k][1].record(stream)
+        launches += S.launch_count()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_max = max_over_ranks(ms, world)
+    value = units * args.steps * world / (ms_max * 1e-3)
+
+    # ---- fused-stage kernel timing over K more steps (events around every launch)
+    S.set_kernel_timing(True)
+    S.kernel_times()
+    for k in range(args.steps):
+        l2_flush(k)
+        S.step(1)
+    stream_ms, n_stream, closure_ms, n_closure = S.kernel_times()
+    S.set_kernel_timing(False)
+    clocks = sampler.stop()
+
+    # ---- hot-L2 rate (steps back to back, no flush) for context
+    torch.cuda.synchronize()
+    S.set_graph_steps(20)
+    S.step(20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.step(200)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hot_value = units * 200 / (e0.elapsed_time(e1) * 1e-3)
+    S.set_graph_steps(1)
+
+    # ---- end to end through the C ABI with host buffers: H2D of the state, one step,
+    # D2H of the per-cell moments, every step
+    n_inst = len(ds)
+    host_state = [torch.empty(S.raw_elements(q) * tsize, dtype=torch.uint8, pin_memory=True) for q in range(n_inst)]
+    for q in range(n_inst):
+        S.get_state_raw(host_state[q].data_ptr(), q)
+    e2e_steps = max(5, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for k in range(e2e_steps):
+        for q in range(n_inst):
+            S.set_state_raw(host_state[q].data_ptr(), q)
+        S.step(1)
+        for q in range(n_inst):
+            m = S.moments(q)
+            d2h += m["n"].size * fdlb.NMOM * 8
+    el = time.perf_counter() - t0
+    el = max_over_ranks(el, world)
+    e2e = {"value": units * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": d2h // e2e_steps}
+
+    # ---- roofline of the fused-stage kernel: 8 population passes per SSP-RK3 step
+    # (3 stage inputs, 3 stage outputs, 2 re-reads of f^n) -> 8/3 passes per launch
+    peak, peak_kind = measured_peaks()
+    avg_stream_ms = stream_ms / max(n_stream, 1)
+    alg_bytes = 8.0 / 3.0 * state_bytes
+    achieved = alg_bytes / (avg_stream_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": "stream_kernel",
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_stream_ms,
+                "closure_avg_launch_ms": closure_ms / max(n_closure, 1)}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(ds)
+    if rank == 0:
+        d = ds[0]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if tsize == 4 else "f64", "data": "synthetic",
+                "config": bench_config(args, ds, world, flush_needed),
+                "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "hot_l2_value": hot_value}
+        print(json.dumps(line))
+    S.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="fourier_cyl_1024",
+                    choices=["fourier_cyl_1024", "couette_cyl_64", "fourier_sph_2048", "batch_512"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,260 @@
+/*
+ * fdlb.h - C ABI of the GB300 (sm_103a) finite-difference lattice Boltzmann (FDLB) solver
+ * for the simplified Enskog equation in cylindrical and spherical geometry
+ * (S. Busuioc, "Mesoscopic Lattice Boltzmann modeling of dense gas flows in curvilinear
+ * geometries", arXiv 2403.15051).
+ *
+ * The library advances the weighted populations f(R, p_ijk) over all radial cells and all
+ * momenta of the mixed half-range x full-range Gauss-Hermite quadrature (Sec. III.A) with
+ * the three-stage SSP Runge-Kutta scheme (Sec. III).  Each right-hand-side evaluation is
+ *   L(f) = - radial advection (Sec. II.B/C, conservative form, WENO5)
+ *          - curvature force in momentum space (Sec. II.B/C with the matrices of Sec. III.B)
+ *          - (f - f^S)/tau + J1[f^MB]  (Eqs. j0, j1; Shakhov f^S, Carnahan-Starling chi, Eq. chi,
+ *                                       with the Fischer-Methfessel average of Eq. fm)
+ * with diffuse-reflection walls on the half-range radial axis at R_L + sigma/2 and
+ * R_R - sigma/2 (Sec. IV).
+ *
+ * Conventions
+ *  - Units: m = k_B = 1; momenta in units of sqrt(T_ref), T_ref = 1.
+ *  - Every call returns FDLB_OK (0) or an error code; no exception crosses the ABI.
+ *  - Device state is owned by the library (or carved from a caller workspace, see
+ *    fdlb_create_in).  Output buffers are owned by the caller.
+ *  - Population layout seen through the ABI (fdlb_get_f / fdlb_set_f / fdlb_eval_rhs):
+ *    host FP64 array [cell][i][j][k], i over the 2 Q_R radial momenta (positive half first,
+ *    each half in ascending |p|), j over the Q_2 nodes of the second axis (ascending), k over
+ *    the Q_3 nodes of the third axis (ascending).  Axes: cylinder (R, phi, z), sphere
+ *    (r, theta, phi).  The values are weighted populations f_ijk = w_i w_j w_k f(p)/omega^3
+ *    (Sec. III.A), so plain sums give moments.
+ *  - Moments are always returned in FP64, in both precision modes.
+ *  - All device work is issued on the stream given at creation; calls that return host data
+ *    synchronise that stream.
+ */
+#ifndef FDLB_H
+#define FDLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- status codes */
+#define FDLB_OK 0
+#define FDLB_EINVAL 1          /* invalid argument or parameter set                     */
+#define FDLB_ECUDA 2           /* a CUDA runtime call failed                            */
+#define FDLB_ENOMEM 3          /* device or host allocation failed / workspace too small */
+#define FDLB_ENOTCONVERGED 4   /* run_to_steady hit max_steps                           */
+#define FDLB_ETIMEOUT 5        /* run_to_steady hit max_seconds, or a device wait gave up */
+#define FDLB_ENAN 6            /* non-finite moments detected                           */
+#define FDLB_EIO 7             /* checkpoint file could not be read or written          */
+#define FDLB_ENOGPU 8          /* no usable CUDA device                                 */
+
+/* ----------------------------------------------------------------------- enumerations */
+#define FDLB_CYL 0             /* coaxial cylinders, axes (R, phi, z)  (Sec. II.B)        */
+#define FDLB_SPH 1             /* concentric spheres, axes (r, theta, phi)  (Sec. II.C)   */
+#define FDLB_FP64 0            /* populations and arithmetic in FP64                      */
+#define FDLB_FP32 1            /* FP32 populations and streaming, FP64 moment sums         */
+#define FDLB_CHI_RET_FM 0      /* chi_SET at the Fischer-Methfessel density (Eqs. chi_ret, fm) */
+#define FDLB_CHI_SET_LOCAL 1   /* chi_SET at the local density (Eq. chi)                   */
+
+#define FDLB_QUAD_FULL 0       /* full-range Gauss-Hermite, Q nodes (Sec. III.A)           */
+#define FDLB_QUAD_HALF 1       /* half-range Gauss-Hermite, 2Q nodes (Sec. III.A)          */
+
+#define FDLB_NMOM 9            /* per-cell moments: n, u_1, u_2, u_3, T, q_1, q_2, q_3, P_12 */
+
+/* ----------------------------------------------------------------------- parameters */
+typedef struct fdlb_params {
+    int geometry;          /* FDLB_CYL or FDLB_SPH                                         */
+    double R_in, R_out;    /* physical wall radii, R_out > R_in > 0 (Sec. IV)              */
+    int n_cells;           /* radial cells on [R_in + sigma/2, R_out - sigma/2], >= 8       */
+    double stretch_beta;   /* 0: uniform cells; > 0: tanh map with this beta (finer at walls) */
+    int Q_R, Q_2, Q_3;     /* half-range order on the radial axis (2 Q_R nodes), full-range
+                              orders on the two homogeneous axes; 1 <= Q <= 24             */
+    int N_R, N_2, N_3;     /* equilibrium expansion orders (Sec. III.C), 0 <= N < Q;
+                              negative: min(Q - 1, 7)                                      */
+    double eta0;           /* mean reduced density eta0 = pi sigma^3 n0 / 6, in (0, 0.5)    */
+    double Kn;             /* Knudsen number; sets C by Kn = 1/(6 sqrt2 eta0 chi(eta0) C)
+                              (Sec. II) when sigma <= 0                                    */
+    double sigma;          /* molecular diameter; > 0 overrides Kn                         */
+    int chi_model;         /* FDLB_CHI_RET_FM or FDLB_CHI_SET_LOCAL                         */
+    int precision;         /* FDLB_FP64 or FDLB_FP32                                       */
+    double dt;             /* > 0: fixed time step; <= 0: min(cfl dR_min/(max|p_R| sqrt(T_max)),
+                              tau_min/2) at the mean state                                 */
+    double cfl;            /* CFL number when dt <= 0; <= 0 selects 0.4                    */
+    double T_wall[2];      /* wall temperatures, inner [0] and outer [1], > 0              */
+    double u_wall[2];      /* tangential wall speeds along the second axis (cylinder only) */
+} fdlb_params;
+
+/* Read-only facts about one instance, filled by fdlb_get_info. */
+typedef struct fdlb_info {
+    double C;              /* confinement ratio L / sigma                                  */
+    double sigma, n0;      /* molecular diameter and mean number density                   */
+    double dt;             /* time step in use                                             */
+    double R_first, R_last;/* computational domain [R_L^c, R_R^c]                          */
+    int n_cells;
+    int n_momenta;         /* 2 Q_R Q_2 Q_3                                                */
+    int fm_band;           /* width of the stored Fischer-Methfessel band (cells)          */
+    int precision;
+    int64_t step;          /* RK3 steps taken since the last init                          */
+} fdlb_info;
+
+typedef struct fdlb_solver* fdlb_handle;
+
+/* ----------------------------------------------------------------------- lifecycle */
+
+/* Build one solver instance: quadrature, derivative matrices, equilibrium tables, grid and
+ * FM weights on the host (Secs. III.A-C, App. A), then device state.  `cuda_stream` is a
+ * cudaStream_t (NULL: legacy default stream).  The state is left at the uniform equilibrium
+ * (fdlb_init_uniform with defaults).  Errors: FDLB_EINVAL for a parameter outside the ranges
+ * above or C = L/sigma < 3; FDLB_ENOGPU / FDLB_ECUDA / FDLB_ENOMEM from the device. */
+int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out);
+
+/* Many independent instances advanced together by one set of launches (the batched sweep):
+ * all instances share the geometry kind, Q_R, Q_2, Q_3, the expansion orders and the
+ * precision; everything else (size, radii, Kn, eta0, walls, dt) may differ.  Instance ids are
+ * 0..n_instances-1 in the order given. */
+int fdlb_batch_create(const fdlb_params* ps, int n_instances, void* cuda_stream, fdlb_handle* out);
+
+/* Device bytes needed by fdlb_create_in for these instances. */
+int fdlb_workspace_bytes(const fdlb_params* ps, int n_instances, size_t* bytes);
+
+/* As fdlb_batch_create, but all device state lives in the caller's device buffer
+ * `workspace` (at least fdlb_workspace_bytes, 256-byte aligned); the library allocates
+ * no device memory of its own and the buffer must outlive the handle. */
+int fdlb_create_in(const fdlb_params* ps, int n_instances, void* cuda_stream, void* workspace,
+                   size_t workspace_bytes, fdlb_handle* out);
+
+void fdlb_destroy(fdlb_handle h);
+
+/* ----------------------------------------------------------------------- set-up calls */
+
+/* Diffuse-reflection wall (Sec. IV): side 0 = inner, 1 = outer; temperature T_w > 0 and
+ * tangential speed along the second axis (must be 0 for the sphere).  Takes effect at the
+ * next step. */
+int fdlb_set_wall(fdlb_handle h, int instance, int side, double T_w, double u_tangential);
+
+/* Uniform equilibrium n0 g_R(0,T0) g_2(0,T0) g_3(0,T0) (Sec. III.C); n0 <= 0 selects the
+ * instance's mean density, T0 <= 0 the mean wall temperature.  instance < 0: all. */
+int fdlb_init_uniform(fdlb_handle h, int instance, double n0, double T0);
+
+/* Warm start from moment profiles given at n_points >= 2 equally spaced points of the
+ * normalised radius x = (R - R_L^c)/(R_R^c - R_L^c) in [0, 1] (host arrays): n, u_2 (second
+ * axis velocity), T and the radial heat flux q_R, linearly interpolated onto the cells.
+ * f = n g_R(0,T) g_2(u_2,T) g_3(0,T) [1 + (xi^2/(5T) - 1) xi_R q_R/(n T^2)]  (the Shakhov
+ * factor of Sec. II with 1 - Pr set to 1). */
+int fdlb_init_from_moments(fdlb_handle h, int instance, const double* n, const double* u2,
+                           const double* T, const double* qR, int n_points);
+
+/* Replace / read the populations of one instance: host FP64 [cell][i][j][k] (see layout). */
+int fdlb_set_f(fdlb_handle h, int instance, const double* f_host);
+int fdlb_get_f(fdlb_handle h, int instance, double* f_host);
+
+/* ----------------------------------------------------------------------- time stepping */
+
+/* Advance all active instances by n_steps SSP-RK3 steps (asynchronous on the stream;
+ * repeated blocks of steps are replayed from a captured CUDA graph). */
+int fdlb_step(fdlb_handle h, int64_t n_steps);
+
+/* Step until the moment residual r <= tol for every instance (checked every `check_every`
+ * steps; r = max over n, u_2, T, q_R of max_cells |M(t+K dt) - M(t)| / (K max(max|M(t)|,
+ * scale)), scales n0, 1, T0, n0 T0^1.5), or max_steps / max_seconds is reached.  In a batch,
+ * converged instances stop stepping.  steps_taken (per instance, may be NULL) and residual
+ * (per instance, may be NULL) are host arrays of length n_instances.
+ * Returns FDLB_OK, FDLB_ENOTCONVERGED, FDLB_ETIMEOUT or FDLB_ENAN. */
+int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_seconds,
+                       int check_every, int64_t* steps_taken, double* residual);
+
+/* Evaluate L(f) of the current state of one instance without advancing it (Secs. II-III);
+ * host FP64 [cell][i][j][k]. */
+int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host);
+
+/* ----------------------------------------------------------------------- outputs */
+
+/* Per-cell moments of one instance (Eq. macro_def from the quadrature sums of Eq. mom_quad):
+ * out[cell][FDLB_NMOM] = n, u_1, u_2, u_3, T, q_1, q_2, q_3, P_12 (P_12 = shear stress between
+ * the radial and second axis), FP64.  on_device != 0: `out` is a device pointer, written
+ * asynchronously on the stream; else a host pointer (the call synchronises). */
+int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device);
+
+/* Closure diagnostics of the current state of one instance, host FP64 arrays of n_cells
+ * (any may be NULL): the Fischer-Methfessel density nbar (Eq. fm), chi (Eq. chi), tau
+ * (Eq. tau); and the two wall densities n_w (inner, outer) of the diffuse walls. */
+int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, double* tau,
+                     double* n_wall2);
+
+/* Total mass sum_c V_c n_c (FP64), the last residual and the step count of one instance. */
+int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double* residual,
+                         int64_t* step);
+
+int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out);
+
+/* Checkpoint: step count, parameters and populations (native precision) of all instances. */
+int fdlb_save(fdlb_handle h, const char* path);
+/* Restore a checkpoint written by fdlb_save for a handle created with the same parameters;
+ * FDLB_EINVAL if they differ, FDLB_EIO on a read error. */
+int fdlb_load(fdlb_handle h, const char* path);
+
+const char* fdlb_error_string(int code);
+
+/* Kernel-tuning knobs of the streaming kernel (cells per tile, p_3 values per momentum slice,
+ * threads per block); 0 keeps the current value.  fdlb_autotune times the candidates on the
+ * device and keeps the fastest (the choice is cached per momentum set and precision). */
+int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads);
+int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
+
+/* Number of kernel launches issued by the last fdlb_step call (for launch accounting). */
+int64_t fdlb_launch_count(fdlb_handle h);
+
+/* SSP-RK3 steps per captured CUDA graph replayed by fdlb_step (1..1000, default 20). */
+int fdlb_set_graph_steps(fdlb_handle h, int steps);
+
+/* Per-kernel timing.  When on, fdlb_step launches the kernels directly (no graph) and brackets
+ * every closure and streaming launch with CUDA events on the solver's stream; fdlb_kernel_times
+ * returns the accumulated durations (ms) and launch counts since the last call and clears them.
+ * Any output pointer may be NULL. */
+int fdlb_set_kernel_timing(fdlb_handle h, int on);
+int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, double* closure_ms,
+                      int64_t* n_closure);
+
+/* The cudaStream_t the solver issues its work on (the one given at creation, or a private
+ * blocking stream when NULL was given). */
+int fdlb_get_stream(fdlb_handle h, void** stream);
+
+/* Populations of one instance in the library's own layout and precision: [cell][k][i][j]
+ * (k outermost inside a cell), n_cells * n_momenta elements of FP32 (FDLB_FP32) or FP64.
+ * on_device != 0: `src`/`dst` is a device pointer; else host (pinned memory gives the fastest
+ * copies).  fdlb_set_state_raw also recomputes the quadrature sums of the new state. */
+int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device);
+int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device);
+
+/* ----------------------------------------------------------------------- host-only set-up
+ * These run on the host only (no GPU needed). */
+
+/* Quadrature rule of Sec. III.A.  kind FDLB_QUAD_FULL: Q nodes ascending, weights summing
+ * to 1.  FDLB_QUAD_HALF: 2Q nodes, positive half first in ascending order, then their mirror
+ * images; weights sum to 1 (1/2 per half).  nodes/weights: host arrays of Q or 2Q. */
+int fdlb_quadrature(int kind, int Q, double* nodes, double* weights);
+
+/* Momentum-derivative matrix of Sec. III.B acting on weighted populations, row-major:
+ * FDLB_QUAD_HALF: (d f/dp) on the half-range axis, 2Q x 2Q (Eq. force1, half range);
+ * FDLB_QUAD_FULL: (d (f p)/dp) on a full-range axis, Q x Q (Eq. force2, full range). */
+int fdlb_derivative_matrix(int kind, int Q, double* K);
+
+/* Confinement ratio, molecular diameter and mean density from (Kn, eta0, L) (Sec. II). */
+int fdlb_physical_parameters(double Kn, double eta0, double L, double* C, double* sigma, double* n0);
+
+/* Grid of the computational domain (Sec. IV): cell-centre radii R_c[n_cells], face radii
+ * R_f[n_cells+1], cell volumes V[n_cells] and curvature factors kappa[n_cells] (any may be NULL). */
+int fdlb_grid(int geometry, double R_in, double R_out, double sigma, int n_cells, double beta,
+              double* R_c, double* R_f, double* V, double* kappa);
+
+/* Fischer-Methfessel weights (Eq. fm, App. A) as a dense row-major n_cells x n_cells matrix:
+ * nbar_i = sum_j W[i][j] n_j with n = 0 outside the computational domain. */
+int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n_cells,
+                    double beta, double* W);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDLB_H */

@@ -1,0 +1,116 @@
+// Device helpers shared by the kernel translation units: PTX wrappers for the bulk-copy
+// engine and mbarriers, the WENO5 reconstruction, the Carnahan-Starling contact value and
+// warp reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdlb {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// One-dimensional bulk copy global -> shared by the TMA engine; completion is counted in
+// bytes on `bar`.  Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: each try_wait suspends for a hardware-chosen interval, so 2^22 tries end
+// within seconds.  Returns false if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg_t(const T* p) {
+    return __ldg(p);
+}
+
+// Fifth-order WENO reconstruction (Jiang & Shu 1996; epsilon 1e-6, power 2) at the right face
+// of the cell holding c, upwind from the left; reversing the five arguments gives the value at
+// the left face of the cell holding c, upwind from the right.  The nonlinear weights
+// d_k / (eps + beta_k)^2 are put on a common denominator, leaving one division.
+template <typename T>
+__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
+    const T eps = T(1e-6);
+    const T k13 = T(13.0 / 12.0), q = T(0.25);
+    const T t0 = a - T(2) * b + c, t1 = a - T(4) * b + T(3) * c;
+    const T t2 = b - T(2) * c + d, t3 = b - d;
+    const T t4 = c - T(2) * d + e, t5 = T(3) * c - T(4) * d + e;
+    T e0 = eps + k13 * t0 * t0 + q * t1 * t1;
+    T e1 = eps + k13 * t2 * t2 + q * t3 * t3;
+    T e2 = eps + k13 * t4 * t4 + q * t5 * t5;
+    e0 *= e0;
+    e1 *= e1;
+    e2 *= e2;
+    const T a0 = T(0.1) * e1 * e2, a1 = T(0.6) * e0 * e2, a2 = T(0.3) * e0 * e1;
+    const T r0 = T(2) * a - T(7) * b + T(11) * c;
+    const T r1 = -b + T(5) * c + T(2) * d;
+    const T r2 = T(2) * c + T(5) * d - e;
+    return (a0 * r0 + a1 * r1 + a2 * r2) / (T(6) * (a0 + a1 + a2));
+}
+
+__device__ __forceinline__ double chi_cs(double eta) {
+    const double om = 1.0 - eta;
+    return (2.0 - eta) / (2.0 * om * om * om);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Five-point derivative stencil in the mapped coordinate (gradients of Eq. j1): fourth-order
+// central in the interior, one-sided fourth-order at the two cells next to each wall.
+__device__ __forceinline__ void stencil5(int c, int N, int* idx, double* w) {
+    const double k = 1.0 / 12.0;
+    if (c >= 2 && c <= N - 3) {
+        idx[0] = c - 2; idx[1] = c - 1; idx[2] = c; idx[3] = c + 1; idx[4] = c + 2;
+        w[0] = k; w[1] = -8 * k; w[2] = 0; w[3] = 8 * k; w[4] = -k;
+    } else if (c == 0) {
+        for (int q = 0; q < 5; ++q) idx[q] = q;
+        w[0] = -25 * k; w[1] = 48 * k; w[2] = -36 * k; w[3] = 16 * k; w[4] = -3 * k;
+    } else if (c == 1) {
+        for (int q = 0; q < 5; ++q) idx[q] = q;
+        w[0] = -3 * k; w[1] = -10 * k; w[2] = 18 * k; w[3] = -6 * k; w[4] = k;
+    } else if (c == N - 2) {
+        for (int q = 0; q < 5; ++q) idx[q] = N - 1 - q;
+        w[0] = 3 * k; w[1] = 10 * k; w[2] = -18 * k; w[3] = 6 * k; w[4] = -k;
+    } else {
+        for (int q = 0; q < 5; ++q) idx[q] = N - 1 - q;
+        w[0] = 25 * k; w[1] = -48 * k; w[2] = 36 * k; w[3] = -16 * k; w[4] = 3 * k;
+    }
+}
+
+}  // namespace fdlb

@@ -1,0 +1,1205 @@
+// Host side of the FDLB library: device state, launch sequencing, CUDA graphs, steady-state
+// driver, checkpoints and the C ABI declared in include/fdlb.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+#include "kernels_decl.h"
+
+namespace fdlb {
+
+namespace {
+
+constexpr double kPiH = 3.14159265358979323846;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Byte layout of all device state, computed identically for sizing and carving.
+struct Layout {
+    size_t f[3], sums[3], ca, tab, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err, rprev,
+        rout, total;
+};
+
+}  // namespace
+
+struct Solver {
+    int n_inst = 0, geometry = 0, precision = 0;
+    size_t tsize = 8;
+    AxisRule aR, a2, a3;
+    int NR = 0, N2 = 0, N3 = 0, nR = 0, n2 = 0, n3 = 0, Np = 0;
+    std::vector<InstanceSetup> setup;
+    std::vector<InstDev> inst_h;
+    std::vector<long long> f_off;
+    std::vector<int> cell_off;
+    int total_cells = 0;
+    size_t f_elems = 0, band_elems = 0;
+    int max_sitems = 0, max_citems = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, n_sm = 0;
+    size_t smem_optin = 0;
+    // device memory
+    unsigned char* ws = nullptr;
+    bool own_ws = false;
+    Layout lay{};
+    void* f[3] = {nullptr, nullptr, nullptr};
+    double* sums[3] = {nullptr, nullptr, nullptr};
+    double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *nw = nullptr, *rprev = nullptr,
+           *rout = nullptr;
+    InstDev* inst_d = nullptr;
+    void* band = nullptr;
+    int* band_lo = nullptr;
+    int4 *sitems = nullptr, *citems = nullptr;
+    int *n_sitems = nullptr, *n_citems = nullptr, *err = nullptr;
+    std::vector<double> tab_h;
+    MomSet M{};
+    // tiling of the stream kernel
+    int B = 16, KS = 1, threads = 0, mpt = 1;
+    size_t smem_stream = 0;
+    int use_bulk = 0;
+    int closure_cells = 32, closure_threads = 256;
+    int grid_stream = 1, grid_closure = 1;
+    size_t closure_smem = 0;
+    std::vector<char> active;
+    std::vector<int64_t> inst_steps;
+    std::vector<double> last_res;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0, last_launches = 0;
+    bool prev_valid = false;
+    int graph_steps = 20;
+    // per-kernel timing (events around each launch, direct launches)
+    bool timing = false;
+    cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+    double t_stream_ms = 0.0, t_closure_ms = 0.0;
+    int64_t n_stream_t = 0, n_closure_t = 0;
+};
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FDLB_OK;
+    if (e == cudaErrorMemoryAllocation) return FDLB_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return FDLB_ENOGPU;
+    return FDLB_ECUDA;
+}
+
+namespace {
+
+#define FDLB_CUDA(call)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::fdlb::cuda_status(e_); \
+    } while (0)
+
+// Table buffer (FP64) shared by all instances: nodes, weights, K matrices, equilibrium
+// tables of Sec. III.C and the half-range recurrence.
+void build_tables(Solver& S) {
+    auto& t = S.tab_h;
+    t.clear();
+    auto put = [&](const std::vector<double>& v) {
+        int o = (int)t.size();
+        t.insert(t.end(), v.begin(), v.end());
+        return o;
+    };
+    MomSet& M = S.M;
+    M.o_pR = put(S.aR.p);
+    M.o_wR = put(S.aR.w);
+    M.o_p2 = put(S.a2.p);
+    M.o_w2 = put(S.a2.w);
+    M.o_p3 = put(S.a3.p);
+    M.o_w3 = put(S.a3.w);
+    std::vector<double> K;
+    k_half_matrix(S.aR, K);
+    M.o_KR = put(K);
+    k2_full_matrix(S.a2, K);
+    M.o_K2 = put(K);
+    k2_full_matrix(S.a3, K);
+    M.o_K3 = put(K);
+    // GR[k][l] = w_k h_l(|p_k|);  G2[j][l] = w_j He_l(p_j) / l!
+    const int QR = S.aR.Q;
+    std::vector<double> GR((size_t)S.nR * kMaxE, 0.0), G2((size_t)S.n2 * kMaxE, 0.0), G3((size_t)S.n3 * kMaxE, 0.0);
+    for (int k = 0; k < S.nR; ++k) {
+        const double x = std::fabs(S.aR.p[k]);
+        double h[kMaxE + 2];
+        h[0] = 1.0 / std::sqrt(S.aR.beta[0]);
+        if (S.NR >= 1) h[1] = (x - S.aR.alpha[0]) * h[0] / std::sqrt(S.aR.beta[1]);
+        for (int l = 1; l < S.NR; ++l)
+            h[l + 1] = ((x - S.aR.alpha[l]) * h[l] - std::sqrt(S.aR.beta[l]) * h[l - 1]) / std::sqrt(S.aR.beta[l + 1]);
+        for (int l = 0; l <= S.NR; ++l) GR[(size_t)k * kMaxE + l] = S.aR.w[k] * h[l];
+    }
+    auto fill_full = [&](const AxisRule& ax, int N, std::vector<double>& G) {
+        for (int j = 0; j < ax.Q; ++j) {
+            double h0 = 1.0, h1 = ax.p[j], fact = 1.0;
+            for (int l = 0; l <= N; ++l) {
+                double He = l == 0 ? 1.0 : (l == 1 ? ax.p[j] : 0.0);
+                if (l >= 2) {
+                    He = ax.p[j] * h1 - (l - 1) * h0;
+                    h0 = h1;
+                    h1 = He;
+                }
+                if (l > 0) fact *= l;
+                G[(size_t)j * kMaxE + l] = ax.w[j] * He / fact;
+            }
+        }
+    };
+    fill_full(S.a2, S.N2, G2);
+    fill_full(S.a3, S.N3, G3);
+    M.o_GR = put(GR);
+    M.o_G2 = put(G2);
+    M.o_G3 = put(G3);
+    std::vector<double> ha(kMaxE, 0.0), hb(kMaxE + 1, 0.0), h0(kMaxE, 0.0);
+    for (int l = 0; l < kMaxE && l < (int)S.aR.alpha.size(); ++l) ha[l] = S.aR.alpha[l];
+    for (int l = 0; l <= kMaxE && l < (int)S.aR.beta.size(); ++l) hb[l] = std::sqrt(S.aR.beta[l]);
+    {
+        double h[kMaxE + 2];
+        h[0] = 1.0 / std::sqrt(S.aR.beta[0]);
+        if (kMaxE > 1 && (int)S.aR.beta.size() > 1) h[1] = (0.0 - S.aR.alpha[0]) * h[0] / std::sqrt(S.aR.beta[1]);
+        for (int l = 1; l + 1 < kMaxE && l + 1 < (int)S.aR.beta.size(); ++l)
+            h[l + 1] = ((0.0 - S.aR.alpha[l]) * h[l] - std::sqrt(S.aR.beta[l]) * h[l - 1]) / std::sqrt(S.aR.beta[l + 1]);
+        for (int l = 0; l < kMaxE && l <= QR; ++l) h0[l] = h[l];
+    }
+    M.o_ha = put(ha);
+    M.o_hb = put(hb);
+    M.o_h0 = put(h0);
+}
+
+Layout make_layout(const Solver& S) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + std::max<size_t>(bytes, 1), kAlign);
+        return o;
+    };
+    for (int b = 0; b < 3; ++b) L.f[b] = take(S.f_elems * S.tsize);
+    for (int b = 0; b < 3; ++b) L.sums[b] = take((size_t)S.total_cells * S.n3 * kSums * sizeof(double));
+    L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
+    L.tab = take(S.tab_h.size() * sizeof(double));
+    L.inst = take(S.n_inst * sizeof(InstDev));
+    L.geo = take((size_t)S.total_cells * kGeo * sizeof(double));
+    L.gw = take((size_t)S.n_inst * 2 * (S.nR + S.n2 + S.n3) * sizeof(double));
+    L.band = take(S.band_elems * S.tsize);
+    L.band_lo = take((size_t)S.total_cells * sizeof(int));
+    L.sitems = take((size_t)S.max_sitems * sizeof(int4));
+    L.n_sitems = take(sizeof(int));
+    L.citems = take((size_t)S.max_citems * sizeof(int4));
+    L.n_citems = take(sizeof(int));
+    L.nw = take((size_t)S.n_inst * 2 * sizeof(double));
+    L.err = take(sizeof(int));
+    L.rprev = take((size_t)S.total_cells * 4 * sizeof(double));
+    L.rout = take((size_t)S.n_inst * 10 * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+// Host-side plan of one handle: validation, quadrature, per-instance set-up, sizes.
+int plan_solver(const fdlb_params* ps, int n, Solver& S) {
+    if (!ps || n < 1) return FDLB_EINVAL;
+    const fdlb_params& p0 = ps[0];
+    for (int q = 0; q < n; ++q) {
+        const fdlb_params& p = ps[q];
+        if (p.geometry != p0.geometry || p.Q_R != p0.Q_R || p.Q_2 != p0.Q_2 || p.Q_3 != p0.Q_3 ||
+            p.precision != p0.precision || p.N_R != p0.N_R || p.N_2 != p0.N_2 || p.N_3 != p0.N_3)
+            return FDLB_EINVAL;
+    }
+    int rc = validate_params([&] {
+        fdlb_params t = p0;
+        auto order = [](int N, int Q) { return N < 0 ? std::min(Q - 1, kMaxN) : N; };
+        t.N_R = order(t.N_R, t.Q_R);
+        t.N_2 = order(t.N_2, t.Q_2);
+        t.N_3 = order(t.N_3, t.Q_3);
+        return t;
+    }());
+    if (rc) return rc;
+    S.n_inst = n;
+    S.geometry = p0.geometry;
+    S.precision = p0.precision;
+    S.tsize = p0.precision == FDLB_FP32 ? 4 : 8;
+    S.aR = make_axis(p0.Q_R, true);
+    S.a2 = make_axis(p0.Q_2, false);
+    S.a3 = make_axis(p0.Q_3, false);
+    S.nR = 2 * p0.Q_R;
+    S.n2 = p0.Q_2;
+    S.n3 = p0.Q_3;
+    S.Np = S.nR * S.n2 * S.n3;
+    S.setup.resize(n);
+    for (int q = 0; q < n; ++q) {
+        rc = build_instance(ps[q], S.aR, S.setup[q]);
+        if (rc) return rc;
+    }
+    S.NR = S.setup[0].NR;
+    S.N2 = S.setup[0].N2;
+    S.N3 = S.setup[0].N3;
+    build_tables(S);
+    S.f_off.resize(n);
+    S.cell_off.resize(n);
+    S.total_cells = 0;
+    S.f_elems = 0;
+    S.band_elems = 0;
+    S.max_sitems = 0;
+    S.max_citems = 0;
+    const size_t falign = kAlign / S.tsize;
+    for (int q = 0; q < n; ++q) {
+        const int N = S.setup[q].p.n_cells;
+        S.cell_off[q] = S.total_cells;
+        S.f_off[q] = (long long)S.f_elems;
+        S.total_cells += N;
+        S.f_elems += align_up((size_t)N * S.Np, falign);
+        S.band_elems += (size_t)N * S.setup[q].band.width;
+        S.max_sitems += ((N + 3) / 4) * S.n3;
+        S.max_citems += (N + S.closure_cells - 1) / S.closure_cells;
+    }
+    S.active.assign(n, 1);
+    S.inst_steps.assign(n, 0);
+    S.last_res.assign(n, -1.0);
+    return FDLB_OK;
+}
+
+// Wall Maxwellians per axis and the incoming-flux normaliser of the diffuse wall.
+void wall_tables(const Solver& S, int q, double* out, double* den) {
+    const InstanceSetup& I = S.setup[q];
+    const int stride = S.nR + S.n2 + S.n3;
+    for (int side = 0; side < 2; ++side) {
+        double* o = out + side * stride;
+        const double Tw = I.p.T_wall[side], uw = I.p.u_wall[side];
+        g_half_host(S.aR, S.NR, 0.0, Tw, o);
+        g_full_host(S.a2, S.N2, uw, Tw, o + S.nR);
+        g_full_host(S.a3, S.N3, 0.0, Tw, o + S.nR + S.n2);
+        double sR = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int i = 0; i < S.nR; ++i)
+            if (side == 0 ? S.aR.p[i] > 0 : S.aR.p[i] < 0) sR += std::fabs(S.aR.p[i]) * o[i];
+        for (int j = 0; j < S.n2; ++j) s2 += o[S.nR + j];
+        for (int k = 0; k < S.n3; ++k) s3 += o[S.nR + S.n2 + k];
+        den[side] = sR * s2 * s3;
+    }
+}
+
+void fill_inst(Solver& S, int q) {
+    const InstanceSetup& I = S.setup[q];
+    InstDev& d = S.inst_h[q];
+    d.n_cells = I.p.n_cells;
+    d.cell_off = S.cell_off[q];
+    d.f_off = S.f_off[q];
+    d.band_w = I.band.width;
+    d.chi_local = I.p.chi_model == FDLB_CHI_SET_LOCAL ? 1 : 0;
+    d.geometry = I.p.geometry;
+    d.sigma = I.sigma;
+    d.bfac = 2.0 * kPiH / 3.0 * I.sigma * I.sigma * I.sigma;
+    d.etafac = kPiH * I.sigma * I.sigma * I.sigma / 6.0;
+    d.dt = I.dt;
+    d.ds = I.grid.ds;
+    std::vector<double> tmp(2 * (S.nR + S.n2 + S.n3));
+    wall_tables(S, q, tmp.data(), d.nw_den);
+}
+
+// Work lists: stream items (instance, first cell, cells, slice) over the active instances,
+// tiles of 3..B cells, largest instances first; closure items (instance, first cell, cells).
+int upload_items(Solver& S) {
+    std::vector<int> order;
+    for (int q = 0; q < S.n_inst; ++q)
+        if (S.active[q]) order.push_back(q);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return S.setup[a].p.n_cells > S.setup[b].p.n_cells; });
+    std::vector<int4> si, ci;
+    const int slices = S.n3 / S.KS;
+    for (int q : order) {
+        const int N = S.setup[q].p.n_cells;
+        const int nt = (N + S.B - 1) / S.B;
+        const int base = N / nt, rem = N % nt;
+        int c0 = 0;
+        for (int t = 0; t < nt; ++t) {
+            const int cnt = base + (t < rem ? 1 : 0);
+            for (int sl = 0; sl < slices; ++sl) si.push_back(make_int4(q, c0, cnt, sl));
+            c0 += cnt;
+        }
+        for (int c = 0; c < N; c += S.closure_cells) ci.push_back(make_int4(q, c, std::min(S.closure_cells, N - c), 0));
+    }
+    if ((int)si.size() > S.max_sitems || (int)ci.size() > S.max_citems) return FDLB_EINVAL;
+    const int ns = (int)si.size(), nc = (int)ci.size();
+    if (ns) FDLB_CUDA(cudaMemcpyAsync(S.sitems, si.data(), ns * sizeof(int4), cudaMemcpyHostToDevice, S.stream));
+    if (nc) FDLB_CUDA(cudaMemcpyAsync(S.citems, ci.data(), nc * sizeof(int4), cudaMemcpyHostToDevice, S.stream));
+    FDLB_CUDA(cudaMemcpyAsync(S.n_sitems, &ns, sizeof(int), cudaMemcpyHostToDevice, S.stream));
+    FDLB_CUDA(cudaMemcpyAsync(S.n_citems, &nc, sizeof(int), cudaMemcpyHostToDevice, S.stream));
+    FDLB_CUDA(cudaStreamSynchronize(S.stream));  // host vectors go out of scope
+    // closure shared memory: union band of one closure item
+    int max_union = 1;
+    for (const int4& w : ci) {
+        const InstanceSetup& I = S.setup[w.x];
+        if (I.band.width == 0) continue;
+        const int lo = I.band.lo[w.y];
+        const int hi = std::min(I.p.n_cells - 1, I.band.lo[w.y + w.z - 1] + I.band.width - 1);
+        max_union = std::max(max_union, hi - lo + 1);
+    }
+    S.closure_smem = (size_t)max_union * S.tsize;
+    S.grid_closure = std::max(1, std::min(nc, S.n_sm * 8));
+    S.grid_stream = std::max(1, ns);
+    return FDLB_OK;
+}
+
+int launch_moments_all(Solver& S, int buf);
+
+int configure_tiling(Solver& S, int B, int KS, int threads) {
+    if (B > 0) S.B = std::max(4, B);
+    if (KS > 0) S.KS = KS;
+    if (S.geometry == FDLB_SPH) S.KS = S.n3;  // every axis is coupled by the force term
+    if (S.KS < 1 || S.n3 % S.KS) S.KS = S.n3;
+    const int Ms = S.nR * S.n2 * S.KS;
+    S.M.nR = S.nR;
+    S.M.n2 = S.n2;
+    S.M.n3 = S.n3;
+    S.M.Np = S.Np;
+    S.M.NR = S.NR;
+    S.M.N2 = S.N2;
+    S.M.N3 = S.N3;
+    S.M.KS = S.KS;
+    S.M.slices = S.n3 / S.KS;
+    S.M.Ms = Ms;
+    int mpt = 1;
+    const int cap = threads > 0 ? threads : 256;
+    while (mpt < 8 && (Ms + mpt - 1) / mpt > cap) mpt *= 2;
+    int nt = ((Ms + mpt - 1) / mpt + 31) / 32 * 32;
+    if (nt > 512) return FDLB_EINVAL;
+    S.mpt = mpt;
+    S.threads = nt;
+    // shrink the tile until it fits in shared memory
+    for (;;) {
+        StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize);
+        if ((size_t)P.total <= S.smem_optin || S.B <= 4) {
+            S.smem_stream = P.total;
+            break;
+        }
+        S.B = std::max(4, S.B / 2);
+    }
+    if (S.smem_stream > S.smem_optin) return FDLB_EINVAL;
+    S.use_bulk = ((size_t)Ms * S.tsize % 16 == 0 && (size_t)S.Np * S.tsize % 16 == 0) ? 1 : 0;
+    if (S.gexec) {
+        cudaGraphExecDestroy(S.gexec);
+        S.gexec = nullptr;
+    }
+    int rc = upload_items(S);
+    if (rc) return rc;
+    // the partial sums are stored per slice: rebuild them for the new slice count
+    return launch_moments_all(S, 0);
+}
+
+template <typename T>
+void to_device_layout(const Solver& S, const double* src, std::vector<T>& dst, int N) {
+    // ABI [cell][i][j][k] -> device [cell][k][i][j]
+    dst.resize((size_t)N * S.Np);
+    for (int c = 0; c < N; ++c)
+        for (int i = 0; i < S.nR; ++i)
+            for (int j = 0; j < S.n2; ++j)
+                for (int k = 0; k < S.n3; ++k)
+                    dst[(size_t)c * S.Np + ((size_t)k * S.nR + i) * S.n2 + j] =
+                        (T)src[(size_t)c * S.Np + ((size_t)i * S.n2 + j) * S.n3 + k];
+}
+
+template <typename T>
+void from_device_layout(const Solver& S, const std::vector<T>& src, double* dst, int N) {
+    for (int c = 0; c < N; ++c)
+        for (int i = 0; i < S.nR; ++i)
+            for (int j = 0; j < S.n2; ++j)
+                for (int k = 0; k < S.n3; ++k)
+                    dst[(size_t)c * S.Np + ((size_t)i * S.n2 + j) * S.n3 + k] =
+                        (double)src[(size_t)c * S.Np + ((size_t)k * S.nR + i) * S.n2 + j];
+}
+
+int launch_moments_all(Solver& S, int buf) {
+    const int nc = S.max_citems;
+    if (S.precision == FDLB_FP32)
+        launch_moments<float>((const float*)S.f[buf], S.sums[buf], S.citems, S.n_citems, std::max(1, std::min(nc, S.n_sm * 8)),
+                              S.inst_d, S.tab, S.M, S.stream);
+    else
+        launch_moments<double>((const double*)S.f[buf], S.sums[buf], S.citems, S.n_citems,
+                               std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
+    S.launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_closure_buf(Solver& S, int buf) {
+    ClosureArgs A{};
+    A.sums = S.sums[buf];
+    A.ca = S.ca;
+    A.items = S.citems;
+    A.n_items = S.n_citems;
+    A.inst = S.inst_d;
+    A.band = S.band;
+    A.band_lo = S.band_lo;
+    A.slices = S.M.slices;
+    A.max_union = (int)(S.closure_smem / S.tsize);
+    if (S.precision == FDLB_FP32)
+        launch_closure<float>(A, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+    else
+        launch_closure<double>(A, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+    S.launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, int mode);
+
+// One right-hand-side evaluation and RK combination: closure launch, then the fused stage.
+// In timing mode each launch is bracketed by events and its duration accumulated.
+int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mode) {
+    if (S.timing) {
+        FDLB_CUDA(cudaEventRecord(S.tev[0], S.stream));
+        int rc = launch_closure_buf(S, in);
+        if (rc) return rc;
+        FDLB_CUDA(cudaEventRecord(S.tev[1], S.stream));
+        rc = launch_stream_only(S, in, fn, out, a, b, mode);
+        if (rc) return rc;
+        FDLB_CUDA(cudaEventRecord(S.tev[2], S.stream));
+        FDLB_CUDA(cudaEventSynchronize(S.tev[2]));
+        float m1 = 0.f, m2 = 0.f;
+        FDLB_CUDA(cudaEventElapsedTime(&m1, S.tev[0], S.tev[1]));
+        FDLB_CUDA(cudaEventElapsedTime(&m2, S.tev[1], S.tev[2]));
+        S.t_closure_ms += m1;
+        S.t_stream_ms += m2;
+        S.n_closure_t++;
+        S.n_stream_t++;
+        return FDLB_OK;
+    }
+    int rc = launch_closure_buf(S, in);
+    if (rc) return rc;
+    return launch_stream_only(S, in, fn, out, a, b, mode);
+}
+
+int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, int mode) {
+    StageArgs A{};
+    A.f_in = S.f[in];
+    A.f_n = S.f[fn];
+    A.f_out = S.f[out];
+    A.ca = S.ca;
+    A.sums_out = S.sums[out];
+    A.items = S.sitems;
+    A.n_items = S.n_sitems;
+    A.inst = S.inst_d;
+    A.tab = S.tab;
+    A.geo = S.geo;
+    A.gw = S.gw;
+    A.nw_out = S.nw;
+    A.err = S.err;
+    A.a = a;
+    A.b = b;
+    A.mode = mode;
+    A.B = S.B;
+    A.use_bulk = S.use_bulk;
+    cudaError_t e;
+    const int g = S.geometry;
+    if (S.precision == FDLB_FP32)
+        e = g == FDLB_CYL ? launch_stream_float_0(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
+                          : launch_stream_float_1(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
+    else
+        e = g == FDLB_CYL ? launch_stream_double_0(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
+                          : launch_stream_double_1(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
+    S.launches++;
+    return cuda_status(e);
+}
+
+// One SSP-RK3 step (Sec. III): f1 = f + dt L(f); f2 = 3/4 f + 1/4 (f1 + dt L(f1));
+// f^{n+1} = 1/3 f + 2/3 (f2 + dt L(f2)).  Buffers: 0 = f^n (and f^{n+1}), 1 = f1, 2 = f2.
+int launch_step(Solver& S) {
+    int rc = launch_stage(S, 0, 0, 1, 0.0, 1.0, 0);
+    if (!rc) rc = launch_stage(S, 1, 0, 2, 0.75, 0.25, 0);
+    if (!rc) rc = launch_stage(S, 2, 0, 0, 1.0 / 3.0, 2.0 / 3.0, 0);
+    return rc;
+}
+
+int upload_state(Solver& S, int q, const double* f_host) {
+    const int N = S.setup[q].p.n_cells;
+    if (S.precision == FDLB_FP32) {
+        std::vector<float> t;
+        to_device_layout(S, f_host, t, N);
+        FDLB_CUDA(cudaMemcpyAsync((float*)S.f[0] + S.f_off[q], t.data(), t.size() * 4, cudaMemcpyHostToDevice, S.stream));
+        FDLB_CUDA(cudaStreamSynchronize(S.stream));
+    } else {
+        std::vector<double> t;
+        to_device_layout(S, f_host, t, N);
+        FDLB_CUDA(cudaMemcpyAsync((double*)S.f[0] + S.f_off[q], t.data(), t.size() * 8, cudaMemcpyHostToDevice, S.stream));
+        FDLB_CUDA(cudaStreamSynchronize(S.stream));
+    }
+    S.inst_steps[q] = 0;
+    S.prev_valid = false;
+    return launch_moments_all(S, 0);
+}
+
+int download_buf(Solver& S, int q, int buf, double* out) {
+    const int N = S.setup[q].p.n_cells;
+    if (S.precision == FDLB_FP32) {
+        std::vector<float> t((size_t)N * S.Np);
+        FDLB_CUDA(cudaMemcpyAsync(t.data(), (const float*)S.f[buf] + S.f_off[q], t.size() * 4, cudaMemcpyDeviceToHost,
+                                  S.stream));
+        FDLB_CUDA(cudaStreamSynchronize(S.stream));
+        from_device_layout(S, t, out, N);
+    } else {
+        std::vector<double> t((size_t)N * S.Np);
+        FDLB_CUDA(cudaMemcpyAsync(t.data(), (const double*)S.f[buf] + S.f_off[q], t.size() * 8, cudaMemcpyDeviceToHost,
+                                  S.stream));
+        FDLB_CUDA(cudaStreamSynchronize(S.stream));
+        from_device_layout(S, t, out, N);
+    }
+    return FDLB_OK;
+}
+
+// Host evaluation of the uniform equilibrium or the Shakhov-type seed of one instance.
+void seed_state(const Solver& S, int q, const std::vector<double>& n, const std::vector<double>& u2,
+                const std::vector<double>& T, const std::vector<double>& qR, std::vector<double>& f) {
+    const int N = S.setup[q].p.n_cells;
+    f.assign((size_t)N * S.Np, 0.0);
+    std::vector<double> gR(S.nR), g2(S.n2), g3(S.n3);
+    for (int c = 0; c < N; ++c) {
+        g_half_host(S.aR, S.NR, 0.0, T[c], gR.data());
+        g_full_host(S.a2, S.N2, u2[c], T[c], g2.data());
+        g_full_host(S.a3, S.N3, 0.0, T[c], g3.data());
+        for (int i = 0; i < S.nR; ++i)
+            for (int j = 0; j < S.n2; ++j)
+                for (int k = 0; k < S.n3; ++k) {
+                    const double pR = S.aR.p[i], x1 = S.a2.p[j] - u2[c], x2 = S.a3.p[k];
+                    const double xs = pR * pR + x1 * x1 + x2 * x2;
+                    const double fac = 1.0 + (xs / (5.0 * T[c]) - 1.0) * pR * qR[c] / (n[c] * T[c] * T[c]);
+                    f[(size_t)c * S.Np + ((size_t)i * S.n2 + j) * S.n3 + k] = n[c] * gR[i] * g2[j] * g3[k] * fac;
+                }
+    }
+}
+
+int ensure_graph(Solver& S) {
+    if (S.gexec) return FDLB_OK;
+    cudaGraph_t graph = nullptr;
+    const int64_t before = S.launches;
+    FDLB_CUDA(cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeThreadLocal));
+    int rc = FDLB_OK;
+    for (int s = 0; s < S.graph_steps && !rc; ++s) rc = launch_step(S);
+    cudaError_t e = cudaStreamEndCapture(S.stream, &graph);
+    S.launches = before;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    FDLB_CUDA(e);
+    e = cudaGraphInstantiate(&S.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    return cuda_status(e);
+}
+
+int do_steps(Solver& S, int64_t n) {
+    const int64_t before = S.launches;
+    int64_t done = 0;
+    if (n >= S.graph_steps && !S.timing) {
+        int rc = ensure_graph(S);
+        if (rc) return rc;
+        while (n - done >= S.graph_steps) {
+            FDLB_CUDA(cudaGraphLaunch(S.gexec, S.stream));
+            S.launches += (int64_t)S.graph_steps * 6;
+            done += S.graph_steps;
+        }
+    }
+    for (; done < n; ++done) {
+        int rc = launch_step(S);
+        if (rc) return rc;
+    }
+    for (int q = 0; q < S.n_inst; ++q)
+        if (S.active[q]) S.inst_steps[q] += n;
+    S.last_launches = S.launches - before;
+    return FDLB_OK;
+}
+
+int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, size_t ws_bytes, fdlb_handle* out) {
+    if (!out) return FDLB_EINVAL;
+    *out = nullptr;
+    auto S = std::make_unique<Solver>();
+    int rc = plan_solver(ps, n, *S);
+    if (rc) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return FDLB_ENOGPU;
+    FDLB_CUDA(cudaGetDevice(&S->device));
+    FDLB_CUDA(cudaDeviceGetAttribute(&S->n_sm, cudaDevAttrMultiProcessorCount, S->device));
+    int optin = 0;
+    FDLB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device));
+    S->smem_optin = (size_t)optin;
+    S->stream = (cudaStream_t)stream;
+    if (!S->stream) {
+        // the legacy default stream cannot be captured into a graph: use a private blocking
+        // stream (it still orders itself with the legacy stream)
+        FDLB_CUDA(cudaStreamCreate(&S->stream));
+        S->own_stream = true;
+    }
+    S->lay = make_layout(*S);
+    if (workspace) {
+        if (ws_bytes < S->lay.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) return FDLB_ENOMEM;
+        S->ws = (unsigned char*)workspace;
+    } else {
+        FDLB_CUDA(cudaMalloc(&S->ws, S->lay.total));
+        S->own_ws = true;
+    }
+    Solver& R = *S;
+    const Layout& L = R.lay;
+    for (int b = 0; b < 3; ++b) {
+        R.f[b] = R.ws + L.f[b];
+        R.sums[b] = (double*)(R.ws + L.sums[b]);
+    }
+    R.ca = (double*)(R.ws + L.ca);
+    R.tab = (double*)(R.ws + L.tab);
+    R.inst_d = (InstDev*)(R.ws + L.inst);
+    R.geo = (double*)(R.ws + L.geo);
+    R.gw = (double*)(R.ws + L.gw);
+    R.band = R.ws + L.band;
+    R.band_lo = (int*)(R.ws + L.band_lo);
+    R.sitems = (int4*)(R.ws + L.sitems);
+    R.n_sitems = (int*)(R.ws + L.n_sitems);
+    R.citems = (int4*)(R.ws + L.citems);
+    R.n_citems = (int*)(R.ws + L.n_citems);
+    R.nw = (double*)(R.ws + L.nw);
+    R.err = (int*)(R.ws + L.err);
+    R.rprev = (double*)(R.ws + L.rprev);
+    R.rout = (double*)(R.ws + L.rout);
+    FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
+    // tables, instances, geometry, walls, FM band
+    FDLB_CUDA(cudaMemcpyAsync(R.tab, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    R.inst_h.resize(n);
+    std::vector<double> geo((size_t)R.total_cells * kGeo), gw((size_t)n * 2 * (R.nR + R.n2 + R.n3));
+    std::vector<int> blo(R.total_cells, 0);
+    std::vector<float> bandf;
+    std::vector<double> bandd;
+    size_t boff = 0;
+    for (int q = 0; q < n; ++q) {
+        fill_inst(R, q);
+        R.inst_h[q].band_off = (int)boff;
+        const InstanceSetup& I = R.setup[q];
+        const Grid& g = I.grid;
+        for (int c = 0; c < g.N; ++c) {
+            double* o = &geo[(size_t)(R.cell_off[q] + c) * kGeo];
+            o[0] = g.R_c[c];
+            o[1] = 1.0 / g.dRds_c[c];
+            o[2] = g.A_f[c + 1] / g.V_c[c];
+            o[3] = g.A_f[c] / g.V_c[c];
+            o[4] = I.p.geometry == FDLB_CYL ? g.kappa[c] : 0.5 * g.kappa[c];
+            o[5] = g.V_c[c];
+            if (I.band.width) blo[R.cell_off[q] + c] = I.band.lo[c];
+        }
+        double den[2];
+        wall_tables(R, q, &gw[(size_t)q * 2 * (R.nR + R.n2 + R.n3)], den);
+        for (double v : I.band.W) {
+            if (R.precision == FDLB_FP32) bandf.push_back((float)v);
+            else bandd.push_back(v);
+        }
+        boff += I.band.W.size();
+    }
+    FDLB_CUDA(cudaMemcpyAsync(R.inst_d, R.inst_h.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, R.stream));
+    FDLB_CUDA(cudaMemcpyAsync(R.geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    FDLB_CUDA(cudaMemcpyAsync(R.gw, gw.data(), gw.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    FDLB_CUDA(cudaMemcpyAsync(R.band_lo, blo.data(), blo.size() * sizeof(int), cudaMemcpyHostToDevice, R.stream));
+    if (R.precision == FDLB_FP32 && !bandf.empty())
+        FDLB_CUDA(cudaMemcpyAsync(R.band, bandf.data(), bandf.size() * 4, cudaMemcpyHostToDevice, R.stream));
+    if (R.precision == FDLB_FP64 && !bandd.empty())
+        FDLB_CUDA(cudaMemcpyAsync(R.band, bandd.data(), bandd.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    FDLB_CUDA(cudaStreamSynchronize(R.stream));
+    // default tiling: a slice per p_3 value on the cylinder (p_3 is passive there)
+    const int KS0 = R.geometry == FDLB_CYL && ((size_t)R.nR * R.n2 * R.tsize) % 16 == 0 ? 1 : R.n3;
+    rc = configure_tiling(R, R.geometry == FDLB_CYL ? 16 : 8, KS0, 256);
+    for (int q = 0; q < n && !rc; ++q) rc = fdlb_init_uniform(reinterpret_cast<fdlb_handle>(S.get()), q, 0.0, 0.0);
+    if (rc) {
+        if (R.own_ws) cudaFree(R.ws);
+        if (R.own_stream) cudaStreamDestroy(R.stream);
+        return rc;
+    }
+    *out = reinterpret_cast<fdlb_handle>(S.release());
+    return FDLB_OK;
+}
+
+}  // namespace
+}  // namespace fdlb
+
+using fdlb::Solver;
+
+static Solver* SOL(fdlb_handle h) { return reinterpret_cast<Solver*>(h); }
+
+extern "C" {
+
+int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out) {
+    return fdlb::solver_create(p, 1, cuda_stream, nullptr, 0, out);
+}
+
+int fdlb_batch_create(const fdlb_params* ps, int n_instances, void* cuda_stream, fdlb_handle* out) {
+    return fdlb::solver_create(ps, n_instances, cuda_stream, nullptr, 0, out);
+}
+
+int fdlb_workspace_bytes(const fdlb_params* ps, int n_instances, size_t* bytes) {
+    if (!bytes) return FDLB_EINVAL;
+    Solver S;
+    int rc = fdlb::plan_solver(ps, n_instances, S);
+    if (rc) return rc;
+    *bytes = fdlb::make_layout(S).total;
+    return FDLB_OK;
+}
+
+int fdlb_create_in(const fdlb_params* ps, int n_instances, void* cuda_stream, void* workspace, size_t workspace_bytes,
+                   fdlb_handle* out) {
+    if (!workspace) return FDLB_EINVAL;
+    return fdlb::solver_create(ps, n_instances, cuda_stream, workspace, workspace_bytes, out);
+}
+
+void fdlb_destroy(fdlb_handle h) {
+    Solver* S = SOL(h);
+    if (!S) return;
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    else cudaDeviceSynchronize();
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
+    if (S->own_ws && S->ws) cudaFree(S->ws);
+    for (cudaEvent_t e : S->tev)
+        if (e) cudaEventDestroy(e);
+    if (S->own_stream) cudaStreamDestroy(S->stream);
+    delete S;
+}
+
+int fdlb_set_wall(fdlb_handle h, int instance, int side, double T_w, double u_tangential) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || (side != 0 && side != 1)) return FDLB_EINVAL;
+    if (!(T_w > 0.0) || !std::isfinite(u_tangential)) return FDLB_EINVAL;
+    if (S->geometry == FDLB_SPH && u_tangential != 0.0) return FDLB_EINVAL;
+    S->setup[instance].p.T_wall[side] = T_w;
+    S->setup[instance].p.u_wall[side] = u_tangential;
+    fdlb::fill_inst(*S, instance);
+    const int stride = S->nR + S->n2 + S->n3;
+    std::vector<double> gw(2 * stride);
+    double den[2];
+    fdlb::wall_tables(*S, instance, gw.data(), den);
+    FDLB_CUDA(cudaMemcpyAsync(S->gw + (size_t)instance * 2 * stride, gw.data(), gw.size() * 8, cudaMemcpyHostToDevice,
+                              S->stream));
+    FDLB_CUDA(cudaMemcpyAsync(S->inst_d + instance, &S->inst_h[instance], sizeof(fdlb::InstDev),
+                              cudaMemcpyHostToDevice, S->stream));
+    FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    return FDLB_OK;
+}
+
+int fdlb_init_uniform(fdlb_handle h, int instance, double n0, double T0) {
+    Solver* S = SOL(h);
+    if (!S || instance >= S->n_inst) return FDLB_EINVAL;
+    if (instance < 0) {
+        for (int q = 0; q < S->n_inst; ++q) {
+            int rc = fdlb_init_uniform(h, q, n0, T0);
+            if (rc) return rc;
+        }
+        return FDLB_OK;
+    }
+    const fdlb::InstanceSetup& I = S->setup[instance];
+    const int N = I.p.n_cells;
+    const double nn = n0 > 0.0 ? n0 : I.n0;
+    const double TT = T0 > 0.0 ? T0 : 0.5 * (I.p.T_wall[0] + I.p.T_wall[1]);
+    std::vector<double> n(N, nn), u(N, 0.0), T(N, TT), q(N, 0.0), f;
+    fdlb::seed_state(*S, instance, n, u, T, q, f);
+    return fdlb::upload_state(*S, instance, f.data());
+}
+
+int fdlb_init_from_moments(fdlb_handle h, int instance, const double* n, const double* u2, const double* T,
+                           const double* qR, int n_points) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || n_points < 2 || !n || !u2 || !T || !qR) return FDLB_EINVAL;
+    for (int k = 0; k < n_points; ++k)
+        if (!(n[k] > 0.0) || !(T[k] > 0.0) || !std::isfinite(u2[k]) || !std::isfinite(qR[k])) return FDLB_EINVAL;
+    const fdlb::InstanceSetup& I = S->setup[instance];
+    const int N = I.p.n_cells;
+    const double a = I.grid.R_f[0], b = I.grid.R_f[N];
+    std::vector<double> cn(N), cu(N), cT(N), cq(N), f;
+    for (int c = 0; c < N; ++c) {
+        const double x = (I.grid.R_c[c] - a) / (b - a) * (n_points - 1);
+        int k = std::min(n_points - 2, std::max(0, (int)std::floor(x)));
+        const double t = x - k;
+        cn[c] = (1 - t) * n[k] + t * n[k + 1];
+        cu[c] = (1 - t) * u2[k] + t * u2[k + 1];
+        cT[c] = (1 - t) * T[k] + t * T[k + 1];
+        cq[c] = (1 - t) * qR[k] + t * qR[k + 1];
+    }
+    fdlb::seed_state(*S, instance, cn, cu, cT, cq, f);
+    return fdlb::upload_state(*S, instance, f.data());
+}
+
+int fdlb_set_f(fdlb_handle h, int instance, const double* f_host) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !f_host) return FDLB_EINVAL;
+    return fdlb::upload_state(*S, instance, f_host);
+}
+
+int fdlb_get_f(fdlb_handle h, int instance, double* f_host) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !f_host) return FDLB_EINVAL;
+    return fdlb::download_buf(*S, instance, 0, f_host);
+}
+
+int fdlb_step(fdlb_handle h, int64_t n_steps) {
+    Solver* S = SOL(h);
+    if (!S || n_steps < 0) return FDLB_EINVAL;
+    return fdlb::do_steps(*S, n_steps);
+}
+
+int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !L_host) return FDLB_EINVAL;
+    int rc = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1);
+    if (rc) return rc;
+    return fdlb::download_buf(*S, instance, 1, L_host);
+}
+
+int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
+    int rc = fdlb::launch_closure_buf(*S, 0);
+    if (rc) return rc;
+    const int N = S->setup[instance].p.n_cells;
+    const double* src = S->ca + (size_t)S->cell_off[instance] * fdlb::kCA;
+    FDLB_CUDA(cudaMemcpy2DAsync(out, FDLB_NMOM * sizeof(double), src, fdlb::kCA * sizeof(double),
+                                FDLB_NMOM * sizeof(double), N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                S->stream));
+    if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    return FDLB_OK;
+}
+
+int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, double* tau, double* n_wall2) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst) return FDLB_EINVAL;
+    // a right-hand-side evaluation refreshes the closure records and the wall densities
+    int rc = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1);
+    if (rc) return rc;
+    const int N = S->setup[instance].p.n_cells;
+    std::vector<double> ca((size_t)N * fdlb::kCA);
+    double nw[2];
+    FDLB_CUDA(cudaMemcpyAsync(ca.data(), S->ca + (size_t)S->cell_off[instance] * fdlb::kCA, ca.size() * 8,
+                              cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaMemcpyAsync(nw, S->nw + 2 * instance, 16, cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    const fdlb::InstanceSetup& I = S->setup[instance];
+    for (int c = 0; c < N; ++c) {
+        const double* r = &ca[(size_t)c * fdlb::kCA];
+        if (nbar) nbar[c] = r[10];
+        if (chi) chi[c] = r[9];
+        if (tau) tau[c] = fdlb::viscosity(r[0], r[4], r[9], I.sigma) / (r[0] * r[4]);
+    }
+    if (n_wall2) {
+        n_wall2[0] = nw[0];
+        n_wall2[1] = nw[1];
+    }
+    return FDLB_OK;
+}
+
+int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double* residual, int64_t* step) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst) return FDLB_EINVAL;
+    fdlb::launch_residual(S->sums[0], S->M.slices, S->inst_d, S->geo, S->rprev, S->rout, S->n_inst, 0, S->stream);
+    std::vector<double> ro((size_t)S->n_inst * 10);
+    int errflag = 0;
+    FDLB_CUDA(cudaMemcpyAsync(ro.data(), S->rout, ro.size() * 8, cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaMemcpyAsync(&errflag, S->err, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    if (total_mass) *total_mass = ro[(size_t)instance * 10 + 8];
+    if (residual) *residual = S->last_res[instance];
+    if (step) *step = S->inst_steps[instance];
+    if (errflag) return FDLB_ETIMEOUT;
+    if (ro[(size_t)instance * 10 + 9] != 0.0) return FDLB_ENAN;
+    return FDLB_OK;
+}
+
+int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
+                       int64_t* steps_taken, double* residual) {
+    Solver* S = SOL(h);
+    if (!S || !(tol > 0.0) || max_steps < 1 || check_every < 1) return FDLB_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int n = S->n_inst;
+    std::vector<int64_t> taken(n, 0);
+    std::vector<double> ro((size_t)n * 10);
+    auto check = [&](int save) -> int {
+        fdlb::launch_residual(S->sums[0], S->M.slices, S->inst_d, S->geo, S->rprev, S->rout, n, save, S->stream);
+        FDLB_CUDA(cudaMemcpyAsync(ro.data(), S->rout, ro.size() * 8, cudaMemcpyDeviceToHost, S->stream));
+        FDLB_CUDA(cudaStreamSynchronize(S->stream));
+        return FDLB_OK;
+    };
+    int rc = check(1);
+    if (rc) return rc;
+    std::fill(S->active.begin(), S->active.end(), 1);
+    rc = fdlb::upload_items(*S);
+    if (rc) return rc;
+    int status = FDLB_ENOTCONVERGED;
+    int64_t done = 0;
+    while (done < max_steps) {
+        const int64_t k = std::min<int64_t>(check_every, max_steps - done);
+        rc = fdlb::do_steps(*S, k);
+        if (rc) return rc;
+        done += k;
+        for (int q = 0; q < n; ++q)
+            if (S->active[q]) taken[q] += k;
+        rc = check(1);
+        if (rc) return rc;
+        bool any_active = false, changed = false, nan = false;
+        for (int q = 0; q < n; ++q) {
+            if (!S->active[q]) continue;
+            const double* r = &ro[(size_t)q * 10];
+            if (r[9] != 0.0) nan = true;
+            const fdlb::InstanceSetup& I = S->setup[q];
+            const double T0 = 0.5 * (I.p.T_wall[0] + I.p.T_wall[1]);
+            const double scale[4] = {I.n0, 1.0, T0, I.n0 * T0 * std::sqrt(T0)};
+            double res = 0.0;
+            for (int e = 0; e < 4; ++e) res = std::max(res, r[e] / ((double)k * std::max(r[4 + e], scale[e])));
+            S->last_res[q] = res;
+            if (res <= tol) {
+                S->active[q] = 0;
+                changed = true;
+            } else {
+                any_active = true;
+            }
+        }
+        if (nan) {
+            status = FDLB_ENAN;
+            break;
+        }
+        if (!any_active) {
+            status = FDLB_OK;
+            break;
+        }
+        if (changed) {
+            rc = fdlb::upload_items(*S);
+            if (rc) return rc;
+        }
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (max_seconds > 0.0 && el > max_seconds) {
+            status = FDLB_ETIMEOUT;
+            break;
+        }
+    }
+    std::fill(S->active.begin(), S->active.end(), 1);
+    rc = fdlb::upload_items(*S);
+    if (rc) return rc;
+    for (int q = 0; q < n; ++q) {
+        if (steps_taken) steps_taken[q] = taken[q];
+        if (residual) residual[q] = S->last_res[q];
+    }
+    return status;
+}
+
+int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
+    const fdlb::InstanceSetup& I = S->setup[instance];
+    out->C = I.C;
+    out->sigma = I.sigma;
+    out->n0 = I.n0;
+    out->dt = I.dt;
+    out->R_first = I.grid.R_f.front();
+    out->R_last = I.grid.R_f.back();
+    out->n_cells = I.p.n_cells;
+    out->n_momenta = S->Np;
+    out->fm_band = I.band.width;
+    out->precision = S->precision;
+    out->step = S->inst_steps[instance];
+    return FDLB_OK;
+}
+
+static const char kMagic[8] = {'F', 'D', 'L', 'B', 'C', 'K', 'P', '1'};
+
+int fdlb_save(fdlb_handle h, const char* path) {
+    Solver* S = SOL(h);
+    if (!S || !path) return FDLB_EINVAL;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return FDLB_EIO;
+    bool ok = std::fwrite(kMagic, 1, 8, fp) == 8;
+    const int32_t hdr[4] = {S->n_inst, S->Np, S->precision, S->geometry};
+    ok = ok && std::fwrite(hdr, sizeof(hdr), 1, fp) == 1;
+    for (int q = 0; q < S->n_inst && ok; ++q) {
+        ok = std::fwrite(&S->setup[q].p, sizeof(fdlb_params), 1, fp) == 1;
+        ok = ok && std::fwrite(&S->inst_steps[q], sizeof(int64_t), 1, fp) == 1;
+        const size_t bytes = (size_t)S->setup[q].p.n_cells * S->Np * S->tsize;
+        std::vector<unsigned char> buf(bytes);
+        if (cudaMemcpyAsync(buf.data(), (unsigned char*)S->f[0] + S->f_off[q] * S->tsize, bytes, cudaMemcpyDeviceToHost,
+                            S->stream) != cudaSuccess ||
+            cudaStreamSynchronize(S->stream) != cudaSuccess) {
+            std::fclose(fp);
+            return FDLB_ECUDA;
+        }
+        ok = ok && std::fwrite(buf.data(), 1, bytes, fp) == bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? FDLB_OK : FDLB_EIO;
+}
+
+int fdlb_load(fdlb_handle h, const char* path) {
+    Solver* S = SOL(h);
+    if (!S || !path) return FDLB_EINVAL;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return FDLB_EIO;
+    char mg[8];
+    int32_t hdr[4];
+    int rc = FDLB_OK;
+    if (std::fread(mg, 1, 8, fp) != 8 || std::memcmp(mg, kMagic, 8) || std::fread(hdr, sizeof(hdr), 1, fp) != 1) {
+        std::fclose(fp);
+        return FDLB_EIO;
+    }
+    if (hdr[0] != S->n_inst || hdr[1] != S->Np || hdr[2] != S->precision || hdr[3] != S->geometry) {
+        std::fclose(fp);
+        return FDLB_EINVAL;
+    }
+    for (int q = 0; q < S->n_inst && !rc; ++q) {
+        fdlb_params p;
+        int64_t st;
+        if (std::fread(&p, sizeof(p), 1, fp) != 1 || std::fread(&st, sizeof(st), 1, fp) != 1) {
+            rc = FDLB_EIO;
+            break;
+        }
+        const fdlb_params& mine = S->setup[q].p;
+        if (p.n_cells != mine.n_cells || p.R_in != mine.R_in || p.R_out != mine.R_out || p.eta0 != mine.eta0) {
+            rc = FDLB_EINVAL;
+            break;
+        }
+        const size_t bytes = (size_t)mine.n_cells * S->Np * S->tsize;
+        std::vector<unsigned char> buf(bytes);
+        if (std::fread(buf.data(), 1, bytes, fp) != bytes) {
+            rc = FDLB_EIO;
+            break;
+        }
+        if (cudaMemcpyAsync((unsigned char*)S->f[0] + S->f_off[q] * S->tsize, buf.data(), bytes, cudaMemcpyHostToDevice,
+                            S->stream) != cudaSuccess ||
+            cudaStreamSynchronize(S->stream) != cudaSuccess) {
+            rc = FDLB_ECUDA;
+            break;
+        }
+        S->inst_steps[q] = st;
+    }
+    std::fclose(fp);
+    if (rc) return rc;
+    S->prev_valid = false;
+    return fdlb::launch_moments_all(*S, 0);
+}
+
+const char* fdlb_error_string(int code) {
+    switch (code) {
+        case FDLB_OK: return "ok";
+        case FDLB_EINVAL: return "invalid argument";
+        case FDLB_ECUDA: return "CUDA runtime error";
+        case FDLB_ENOMEM: return "out of memory or workspace too small";
+        case FDLB_ENOTCONVERGED: return "not converged within max_steps";
+        case FDLB_ETIMEOUT: return "time limit reached or a device wait gave up";
+        case FDLB_ENAN: return "non-finite moments";
+        case FDLB_EIO: return "checkpoint I/O error";
+        case FDLB_ENOGPU: return "no usable CUDA device";
+        default: return "unknown error";
+    }
+}
+
+int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads) {
+    Solver* S = SOL(h);
+    if (!S || cells_per_tile < 0 || slice_k < 0 || threads < 0) return FDLB_EINVAL;
+    return fdlb::configure_tiling(*S, cells_per_tile, slice_k, threads);
+}
+
+int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    // candidates: tile cells x slice width x thread cap; each timed over 3 RHS evaluations
+    const int Bs[4] = {4, 8, 16, 32};
+    std::vector<int> KSs = {S->n3};
+    if (S->geometry == FDLB_CYL) {
+        KSs.clear();
+        for (int k = 1; k <= S->n3; k *= 2)
+            if (S->n3 % k == 0 && ((size_t)S->nR * S->n2 * k * S->tsize) % 16 == 0) KSs.push_back(k);
+        if (KSs.empty()) KSs.push_back(S->n3);
+    }
+    const int caps[2] = {256, 512};
+    cudaEvent_t e0, e1;
+    FDLB_CUDA(cudaEventCreate(&e0));
+    FDLB_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bB = S->B, bK = S->KS, bT = 256;
+    for (int B : Bs)
+        for (int K : KSs)
+            for (int cap : caps) {
+                if (fdlb::configure_tiling(*S, B, K, cap) != FDLB_OK) continue;
+                if (S->B != B) continue;
+                bool ok = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1) == FDLB_OK;
+                cudaEventRecord(e0, S->stream);
+                for (int r = 0; r < 3 && ok; ++r) ok = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1) == FDLB_OK;
+                cudaEventRecord(e1, S->stream);
+                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    bB = B;
+                    bK = K;
+                    bT = cap;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = fdlb::configure_tiling(*S, bB, bK, bT);
+    if (cells_per_tile) *cells_per_tile = S->B;
+    if (slice_k) *slice_k = S->KS;
+    if (threads) *threads = S->threads;
+    return rc;
+}
+
+int64_t fdlb_launch_count(fdlb_handle h) {
+    Solver* S = SOL(h);
+    return S ? S->last_launches : -1;
+}
+
+int fdlb_set_graph_steps(fdlb_handle h, int steps) {
+    Solver* S = SOL(h);
+    if (!S || steps < 1 || steps > 1000) return FDLB_EINVAL;
+    if (steps != S->graph_steps && S->gexec) {
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+    }
+    S->graph_steps = steps;
+    return FDLB_OK;
+}
+
+int fdlb_set_kernel_timing(fdlb_handle h, int on) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (on && !S->tev[0])
+        for (cudaEvent_t& e : S->tev) FDLB_CUDA(cudaEventCreate(&e));
+    S->timing = on != 0;
+    return FDLB_OK;
+}
+
+int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, double* closure_ms, int64_t* n_closure) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (stream_ms) *stream_ms = S->t_stream_ms;
+    if (n_stream) *n_stream = S->n_stream_t;
+    if (closure_ms) *closure_ms = S->t_closure_ms;
+    if (n_closure) *n_closure = S->n_closure_t;
+    S->t_stream_ms = S->t_closure_ms = 0.0;
+    S->n_stream_t = S->n_closure_t = 0;
+    return FDLB_OK;
+}
+
+int fdlb_get_stream(fdlb_handle h, void** stream) {
+    Solver* S = SOL(h);
+    if (!S || !stream) return FDLB_EINVAL;
+    *stream = (void*)S->stream;
+    return FDLB_OK;
+}
+
+int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !src) return FDLB_EINVAL;
+    const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
+    FDLB_CUDA(cudaMemcpyAsync((unsigned char*)S->f[0] + S->f_off[instance] * S->tsize, src, bytes,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
+    S->inst_steps[instance] = 0;
+    return fdlb::launch_moments_all(*S, 0);
+}
+
+int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device) {
+    Solver* S = SOL(h);
+    if (!S || instance < 0 || instance >= S->n_inst || !dst) return FDLB_EINVAL;
+    const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
+    FDLB_CUDA(cudaMemcpyAsync(dst, (const unsigned char*)S->f[0] + S->f_off[instance] * S->tsize, bytes,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+    if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    return FDLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Device kernels of the FDLB step (sm_103a).
+//
+// Data layout in HBM (per instance, instances packed one after another):
+//   f[cell][k][i][j]   T = float or double; i: 2 Q_R radial momenta, j: Q_2, k: Q_3.
+//                      The passive-or-outermost axis k is outermost inside a cell so that a
+//                      momentum slice (a range of k) is one contiguous run per cell.
+//   sums[cell][slice][13]  FP64 raw quadrature sums (Eq. mom_quad) of the populations,
+//                      one partial per momentum slice (summed by the consumer in a fixed order).
+//   ca[cell][12]       FP64 closure record: n, u1, u2, u3, T, q1, q2, q3, P12, chi, nbar, 0.
+//
+// Per SSP-RK3 stage (Sec. III) two launches:
+//   closure_kernel  - per cell: n, u, T, q from the sums (Eq. macro_def), the Fischer-Methfessel
+//                     density nbar (Eq. fm) over the stored band and chi (Eq. chi / chi_ret).
+//   stream_kernel   - per (tile of cells) x (momentum slice): gradients of J1 (Eq. j1), tau
+//                     (Eq. tau), Pr (Eq. prandtl), the discrete equilibria (Sec. III.C) and the
+//                     wall densities in the prologue; then, per population, WENO5 radial advection
+//                     with metric factors (Sec. II.B/C), the curvature force with the K matrices
+//                     (Sec. III.B), the Shakhov + J1 collision, the RK combination, the store, and
+//                     the raw sums of the new populations (epilogue).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdlb {
+
+constexpr int kSums = 13;
+constexpr int kCA = 12;
+constexpr int kGeo = 6;            // per cell: R_c, 1/(dR/ds), A_+/V, A_-/V, force factor, V
+constexpr int kMaxE = 8;           // expansion coefficients per axis (N <= 7)
+constexpr int kMaxRed = 32;        // warps per block
+
+struct InstDev {
+    int n_cells;
+    int cell_off;                  // first global cell index of this instance
+    long long f_off;               // first element of this instance in the f buffers
+    int band_off;                  // first element of this instance's FM band
+    int band_w;                    // entries per band row (0: local chi)
+    int chi_local;                 // 1: chi at the local density
+    int geometry;
+    double sigma, bfac, etafac;    // sigma, 2 pi sigma^3 / 3, pi sigma^3 / 6
+    double dt, ds;
+    double nw_den[2];              // sum over incoming momenta of |p_R| g_wall
+};
+
+struct MomSet {
+    int nR, n2, n3, Np;            // axis sizes, momenta per cell
+    int NR, N2, N3;                // expansion orders
+    int slices, KS, Ms;            // momentum slices, k values per slice, momenta per slice
+    // offsets into the FP64 table buffer
+    int o_pR, o_wR, o_p2, o_w2, o_p3, o_w3, o_KR, o_K2, o_K3, o_GR, o_G2, o_G3, o_ha, o_hb, o_h0;
+};
+
+struct StageArgs {
+    const void* f_in;
+    const void* f_n;
+    void* f_out;
+    const double* ca;              // closure records of f_in
+    double* sums_out;              // raw sums of f_out
+    const int4* items;             // (instance, first cell, cells, slice)
+    const int* n_items;
+    const InstDev* inst;
+    const double* tab;
+    const double* geo;             // [cell][kGeo]
+    const double* gw;              // [instance][2][nR + n2 + n3] wall Maxwellians per axis
+    double* nw_out;                // [instance][2]
+    int* err;
+    double a, b;                   // f_out = a f_n + b (f_in + dt L(f_in))
+    int mode;                      // 0: RK stage; 1: write L(f_in) to f_out
+    int B;                         // cells per tile
+    int use_bulk;                  // stage the tile with cp.async.bulk
+};
+
+struct ClosureArgs {
+    const double* sums;
+    double* ca;
+    const int4* items;             // (instance, first cell, cells, 0)
+    const int* n_items;
+    const InstDev* inst;
+    const void* band;              // FM band values (T)
+    const int* band_lo;            // per global cell
+    int slices;
+    int max_union;                 // capacity of the shared n buffer
+};
+
+}  // namespace fdlb

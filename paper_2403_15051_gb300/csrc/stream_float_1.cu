@@ -1,0 +1,6 @@
+// Instantiation of the fused stage kernel for float populations, geometry 1 (0 cylinder, 1 sphere).
+#include "stream_kernel.cuh"
+
+namespace fdlb {
+FDLB_STREAM_INSTANCE(float, 1)
+}  // namespace fdlb
