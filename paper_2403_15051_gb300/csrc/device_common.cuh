@@ -55,10 +55,15 @@ __device__ __forceinline__ T ldg_t(const T* p) {
     return __ldg(p);
 }
 
+__device__ __forceinline__ float ratio_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double ratio_fast(double a, double b) { return a / b; }
+
 // Fifth-order WENO reconstruction (Jiang & Shu 1996; epsilon 1e-6, power 2) at the right face
 // of the cell holding c, upwind from the left; reversing the five arguments gives the value at
 // the left face of the cell holding c, upwind from the right.  The nonlinear weights
-// d_k / (eps + beta_k)^2 are put on a common denominator, leaving one division.
+// d_k / (eps + beta_k)^2 are scaled by the square of the smallest (eps + beta_k), which leaves
+// the normalised weights unchanged and keeps every intermediate in [0, 1] (no FP32 overflow for
+// large populations).
 template <typename T>
 __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     const T eps = T(1e-6);
@@ -66,13 +71,12 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     const T t0 = a - T(2) * b + c, t1 = a - T(4) * b + T(3) * c;
     const T t2 = b - T(2) * c + d, t3 = b - d;
     const T t4 = c - T(2) * d + e, t5 = T(3) * c - T(4) * d + e;
-    T e0 = eps + k13 * t0 * t0 + q * t1 * t1;
-    T e1 = eps + k13 * t2 * t2 + q * t3 * t3;
-    T e2 = eps + k13 * t4 * t4 + q * t5 * t5;
-    e0 *= e0;
-    e1 *= e1;
-    e2 *= e2;
-    const T a0 = T(0.1) * e1 * e2, a1 = T(0.6) * e0 * e2, a2 = T(0.3) * e0 * e1;
+    const T e0 = eps + k13 * t0 * t0 + q * t1 * t1;
+    const T e1 = eps + k13 * t2 * t2 + q * t3 * t3;
+    const T e2 = eps + k13 * t4 * t4 + q * t5 * t5;
+    const T m = fmin(e0, fmin(e1, e2));
+    const T s0 = ratio_fast(m, e0), s1 = ratio_fast(m, e1), s2 = ratio_fast(m, e2);
+    const T a0 = T(0.1) * s0 * s0, a1 = T(0.6) * s1 * s1, a2 = T(0.3) * s2 * s2;
     const T r0 = T(2) * a - T(7) * b + T(11) * c;
     const T r1 = -b + T(5) * c + T(2) * d;
     const T r2 = T(2) * c + T(5) * d - e;

@@ -24,8 +24,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
-    size_t f[3], sums[3], ca, tab, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err, rprev,
-        rout, total;
+    size_t f[3], sums[3], ca, rec, tab, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err,
+        rprev, rout, total;
 };
 
 }  // namespace
@@ -52,6 +52,7 @@ struct Solver {
     Layout lay{};
     void* f[3] = {nullptr, nullptr, nullptr};
     double* sums[3] = {nullptr, nullptr, nullptr};
+    void* rec = nullptr;
     double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *nw = nullptr, *rprev = nullptr,
            *rout = nullptr;
     InstDev* inst_d = nullptr;
@@ -65,9 +66,10 @@ struct Solver {
     int B = 16, KS = 1, threads = 0, mpt = 1;
     size_t smem_stream = 0;
     int use_bulk = 0;
-    int closure_cells = 32, closure_threads = 256;
+    int closure_cells = 4, closure_threads = 256;  // one warp per cell in reach (4 + 4 halo)
     int grid_stream = 1, grid_closure = 1;
     size_t closure_smem = 0;
+    int max_union = 1;
     std::vector<char> active;
     std::vector<int64_t> inst_steps;
     std::vector<double> last_res;
@@ -180,6 +182,7 @@ Layout make_layout(const Solver& S) {
     for (int b = 0; b < 3; ++b) L.f[b] = take(S.f_elems * S.tsize);
     for (int b = 0; b < 3; ++b) L.sums[b] = take((size_t)S.total_cells * S.n3 * kSums * sizeof(double));
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
+    L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
     L.inst = take(S.n_inst * sizeof(InstDev));
     L.geo = take((size_t)S.total_cells * kGeo * sizeof(double));
@@ -332,11 +335,14 @@ int upload_items(Solver& S) {
     for (const int4& w : ci) {
         const InstanceSetup& I = S.setup[w.x];
         if (I.band.width == 0) continue;
-        const int lo = I.band.lo[w.y];
-        const int hi = std::min(I.p.n_cells - 1, I.band.lo[w.y + w.z - 1] + I.band.width - 1);
+        const int N = I.p.n_cells;
+        const int h0 = std::max(0, std::min(w.y - 2, N - 5)), h1 = std::min(N, std::max(w.y + w.z + 2, 5));
+        const int lo = I.band.lo[h0];
+        const int hi = std::min(I.p.n_cells - 1, I.band.lo[h1 - 1] + I.band.width - 1);
         max_union = std::max(max_union, hi - lo + 1);
     }
-    S.closure_smem = (size_t)max_union * S.tsize;
+    S.max_union = max_union;
+    S.closure_smem = closure_smem(S.closure_cells, max_union, (int)S.tsize);
     S.grid_closure = std::max(1, std::min(nc, S.n_sm * 8));
     S.grid_stream = std::max(1, ns);
     return FDLB_OK;
@@ -425,18 +431,26 @@ int launch_moments_all(Solver& S, int buf) {
 int launch_closure_buf(Solver& S, int buf) {
     ClosureArgs A{};
     A.sums = S.sums[buf];
+    A.f_in = S.f[buf];
     A.ca = S.ca;
+    A.rec = S.rec;
+    A.rec_stride = record_stride(S.nR, S.n2, S.n3);
+    A.nw = S.nw;
     A.items = S.citems;
     A.n_items = S.n_citems;
     A.inst = S.inst_d;
     A.band = S.band;
     A.band_lo = S.band_lo;
+    A.tab = S.tab;
+    A.geo = S.geo;
+    A.gw = S.gw;
     A.slices = S.M.slices;
-    A.max_union = (int)(S.closure_smem / S.tsize);
+    A.max_cells = S.closure_cells;
+    A.max_union = S.max_union;
     if (S.precision == FDLB_FP32)
-        launch_closure<float>(A, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+        launch_closure<float>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
     else
-        launch_closure<double>(A, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+        launch_closure<double>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
     S.launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -474,7 +488,9 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.f_in = S.f[in];
     A.f_n = S.f[fn];
     A.f_out = S.f[out];
-    A.ca = S.ca;
+    A.rec = S.rec;
+    A.rec_stride = record_stride(S.nR, S.n2, S.n3);
+    A.nw = S.nw;
     A.sums_out = S.sums[out];
     A.items = S.sitems;
     A.n_items = S.n_sitems;
@@ -482,7 +498,6 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.tab = S.tab;
     A.geo = S.geo;
     A.gw = S.gw;
-    A.nw_out = S.nw;
     A.err = S.err;
     A.a = a;
     A.b = b;
@@ -643,6 +658,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         R.sums[b] = (double*)(R.ws + L.sums[b]);
     }
     R.ca = (double*)(R.ws + L.ca);
+    R.rec = R.ws + L.rec;
     R.tab = (double*)(R.ws + L.tab);
     R.inst_d = (InstDev*)(R.ws + L.inst);
     R.geo = (double*)(R.ws + L.geo);
@@ -699,8 +715,9 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         FDLB_CUDA(cudaMemcpyAsync(R.band, bandd.data(), bandd.size() * 8, cudaMemcpyHostToDevice, R.stream));
     FDLB_CUDA(cudaStreamSynchronize(R.stream));
     // default tiling: a slice per p_3 value on the cylinder (p_3 is passive there)
-    const int KS0 = R.geometry == FDLB_CYL && ((size_t)R.nR * R.n2 * R.tsize) % 16 == 0 ? 1 : R.n3;
-    rc = configure_tiling(R, R.geometry == FDLB_CYL ? 16 : 8, KS0, 256);
+    // default tiling (the fastest of a sweep on GB300; fdlb_autotune refines it per workload):
+    // whole cells per block, 4 cells per tile (cylinder, 256 threads) or 8 (sphere, 512 threads)
+    rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, 256) : configure_tiling(R, 8, R.n3, 512);
     for (int q = 0; q < n && !rc; ++q) rc = fdlb_init_uniform(reinterpret_cast<fdlb_handle>(S.get()), q, 0.0, 0.0);
     if (rc) {
         if (R.own_ws) cudaFree(R.ws);

@@ -9,11 +9,11 @@
 //   ca[cell][12]       FP64 closure record: n, u1, u2, u3, T, q1, q2, q3, P12, chi, nbar, 0.
 //
 // Per SSP-RK3 stage (Sec. III) two launches:
-//   closure_kernel  - per cell: n, u, T, q from the sums (Eq. macro_def), the Fischer-Methfessel
-//                     density nbar (Eq. fm) over the stored band and chi (Eq. chi / chi_ret).
-//   stream_kernel   - per (tile of cells) x (momentum slice): gradients of J1 (Eq. j1), tau
-//                     (Eq. tau), Pr (Eq. prandtl), the discrete equilibria (Sec. III.C) and the
-//                     wall densities in the prologue; then, per population, WENO5 radial advection
+//   closure_kernel  - per cell, once: n, u, T, q from the sums (Eq. macro_def), the Fischer-
+//                     Methfessel density nbar (Eq. fm) over the stored band, chi (Eq. chi /
+//                     chi_ret), the J1 gradients (Eq. j1), tau (Eq. tau), Pr (Eq. prandtl) and the
+//                     discrete equilibria (Sec. III.C) -> a per-cell record; the wall densities.
+//   stream_kernel   - per (tile of cells) x (momentum slice), per population: WENO5 radial advection
 //                     with metric factors (Sec. II.B/C), the curvature force with the K matrices
 //                     (Sec. III.B), the Shakhov + J1 collision, the RK combination, the store, and
 //                     the raw sums of the new populations (epilogue).
@@ -55,7 +55,9 @@ struct StageArgs {
     const void* f_in;
     const void* f_n;
     void* f_out;
-    const double* ca;              // closure records of f_in
+    const void* rec;               // per-cell collision records of f_in (T), [cell][rec_stride]
+    int rec_stride;
+    const double* nw;              // [instance][2] wall densities of f_in
     double* sums_out;              // raw sums of f_out
     const int4* items;             // (instance, first cell, cells, slice)
     const int* n_items;
@@ -63,7 +65,6 @@ struct StageArgs {
     const double* tab;
     const double* geo;             // [cell][kGeo]
     const double* gw;              // [instance][2][nR + n2 + n3] wall Maxwellians per axis
-    double* nw_out;                // [instance][2]
     int* err;
     double a, b;                   // f_out = a f_n + b (f_in + dt L(f_in))
     int mode;                      // 0: RK stage; 1: write L(f_in) to f_out
@@ -73,13 +74,21 @@ struct StageArgs {
 
 struct ClosureArgs {
     const double* sums;
-    double* ca;
+    const void* f_in;              // populations (T), for the wall densities
+    double* ca;                    // FP64 closure records
+    void* rec;                     // per-cell collision records (T)
+    int rec_stride;
+    double* nw;                    // [instance][2] wall densities
     const int4* items;             // (instance, first cell, cells, 0)
     const int* n_items;
     const InstDev* inst;
     const void* band;              // FM band values (T)
     const int* band_lo;            // per global cell
+    const double* tab;
+    const double* geo;
+    const double* gw;
     int slices;
+    int max_cells;                 // cells per closure item
     int max_union;                 // capacity of the shared n buffer
 };
 

@@ -29,9 +29,7 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
     s.red = off;
     off += al((long long)2 * nwarps * kSums * 8);
     s.ecoef = off;
-    off += al((long long)B * 4 * kMaxE * 8);
     s.misc = off;
-    off += al((long long)(nwarps + 4) * 8);
     s.total = off;
     return s;
 }
@@ -42,7 +40,12 @@ void launch_moments(const T* f, double* sums, const int4* items, const int* n_it
                     const double* tab, const MomSet& M, cudaStream_t s);
 
 template <typename T>
-void launch_closure(const ClosureArgs& A, int grid, int threads, size_t smem, cudaStream_t s);
+void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s);
+
+size_t closure_smem(int max_cells, int max_union, int tsize);
+
+// Per-cell collision record: kCellScalars scalars then g_R, g_2, g_3; padded to 4 entries.
+inline int record_stride(int nR, int n2, int n3) { return (kCellScalars + nR + n2 + n3 + 3) / 4 * 4; }
 
 #define FDLB_STREAM_DECL(T, G)                                                                             \
     cudaError_t launch_stream_##T##_##G(int mpt, const StageArgs& A, const MomSet& M, int grid, int threads, \

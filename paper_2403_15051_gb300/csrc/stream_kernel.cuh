@@ -3,16 +3,15 @@
 // Per work item (instance, first cell c0, cells Be, slice sl):
 //  1. the TMA engine copies the populations of cells c0-3 .. c0+Be+2 (this slice) into shared
 //     memory (one bulk copy when the slice is the whole cell, else one per cell);
-//  2. meanwhile the block builds the per-cell collision data from the closure records (FP64):
-//     J1 gradients by the five-point stencil, tau (Eq. tau), Pr (Eq. prandtl), the covariant
-//     strain (A2 reading) and the per-axis equilibrium vectors (Sec. III.C, recurrences), and
-//     at a wall tile the wall density n_w from zero net mass flux;
+//  2. meanwhile the block loads the per-cell collision records written by the closure kernel
+//     (J1 gradients, tau, Pr, strain, equilibrium vectors) and the wall densities;
 //  3. ghost rows at a wall: incoming directions carry n_w times the wall Maxwellian, outgoing
 //     directions the cubic extrapolation of the four cells next to the wall;
 //  4. per population: WENO5 face values of f/w upwinded by sign(p_R), conservative advection
 //     with the face areas and cell volume (Sec. II.B/C), the curvature force with the K matrices
 //     (Sec. III.B), the Shakhov + J1 collision (Eqs. j0, j1), the RK combination and the store;
-//  5. the 13 raw sums of the new populations per cell (FP64 warp and block reduction).
+//  5. the 13 raw sums of the new populations per cell (warp tree in the populations' precision,
+//     FP64 across warps).
 #pragma once
 
 #include "device_common.cuh"
@@ -33,7 +32,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NT = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Ms = M.Ms, Np = M.Np, QR = nR / 2;
+    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Ms = M.Ms, Np = M.Np;
     const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);  // rows: cells c0-3 .. c0+B+2
@@ -51,8 +50,6 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     const int cstride = kCellScalars + nR + n2 + n3;
     T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
     double* red = reinterpret_cast<double*>(smem_raw + P.red);
-    double* ecoef = reinterpret_cast<double*>(smem_raw + P.ecoef);
-    double* misc = reinterpret_cast<double*>(smem_raw + P.misc);
     const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
     T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
@@ -111,7 +108,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                     frow0[(long long)(cc - lo) * Ms + e] = ldg_t(fin + (long long)cc * Np + slice_off + e);
         }
 
-        // ---- 2. prologue, overlapping the copy
+        // ---- 2. per-cell collision records and geometry of the tile (overlapping the copy)
         const double* gwi = A.gw + (long long)wi.x * 2 * gwstride;
         for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = (T)gwi[e];
         for (int c = tid; c < Be; c += NT) {
@@ -120,152 +117,14 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             sgeo[c * 3 + 1] = (T)g[3];
             sgeo[c * 3 + 2] = (T)g[4];
         }
-        const double* ca = A.ca + (long long)I.cell_off * kCA;
-        for (int cl = warp; cl < Be; cl += nwarps) {
-            const int c = c0 + cl;
-            const double* rc = ca + (long long)c * kCA;
-            const double n = rc[0], u0 = rc[1], u1 = rc[2], u2 = rc[3], Tc = rc[4];
-            if (lane < 4) {
-                // expansion coefficients e_l of the per-axis equilibria (Sec. III.C)
-                double e[kMaxE];
-                for (int l = 0; l < kMaxE; ++l) e[l] = 0.0;
-                if (lane < 2) {
-                    // half range, positive (lane 0) / negative (lane 1) half line, v = +-u_R:
-                    // e_0 = h_0 (1 + erf(v/sqrt(2T)))/2,
-                    // b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
-                    //                   + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)]
-                    const double v = lane == 0 ? u0 : -u0;
-                    const double* ha = tab + M.o_ha;
-                    const double* hb = tab + M.o_hb;
-                    const double* h0 = tab + M.o_h0;
-                    const double G0 = exp(-v * v / (2.0 * Tc)) / sqrt(6.283185307179586477 * Tc);
-                    e[0] = h0[0] * 0.5 * (1.0 + erf(v / sqrt(2.0 * Tc)));
-                    double run = 0.0;
-                    for (int l = 0; l < M.NR; ++l) {
-                        const double em1 = l ? e[l - 1] : 0.0;
-                        const double bl = l ? hb[l] : 0.0;
-                        const double val = (v - ha[l]) * e[l] + (Tc - 1.0) * bl * em1 +
-                                           Tc * h0[l] * (G0 - run * 0.39894228040143267794);
-                        e[l + 1] = val / hb[l + 1];
-                        run += h0[l] * e[l];
-                    }
-                } else {
-                    // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                    const double u = lane == 2 ? u1 : u2;
-                    const int Nax = lane == 2 ? M.N2 : M.N3;
-                    e[0] = 1.0;
-                    if (Nax >= 1) e[1] = u;
-                    for (int l = 1; l < Nax; ++l) e[l + 1] = u * e[l] + l * (Tc - 1.0) * e[l - 1];
-                }
-                for (int l = 0; l < kMaxE; ++l) ecoef[(cl * 4 + lane) * kMaxE + l] = e[l];
-            } else if (lane == 4) {
-                int idx[5];
-                double sw[5];
-                stencil5(c, N, idx, sw);
-                const double* gc = A.geo + (long long)(I.cell_off + c) * kGeo;
-                const double R = gc[0], sc = gc[1] / I.ds;
-                double X = 0.0, Y = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
-                for (int q = 0; q < 5; ++q) {
-                    const double* r = ca + (long long)idx[q] * kCA;
-                    X += sw[q] * log(r[0] * r[0] * r[9] * r[4]);
-                    Y += sw[q] * log(r[4]);
-                    d0 += sw[q] * r[1];
-                    d1 += sw[q] * r[2];
-                    d2 += sw[q] * r[3];
-                }
-                X *= sc;
-                Y *= sc;
-                d0 *= sc;
-                d1 *= sc;
-                d2 *= sc;
-                const double chi = rc[9], br = I.bfac * n, x = br * chi;
-                const double pi = 3.14159265358979323846;
-                const double mu = 5.0 / (16.0 * I.sigma * I.sigma) * sqrt(Tc / pi) *
-                                  (1.0 / chi + 0.8 * br + 4.0 / 25.0 * (1.0 + 12.0 / pi) * br * br * chi);
-                const double Pr = 2.0 / 3.0 * (1.0 + 0.8 * x + 4.0 / 25.0 * (1.0 + 12.0 / pi) * x * x) /
-                                  (1.0 + 1.2 * x + 9.0 / 25.0 * (1.0 + 32.0 / (9.0 * pi)) * x * x);
-                const double tau = mu / (n * Tc);
-                double S11, S22, S01, S02, div;
-                if (GEOM == 0) {
-                    S11 = u0 / R;
-                    S22 = 0.0;
-                    S01 = 0.5 * (d1 - u1 / R);
-                    S02 = 0.5 * d2;
-                    div = d0 + u0 / R;
-                } else {
-                    S11 = S22 = u0 / R;
-                    S01 = 0.5 * (d1 - u1 / R);
-                    S02 = 0.5 * (d2 - u2 / R);
-                    div = d0 + 2.0 * u0 / R;
-                }
-                T* ct = cellT + cl * cstride;
-                ct[0] = (T)n;
-                ct[1] = (T)u0;
-                ct[2] = (T)u1;
-                ct[3] = (T)u2;
-                ct[4] = (T)(1.0 / Tc);
-                ct[5] = (T)(1.0 / tau);
-                ct[6] = (T)((1.0 - Pr) / (n * Tc * Tc));
-                ct[7] = (T)rc[5];
-                ct[8] = (T)rc[6];
-                ct[9] = (T)rc[7];
-                ct[10] = (T)x;
-                ct[11] = (T)X;
-                ct[12] = (T)Y;
-                ct[13] = (T)d0;
-                ct[14] = (T)S11;
-                ct[15] = (T)S22;
-                ct[16] = (T)S01;
-                ct[17] = (T)S02;
-                ct[18] = (T)0.0;
-                ct[19] = (T)div;
-            }
-            __syncwarp();
-            for (int e = lane; e < nR + n2 + n3; e += 32) {
-                double acc = 0.0;
-                if (e < nR) {
-                    const int half = e >= QR ? 1 : 0;
-                    for (int l = 0; l <= M.NR; ++l) acc += tab[M.o_GR + e * kMaxE + l] * ecoef[(cl * 4 + half) * kMaxE + l];
-                } else if (e < nR + n2) {
-                    const int j = e - nR;
-                    for (int l = 0; l <= M.N2; ++l) acc += tab[M.o_G2 + j * kMaxE + l] * ecoef[(cl * 4 + 2) * kMaxE + l];
-                } else {
-                    const int k = e - nR - n2;
-                    for (int l = 0; l <= M.N3; ++l) acc += tab[M.o_G3 + k * kMaxE + l] * ecoef[(cl * 4 + 3) * kMaxE + l];
-                }
-                cellT[cl * cstride + kCellScalars + e] = (T)acc;
+        {
+            const T* rsrc = reinterpret_cast<const T*>(A.rec) + (long long)(I.cell_off + c0) * A.rec_stride;
+            for (int e = tid; e < Be * cstride; e += NT) {
+                const int cl = e / cstride, q = e % cstride;
+                cellT[e] = rsrc[(long long)cl * A.rec_stride + q];
             }
         }
-        __syncthreads();
-
-        // wall densities: n_w = sum_out |p_R| w vhat_wall / sum_in |p_R| g_wall (zero net mass flux)
-        double nwall[2] = {0.0, 0.0};
-        for (int side = 0; side < 2; ++side) {
-            const bool here = side == 0 ? (c0 == 0) : (c0 + Be == N);
-            if (!here) continue;
-            double acc = 0.0;
-            for (int m = tid; m < Np; m += NT) {
-                const int k = m / (nR * n2), rem = m % (nR * n2), i = rem / n2, j = rem % n2;
-                const T pr = sp_R[i];
-                if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
-                const T wm = sw_R[i] * sw_2[j] * sw_3[k], iw = T(1) / wm;
-                const long long b = side == 0 ? (long long)m : (long long)(N - 1) * Np + m;
-                const long long st = side == 0 ? (long long)Np : -(long long)Np;
-                const T f0 = ldg_t(fin + b), f1 = ldg_t(fin + b + st), f2 = ldg_t(fin + b + 2 * st), f3 = ldg_t(fin + b + 3 * st);
-                T g1, g2;
-                wall_ghosts(f0, f1, f2, f3, g1, g2);
-                const T vh = weno5(f2 * iw, f1 * iw, f0 * iw, g1 * iw, g2 * iw);
-                acc += (double)(fabs(pr) * wm * vh);
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) misc[warp] = acc;
-            __syncthreads();
-            double tot = 0.0;
-            for (int ww = 0; ww < nwarps; ++ww) tot += misc[ww];
-            nwall[side] = tot / I.nw_den[side];
-            if (tid == 0 && sl == 0) A.nw_out[wi.x * 2 + side] = nwall[side];
-            __syncthreads();
-        }
+        const double nwall[2] = {A.nw[wi.x * 2], A.nw[wi.x * 2 + 1]};
 
         // ---- wait for the staged cells
         if (A.use_bulk) {
@@ -430,14 +289,14 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                     acc[12] += out * ps * p3v;
                 }
             }
-            // ---- 5. raw sums of the new populations: per-thread partial, FP64 warp and
-            // block reduction in a fixed order
+            // ---- 5. raw sums of the new populations: per-thread partial and warp tree in the
+            // populations' precision, FP64 sum over the warps in a fixed order
             if (A.mode == 0) {
                 double* rb = red + (cl & 1) * nwarps * kSums;
 #pragma unroll
                 for (int q = 0; q < kSums; ++q) {
-                    const double s = warp_sum((double)acc[q]);
-                    if (lane == 0) rb[warp * kSums + q] = s;
+                    const T s = warp_sum(acc[q]);  // warp tree in the populations' precision
+                    if (lane == 0) rb[warp * kSums + q] = (double)s;
                 }
                 __syncthreads();
                 if (tid < kSums) {

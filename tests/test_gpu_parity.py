@@ -178,3 +178,48 @@ def test_config1_couette_2000_steps_fp64():
     errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
     assert max(errs.values()) <= 1e-10, errs
     assert np.abs(S.moments()["u2"]).max() > 1e-3  # the flow has developed
+
+
+def test_config2_fourier_cyl_full_size_fp32():
+    """Cylindrical Fourier flow at full size: 1024 stretched cells x 1024 momenta, FP32, in the
+    launch configuration the benchmark uses; ten steps from a seeded perturbed equilibrium."""
+    d = wl.fourier_cyl_1024()
+    P, f0, S = _pair(d, seed=21, amp=0.02)
+    L = S.eval_rhs()
+    L_or = osolver.rhs(f0, P)
+    assert np.max(np.abs(L - L_or)) / np.max(np.abs(L_or)) <= RHS_TOL["fp32"]
+    S.step(10)
+    f_or = osolver.run(f0, P, 10)
+    errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
+    assert max(errs.values()) <= TOL["fp32"], errs
+
+
+def test_config3_fourier_sph_full_size_fp32():
+    """Spherical Fourier flow at full size: 2048 cells x 3456 momenta (24 x 12 x 12), eta0 0.3,
+    seeded Kn; right-hand side and one SSP-RK3 step."""
+    from .cases import accept_kn
+
+    d = wl.fourier_sph_2048(accept_kn)
+    P, f0, S = _pair(d, seed=22, amp=0.02)
+    L = S.eval_rhs()
+    L_or = osolver.rhs(f0, P)
+    assert np.max(np.abs(L - L_or)) / np.max(np.abs(L_or)) <= RHS_TOL["fp32"]
+    S.step(1)
+    f_or = osolver.rk3_step(f0, P)
+    errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
+    assert max(errs.values()) <= TOL["fp32"], errs
+
+
+def test_batch_instances_of_the_sweep_match_oracle():
+    """Three instances of the seeded 512-instance sweep (1024 momenta each, uneven sizes) in one
+    batched handle; each compared with the oracle after three steps."""
+    from .cases import accept_kn
+
+    ds = wl.batch_instances(lambda kn, e, r: accept_kn(kn, e), n=3)
+    S = fdlb.Solver(ds)
+    S.step(3)
+    for q, d in enumerate(ds):
+        P = oracle_problem(d)
+        f_or = osolver.run(osolver.uniform_state(P), P, 3)
+        errs = compare_moments(S.moments(q), osolver.moments(f_or, P), P)
+        assert max(errs.values()) <= TOL["fp32"], (q, errs)
