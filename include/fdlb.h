@@ -228,6 +228,29 @@ int fdlb_get_stream(fdlb_handle h, void** stream);
 int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device);
 int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device);
 
+/* ----------------------------------------------------------------------- no device allocation
+ * Per-cell moments of populations the caller already holds on the device, for callers that
+ * cannot allocate device memory (plugins inside an application that owns the whole device
+ * budget, latency-critical loops that cannot afford cudaMalloc's implicit synchronisation).
+ * The paper has no counterpart: this is a library service around the moment reduction of
+ * Eq. mom_quad / Eq. macro_def.
+ *
+ * f_dev: device array of n_cells * 2Q_R * Q_2 * Q_3 populations in the library's own layout
+ * ([cell][k][i][j], as fdlb_get_state_raw writes it), FP32 or FP64 per `precision`.
+ * nodes_host: host array [2Q_R radial nodes | Q_2 nodes | Q_3 nodes] as fdlb_quadrature returns
+ * them.  moments_dev: device array [n_cells][FDLB_NMOM] (n, u_1..3, T, q_1..3, P_12), FP64.
+ * Work is issued on `cuda_stream` (a cudaStream_t; NULL = legacy stream), asynchronously.
+ *
+ * Allocates no device memory: the partial sums live in a fixed scratch array of this library
+ * (3.4 MB, held by every GPU that loads the library until the process exits), so n_cells is
+ * limited to 32768 (FDLB_EINVAL beyond).  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) and should come before any stream capture on that device.
+ * Every call shares the one scratch array, which keeps the last call's contents; calls that
+ * overlap on the GPU (different streams, no ordering) race on it and must be serialised by the
+ * caller.  Returns FDLB_OK, FDLB_EINVAL, FDLB_ENOGPU or FDLB_ECUDA. */
+int fdlb_moments_noalloc(int precision, int Q_R, int Q_2, int Q_3, const double* nodes_host, int n_cells,
+                         const void* f_dev, double* moments_dev, void* cuda_stream);
+
 /* ----------------------------------------------------------------------- host-only set-up
  * These run on the host only (no GPU needed). */
 

@@ -97,6 +97,7 @@ def load_library():
         "fdlb_get_stream": (c_int, [H, POINTER(c_void_p)]),
         "fdlb_set_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
         "fdlb_get_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
+        "fdlb_moments_noalloc": (c_int, [c_int, c_int, c_int, c_int, _DP, c_int, c_void_p, c_void_p, c_void_p]),
         "fdlb_quadrature": (c_int, [c_int, c_int, _DP, _DP]),
         "fdlb_derivative_matrix": (c_int, [c_int, c_int, _DP]),
         "fdlb_physical_parameters": (c_int, [c_double, c_double, c_double, POINTER(c_double), POINTER(c_double),
@@ -323,6 +324,17 @@ def quadrature(kind, Q):
     x, w = np.empty(n), np.empty(n)
     _check(L.fdlb_quadrature(kind, Q, x, w), "fdlb_quadrature")
     return x, w
+
+
+def moments_noalloc(precision, Q_R, Q_2, Q_3, n_cells, f_dev_ptr, moments_dev_ptr, stream=0):
+    """Per-cell moments of device populations in the library layout, without any device
+    allocation by the library (see fdlb_moments_noalloc in include/fdlb.h)."""
+    L = load_library()
+    nodes = np.concatenate([quadrature(QUAD_HALF, Q_R)[0], quadrature(QUAD_FULL, Q_2)[0],
+                            quadrature(QUAD_FULL, Q_3)[0]])
+    prec = FP32 if precision in ("fp32", FP32) else FP64
+    _check(L.fdlb_moments_noalloc(prec, Q_R, Q_2, Q_3, nodes, int(n_cells), c_void_p(f_dev_ptr),
+                                  c_void_p(moments_dev_ptr), c_void_p(int(stream))), "fdlb_moments_noalloc")
 
 
 def derivative_matrix(kind, Q):
