@@ -105,7 +105,8 @@ typedef struct fdlb_solver* fdlb_handle;
 
 /* Build one solver instance: quadrature, derivative matrices, equilibrium tables, grid and
  * FM weights on the host (Secs. III.A-C, App. A), then device state.  `cuda_stream` is a
- * cudaStream_t (NULL: legacy default stream).  The state is left at the uniform equilibrium
+ * cudaStream_t; NULL makes the handle create (and later destroy) a private blocking stream, so
+ * that the step can be captured into a CUDA graph.  The state is left at the uniform equilibrium
  * (fdlb_init_uniform with defaults).  Errors: FDLB_EINVAL for a parameter outside the ranges
  * above or C = L/sigma < 3; FDLB_ENOGPU / FDLB_ECUDA / FDLB_ENOMEM from the device. */
 int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out);
@@ -227,6 +228,42 @@ int fdlb_get_stream(fdlb_handle h, void** stream);
  * copies).  fdlb_set_state_raw also recomputes the quadrature sums of the new state. */
 int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device);
 int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device);
+
+/* ----------------------------------------------------------------------- learned warm start
+ * A one-dimensional Fourier neural operator that maps the five parameters of a cylindrical
+ * instance (Kn, eta0, radius ratio R_out/R_in, inner wall speed, wall temperature ratio
+ * T_out/T_in) to its steady moment profiles on n_points equally spaced points of the normalised
+ * radius x = (R - R_L^c)/(R_R^c - R_L^c); the profiles seed a Shakhov-type warm start
+ * (fdlb_init_from_moments).  The paper has no network: this is a library service, trained on the
+ * solver's own steady states.  Architecture: input channels = 5 normalised parameters + x; lift
+ * to `width`; `layers` Fourier layers v <- GELU(v W + b + G R F v) keeping `modes` modes; GELU
+ * hidden layer of `hidden`; 4 outputs.  BF16 weights in every product, FP32 accumulation and
+ * activations, FP32 master weights with Adam (beta1 0.9, beta2 0.999).
+ * Output channels (normalised): o0 = n/n0 - 1, o1 = u_2/0.1, o2 = (T/T_in - 1)/0.1,
+ * o3 = q_R/(0.01 n0 T_in^1.5).  Raw parameters are float[batch][5] in the order above; targets
+ * and outputs float[batch][n_points][4].  The parameter vector is float[n] in the layout
+ * lift W [6][width], lift b; per layer R_re [modes][width][width], R_im, W [width][width], b;
+ * P1 [width][hidden], c1; P2 [hidden][4], c2. */
+typedef struct fdlb_nn* fdlb_nn_handle;
+int fdlb_nn_create(int width, int modes, int layers, int hidden, int n_points, int max_batch, void* cuda_stream,
+                   fdlb_nn_handle* out);
+void fdlb_nn_destroy(fdlb_nn_handle h);
+int fdlb_nn_num_params(fdlb_nn_handle h, int64_t* count);
+int fdlb_nn_set_params(fdlb_nn_handle h, const float* theta_host);   /* also resets Adam */
+/* Seeded initialisation: weight matrices U(-1, 1)/sqrt(fan_in), spectral weights U(0, 1)/width^2,
+ * biases 0 (splitmix64 stream); also resets Adam. */
+int fdlb_nn_init_params(fdlb_nn_handle h, uint64_t seed);
+int fdlb_nn_get_params(fdlb_nn_handle h, float* theta_host);
+int fdlb_nn_forward(fdlb_nn_handle h, const float* raw_params_host, int batch, float* out_host);
+/* MSE loss mean((out - target)^2) and its gradient with respect to every parameter. */
+int fdlb_nn_loss_grad(fdlb_nn_handle h, const float* raw_params_host, const float* targets_host, int batch,
+                      float* loss, float* grad_host);
+/* One Adam step on one batch (forward, backward, update); returns the batch loss. */
+int fdlb_nn_train_step(fdlb_nn_handle h, const float* raw_params_host, const float* targets_host, int batch,
+                       float lr, float* loss);
+/* Predict the profiles of one instance of `solver` from its parameters and seed its state with
+ * them (decode the outputs as above, then fdlb_init_from_moments). */
+int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const float* raw_params_host);
 
 /* ----------------------------------------------------------------------- no device allocation
  * Per-cell moments of populations the caller already holds on the device, for callers that

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlb_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["fdlb.cu", "kernels_aux.cu", "stream_float_0.cu", "stream_float_1.cu", "stream_double_0.cu",
-              "stream_double_1.cu", "noalloc.cu"]
+              "stream_double_1.cu", "noalloc.cu", "nn.cu"]
 CPP_SOURCES = ["setup.cpp"]
 
 

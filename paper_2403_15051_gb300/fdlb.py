@@ -56,6 +56,7 @@ class Info(ctypes.Structure):
 
 _lib = None
 _DP = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_FP = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
 
 def load_library():
@@ -98,6 +99,16 @@ def load_library():
         "fdlb_set_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
         "fdlb_get_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
         "fdlb_moments_noalloc": (c_int, [c_int, c_int, c_int, c_int, _DP, c_int, c_void_p, c_void_p, c_void_p]),
+        "fdlb_nn_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, POINTER(H)]),
+        "fdlb_nn_destroy": (None, [H]),
+        "fdlb_nn_num_params": (c_int, [H, POINTER(c_int64)]),
+        "fdlb_nn_set_params": (c_int, [H, _FP]),
+        "fdlb_nn_get_params": (c_int, [H, _FP]),
+        "fdlb_nn_init_params": (c_int, [H, ctypes.c_uint64]),
+        "fdlb_nn_forward": (c_int, [H, _FP, c_int, _FP]),
+        "fdlb_nn_loss_grad": (c_int, [H, _FP, _FP, c_int, POINTER(ctypes.c_float), c_void_p]),
+        "fdlb_nn_train_step": (c_int, [H, _FP, _FP, c_int, ctypes.c_float, POINTER(ctypes.c_float)]),
+        "fdlb_nn_warm_start": (c_int, [H, H, c_int, _FP]),
         "fdlb_quadrature": (c_int, [c_int, c_int, _DP, _DP]),
         "fdlb_derivative_matrix": (c_int, [c_int, c_int, _DP]),
         "fdlb_physical_parameters": (c_int, [c_double, c_double, c_double, POINTER(c_double), POINTER(c_double),
@@ -365,3 +376,69 @@ def fm_weights(geometry, R_in, R_out, sigma, n_cells, beta=0.0):
     W = np.empty((n_cells, n_cells))
     _check(L.fdlb_fm_weights(geometry, R_in, R_out, sigma, n_cells, beta, W.reshape(-1)), "fdlb_fm_weights")
     return W
+
+
+class WarmStartNet:
+    """The learned warm-start network of the library (fdlb_nn_* in include/fdlb.h)."""
+
+    def __init__(self, width=64, modes=6, layers=4, hidden=128, n_points=256, max_batch=64, stream=None):
+        L = load_library()
+        h = c_void_p()
+        _check(L.fdlb_nn_create(width, modes, layers, hidden, n_points, max_batch,
+                                c_void_p(int(stream) if stream else 0), byref(h)), "fdlb_nn_create")
+        self._h, self._L = h, L
+        self.n_points, self.max_batch = n_points, max_batch
+        cnt = c_int64()
+        _check(L.fdlb_nn_num_params(h, byref(cnt)), "fdlb_nn_num_params")
+        self.n_params = int(cnt.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.fdlb_nn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.n_params
+        _check(self._L.fdlb_nn_set_params(self._h, t), "fdlb_nn_set_params")
+
+    def init_params(self, seed=0):
+        _check(self._L.fdlb_nn_init_params(self._h, int(seed)), "fdlb_nn_init_params")
+
+    def get_params(self):
+        t = np.empty(self.n_params, np.float32)
+        _check(self._L.fdlb_nn_get_params(self._h, t), "fdlb_nn_get_params")
+        return t
+
+    def forward(self, raw):
+        raw = np.ascontiguousarray(raw, dtype=np.float32).reshape(-1, 5)
+        out = np.empty((raw.shape[0], self.n_points, 4), np.float32)
+        _check(self._L.fdlb_nn_forward(self._h, raw, raw.shape[0], out), "fdlb_nn_forward")
+        return out
+
+    def loss_grad(self, raw, target):
+        raw = np.ascontiguousarray(raw, dtype=np.float32).reshape(-1, 5)
+        target = np.ascontiguousarray(target, dtype=np.float32)
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32)
+        _check(self._L.fdlb_nn_loss_grad(self._h, raw, target, raw.shape[0], byref(loss), g.ctypes.data_as(c_void_p)),
+               "fdlb_nn_loss_grad")
+        return float(loss.value), g
+
+    def train_step(self, raw, target, lr):
+        raw = np.ascontiguousarray(raw, dtype=np.float32).reshape(-1, 5)
+        target = np.ascontiguousarray(target, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._L.fdlb_nn_train_step(self._h, raw, target, raw.shape[0], float(lr), byref(loss)),
+               "fdlb_nn_train_step")
+        return float(loss.value)
+
+    def warm_start(self, solver, instance, raw):
+        raw = np.ascontiguousarray(raw, dtype=np.float32).reshape(5)
+        _check(self._L.fdlb_nn_warm_start(self._h, solver._h, instance, raw), "fdlb_nn_warm_start")
