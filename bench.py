@@ -391,6 +391,81 @@ def run_ours(args):
     return 0
 
 
+def run_time_to_steady(args):
+    """Time to steady state (moment residual <= tol) on held-out sweep instances:
+    (A) the plain form - FP64, one instance at a time, uniform start;
+    (B) the batched form - all instances in one FP32 handle, warm-started by the network trained
+    on the solver's own steady states of other sweep instances.
+    Reports wall times, steps and the moment difference of (B) against (A)."""
+    import torch
+
+    from paper_2403_15051_gb300 import build as fbuild
+    from paper_2403_15051_gb300 import fdlb
+    from paper_2403_15051_gb300 import warmstart as wsm
+
+    fbuild.build()
+    torch.cuda.set_device(0)
+
+    def instances(n, seed):
+        ds = wl.batch_instances(lambda kn, e, r: accept_kn(kn, e) and kn >= args.tts_min_kn, n=n, seed=seed,
+                                n_lo=args.tts_cells, n_hi=args.tts_cells)
+        for d in ds:
+            d.update(Q_R=args.tts_q, Q_2=args.tts_q, Q_3=args.tts_q)
+        return ds
+
+    P = 256
+    t0 = time.perf_counter()
+    train_ds = instances(args.tts_train, 1)
+    raw, tg, st_train, _, rc = wsm.steady_states(train_ds, n_points=P, tol=args.tts_tol, max_steps=args.tts_max_steps)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, losses = wsm.train(raw, tg, epochs=args.tts_epochs, batch=32, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    eval_ds = instances(args.tts_eval, 2)
+    # (A) plain FP64, one instance after another, uniform start
+    plain_steps, plain_m = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d in eval_ds:
+        S = fdlb.Solver(dict(d, precision="fp64"))
+        rcA, st, _ = S.run_to_steady(tol=args.tts_tol, max_steps=args.tts_max_steps, check_every=200)
+        plain_steps.append(int(st[0]))
+        plain_m.append(S.moments())
+        S.close()
+    t_plain = time.perf_counter() - t0
+    # (B) batched FP32 with the warm start
+    t0 = time.perf_counter()
+    B = fdlb.Solver([dict(d, precision="fp32") for d in eval_ds])
+    for q, d in enumerate(eval_ds):
+        net.warm_start(B, q, wsm.raw_parameters(d))
+    rcB, stB, _ = B.run_to_steady(tol=args.tts_tol, max_steps=args.tts_max_steps, check_every=200)
+    t_batch = time.perf_counter() - t0
+    # (C) batched FP32 from the uniform start (what the network gains)
+    t0 = time.perf_counter()
+    U = fdlb.Solver([dict(d, precision="fp32") for d in eval_ds])
+    rcC, stC, _ = U.run_to_steady(tol=args.tts_tol, max_steps=args.tts_max_steps, check_every=200)
+    t_uniform_batch = time.perf_counter() - t0
+    err = {"n": 0.0, "u2": 0.0, "T": 0.0}
+    for q, mA in enumerate(plain_m):
+        mB = B.moments(q)
+        n0 = B.info(q)["n0"]
+        err["n"] = max(err["n"], float(np.max(np.abs(mB["n"] - mA["n"]))) / n0)
+        err["u2"] = max(err["u2"], float(np.max(np.abs(mB["u2"] - mA["u2"]))))
+        err["T"] = max(err["T"], float(np.max(np.abs(mB["T"] - mA["T"]))))
+    line = {"metric": "time to steady state (moment residual <= %g)" % args.tts_tol, "unit": "s",
+            "higher_is_better": False, "instances": len(eval_ds), "cells": args.tts_cells,
+            "momenta": 2 * args.tts_q ** 3,
+            "plain_fp64_sequential": {"seconds": t_plain, "steps": plain_steps, "status": rcA},
+            "batched_fp32_warm_start": {"seconds": t_batch, "steps": [int(x) for x in stB], "status": rcB},
+            "batched_fp32_uniform_start": {"seconds": t_uniform_batch, "steps": [int(x) for x in stC], "status": rcC},
+            "speedup_vs_plain": t_plain / t_batch,
+            "moment_difference_vs_plain_fp64": err,
+            "training": {"instances": len(train_ds), "data_seconds": t_data, "train_seconds": t_train,
+                         "final_loss": losses[-1], "first_loss": losses[0], "data_status": rc}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,11 +476,23 @@ def main():
                     choices=["fourier_cyl_1024", "couette_cyl_64", "fourier_sph_2048", "batch_512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")
+    ap.add_argument("--time-to-steady", action="store_true",
+                    help="time-to-steady comparison: plain FP64 sequential vs batched warm-started FP32")
+    ap.add_argument("--tts-train", type=int, default=256)
+    ap.add_argument("--tts-eval", type=int, default=32)
+    ap.add_argument("--tts-cells", type=int, default=64)
+    ap.add_argument("--tts-q", type=int, default=4)
+    ap.add_argument("--tts-tol", type=float, default=1e-8)
+    ap.add_argument("--tts-min-kn", type=float, default=0.01)
+    ap.add_argument("--tts-max-steps", type=int, default=400_000)
+    ap.add_argument("--tts-epochs", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.time_to_steady:
+        return run_time_to_steady(args)
     return run_ours(args)
 
 

@@ -80,7 +80,7 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     const T r0 = T(2) * a - T(7) * b + T(11) * c;
     const T r1 = -b + T(5) * c + T(2) * d;
     const T r2 = T(2) * c + T(5) * d - e;
-    return (a0 * r0 + a1 * r1 + a2 * r2) / (T(6) * (a0 + a1 + a2));
+    return ratio_fast(a0 * r0 + a1 * r1 + a2 * r2, T(6) * (a0 + a1 + a2));
 }
 
 __device__ __forceinline__ double chi_cs(double eta) {

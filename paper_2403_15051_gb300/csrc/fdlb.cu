@@ -24,7 +24,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
-    size_t f[3], sums[3], ca, rec, tab, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err,
+    size_t f[3], sums[3], ca, rec, tab, tabT, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err,
         rprev, rout, total;
 };
 
@@ -53,6 +53,7 @@ struct Solver {
     void* f[3] = {nullptr, nullptr, nullptr};
     double* sums[3] = {nullptr, nullptr, nullptr};
     void* rec = nullptr;
+    void* tabT = nullptr;
     double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *nw = nullptr, *rprev = nullptr,
            *rout = nullptr;
     InstDev* inst_d = nullptr;
@@ -184,6 +185,7 @@ Layout make_layout(const Solver& S) {
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
+    L.tabT = take(S.tab_h.size() * S.tsize);
     L.inst = take(S.n_inst * sizeof(InstDev));
     L.geo = take((size_t)S.total_cells * kGeo * sizeof(double));
     L.gw = take((size_t)S.n_inst * 2 * (S.nR + S.n2 + S.n3) * sizeof(double));
@@ -442,6 +444,7 @@ int launch_closure_buf(Solver& S, int buf) {
     A.band = S.band;
     A.band_lo = S.band_lo;
     A.tab = S.tab;
+    A.tabT = S.tabT;
     A.geo = S.geo;
     A.gw = S.gw;
     A.slices = S.M.slices;
@@ -659,6 +662,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     }
     R.ca = (double*)(R.ws + L.ca);
     R.rec = R.ws + L.rec;
+    R.tabT = R.ws + L.tabT;
     R.tab = (double*)(R.ws + L.tab);
     R.inst_d = (InstDev*)(R.ws + L.inst);
     R.geo = (double*)(R.ws + L.geo);
@@ -676,6 +680,11 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
     // tables, instances, geometry, walls, FM band
     FDLB_CUDA(cudaMemcpyAsync(R.tab, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    std::vector<float> tabf(R.tab_h.begin(), R.tab_h.end());
+    if (R.precision == FDLB_FP32)
+        FDLB_CUDA(cudaMemcpyAsync(R.tabT, tabf.data(), tabf.size() * 4, cudaMemcpyHostToDevice, R.stream));
+    else
+        FDLB_CUDA(cudaMemcpyAsync(R.tabT, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
     R.inst_h.resize(n);
     std::vector<double> geo((size_t)R.total_cells * kGeo), gw((size_t)n * 2 * (R.nR + R.n2 + R.n3));
     std::vector<int> blo(R.total_cells, 0);

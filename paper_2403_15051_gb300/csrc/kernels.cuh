@@ -85,6 +85,7 @@ struct ClosureArgs {
     const void* band;              // FM band values (T)
     const int* band_lo;            // per global cell
     const double* tab;
+    const void* tabT;              // the same tables in the populations' precision
     const double* geo;
     const double* gw;
     int slices;

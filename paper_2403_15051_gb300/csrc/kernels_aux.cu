@@ -77,7 +77,7 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
 // precision, [20 scalars | g_R | g_2 | g_3].
 __host__ __device__ inline size_t closure_smem_bytes(int max_cells, int max_union, int tsize) {
     const size_t CH = (size_t)max_cells + 4;
-    return (CH * kSums + 9 * CH + (size_t)max_cells * 4 * kMaxE + 32) * sizeof(double) + (size_t)max_union * tsize + 16;
+    return (CH * kSums + 9 * CH + 32) * sizeof(double) + ((size_t)max_cells * 4 * kMaxE + max_union) * tsize + 16;
 }
 
 template <typename T>
@@ -87,9 +87,10 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
     const int CH = A.max_cells + 4;
     double* ssum = reinterpret_cast<double*>(smem_raw);  // [CH][13] raw sums of the cells in reach
     double* cb = ssum + CH * kSums;                       // [9][CH]: n u0 u1 u2 T chi phi1 phi2 nbar
-    double* ec = cb + 9 * CH;                             // [max_cells][4][kMaxE]
-    double* red = ec + (size_t)A.max_cells * 4 * kMaxE;   // [32]
-    T* nbuf = reinterpret_cast<T*>(red + 32);
+    double* red = cb + 9 * CH;                            // [32]
+    T* ec = reinterpret_cast<T*>(red + 32);               // [max_cells][4][kMaxE]
+    T* nbuf = ec + (size_t)A.max_cells * 4 * kMaxE;
+    const T* tabT = reinterpret_cast<const T*>(A.tabT);   // the tables in the populations' precision
     const T* band = reinterpret_cast<const T*>(A.band);
     const T* fin_all = reinterpret_cast<const T*>(A.f_in);
     T* rec_all = reinterpret_cast<T*>(A.rec);
@@ -131,11 +132,11 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
         for (int t = tid; t < nh; t += NT) {
             const int c = h0 + t;
             const double* s = ssum + t * kSums;
-            const double n = s[0];
-            const double u0 = s[1] / n, u1 = s[2] / n, u2 = s[3] / n;
+            const double n = s[0], in = 1.0 / n;
+            const double u0 = s[1] * in, u1 = s[2] * in, u2 = s[3] * in;
             const double tr = s[4] + s[5] + s[6];
             const double uu = u0 * u0 + u1 * u1 + u2 * u2;
-            const double Tc = (tr - n * uu) / (3.0 * n);
+            const double Tc = (tr - n * uu) * in * (1.0 / 3.0);
             cb[0 * CH + t] = n;
             cb[1 * CH + t] = u0;
             cb[2 * CH + t] = u1;
@@ -222,48 +223,55 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
                     d0 *= sc;
                     d1 *= sc;
                     d2 *= sc;
-                    const double br = I.bfac * n, x = br * chi;
-                    const double pi = 3.14159265358979323846;
-                    const double mu = 5.0 / (16.0 * I.sigma * I.sigma) * sqrt(Tc / pi) *
-                                      (1.0 / chi + 0.8 * br + 4.0 / 25.0 * (1.0 + 12.0 / pi) * br * br * chi);
-                    const double Pr = 2.0 / 3.0 * (1.0 + 0.8 * x + 4.0 / 25.0 * (1.0 + 12.0 / pi) * x * x) /
-                                      (1.0 + 1.2 * x + 9.0 / 25.0 * (1.0 + 32.0 / (9.0 * pi)) * x * x);
-                    const double tau = mu / (n * Tc);
-                    double S11, S22, S01, S02, div;
+                    // transport, strain and Shakhov coefficient in the populations' precision
+                    // (they are stored in it); FP64 above only for the gradients of logarithms
+                    using C = T;
+                    const C cn = (C)n, cT = (C)Tc, cchi = (C)chi, iR = (C)(1.0 / R);
+                    const C cu0 = (C)u0, cu1 = (C)u1, cu2 = (C)u2, sg = (C)I.sigma;
+                    const C br = (C)I.bfac * cn, x = br * cchi;
+                    const C pi = C(3.14159265358979323846);
+                    const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
+                                 (C(1) / cchi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
+                    const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
+                                 (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
+                    const C itau = cn * cT / mu;
+                    C S11, S22, S01, S02, div;
+                    const C cd0 = (C)d0, cd1 = (C)d1, cd2 = (C)d2;
                     if (I.geometry == 0) {
-                        S11 = u0 / R;
-                        S22 = 0.0;
-                        S01 = 0.5 * (d1 - u1 / R);
-                        S02 = 0.5 * d2;
-                        div = d0 + u0 / R;
+                        S11 = cu0 * iR;
+                        S22 = C(0);
+                        S01 = C(0.5) * (cd1 - cu1 * iR);
+                        S02 = C(0.5) * cd2;
+                        div = cd0 + cu0 * iR;
                     } else {
-                        S11 = S22 = u0 / R;
-                        S01 = 0.5 * (d1 - u1 / R);
-                        S02 = 0.5 * (d2 - u2 / R);
-                        div = d0 + 2.0 * u0 / R;
+                        S11 = S22 = cu0 * iR;
+                        S01 = C(0.5) * (cd1 - cu1 * iR);
+                        S02 = C(0.5) * (cd2 - cu2 * iR);
+                        div = cd0 + C(2) * cu0 * iR;
                     }
                     const double* rc = ca + (long long)c * kCA;
                     T* ct = rec + (long long)c * rs;
-                    ct[0] = (T)n;
-                    ct[1] = (T)u0;
-                    ct[2] = (T)u1;
-                    ct[3] = (T)u2;
-                    ct[4] = (T)(1.0 / Tc);
-                    ct[5] = (T)(1.0 / tau);
-                    ct[6] = (T)((1.0 - Pr) / (n * Tc * Tc));
+                    const C iT = C(1) / cT;
+                    ct[0] = cn;
+                    ct[1] = cu0;
+                    ct[2] = cu1;
+                    ct[3] = cu2;
+                    ct[4] = iT;
+                    ct[5] = itau;
+                    ct[6] = (C(1) - Pr) * iT * iT / cn;
                     ct[7] = (T)rc[5];
                     ct[8] = (T)rc[6];
                     ct[9] = (T)rc[7];
-                    ct[10] = (T)x;
+                    ct[10] = x;
                     ct[11] = (T)X;
                     ct[12] = (T)Y;
-                    ct[13] = (T)d0;
-                    ct[14] = (T)S11;
-                    ct[15] = (T)S22;
-                    ct[16] = (T)S01;
-                    ct[17] = (T)S02;
-                    ct[18] = (T)0.0;
-                    ct[19] = (T)div;
+                    ct[13] = cd0;
+                    ct[14] = S11;
+                    ct[15] = S22;
+                    ct[16] = S01;
+                    ct[17] = S02;
+                    ct[18] = T(0);
+                    ct[19] = div;
                     ca[(long long)c * kCA + 9] = chi;
                     ca[(long long)c * kCA + 10] = cb[8 * CH + lt];
                 } else if (job <= 2) {
@@ -271,32 +279,35 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
                     //   e_0 = h_0 (1 + erf(v/sqrt(2T)))/2,
                     //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
                     //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)]
-                    double* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
-                    const double* ha = tab + M.o_ha;
-                    const double* hb = tab + M.o_hb;
-                    const double* h0t = tab + M.o_h0;
-                    for (int l = 0; l < kMaxE; ++l) e[l] = 0.0;
-                    const double v = job == 1 ? u0 : -u0;
-                    const double G0 = exp(-v * v / (2.0 * Tc)) / sqrt(6.283185307179586477 * Tc);
-                    e[0] = h0t[0] * 0.5 * (1.0 + erf(v / sqrt(2.0 * Tc)));
-                    double run = 0.0;
+                    // (in the populations' precision)
+                    using C = T;
+                    T* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
+                    const T* ha = tabT + M.o_ha;
+                    const T* hb = tabT + M.o_hb;
+                    const T* h0t = tabT + M.o_h0;
+                    for (int l = 0; l < kMaxE; ++l) e[l] = C(0);
+                    const C cT = (C)Tc, v = job == 1 ? (C)u0 : -(C)u0;
+                    const C G0 = exp(-v * v / (C(2) * cT)) / sqrt(C(6.283185307179586477) * cT);
+                    e[0] = h0t[0] * C(0.5) * (C(1) + erf(v / sqrt(C(2) * cT)));
+                    C run = C(0);
                     for (int l = 0; l < M.NR; ++l) {
-                        const double em1 = l ? e[l - 1] : 0.0;
-                        const double bl = l ? hb[l] : 0.0;
-                        const double val = (v - ha[l]) * e[l] + (Tc - 1.0) * bl * em1 +
-                                           Tc * h0t[l] * (G0 - run * 0.39894228040143267794);
+                        const C em1 = l ? e[l - 1] : C(0);
+                        const C bl = l ? hb[l] : C(0);
+                        const C val = (v - ha[l]) * e[l] + (cT - C(1)) * bl * em1 +
+                                      cT * h0t[l] * (G0 - run * C(0.39894228040143267794));
                         e[l + 1] = val / hb[l + 1];
                         run += h0t[l] * e[l];
                     }
                 } else {
                     // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                    double* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
-                    for (int l = 0; l < kMaxE; ++l) e[l] = 0.0;
-                    const double u = job == 3 ? u1 : u2;
+                    using C = T;
+                    T* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
+                    for (int l = 0; l < kMaxE; ++l) e[l] = C(0);
+                    const C u = job == 3 ? (C)u1 : (C)u2, cT = (C)Tc;
                     const int Nax = job == 3 ? M.N2 : M.N3;
-                    e[0] = 1.0;
+                    e[0] = C(1);
                     if (Nax >= 1) e[1] = u;
-                    for (int l = 1; l < Nax; ++l) e[l + 1] = u * e[l] + l * (Tc - 1.0) * e[l - 1];
+                    for (int l = 1; l < Nax; ++l) e[l + 1] = u * e[l] + C(l) * (cT - C(1)) * e[l - 1];
                 }
             }
         }
@@ -305,17 +316,17 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
         const int ng = nR + n2 + n3;
         for (int e = tid; e < cnt * ng; e += NT) {
             const int t = e / ng, k = e % ng;
-            const double* e4 = ec + (long long)t * 4 * kMaxE;
+            const T* e4 = ec + (long long)t * 4 * kMaxE;
             T acc = T(0);
             if (k < nR) {
-                const double* eh = e4 + (k >= QR ? kMaxE : 0);
-                for (int l = 0; l <= M.NR; ++l) acc += (T)tab[M.o_GR + k * kMaxE + l] * (T)eh[l];
+                const T* eh = e4 + (k >= QR ? kMaxE : 0);
+                for (int l = 0; l <= M.NR; ++l) acc += tabT[M.o_GR + k * kMaxE + l] * eh[l];
             } else if (k < nR + n2) {
                 const int j = k - nR;
-                for (int l = 0; l <= M.N2; ++l) acc += (T)tab[M.o_G2 + j * kMaxE + l] * (T)e4[2 * kMaxE + l];
+                for (int l = 0; l <= M.N2; ++l) acc += tabT[M.o_G2 + j * kMaxE + l] * e4[2 * kMaxE + l];
             } else {
                 const int j = k - nR - n2;
-                for (int l = 0; l <= M.N3; ++l) acc += (T)tab[M.o_G3 + j * kMaxE + l] * (T)e4[3 * kMaxE + l];
+                for (int l = 0; l <= M.N3; ++l) acc += tabT[M.o_G3 + j * kMaxE + l] * e4[3 * kMaxE + l];
             }
             rec[(long long)(c0 + t) * rs + kCellScalars + k] = acc;
         }

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     T* cellT = reinterpret_cast<T*>(smem_raw + P.cell);
     const int cstride = kCellScalars + nR + n2 + n3;
     T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
-    double* red = reinterpret_cast<double*>(smem_raw + P.red);
+    T* red = reinterpret_cast<T*>(smem_raw + P.red);  // warp partials of the raw sums
     const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
     T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
@@ -240,9 +240,11 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                     const T p2v = sp_2[j], p3v = sp_3[k];
                     const T* colR = fc + (kk * nR) * n2 + j;
                     T KRf = T(0);
+#pragma unroll 8
                     for (int a = 0; a < nR; ++a) KRf += sKR[i * nR + a] * colR[a * n2];
                     const T* row2 = fc + (kk * nR + i) * n2;
                     T K2f = T(0);
+#pragma unroll 8
                     for (int a = 0; a < n2; ++a) K2f += sK2[j * n2 + a] * row2[a];
                     T frc;
                     if (GEOM == 0) {
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                     } else {
                         const T* col3 = fc + i * n2 + j;
                         T K3f = T(0);
+#pragma unroll 4
                         for (int a = 0; a < n3; ++a) K3f += sK3[k * n3 + a] * col3[a * nR * n2];
                         frc = kf * ((p2v * p2v + p3v * p3v) * KRf - pr * (K2f + K3f));
                     }
@@ -292,16 +295,16 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             // ---- 5. raw sums of the new populations: per-thread partial and warp tree in the
             // populations' precision, FP64 sum over the warps in a fixed order
             if (A.mode == 0) {
-                double* rb = red + (cl & 1) * nwarps * kSums;
+                T* rb = red + (cl & 1) * nwarps * kSums;
 #pragma unroll
                 for (int q = 0; q < kSums; ++q) {
                     const T s = warp_sum(acc[q]);  // warp tree in the populations' precision
-                    if (lane == 0) rb[warp * kSums + q] = (double)s;
+                    if (lane == 0) rb[warp * kSums + q] = s;
                 }
                 __syncthreads();
                 if (tid < kSums) {
-                    double s = 0.0;
-                    for (int ww = 0; ww < nwarps; ++ww) s += rb[ww * kSums + tid];
+                    double s = 0.0;  // FP64 sum over the warps, fixed order
+                    for (int ww = 0; ww < nwarps; ++ww) s += (double)rb[ww * kSums + tid];
                     A.sums_out[((long long)(I.cell_off + c) * M.slices + sl) * kSums + tid] = s;
                 }
             }
