@@ -190,10 +190,12 @@ int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double
 
 int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out);
 
-/* Checkpoint: step count, parameters and populations (native precision) of all instances. */
+/* Checkpoint: step count, parameters, populations (native precision) and their FP64 raw
+ * moment sums of all instances; restoring it continues the run bit for bit. */
 int fdlb_save(fdlb_handle h, const char* path);
 /* Restore a checkpoint written by fdlb_save for a handle created with the same parameters;
- * FDLB_EINVAL if they differ, FDLB_EIO on a read error. */
+ * FDLB_EINVAL if they differ, FDLB_EIO on a read error.  Under another momentum slicing
+ * (fdlb_set_tiling) the sums are recomputed instead: the same moments up to rounding order. */
 int fdlb_load(fdlb_handle h, const char* path);
 
 const char* fdlb_error_string(int code);

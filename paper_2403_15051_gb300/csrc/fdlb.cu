@@ -64,7 +64,8 @@ struct Solver {
     std::vector<double> tab_h;
     MomSet M{};
     // tiling of the stream kernel
-    int B = 16, KS = 1, threads = 0, mpt = 1;
+    int B = 16, KS = 1, threads = 0;
+    StreamCfg scfg{1, 4, 0};
     size_t smem_stream = 0;
     int use_bulk = 0;
     int closure_cells = 4, closure_threads = 256;  // one warp per cell in reach (4 + 4 halo)
@@ -353,7 +354,7 @@ int upload_items(Solver& S) {
 int launch_moments_all(Solver& S, int buf);
 
 int configure_tiling(Solver& S, int B, int KS, int threads) {
-    if (B > 0) S.B = std::max(4, B);
+    if (B > 0) S.B = std::max(2, B);
     if (KS > 0) S.KS = KS;
     if (S.geometry == FDLB_SPH) S.KS = S.n3;  // every axis is coupled by the force term
     if (S.KS < 1 || S.n3 % S.KS) S.KS = S.n3;
@@ -368,21 +369,39 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     S.M.KS = S.KS;
     S.M.slices = S.n3 / S.KS;
     S.M.Ms = Ms;
-    int mpt = 1;
+    // vectors of VW consecutive j momenta; compile-time shapes for the benchmark workloads
+    StreamCfg cfg{};
+    if (S.tsize == 4)
+        cfg.vw = S.n2 % 4 == 0 ? 4 : (S.n2 % 2 == 0 ? 2 : 1);
+    else
+        cfg.vw = S.n2 % 2 == 0 ? 2 : 1;
+    cfg.spec = ((S.geometry == FDLB_CYL && S.nR == 16 && S.n2 == 8 && S.n3 == 8) ||
+                (S.geometry == FDLB_SPH && S.nR == 24 && S.n2 == 12 && S.n3 == 12)) &&
+               cfg.vw == (S.tsize == 4 ? 4 : 2);
+    const int Vs = Ms / cfg.vw;
     const int cap = threads > 0 ? threads : 256;
-    while (mpt < 8 && (Ms + mpt - 1) / mpt > cap) mpt *= 2;
-    int nt = ((Ms + mpt - 1) / mpt + 31) / 32 * 32;
-    if (nt > 512) return FDLB_EINVAL;
-    S.mpt = mpt;
+    int nt = 0;
+    if (cfg.spec) {
+        // vectors per thread fixed by the instantiation: the smaller count whose block fits the cap
+        const int na = S.geometry == FDLB_CYL ? 1 : 2, nb = 2 * na;
+        cfg.nv = ((Vs + na - 1) / na + 31) / 32 * 32 <= std::max(cap, 32) ? na : nb;
+        nt = ((Vs + cfg.nv - 1) / cfg.nv + 31) / 32 * 32;
+    } else {
+        cfg.nv = cfg.vw == 4 ? 2 : 4;  // the most a thread holds; fewer when the block has room
+        nt = (std::min(Vs, cap) + 31) / 32 * 32;
+        if ((long long)nt * cfg.nv < Vs) nt = ((Vs + cfg.nv - 1) / cfg.nv + 31) / 32 * 32;
+    }
+    if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
+    S.scfg = cfg;
     S.threads = nt;
     // shrink the tile until it fits in shared memory
     for (;;) {
         StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize);
-        if ((size_t)P.total <= S.smem_optin || S.B <= 4) {
+        if ((size_t)P.total <= S.smem_optin || S.B <= 2) {
             S.smem_stream = P.total;
             break;
         }
-        S.B = std::max(4, S.B / 2);
+        S.B = std::max(2, S.B / 2);
     }
     if (S.smem_stream > S.smem_optin) return FDLB_EINVAL;
     S.use_bulk = ((size_t)Ms * S.tsize % 16 == 0 && (size_t)S.Np * S.tsize % 16 == 0) ? 1 : 0;
@@ -510,11 +529,11 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
-        e = g == FDLB_CYL ? launch_stream_float_0(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
-                          : launch_stream_float_1(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
+        e = g == FDLB_CYL ? launch_stream_float_0(S.scfg, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
+                          : launch_stream_float_1(S.scfg, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
     else
-        e = g == FDLB_CYL ? launch_stream_double_0(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
-                          : launch_stream_double_1(S.mpt, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
+        e = g == FDLB_CYL ? launch_stream_double_0(S.scfg, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream)
+                          : launch_stream_double_1(S.scfg, A, S.M, S.grid_stream, S.threads, S.smem_stream, S.stream);
     S.launches++;
     return cuda_status(e);
 }
@@ -1022,7 +1041,7 @@ int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) {
     return FDLB_OK;
 }
 
-static const char kMagic[8] = {'F', 'D', 'L', 'B', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'F', 'D', 'L', 'B', 'C', 'K', 'P', '2'};
 
 int fdlb_save(fdlb_handle h, const char* path) {
     Solver* S = SOL(h);
@@ -1044,6 +1063,19 @@ int fdlb_save(fdlb_handle h, const char* path) {
             return FDLB_ECUDA;
         }
         ok = ok && std::fwrite(buf.data(), 1, bytes, fp) == bytes;
+        // the raw sums of the state as the stage epilogue computed them, so that a restart
+        // continues bit for bit (a recomputation sums in another order)
+        const int32_t slices = S->M.slices;
+        const size_t sbytes = (size_t)S->setup[q].p.n_cells * slices * fdlb::kSums * sizeof(double);
+        std::vector<unsigned char> sb(sbytes);
+        if (cudaMemcpyAsync(sb.data(), S->sums[0] + (size_t)S->cell_off[q] * slices * fdlb::kSums, sbytes,
+                            cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+            cudaStreamSynchronize(S->stream) != cudaSuccess) {
+            std::fclose(fp);
+            return FDLB_ECUDA;
+        }
+        ok = ok && std::fwrite(&slices, sizeof(slices), 1, fp) == 1;
+        ok = ok && std::fwrite(sb.data(), 1, sbytes, fp) == sbytes;
     }
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? FDLB_OK : FDLB_EIO;
@@ -1065,6 +1097,7 @@ int fdlb_load(fdlb_handle h, const char* path) {
         std::fclose(fp);
         return FDLB_EINVAL;
     }
+    bool recompute = false;
     for (int q = 0; q < S->n_inst && !rc; ++q) {
         fdlb_params p;
         int64_t st;
@@ -1090,11 +1123,30 @@ int fdlb_load(fdlb_handle h, const char* path) {
             break;
         }
         S->inst_steps[q] = st;
+        int32_t slices = 0;
+        if (std::fread(&slices, sizeof(slices), 1, fp) != 1 || slices < 1 || slices > S->n3) {
+            rc = FDLB_EIO;
+            break;
+        }
+        const size_t sbytes = (size_t)mine.n_cells * slices * fdlb::kSums * sizeof(double);
+        std::vector<unsigned char> sb(sbytes);
+        if (std::fread(sb.data(), 1, sbytes, fp) != sbytes) {
+            rc = FDLB_EIO;
+            break;
+        }
+        if (slices != S->M.slices) {
+            recompute = true;  // saved under another momentum slicing
+        } else if (cudaMemcpyAsync(S->sums[0] + (size_t)S->cell_off[q] * slices * fdlb::kSums, sb.data(), sbytes,
+                                   cudaMemcpyHostToDevice, S->stream) != cudaSuccess ||
+                   cudaStreamSynchronize(S->stream) != cudaSuccess) {
+            rc = FDLB_ECUDA;
+            break;
+        }
     }
     std::fclose(fp);
     if (rc) return rc;
     S->prev_valid = false;
-    return fdlb::launch_moments_all(*S, 0);
+    return recompute ? fdlb::launch_moments_all(*S, 0) : FDLB_OK;
 }
 
 const char* fdlb_error_string(int code) {

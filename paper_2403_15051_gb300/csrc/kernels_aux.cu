@@ -318,17 +318,21 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
             const int t = e / ng, k = e % ng;
             const T* e4 = ec + (long long)t * 4 * kMaxE;
             T acc = T(0);
+            int dst;
             if (k < nR) {
                 const T* eh = e4 + (k >= QR ? kMaxE : 0);
                 for (int l = 0; l <= M.NR; ++l) acc += tabT[M.o_GR + k * kMaxE + l] * eh[l];
+                dst = rec_off_gR(n2) + k;
             } else if (k < nR + n2) {
                 const int j = k - nR;
                 for (int l = 0; l <= M.N2; ++l) acc += tabT[M.o_G2 + j * kMaxE + l] * e4[2 * kMaxE + l];
+                dst = rec_off_g2() + j;
             } else {
                 const int j = k - nR - n2;
                 for (int l = 0; l <= M.N3; ++l) acc += tabT[M.o_G3 + j * kMaxE + l] * e4[3 * kMaxE + l];
+                dst = rec_off_g3(nR, n2) + j;
             }
-            rec[(long long)(c0 + t) * rs + kCellScalars + k] = acc;
+            rec[(long long)(c0 + t) * rs + dst] = acc;
         }
         // ---- 6. wall densities (diffuse walls): n_w = sum_out |p_R| w vhat_wall / sum_in |p_R| g_wall
         const T* fin = fin_all + I.f_off;

@@ -9,31 +9,45 @@ namespace fdlb {
 
 constexpr int kCellScalars = 20;   // per-cell collision scalars kept in shared memory
 
+// Per-cell collision record (populations' precision): kCellScalars scalars, then g_2, g_R, g_3
+// (g_2 first so that a vector of consecutive j starts on a vector boundary); padded to 4 entries.
+inline __host__ __device__ int record_stride(int nR, int n2, int n3) { return (kCellScalars + nR + n2 + n3 + 3) / 4 * 4; }
+inline __host__ __device__ int rec_off_g2() { return kCellScalars; }
+inline __host__ __device__ int rec_off_gR(int n2) { return kCellScalars + n2; }
+inline __host__ __device__ int rec_off_g3(int nR, int n2) { return kCellScalars + n2 + nR; }
+
 struct StreamSmem {
-    int fs, tabs, cell, geo, red, ecoef, misc, total;
+    int fs, rec, tabs, geo, red, total;
 };
 
-// Shared-memory plan of the stream kernel (byte offsets), shared with the host.
+// Shared-memory plan of the stream kernel (byte offsets), shared with the host: the staged rows
+// of cells c0-3 .. c0+B+2, the tile's collision records, the tables (radial nodes and weights,
+// K^h with row stride nR+1, K_2 in the vector-swizzled order, K_3 with row stride n3+1, wall
+// Maxwellians), the cell geometry and the per-warp partial sums.
 __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize) {
     auto al = [](long long x) { return (int)((x + 15) & ~15LL); };
     StreamSmem s;
     int off = 16;  // mbarrier
     s.fs = off;
-    off += al((long long)(B + 6) * Ms * tsize);  // rows of cells c0-3 .. c0+B+2
+    off += al((long long)(B + 6) * Ms * tsize);
+    s.rec = off;
+    off += al((long long)B * record_stride(nR, n2, n3) * tsize);
     s.tabs = off;
-    off += al((long long)(2 * (nR + n2 + n3) + nR * nR + n2 * n2 + n3 * n3 + 2 * (nR + n2 + n3)) * tsize);
-    s.cell = off;
-    off += al((long long)B * (kCellScalars + nR + n2 + n3) * tsize);
+    off += al((long long)(2 * (nR + n2 + n3) + nR * (nR + 1) + n2 * n2 + n3 * (n3 + 1) + 2 * (nR + n2 + n3)) * tsize);
     s.geo = off;
     off += al((long long)B * 3 * tsize);
     s.red = off;
-    off += al((long long)2 * nwarps * kSums * 8);
-    s.ecoef = off;
-    s.misc = off;
+    off += al((long long)B * nwarps * 16 * tsize);
     s.total = off;
     return s;
 }
 
+// Launch shape of the stream kernel: VW consecutive j momenta per vector, at most NV vectors
+// per thread, and whether the compile-time shape (cylinder 16 x 8 x 8, sphere 24 x 12 x 12)
+// is used.
+struct StreamCfg {
+    int vw, nv, spec;
+};
 
 template <typename T>
 void launch_moments(const T* f, double* sums, const int4* items, const int* n_items, int grid, const InstDev* inst,
@@ -44,12 +58,10 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
 
 size_t closure_smem(int max_cells, int max_union, int tsize);
 
-// Per-cell collision record: kCellScalars scalars then g_R, g_2, g_3; padded to 4 entries.
-inline int record_stride(int nR, int n2, int n3) { return (kCellScalars + nR + n2 + n3 + 3) / 4 * 4; }
 
 #define FDLB_STREAM_DECL(T, G)                                                                             \
-    cudaError_t launch_stream_##T##_##G(int mpt, const StageArgs& A, const MomSet& M, int grid, int threads, \
-                                        size_t smem, cudaStream_t s);
+    cudaError_t launch_stream_##T##_##G(const StreamCfg& cfg, const StageArgs& A, const MomSet& M, int grid, \
+                                        int threads, size_t smem, cudaStream_t s);
 FDLB_STREAM_DECL(float, 0)
 FDLB_STREAM_DECL(float, 1)
 FDLB_STREAM_DECL(double, 0)

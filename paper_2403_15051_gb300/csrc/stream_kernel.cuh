@@ -1,17 +1,22 @@
 // The fused stage kernel: one SSP-RK3 stage for a tile of radial cells x one momentum slice.
 //
 // Per work item (instance, first cell c0, cells Be, slice sl):
-//  1. the TMA engine copies the populations of cells c0-3 .. c0+Be+2 (this slice) into shared
-//     memory (one bulk copy when the slice is the whole cell, else one per cell);
-//  2. meanwhile the block loads the per-cell collision records written by the closure kernel
-//     (J1 gradients, tau, Pr, strain, equilibrium vectors) and the wall densities;
+//  1. the TMA engine copies the populations of cells c0-3 .. c0+Be+2 (this slice) and the
+//     tile's collision records (written by the closure kernel) into shared memory;
+//  2. meanwhile the block loads the cell geometry and the wall densities;
 //  3. ghost rows at a wall: incoming directions carry n_w times the wall Maxwellian, outgoing
 //     directions the cubic extrapolation of the four cells next to the wall;
 //  4. per population: WENO5 face values of f/w upwinded by sign(p_R), conservative advection
 //     with the face areas and cell volume (Sec. II.B/C), the curvature force with the K matrices
 //     (Sec. III.B), the Shakhov + J1 collision (Eqs. j0, j1), the RK combination and the store;
-//  5. the 13 raw sums of the new populations per cell (warp tree in the populations' precision,
-//     FP64 across warps).
+//  5. the 13 raw sums of the new populations per cell: per-thread partials, a transposing warp
+//     reduction in the populations' precision, FP64 across the warps at the end of the item.
+//
+// Thread mapping: a "vector" is VW momenta with the same (k, i) and consecutive j, which are
+// contiguous in the [k][i][j] layout.  A thread owns up to NV vectors for the whole kernel, so
+// every shared-memory access is a VW-wide load: the five WENO rows, the column of the K^h
+// contraction (shared by the VW momenta), the row of the K_2 contraction.  All momenta of a
+// vector share p_R and hence the upwind direction.
 #pragma once
 
 #include "device_common.cuh"
@@ -27,32 +32,122 @@ __device__ __forceinline__ void wall_ghosts(T f0, T f1, T f2, T f3, T& g1, T& g2
     g2 = T(10) * f0 - T(20) * f1 + T(15) * f2 - T(4) * f3;
 }
 
-template <typename T, int GEOM, int MPT>
+// VW consecutive elements (16-byte aligned for VW * sizeof(T) >= 16; 8-byte for float2).
+template <typename T, int VW>
+__device__ __forceinline__ void ld_vec(const T* p, T (&o)[VW]) {
+    if constexpr (sizeof(T) == 4 && VW == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 2) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        o[0] = x.x; o[1] = x.y;
+    } else if constexpr (sizeof(T) == 8 && VW >= 2) {
+#pragma unroll
+        for (int h = 0; h < VW / 2; ++h) {
+            const double2 x = *reinterpret_cast<const double2*>(p + 2 * h);
+            o[2 * h] = x.x; o[2 * h + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) o[e] = p[e];
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void ldg_vec(const T* p, T (&o)[VW]) {
+    if constexpr (sizeof(T) == 4 && VW == 4) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 2) {
+        const float2 x = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = x.x; o[1] = x.y;
+    } else if constexpr (sizeof(T) == 8 && VW >= 2) {
+#pragma unroll
+        for (int h = 0; h < VW / 2; ++h) {
+            const double2 x = __ldg(reinterpret_cast<const double2*>(p + 2 * h));
+            o[2 * h] = x.x; o[2 * h + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) o[e] = __ldg(p + e);
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
+    if constexpr (sizeof(T) == 4 && VW == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 4 && VW == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    } else if constexpr (sizeof(T) == 8 && VW >= 2) {
+#pragma unroll
+        for (int h = 0; h < VW / 2; ++h) *reinterpret_cast<double2*>(p + 2 * h) = make_double2(o[2 * h], o[2 * h + 1]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) p[e] = o[e];
+    }
+}
+
+// Sums of 16 values over the 32 lanes of a warp, transposed: at every level of the butterfly a
+// lane keeps half of its values and sends the other half, so the warp needs 16 shuffles instead
+// of 16 x 5.  Lane L returns the sum of value (L >> 1).  Fixed order: deterministic.
+template <typename T>
+__device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
+    T w8[8], w4[4], w2[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const T send = b4 ? v[t] : v[t + 8], keep = b4 ? v[t + 8] : v[t];
+        w8[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const T send = b3 ? w8[t] : w8[t + 4], keep = b3 ? w8[t + 4] : w8[t];
+        w4[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const T send = b2 ? w4[t] : w4[t + 2], keep = b2 ? w4[t + 2] : w4[t];
+        w2[t] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const T send = b1 ? w2[0] : w2[1], keep = b1 ? w2[1] : w2[0];
+    const T w1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return w1 + __shfl_xor_sync(0xffffffffu, w1, 1);
+}
+
+// NR_, N2_, N3_: compile-time axis sizes (0: taken from M at run time).
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
 __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NT = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Ms = M.Ms, Np = M.Np;
+    const int nR = NR_ ? NR_ : M.nR, n2 = N2_ ? N2_ : M.n2, n3 = N3_ ? N3_ : M.n3;
+    const int KS = GEOM == 1 ? n3 : M.KS;  // the sphere couples every axis: one slice
+    const int Ms = nR * n2 * KS, Np = nR * n2 * n3;
+    const int n2v = n2 / VW;               // vectors per (k, i) row
+    const int Vs = Ms / VW;                // vectors per slice
+    const int rs = record_stride(nR, n2, n3);
     const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T));
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);  // rows: cells c0-3 .. c0+B+2
-    T* sp_R = reinterpret_cast<T*>(smem_raw + P.tabs);
+    T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);
+    T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);  // K_2 swizzled (vector loads: first, aligned):
+                                                       // [e][b / VW][j / VW][b % VW], j = (j / VW) VW + e
+    T* sKR = sK2 + n2 * n2;        // K^h, row stride nR + 1
+    T* sK3 = sKR + nR * (nR + 1);  // K_3, row stride n3 + 1
+    T* sp_R = sK3 + n3 * (n3 + 1);
     T* sp_2 = sp_R + nR;
     T* sp_3 = sp_2 + n2;
     T* sw_R = sp_3 + n3;
     T* sw_2 = sw_R + nR;
     T* sw_3 = sw_2 + n2;
-    T* sKR = sw_3 + n3;
-    T* sK2 = sKR + nR * nR;
-    T* sK3 = sK2 + n2 * n2;
-    T* sgw = sK3 + n3 * n3;  // [2][nR + n2 + n3]: inner and outer wall Maxwellian per axis
-    T* cellT = reinterpret_cast<T*>(smem_raw + P.cell);
-    const int cstride = kCellScalars + nR + n2 + n3;
+    T* sgw = sw_3 + n3;            // [2][nR + n2 + n3]: inner and outer wall Maxwellian per axis
     T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
-    T* red = reinterpret_cast<T*>(smem_raw + P.red);  // warp partials of the raw sums
+    T* red = reinterpret_cast<T*>(smem_raw + P.red);  // [cell][warp][16] warp sums
     const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
     T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
+    const T* __restrict__ rec_all = reinterpret_cast<const T*>(A.rec);
     const double* __restrict__ tab = A.tab;
     const int gwstride = nR + n2 + n3;
 
@@ -72,9 +167,13 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         sp_3[e] = (T)tab[M.o_p3 + e];
         sw_3[e] = (T)tab[M.o_w3 + e];
     }
-    for (int e = tid; e < nR * nR; e += NT) sKR[e] = (T)tab[M.o_KR + e];
-    for (int e = tid; e < n2 * n2; e += NT) sK2[e] = (T)tab[M.o_K2 + e];
-    for (int e = tid; e < n3 * n3; e += NT) sK3[e] = (T)tab[M.o_K3 + e];
+    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * (nR + 1) + e % nR] = (T)tab[M.o_KR + e];
+    for (int e = tid; e < n2 * n2; e += NT) {
+        const int j = e / n2, b = e % n2;
+        sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = (T)tab[M.o_K2 + e];
+    }
+    if (GEOM == 1)
+        for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = (T)tab[M.o_K3 + e];
     __syncthreads();
 
     uint32_t phase = 0;
@@ -88,12 +187,13 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         const int lo = c0 >= 3 ? c0 - 3 : 0;
         const int hi = min(c0 + Be + 3, N);  // staged cells [lo, hi)
         T* const frow0 = fs + (long long)(lo - c0 + 3) * Ms;
+        const T* rsrc = rec_all + (long long)(I.cell_off + c0) * rs;
 
-        // ---- 1. stage the cells (this slice) into shared memory
+        // ---- 1. stage the cells (this slice) and the tile's collision records
         if (A.use_bulk) {
             if (tid == 0) {
                 fence_proxy_async();
-                mbar_expect_tx(bar, (uint32_t)((hi - lo) * Ms * sizeof(T)));
+                mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + Be * rs) * sizeof(T)));
                 if (M.slices == 1) {
                     bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
                 } else {
@@ -101,14 +201,16 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                         bulk_g2s(frow0 + (long long)(cc - lo) * Ms, fin + (long long)cc * Np + slice_off,
                                  (uint32_t)(Ms * sizeof(T)), bar);
                 }
+                bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
             }
         } else {
             for (int cc = lo; cc < hi; ++cc)
                 for (int e = tid; e < Ms; e += NT)
                     frow0[(long long)(cc - lo) * Ms + e] = ldg_t(fin + (long long)cc * Np + slice_off + e);
+            for (int e = tid; e < Be * rs; e += NT) cellT[e] = rsrc[e];
         }
 
-        // ---- 2. per-cell collision records and geometry of the tile (overlapping the copy)
+        // ---- 2. geometry of the tile and the wall densities (overlapping the copy)
         const double* gwi = A.gw + (long long)wi.x * 2 * gwstride;
         for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = (T)gwi[e];
         for (int c = tid; c < Be; c += NT) {
@@ -117,14 +219,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             sgeo[c * 3 + 1] = (T)g[3];
             sgeo[c * 3 + 2] = (T)g[4];
         }
-        {
-            const T* rsrc = reinterpret_cast<const T*>(A.rec) + (long long)(I.cell_off + c0) * A.rec_stride;
-            for (int e = tid; e < Be * cstride; e += NT) {
-                const int cl = e / cstride, q = e % cstride;
-                cellT[e] = rsrc[(long long)cl * A.rec_stride + q];
-            }
-        }
-        const double nwall[2] = {A.nw[wi.x * 2], A.nw[wi.x * 2 + 1]};
+        const T nwL = (T)A.nw[wi.x * 2], nwR = (T)A.nw[wi.x * 2 + 1];
 
         // ---- wait for the staged cells
         if (A.use_bulk) {
@@ -140,13 +235,12 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         __syncthreads();
 
         // ---- 3. ghost rows at the walls
-        const T nwL = (T)nwall[0], nwR = (T)nwall[1];
         const T* gwL = sgw;
         const T* gwR = sgw + gwstride;
         if (c0 == 0 || c0 + Be == N) {
             for (int ml = tid; ml < Ms; ml += NT) {
                 const int kk = ml / (nR * n2), rem = ml % (nR * n2), i = rem / n2, j = rem % n2;
-                const int k = sl * M.KS + kk;
+                const int k = sl * KS + kk;
                 const T pr = sp_R[i];
                 if (c0 == 0) {
                     T g1, g2;
@@ -174,30 +268,51 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             __syncthreads();
         }
 
-        // ---- 4. per-thread momenta of this slice; value of the left face of c0
-        int code[MPT];
-        T pr_[MPT], wm_[MPT], iw_[MPT], vl_[MPT];
+        // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
+        int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
+        T pr_[NV], p3_[NV];
+        T wm_[NV][VW], iw_[NV][VW], p2_[NV][VW], vl_[NV][VW];
 #pragma unroll
-        for (int r = 0; r < MPT; ++r) {
-            const int ml = tid + r * NT;
-            code[r] = 0;
-            pr_[r] = wm_[r] = iw_[r] = vl_[r] = T(0);
-            if (ml < Ms) {
-                const int kk = ml / (nR * n2), rem = ml % (nR * n2), i = rem / n2, j = rem % n2;
-                const int k = sl * M.KS + kk;
-                code[r] = (kk << 16) | (i << 8) | j;
+        for (int g = 0; g < NV; ++g) {
+            const int v = tid + g * NT;
+            vcode[g] = -1;
+            pr_[g] = p3_[g] = T(0);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) wm_[g][e] = iw_[g][e] = p2_[g][e] = vl_[g][e] = T(0);
+            if (v < Vs) {
+                const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
+                const int k = sl * KS + kk;
+                vcode[g] = (kk << 20) | (i << 10) | jb;
                 const T pr = sp_R[i];
-                pr_[r] = pr;
-                wm_[r] = sw_R[i] * sw_2[j] * sw_3[k];
-                const T iw = T(1) / wm_[r];
-                iw_[r] = iw;
+                pr_[g] = pr;
+                p3_[g] = sp_3[k];
+                const T wik = sw_R[i] * sw_3[k];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const int j = jb * VW + e;
+                    p2_[g][e] = sp_2[j];
+                    wm_[g][e] = wik * sw_2[j];
+                    iw_[g][e] = T(1) / wm_[g][e];
+                }
                 if (c0 == 0 && pr > T(0)) {
-                    vl_[r] = nwL * gwL[i] * gwL[nR + j] * gwL[nR + n2 + k] * iw;
+                    const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e] * iw_[g][e];
                 } else {
                     // rows of cells c0-3..c0+1 (p_R > 0) or c0+2..c0-2 (p_R < 0)
-                    const T* b = fs + (long long)(pr > T(0) ? 0 : 5) * Ms + ml;
-                    const long long s = pr > T(0) ? (long long)Ms : -(long long)Ms;
-                    vl_[r] = weno5(b[0] * iw, b[s] * iw, b[2 * s] * iw, b[3 * s] * iw, b[4 * s] * iw);
+                    const T* b = fs + (long long)(pr > T(0) ? 0 : 5) * Ms + v * VW;
+                    const int s = pr > T(0) ? Ms : -Ms;
+                    T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
+                    ld_vec<T, VW>(b, r0);
+                    ld_vec<T, VW>(b + s, r1);
+                    ld_vec<T, VW>(b + 2 * s, r2);
+                    ld_vec<T, VW>(b + 3 * s, r3);
+                    ld_vec<T, VW>(b + 4 * s, r4);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const T iw = iw_[g][e];
+                        vl_[g][e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                    }
                 }
             }
         }
@@ -205,133 +320,222 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         const T dt = (T)I.dt, ca_ = (T)A.a, cb_ = (T)A.b;
         for (int cl = 0; cl < Be; ++cl) {
             const int c = c0 + cl;
-            const T* ct = cellT + cl * cstride;
-            const T n = ct[0], u0 = ct[1], u1 = ct[2], u2 = ct[3], iT = ct[4], itau = ct[5], cS = ct[6];
-            const T q0 = ct[7], q1 = ct[8], q2 = ct[9], brchi = ct[10], X = ct[11], Y = ct[12];
-            const T S00 = ct[13], S11 = ct[14], S22 = ct[15], S01 = ct[16], S02 = ct[17], dv = ct[19];
-            const T* gR = ct + kCellScalars;
-            const T* g2 = gR + nR;
-            const T* g3 = g2 + n2;
+            const T* ct = cellT + cl * rs;
+            T sc[20];
+#pragma unroll
+            for (int q = 0; q < 20; q += 4) {
+                T t4[4];
+                ld_vec<T, 4>(ct + q, t4);
+                sc[q] = t4[0]; sc[q + 1] = t4[1]; sc[q + 2] = t4[2]; sc[q + 3] = t4[3];
+            }
+            const T n = sc[0], u0 = sc[1], u1 = sc[2], u2 = sc[3], iT = sc[4], itau = sc[5], cS = sc[6];
+            const T q0 = sc[7], q1 = sc[8], q2 = sc[9], brchi = sc[10], X = sc[11], Y = sc[12];
+            const T S00 = sc[13], S11 = sc[14], S22 = sc[15], S01 = sc[16], S02 = sc[17], dv = sc[19];
+            const T* g2c = ct + rec_off_g2();
+            const T* gRc = ct + rec_off_gR(n2);
+            const T* g3c = ct + rec_off_g3(nR, n2);
             const T Ap = sgeo[cl * 3 + 0], Am = sgeo[cl * 3 + 1], kf = sgeo[cl * 3 + 2];
             const T* fc = fs + (long long)(cl + 3) * Ms;  // row of cell c
-            T acc[kSums];
+            T acc[16];
 #pragma unroll
-            for (int q = 0; q < kSums; ++q) acc[q] = T(0);
+            for (int q = 0; q < 16; ++q) acc[q] = T(0);
 #pragma unroll
-            for (int r = 0; r < MPT; ++r) {
-                const int ml = tid + r * NT;
-                if (ml < Ms) {
-                    const int cd = code[r];
-                    const int i = (cd >> 8) & 0xff, j = cd & 0xff, kk = (cd >> 16) & 0xff;
-                    const int k = sl * M.KS + kk;
-                    const T pr = pr_[r], iw = iw_[r];
+            for (int g = 0; g < NV; ++g) {
+                const int cd = vcode[g];
+                if (cd >= 0) {
+                    const int kk = cd >> 20, i = (cd >> 10) & 1023, jb = cd & 1023;
+                    const int k = sl * KS + kk;
+                    const int vb = ((kk * nR + i) * n2v + jb) * VW;  // element offset in the slice
+                    const T pr = pr_[g], p3v = p3_[g];
                     // advection: WENO5 value at the right face, upwind by sign(p_R)
-                    T vr;
+                    T vr[VW];
                     if (c == N - 1 && pr < T(0)) {
-                        vr = nwR * gwR[i] * gwR[nR + j] * gwR[nR + n2 + k] * iw;
+                        const T gik = nwR * gwR[i] * gwR[nR + n2 + k];
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e] * iw_[g][e];
                     } else {
-                        const T* b = fc + (pr > T(0) ? -2LL : 3LL) * Ms + ml;
-                        const long long s = pr > T(0) ? (long long)Ms : -(long long)Ms;
-                        vr = weno5(b[0] * iw, b[s] * iw, b[2 * s] * iw, b[3 * s] * iw, b[4 * s] * iw);
+                        const T* b = fc + (pr > T(0) ? -2 * Ms : 3 * Ms) + vb;
+                        const int s = pr > T(0) ? Ms : -Ms;
+                        T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
+                        ld_vec<T, VW>(b, r0);
+                        ld_vec<T, VW>(b + s, r1);
+                        ld_vec<T, VW>(b + 2 * s, r2);
+                        ld_vec<T, VW>(b + 3 * s, r3);
+                        ld_vec<T, VW>(b + 4 * s, r4);
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) {
+                            const T iw = iw_[g][e];
+                            vr[e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                        }
                     }
-                    const T adv = pr * wm_[r] * (Ap * vr - Am * vl_[r]);
-                    vl_[r] = vr;
-                    // curvature force with the derivative matrices
-                    const T p2v = sp_2[j], p3v = sp_3[k];
-                    const T* colR = fc + (kk * nR) * n2 + j;
-                    T KRf = T(0);
+                    // curvature force: K^h along i (one column shared by the vector), K_2 along j
+                    T KRf[VW], K2f[VW], K3f[VW];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) KRf[e] = K2f[e] = K3f[e] = T(0);
+                    {
+                        const T* col = fc + kk * nR * n2 + jb * VW;
+                        const T* kr = sKR + i * (nR + 1);
 #pragma unroll 8
-                    for (int a = 0; a < nR; ++a) KRf += sKR[i * nR + a] * colR[a * n2];
-                    const T* row2 = fc + (kk * nR + i) * n2;
-                    T K2f = T(0);
-#pragma unroll 8
-                    for (int a = 0; a < n2; ++a) K2f += sK2[j * n2 + a] * row2[a];
-                    T frc;
-                    if (GEOM == 0) {
-                        frc = kf * (p2v * p2v * KRf - pr * K2f);
-                    } else {
-                        const T* col3 = fc + i * n2 + j;
-                        T K3f = T(0);
+                        for (int a = 0; a < nR; ++a) {
+                            T cv[VW];
+                            ld_vec<T, VW>(col + a * n2, cv);
+                            const T kv = kr[a];
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                        }
+                        const T* row = fc + (kk * nR + i) * n2;
 #pragma unroll 4
-                        for (int a = 0; a < n3; ++a) K3f += sK3[k * n3 + a] * col3[a * nR * n2];
-                        frc = kf * ((p2v * p2v + p3v * p3v) * KRf - pr * (K2f + K3f));
+                        for (int b4 = 0; b4 < n2v; ++b4) {
+                            T rv[VW];
+                            ld_vec<T, VW>(row + b4 * VW, rv);
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) {
+                                T kq[VW];
+                                ld_vec<T, VW>(sK2 + ((e * n2v + b4) * n2v + jb) * VW, kq);
+#pragma unroll
+                                for (int t = 0; t < VW; ++t) K2f[e] += kq[t] * rv[t];
+                            }
+                        }
+                        if (GEOM == 1) {
+                            const T* k3 = sK3 + k * (n3 + 1);
+                            const T* c3 = fc + i * n2 + jb * VW;
+#pragma unroll 4
+                            for (int b = 0; b < n3; ++b) {
+                                T cv[VW];
+                                ld_vec<T, VW>(c3 + b * nR * n2, cv);
+                                const T kv = k3[b];
+#pragma unroll
+                                for (int e = 0; e < VW; ++e) K3f[e] += kv * cv[e];
+                            }
+                        }
                     }
-                    // collision: -(f - f^S)/tau + J1[f^MB]
-                    const T f = fc[ml];
-                    const T x0 = pr - u0, x1 = p2v - u1, x2 = p3v - u2;
-                    const T xs = x0 * x0 + x1 * x1 + x2 * x2;
-                    const T xq = x0 * q0 + x1 * q1 + x2 * q2;
-                    const T fmb = n * gR[i] * g2[j] * g3[k];
-                    const T z2 = T(0.5) * xs * iT;
-                    const T strain = iT * (x0 * x0 * S00 + x1 * x1 * S11 + x2 * x2 * S22 + T(2) * (x0 * x1 * S01 + x0 * x2 * S02));
-                    const T j1 = -brchi * (x0 * (X + T(0.6) * (z2 - T(2.5)) * Y) + T(0.4) * (strain + (z2 - T(2.5)) * dv));
-                    const T fS = fmb * (T(1) + cS * (T(0.2) * xs * iT - T(1)) * xq);
-                    const T L = -adv - frc - (f - fS) * itau + fmb * j1;
-                    const long long gidx = I.f_off + (long long)c * Np + slice_off + ml;
-                    T out;
-                    if (A.mode == 1) {
-                        out = L;
-                    } else {
-                        const T fnv = ca_ != T(0) ? ldg_t(f_n + gidx) : T(0);
-                        out = ca_ * fnv + cb_ * (f + dt * L);
+                    // collision: -(f - f^S)/tau + J1[f^MB]; terms without j shared by the vector
+                    T fv[VW], g2v[VW];
+                    ld_vec<T, VW>(fc + vb, fv);
+                    ld_vec<T, VW>(g2c + jb * VW, g2v);
+                    const T x0 = pr - u0, x2 = p3v - u2;
+                    const T xsA = x0 * x0 + x2 * x2, xqA = x0 * q0 + x2 * q2;
+                    const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
+                    const T fmbA = n * gRc[i] * g3c[k];
+                    const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
+                    T out[VW];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const T p2v = p2_[g][e];
+                        const T adv = pr * wm_[g][e] * (Ap * vr[e] - Am * vl_[g][e]);
+                        vl_[g][e] = vr[e];
+                        T frc;
+                        if (GEOM == 0) {
+                            frc = kf * (p2v * p2v * KRf[e] - pr * K2f[e]);
+                        } else {
+                            frc = (kf * p2v * p2v + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
+                        }
+                        const T x1 = p2v - u1;
+                        const T xs = xsA + x1 * x1;
+                        const T xq = xqA + x1 * q1;
+                        const T fmb = fmbA * g2v[e];
+                        const T z2 = T(0.5) * xs * iT;
+                        const T strain = iT * (stA + x1 * x1 * S11 + T(2) * x0 * x1 * S01);
+                        const T j1 = -brchi * (x0 * (X + T(0.6) * (z2 - T(2.5)) * Y) + T(0.4) * (strain + (z2 - T(2.5)) * dv));
+                        const T fS = fmb * (T(1) + cS * (T(0.2) * xs * iT - T(1)) * xq);
+                        out[e] = -adv - frc - (fv[e] - fS) * itau + fmb * j1;
                     }
-                    f_out[gidx] = out;
-                    const T ps = pr * pr + p2v * p2v + p3v * p3v;
-                    acc[0] += out;
-                    acc[1] += out * pr;
-                    acc[2] += out * p2v;
-                    acc[3] += out * p3v;
-                    acc[4] += out * pr * pr;
-                    acc[5] += out * p2v * p2v;
-                    acc[6] += out * p3v * p3v;
-                    acc[7] += out * pr * p2v;
-                    acc[8] += out * pr * p3v;
-                    acc[9] += out * p2v * p3v;
-                    acc[10] += out * ps * pr;
-                    acc[11] += out * ps * p2v;
-                    acc[12] += out * ps * p3v;
+                    const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
+                    if (A.mode == 0) {
+                        T fnv[VW];
+                        if (ca_ != T(0)) {
+                            ldg_vec<T, VW>(f_n + gidx, fnv);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) fnv[e] = T(0);
+                        }
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) out[e] = ca_ * fnv[e] + cb_ * (fv[e] + dt * out[e]);
+                    }
+                    st_vec<T, VW>(f_out + gidx, out);
+                    // raw sums: power sums over the vector's p_2, then the 13 moments
+                    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) {
+                        const T p2v = p2_[g][e];
+                        const T o1 = out[e] * p2v, o2 = o1 * p2v;
+                        s0 += out[e];
+                        s1 += o1;
+                        s2 += o2;
+                        s3 += o2 * p2v;
+                    }
+                    const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
+                    const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
+                    acc[0] += s0;
+                    acc[1] += prs0;
+                    acc[2] += s1;
+                    acc[3] += p3s0;
+                    acc[4] += pr * prs0;
+                    acc[5] += s2;
+                    acc[6] += p3v * p3s0;
+                    acc[7] += pr * s1;
+                    acc[8] += pr * p3s0;
+                    acc[9] += p3v * s1;
+                    acc[10] += pr * e10;
+                    acc[11] += rr * s1 + s3;
+                    acc[12] += p3v * e10;
                 }
             }
-            // ---- 5. raw sums of the new populations: per-thread partial and warp tree in the
-            // populations' precision, FP64 sum over the warps in a fixed order
+            // ---- 5. warp sums of the 13 raw moments of this cell (lane L holds sum L/2)
             if (A.mode == 0) {
-                T* rb = red + (cl & 1) * nwarps * kSums;
-#pragma unroll
-                for (int q = 0; q < kSums; ++q) {
-                    const T s = warp_sum(acc[q]);  // warp tree in the populations' precision
-                    if (lane == 0) rb[warp * kSums + q] = s;
-                }
-                __syncthreads();
-                if (tid < kSums) {
-                    double s = 0.0;  // FP64 sum over the warps, fixed order
-                    for (int ww = 0; ww < nwarps; ++ww) s += (double)rb[ww * kSums + tid];
-                    A.sums_out[((long long)(I.cell_off + c) * M.slices + sl) * kSums + tid] = s;
-                }
+                const T s = warp_sum16_transposed(acc, lane);
+                if (!(lane & 1) && (lane >> 1) < kSums) red[(cl * nwarps + warp) * 16 + (lane >> 1)] = s;
             }
         }
-        __syncthreads();  // the next item overwrites the staged rows and the cell data
+        __syncthreads();
+        if (A.mode == 0) {
+            // FP64 sums over the warps in a fixed order
+            for (int e = tid; e < Be * kSums; e += NT) {
+                const int cl = e / kSums, q = e % kSums;
+                double s = 0.0;
+                for (int ww = 0; ww < nwarps; ++ww) s += (double)red[(cl * nwarps + ww) * 16 + q];
+                A.sums_out[((long long)(I.cell_off + c0 + cl) * M.slices + sl) * kSums + q] = s;
+            }
+        }
+        __syncthreads();  // the next item overwrites the staged rows, the records and the sums
     }
 }
 
-template <typename T, int GEOM, int MPT>
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
 cudaError_t launch_stream_t(const StageArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {
-    auto kern = stream_kernel<T, GEOM, MPT>;
+    auto kern = stream_kernel<T, GEOM, VW, NV, NR_, N2_, N3_>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, threads, smem, s>>>(A, M);
     return cudaGetLastError();
 }
 
-#define FDLB_STREAM_INSTANCE(T, G)                                                                            \
-    cudaError_t launch_stream_##T##_##G(int mpt, const StageArgs& A, const MomSet& M, int grid, int threads, \
-                                        size_t smem, cudaStream_t s) {                                       \
-        switch (mpt) {                                                                                        \
-            case 1: return launch_stream_t<T, G, 1>(A, M, grid, threads, smem, s);                          \
-            case 2: return launch_stream_t<T, G, 2>(A, M, grid, threads, smem, s);                          \
-            case 4: return launch_stream_t<T, G, 4>(A, M, grid, threads, smem, s);                          \
-            case 8: return launch_stream_t<T, G, 8>(A, M, grid, threads, smem, s);                          \
-            default: return cudaErrorInvalidValue;                                                            \
-        }                                                                                                     \
+// Instantiations: generic shapes (VW 1, 2, 4 for float; 1, 2 for double) and the compile-time
+// shapes of the cylinder (16 x 8 x 8) and sphere (24 x 12 x 12) workloads.
+template <typename T, int G>
+cudaError_t launch_stream_dispatch(const StreamCfg& cfg, const StageArgs& A, const MomSet& M, int grid, int threads,
+                                   size_t smem, cudaStream_t s) {
+    constexpr int VS = sizeof(T) == 4 ? 4 : 2;  // vector width of the compile-time shapes
+    constexpr int SR = G == 0 ? 16 : 24, S2 = G == 0 ? 8 : 12, S3 = G == 0 ? 8 : 12;
+    constexpr int NA = G == 0 ? 1 : 2, NB = G == 0 ? 2 : 4;
+    if (cfg.spec) {
+        if (cfg.vw != VS) return cudaErrorInvalidValue;
+        if (cfg.nv == NA) return launch_stream_t<T, G, VS, NA, SR, S2, S3>(A, M, grid, threads, smem, s);
+        if (cfg.nv == NB) return launch_stream_t<T, G, VS, NB, SR, S2, S3>(A, M, grid, threads, smem, s);
+        return cudaErrorInvalidValue;
+    }
+    if (cfg.vw == 1 && cfg.nv == 4) return launch_stream_t<T, G, 1, 4, 0, 0, 0>(A, M, grid, threads, smem, s);
+    if (cfg.vw == 2 && cfg.nv == 4) return launch_stream_t<T, G, 2, 4, 0, 0, 0>(A, M, grid, threads, smem, s);
+    if constexpr (sizeof(T) == 4) {
+        if (cfg.vw == 4 && cfg.nv == 2) return launch_stream_t<T, G, 4, 2, 0, 0, 0>(A, M, grid, threads, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+#define FDLB_STREAM_INSTANCE(T, G)                                                                               \
+    cudaError_t launch_stream_##T##_##G(const StreamCfg& cfg, const StageArgs& A, const MomSet& M, int grid,    \
+                                        int threads, size_t smem, cudaStream_t s) {                              \
+        return launch_stream_dispatch<T, G>(cfg, A, M, grid, threads, smem, s);                                  \
     }
 
 }  // namespace fdlb
