@@ -206,6 +206,12 @@ const char* fdlb_error_string(int code);
 int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads);
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
 
+/* Own cells per closure work item (1..28; default 4).  A closure item also recomputes the
+ * macroscopic fields of two stencil cells on each side, so larger items repeat less work and
+ * smaller items spread the latency-bound closure over more SMs.  FDLB_EINVAL outside the
+ * range. */
+int fdlb_set_closure_cells(fdlb_handle h, int cells);
+
 /* Number of kernel launches issued by the last fdlb_step call (for launch accounting). */
 int64_t fdlb_launch_count(fdlb_handle h);
 

@@ -83,6 +83,73 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     return ratio_fast(a0 * r0 + a1 * r1 + a2 * r2, T(6) * (a0 + a1 + a2));
 }
 
+// ---- wide accumulators: plain FP64 for FP64 populations; for FP32 populations a double-float
+// (hi + lo, about 44 significant bits) on the FP32 pipe, because FP64 arithmetic on GB300 costs
+// 64 cycles per dependent operation and about 440 per division.  The error-free transformations
+// are Knuth's TwoSum and the fused-multiply-add TwoProduct (Dekker 1971; the double-double
+// algorithms of Hida, Li and Bailey 2001, restated for float pairs).
+template <typename T>
+struct Wide;
+template <>
+struct Wide<double> {
+    double v;
+};
+template <>
+struct Wide<float> {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Wide<double> w_from(double s, double*) { return {s}; }
+__device__ __forceinline__ Wide<float> w_from(double s, float*) {
+    const float hi = __double2float_rn(s);
+    return {hi, __double2float_rn(s - (double)hi)};
+}
+__device__ __forceinline__ Wide<double> w_from_t(double x) { return {x}; }
+__device__ __forceinline__ Wide<float> w_from_t(float x) { return {x, 0.f}; }
+__device__ __forceinline__ double w_hi(Wide<double> a) { return a.v; }
+__device__ __forceinline__ float w_hi(Wide<float> a) { return a.hi; }
+__device__ __forceinline__ Wide<double> w_add(Wide<double> a, Wide<double> b) { return {a.v + b.v}; }
+__device__ __forceinline__ Wide<double> w_sub(Wide<double> a, Wide<double> b) { return {a.v - b.v}; }
+__device__ __forceinline__ Wide<double> w_mul(Wide<double> a, Wide<double> b) { return {a.v * b.v}; }
+__device__ __forceinline__ Wide<double> w_div(Wide<double> a, Wide<double> b) { return {a.v / b.v}; }
+__device__ __forceinline__ Wide<double> w_scale(Wide<double> a, double c) { return {a.v * c}; }
+
+__device__ __forceinline__ Wide<float> w_norm(float s, float e) {  // |s| >= |e|
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ Wide<float> w_add(Wide<float> a, Wide<float> b) {
+    const float s = a.hi + b.hi, v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    e += a.lo + b.lo;
+    return w_norm(s, e);
+}
+__device__ __forceinline__ Wide<float> w_sub(Wide<float> a, Wide<float> b) { return w_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ Wide<float> w_mul(Wide<float> a, Wide<float> b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return w_norm(p, e);
+}
+__device__ __forceinline__ Wide<float> w_scale(Wide<float> a, float c) {
+    const float p = a.hi * c;
+    const float e = fmaf(a.lo, c, fmaf(a.hi, c, -p));
+    return w_norm(p, e);
+}
+// a / b: a first quotient, the remainder a - q1 b in double-float, a correction
+__device__ __forceinline__ Wide<float> w_div(Wide<float> a, Wide<float> b) {
+    const float q1 = a.hi / b.hi;
+    const Wide<float> r = w_sub(a, w_scale(b, q1));
+    return w_norm(q1, r.hi / b.hi);
+}
+
+template <typename T>
+__device__ __forceinline__ T chi_cs_t(T eta) {
+    const T om = T(1) - eta;
+    return (T(2) - eta) / (T(2) * om * om * om);
+}
+
 __device__ __forceinline__ double chi_cs(double eta) {
     const double om = 1.0 - eta;
     return (2.0 - eta) / (2.0 * om * om * om);
@@ -97,8 +164,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // Five-point derivative stencil in the mapped coordinate (gradients of Eq. j1): fourth-order
 // central in the interior, one-sided fourth-order at the two cells next to each wall.
-__device__ __forceinline__ void stencil5(int c, int N, int* idx, double* w) {
-    const double k = 1.0 / 12.0;
+template <typename R>
+__device__ __forceinline__ void stencil5(int c, int N, int* idx, R* w) {
+    const R k = R(1) / R(12);
     if (c >= 2 && c <= N - 3) {
         idx[0] = c - 2; idx[1] = c - 1; idx[2] = c; idx[3] = c + 1; idx[4] = c + 2;
         w[0] = k; w[1] = -8 * k; w[2] = 0; w[3] = 8 * k; w[4] = -k;

@@ -24,7 +24,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
-    size_t f[3], sums[3], ca, rec, tab, tabT, inst, geo, gw, band, band_lo, sitems, n_sitems, citems, n_citems, nw, err,
+    size_t f[3], sums[3], dens[3], ca, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
+        n_citems, nwp, err,
         rprev, rout, total;
 };
 
@@ -52,9 +53,11 @@ struct Solver {
     Layout lay{};
     void* f[3] = {nullptr, nullptr, nullptr};
     double* sums[3] = {nullptr, nullptr, nullptr};
+    void* dens[3] = {nullptr, nullptr, nullptr};
+    void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr;
     void* rec = nullptr;
     void* tabT = nullptr;
-    double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *nw = nullptr, *rprev = nullptr,
+    double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *rprev = nullptr,
            *rout = nullptr;
     InstDev* inst_d = nullptr;
     void* band = nullptr;
@@ -68,7 +71,8 @@ struct Solver {
     StreamCfg scfg{1, 4, 0};
     size_t smem_stream = 0;
     int use_bulk = 0;
-    int closure_cells = 4, closure_threads = 256;  // one warp per cell in reach (4 + 4 halo)
+    int closure_cells = 4, closure_threads = 128;  // own cells per closure item (<= kClosureCells)
+    int closure_wst = 0;                           // staged band-row elements per closure block
     int grid_stream = 1, grid_closure = 1;
     size_t closure_smem = 0;
     int max_union = 1;
@@ -183,20 +187,23 @@ Layout make_layout(const Solver& S) {
     };
     for (int b = 0; b < 3; ++b) L.f[b] = take(S.f_elems * S.tsize);
     for (int b = 0; b < 3; ++b) L.sums[b] = take((size_t)S.total_cells * S.n3 * kSums * sizeof(double));
+    for (int b = 0; b < 3; ++b) L.dens[b] = take((size_t)S.total_cells * S.n3 * S.tsize);
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
     L.tabT = take(S.tab_h.size() * S.tsize);
     L.inst = take(S.n_inst * sizeof(InstDev));
     L.geo = take((size_t)S.total_cells * kGeo * sizeof(double));
+    L.geoT = take((size_t)S.total_cells * kGeo * S.tsize);
     L.gw = take((size_t)S.n_inst * 2 * (S.nR + S.n2 + S.n3) * sizeof(double));
+    L.gwT = take((size_t)S.n_inst * 2 * (S.nR + S.n2 + S.n3) * S.tsize);
     L.band = take(S.band_elems * S.tsize);
-    L.band_lo = take((size_t)S.total_cells * sizeof(int));
+    L.band_lo = take((size_t)S.total_cells * 2 * sizeof(int));  // (first column, extent) per cell
     L.sitems = take((size_t)S.max_sitems * sizeof(int4));
     L.n_sitems = take(sizeof(int));
     L.citems = take((size_t)S.max_citems * sizeof(int4));
     L.n_citems = take(sizeof(int));
-    L.nw = take((size_t)S.n_inst * 2 * sizeof(double));
+    L.nwp = take((size_t)S.n_inst * 2 * kWallParts * S.tsize);
     L.err = take(sizeof(int));
     L.rprev = take((size_t)S.total_cells * 4 * sizeof(double));
     L.rout = take((size_t)S.n_inst * 10 * sizeof(double));
@@ -259,7 +266,7 @@ int plan_solver(const fdlb_params* ps, int n, Solver& S) {
         S.f_elems += align_up((size_t)N * S.Np, falign);
         S.band_elems += (size_t)N * S.setup[q].band.width;
         S.max_sitems += ((N + 3) / 4) * S.n3;
-        S.max_citems += (N + S.closure_cells - 1) / S.closure_cells;
+        S.max_citems += N + 2 * kWallParts;  // room for one-cell closure items, + the wall items
     }
     S.active.assign(n, 1);
     S.inst_steps.assign(n, 0);
@@ -302,6 +309,15 @@ void fill_inst(Solver& S, int q) {
     d.ds = I.grid.ds;
     std::vector<double> tmp(2 * (S.nR + S.n2 + S.n3));
     wall_tables(S, q, tmp.data(), d.nw_den);
+    for (int side = 0; side < 2; ++side) {
+        d.nw_iden[side] = 1.0 / d.nw_den[side];
+        d.f_nw_iden[side] = (float)d.nw_iden[side];
+    }
+    d.f_sigma = (float)d.sigma;
+    d.f_bfac = (float)d.bfac;
+    d.f_etafac = (float)d.etafac;
+    d.f_ids = (float)(1.0 / d.ds);
+    d.f_dt = (float)d.dt;
 }
 
 // Work lists: stream items (instance, first cell, cells, slice) over the active instances,
@@ -324,6 +340,9 @@ int upload_items(Solver& S) {
             for (int sl = 0; sl < slices; ++sl) si.push_back(make_int4(q, c0, cnt, sl));
             c0 += cnt;
         }
+        // the wall densities first (their blocks read four cells of populations), then the cells
+        for (int side = 0; side < 2; ++side)
+            for (int part = 0; part < kWallParts; ++part) ci.push_back(make_int4(q, side ? N - 1 : 0, part, 1 + side));
         for (int c = 0; c < N; c += S.closure_cells) ci.push_back(make_int4(q, c, std::min(S.closure_cells, N - c), 0));
     }
     if ((int)si.size() > S.max_sitems || (int)ci.size() > S.max_citems) return FDLB_EINVAL;
@@ -333,19 +352,29 @@ int upload_items(Solver& S) {
     FDLB_CUDA(cudaMemcpyAsync(S.n_sitems, &ns, sizeof(int), cudaMemcpyHostToDevice, S.stream));
     FDLB_CUDA(cudaMemcpyAsync(S.n_citems, &nc, sizeof(int), cudaMemcpyHostToDevice, S.stream));
     FDLB_CUDA(cudaStreamSynchronize(S.stream));  // host vectors go out of scope
-    // closure shared memory: union band of one closure item
+    // closure shared memory: the tables and the union of the FM bands of one item's reach
     int max_union = 1;
     for (const int4& w : ci) {
+        if (w.w != 0) continue;
         const InstanceSetup& I = S.setup[w.x];
         if (I.band.width == 0) continue;
         const int N = I.p.n_cells;
         const int h0 = std::max(0, std::min(w.y - 2, N - 5)), h1 = std::min(N, std::max(w.y + w.z + 2, 5));
         const int lo = I.band.lo[h0];
-        const int hi = std::min(I.p.n_cells - 1, I.band.lo[h1 - 1] + I.band.width - 1);
+        const int hi = std::min(N - 1, I.band.lo[h1 - 1] + I.band.cnt[h1 - 1] - 1 + 3);
         max_union = std::max(max_union, hi - lo + 1);
     }
     S.max_union = max_union;
-    S.closure_smem = closure_smem(S.closure_cells, max_union, (int)S.tsize);
+    // staged band rows of one item's reach (at most closure_cells + 4 rows); instances whose rows
+    // do not fit read them from global memory instead
+    int wst = 0;
+    for (int q = 0; q < S.n_inst; ++q)
+        wst = std::max(wst, std::min(S.setup[q].p.n_cells, S.closure_cells + 4) * S.setup[q].band.width);
+    const size_t base = closure_smem(S.nR, S.n2, S.n3, max_union, 0, (int)S.tsize);
+    if (base > S.smem_optin) return FDLB_EINVAL;
+    wst = (int)std::min<size_t>((size_t)wst, (S.smem_optin - base) / S.tsize);
+    S.closure_wst = wst;
+    S.closure_smem = closure_smem(S.nR, S.n2, S.n3, max_union, wst, (int)S.tsize);
     S.grid_closure = std::max(1, std::min(nc, S.n_sm * 8));
     S.grid_stream = std::max(1, ns);
     return FDLB_OK;
@@ -440,35 +469,37 @@ void from_device_layout(const Solver& S, const std::vector<T>& src, double* dst,
 int launch_moments_all(Solver& S, int buf) {
     const int nc = S.max_citems;
     if (S.precision == FDLB_FP32)
-        launch_moments<float>((const float*)S.f[buf], S.sums[buf], S.citems, S.n_citems, std::max(1, std::min(nc, S.n_sm * 8)),
+        launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.citems, S.n_citems, std::max(1, std::min(nc, S.n_sm * 8)),
                               S.inst_d, S.tab, S.M, S.stream);
     else
-        launch_moments<double>((const double*)S.f[buf], S.sums[buf], S.citems, S.n_citems,
+        launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], S.citems, S.n_citems,
                                std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
     S.launches++;
     return cuda_status(cudaGetLastError());
 }
 
-int launch_closure_buf(Solver& S, int buf) {
+int launch_closure_buf(Solver& S, int buf, int write_ca) {
     ClosureArgs A{};
     A.sums = S.sums[buf];
+    A.dens = S.dens[buf];
     A.f_in = S.f[buf];
     A.ca = S.ca;
     A.rec = S.rec;
     A.rec_stride = record_stride(S.nR, S.n2, S.n3);
-    A.nw = S.nw;
+    A.nwp = S.nwp;
     A.items = S.citems;
     A.n_items = S.n_citems;
     A.inst = S.inst_d;
     A.band = S.band;
     A.band_lo = S.band_lo;
-    A.tab = S.tab;
     A.tabT = S.tabT;
-    A.geo = S.geo;
-    A.gw = S.gw;
+    A.geoT = S.geoT;
     A.slices = S.M.slices;
-    A.max_cells = S.closure_cells;
     A.max_union = S.max_union;
+    A.wall_parts = kWallParts;
+    A.write_ca = write_ca;
+    A.wst_elems = S.closure_wst;
+    A.err = S.err;
     if (S.precision == FDLB_FP32)
         launch_closure<float>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
     else
@@ -481,10 +512,10 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
 
 // One right-hand-side evaluation and RK combination: closure launch, then the fused stage.
 // In timing mode each launch is bracketed by events and its duration accumulated.
-int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mode) {
+int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mode, int write_ca = 0) {
     if (S.timing) {
         FDLB_CUDA(cudaEventRecord(S.tev[0], S.stream));
-        int rc = launch_closure_buf(S, in);
+        int rc = launch_closure_buf(S, in, write_ca);
         if (rc) return rc;
         FDLB_CUDA(cudaEventRecord(S.tev[1], S.stream));
         rc = launch_stream_only(S, in, fn, out, a, b, mode);
@@ -500,7 +531,7 @@ int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mod
         S.n_stream_t++;
         return FDLB_OK;
     }
-    int rc = launch_closure_buf(S, in);
+    int rc = launch_closure_buf(S, in, write_ca);
     if (rc) return rc;
     return launch_stream_only(S, in, fn, out, a, b, mode);
 }
@@ -512,17 +543,21 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.f_out = S.f[out];
     A.rec = S.rec;
     A.rec_stride = record_stride(S.nR, S.n2, S.n3);
-    A.nw = S.nw;
+    A.nwp = S.nwp;
+    A.wall_parts = kWallParts;
     A.sums_out = S.sums[out];
+    A.dens_out = S.dens[out];
     A.items = S.sitems;
     A.n_items = S.n_sitems;
     A.inst = S.inst_d;
     A.tab = S.tab;
-    A.geo = S.geo;
-    A.gw = S.gw;
+    A.geoT = S.geoT;
+    A.gwT = S.gwT;
     A.err = S.err;
     A.a = a;
     A.b = b;
+    A.fa = (float)a;
+    A.fb = (float)b;
     A.mode = mode;
     A.B = S.B;
     A.use_bulk = S.use_bulk;
@@ -678,6 +713,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     for (int b = 0; b < 3; ++b) {
         R.f[b] = R.ws + L.f[b];
         R.sums[b] = (double*)(R.ws + L.sums[b]);
+        R.dens[b] = (void*)(R.ws + L.dens[b]);
     }
     R.ca = (double*)(R.ws + L.ca);
     R.rec = R.ws + L.rec;
@@ -692,7 +728,9 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.n_sitems = (int*)(R.ws + L.n_sitems);
     R.citems = (int4*)(R.ws + L.citems);
     R.n_citems = (int*)(R.ws + L.n_citems);
-    R.nw = (double*)(R.ws + L.nw);
+    R.nwp = (void*)(R.ws + L.nwp);
+    R.geoT = (void*)(R.ws + L.geoT);
+    R.gwT = (void*)(R.ws + L.gwT);
     R.err = (int*)(R.ws + L.err);
     R.rprev = (double*)(R.ws + L.rprev);
     R.rout = (double*)(R.ws + L.rout);
@@ -706,7 +744,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         FDLB_CUDA(cudaMemcpyAsync(R.tabT, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
     R.inst_h.resize(n);
     std::vector<double> geo((size_t)R.total_cells * kGeo), gw((size_t)n * 2 * (R.nR + R.n2 + R.n3));
-    std::vector<int> blo(R.total_cells, 0);
+    std::vector<int> blo((size_t)R.total_cells * 2, 0);
     std::vector<float> bandf;
     std::vector<double> bandd;
     size_t boff = 0;
@@ -723,7 +761,10 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
             o[3] = g.A_f[c] / g.V_c[c];
             o[4] = I.p.geometry == FDLB_CYL ? g.kappa[c] : 0.5 * g.kappa[c];
             o[5] = g.V_c[c];
-            if (I.band.width) blo[R.cell_off[q] + c] = I.band.lo[c];
+            if (I.band.width) {
+                blo[(size_t)(R.cell_off[q] + c) * 2] = I.band.lo[c];
+                blo[(size_t)(R.cell_off[q] + c) * 2 + 1] = I.band.cnt[c];
+            }
         }
         double den[2];
         wall_tables(R, q, &gw[(size_t)q * 2 * (R.nR + R.n2 + R.n3)], den);
@@ -736,6 +777,14 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     FDLB_CUDA(cudaMemcpyAsync(R.inst_d, R.inst_h.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, R.stream));
     FDLB_CUDA(cudaMemcpyAsync(R.geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice, R.stream));
     FDLB_CUDA(cudaMemcpyAsync(R.gw, gw.data(), gw.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    std::vector<float> geof(geo.begin(), geo.end()), gwf(gw.begin(), gw.end());
+    if (R.precision == FDLB_FP32) {
+        FDLB_CUDA(cudaMemcpyAsync(R.geoT, geof.data(), geof.size() * 4, cudaMemcpyHostToDevice, R.stream));
+        FDLB_CUDA(cudaMemcpyAsync(R.gwT, gwf.data(), gwf.size() * 4, cudaMemcpyHostToDevice, R.stream));
+    } else {
+        FDLB_CUDA(cudaMemcpyAsync(R.geoT, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice, R.stream));
+        FDLB_CUDA(cudaMemcpyAsync(R.gwT, gw.data(), gw.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    }
     FDLB_CUDA(cudaMemcpyAsync(R.band_lo, blo.data(), blo.size() * sizeof(int), cudaMemcpyHostToDevice, R.stream));
     if (R.precision == FDLB_FP32 && !bandf.empty())
         FDLB_CUDA(cudaMemcpyAsync(R.band, bandf.data(), bandf.size() * 4, cudaMemcpyHostToDevice, R.stream));
@@ -892,7 +941,7 @@ int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) {
 int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
-    int rc = fdlb::launch_closure_buf(*S, 0);
+    int rc = fdlb::launch_closure_buf(*S, 0, 1);
     if (rc) return rc;
     const int N = S->setup[instance].p.n_cells;
     const double* src = S->ca + (size_t)S->cell_off[instance] * fdlb::kCA;
@@ -907,16 +956,34 @@ int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, dou
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst) return FDLB_EINVAL;
     // a right-hand-side evaluation refreshes the closure records and the wall densities
-    int rc = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1);
+    int rc = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1, 1);
     if (rc) return rc;
     const int N = S->setup[instance].p.n_cells;
     std::vector<double> ca((size_t)N * fdlb::kCA);
-    double nw[2];
+    const int P = fdlb::kWallParts;
+    std::vector<unsigned char> parts((size_t)2 * P * S->tsize);
     FDLB_CUDA(cudaMemcpyAsync(ca.data(), S->ca + (size_t)S->cell_off[instance] * fdlb::kCA, ca.size() * 8,
                               cudaMemcpyDeviceToHost, S->stream));
-    FDLB_CUDA(cudaMemcpyAsync(nw, S->nw + 2 * instance, 16, cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaMemcpyAsync(parts.data(), (unsigned char*)S->nwp + (size_t)instance * 2 * P * S->tsize, parts.size(),
+                              cudaMemcpyDeviceToHost, S->stream));
     FDLB_CUDA(cudaStreamSynchronize(S->stream));
     const fdlb::InstanceSetup& I = S->setup[instance];
+    double nw[2];
+    for (int side = 0; side < 2; ++side) {
+        // the stage kernel's order and precision: parts summed in order, times 1 / nw_den
+        const fdlb::InstDev& d = S->inst_h[instance];
+        if (S->precision == FDLB_FP32) {
+            const float* pp = reinterpret_cast<const float*>(parts.data()) + side * P;
+            float sum = 0.f;
+            for (int p = 0; p < P; ++p) sum += pp[p];
+            nw[side] = (double)(sum * d.f_nw_iden[side]);
+        } else {
+            const double* pp = reinterpret_cast<const double*>(parts.data()) + side * P;
+            double sum = 0.0;
+            for (int p = 0; p < P; ++p) sum += pp[p];
+            nw[side] = sum * d.nw_iden[side];
+        }
+    }
     for (int c = 0; c < N; ++c) {
         const double* r = &ca[(size_t)c * fdlb::kCA];
         if (nbar) nbar[c] = r[10];
@@ -1146,7 +1213,13 @@ int fdlb_load(fdlb_handle h, const char* path) {
     std::fclose(fp);
     if (rc) return rc;
     S->prev_valid = false;
-    return recompute ? fdlb::launch_moments_all(*S, 0) : FDLB_OK;
+    if (recompute) return fdlb::launch_moments_all(*S, 0);
+    const long long nd = (long long)S->total_cells * S->M.slices;
+    if (S->precision == FDLB_FP32)
+        fdlb::launch_dens_from_sums<float>(S->sums[0], (float*)S->dens[0], nd, S->stream);
+    else
+        fdlb::launch_dens_from_sums<double>(S->sums[0], (double*)S->dens[0], nd, S->stream);
+    return fdlb::cuda_status(cudaGetLastError());
 }
 
 const char* fdlb_error_string(int code) {
@@ -1214,6 +1287,17 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
     if (slice_k) *slice_k = S->KS;
     if (threads) *threads = S->threads;
     return rc;
+}
+
+int fdlb_set_closure_cells(fdlb_handle h, int cells) {
+    Solver* S = SOL(h);
+    if (!S || cells < 1 || cells > fdlb::kClosureCells) return FDLB_EINVAL;
+    S->closure_cells = cells;
+    if (S->gexec) {
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+    }
+    return fdlb::upload_items(*S);
 }
 
 int64_t fdlb_launch_count(fdlb_handle h) {

@@ -57,6 +57,7 @@ Grid make_grid(int geometry, double R_in, double R_out, double sigma, int N, dou
 struct FMBand {
     int width = 0;                 // stored entries per row
     std::vector<int> lo;           // first column of each row
+    std::vector<int> cnt;          // stored nonzero extent of each row (a multiple of 4, <= width)
     std::vector<double> W;         // [N][width], zero padded
 };
 FMBand fm_band(int geometry, const Grid& g, double sigma);

@@ -6,6 +6,8 @@
 //                      momentum slice (a range of k) is one contiguous run per cell.
 //   sums[cell][slice][13]  FP64 raw quadrature sums (Eq. mom_quad) of the populations,
 //                      one partial per momentum slice (summed by the consumer in a fixed order).
+//   dens[cell][slice]  the slice densities (sum 0) in the populations' precision, read by the
+//                      FM band sums.
 //   ca[cell][12]       FP64 closure record: n, u1, u2, u3, T, q1, q2, q3, P12, chi, nbar, 0.
 //
 // Per SSP-RK3 stage (Sec. III) two launches:
@@ -29,6 +31,8 @@ constexpr int kCA = 12;
 constexpr int kGeo = 6;            // per cell: R_c, 1/(dR/ds), A_+/V, A_-/V, force factor, V
 constexpr int kMaxE = 8;           // expansion coefficients per axis (N <= 7)
 constexpr int kMaxRed = 32;        // warps per block
+constexpr int kClosureCells = 28;  // own cells per closure item (reach: 32 cells)
+constexpr int kWallParts = 8;      // closure work items per wall (parts of the momentum set)
 
 struct InstDev {
     int n_cells;
@@ -41,6 +45,10 @@ struct InstDev {
     double sigma, bfac, etafac;    // sigma, 2 pi sigma^3 / 3, pi sigma^3 / 6
     double dt, ds;
     double nw_den[2];              // sum over incoming momenta of |p_R| g_wall
+    double nw_iden[2];             // 1 / nw_den
+    // FP32 copies for FP32 populations
+    float f_sigma, f_bfac, f_etafac, f_ids, f_dt;
+    float f_nw_iden[2];
 };
 
 struct MomSet {
@@ -57,16 +65,19 @@ struct StageArgs {
     void* f_out;
     const void* rec;               // per-cell collision records of f_in (T), [cell][rec_stride]
     int rec_stride;
-    const double* nw;              // [instance][2] wall densities of f_in
+    const void* nwp;               // [instance][2][kWallParts] outgoing wall fluxes of f_in (T)
     double* sums_out;              // raw sums of f_out
+    void* dens_out;                // per-slice densities of f_out (T), [cell][slice]
     const int4* items;             // (instance, first cell, cells, slice)
     const int* n_items;
     const InstDev* inst;
     const double* tab;
-    const double* geo;             // [cell][kGeo]
-    const double* gw;              // [instance][2][nR + n2 + n3] wall Maxwellians per axis
+    const void* geoT;              // [cell][kGeo] in T
+    const void* gwT;               // [instance][2][nR + n2 + n3] wall Maxwellians per axis, in T
     int* err;
     double a, b;                   // f_out = a f_n + b (f_in + dt L(f_in))
+    float fa, fb;                  // the same in FP32
+    int wall_parts;
     int mode;                      // 0: RK stage; 1: write L(f_in) to f_out
     int B;                         // cells per tile
     int use_bulk;                  // stage the tile with cp.async.bulk
@@ -74,23 +85,25 @@ struct StageArgs {
 
 struct ClosureArgs {
     const double* sums;
-    const void* f_in;              // populations (T), for the wall densities
-    double* ca;                    // FP64 closure records
+    const void* dens;              // per-slice densities (T), [cell][slice], for the FM bands
+    const void* f_in;              // populations (T), for the wall fluxes
+    double* ca;                    // FP64 closure records (written with write_ca)
     void* rec;                     // per-cell collision records (T)
     int rec_stride;
-    double* nw;                    // [instance][2] wall densities
-    const int4* items;             // (instance, first cell, cells, 0)
+    void* nwp;                     // [instance][2][kWallParts] outgoing wall fluxes (T)
+    const int4* items;             // (instance, first cell, cells, 0) or (instance, -, part, 1 + side)
     const int* n_items;
     const InstDev* inst;
     const void* band;              // FM band values (T)
-    const int* band_lo;            // per global cell
-    const double* tab;
-    const void* tabT;              // the same tables in the populations' precision
-    const double* geo;
-    const double* gw;
+    const int* band_lo;            // per global cell: first column, stored extent
+    const void* tabT;              // the tables in the populations' precision
+    const void* geoT;              // [cell][kGeo] in T
     int slices;
-    int max_cells;                 // cells per closure item
-    int max_union;                 // capacity of the shared n buffer
+    int max_union;                 // capacity of the shared density buffer
+    int wall_parts;
+    int write_ca;
+    int wst_elems;                 // capacity of the staged band rows (elements)
+    int* err;                      // set when a bulk copy never completes
 };
 
 }  // namespace fdlb

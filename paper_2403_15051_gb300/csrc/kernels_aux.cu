@@ -12,7 +12,8 @@ namespace fdlb {
 // Raw quadrature sums (Eq. mom_quad) of the populations of whole cells; written into slice 0
 // of the partial-sum array, the other slices are cleared.
 template <typename T>
-__global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sums, const int4* __restrict__ items,
+__global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sums, T* __restrict__ dens,
+                               const int4* __restrict__ items,
                                const int* __restrict__ n_items, const InstDev* __restrict__ inst,
                                const double* __restrict__ tab, MomSet M) {
     __shared__ double red[kMaxRed][kSums];
@@ -20,6 +21,7 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
     const int nit = *n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const int4 w = items[it];
+        if (w.w != 0) continue;  // wall items of the closure list
         const InstDev I = inst[w.x];
         for (int cl = 0; cl < w.z; ++cl) {
             const int c = w.y + cl;
@@ -58,6 +60,11 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
                 double* dst = sums + ((long long)(I.cell_off + c) * M.slices) * kSums;
                 dst[threadIdx.x] = s;
                 for (int sl = 1; sl < M.slices; ++sl) dst[sl * kSums + threadIdx.x] = 0.0;
+                if (threadIdx.x == 0) {
+                    T* dd = dens + (long long)(I.cell_off + c) * M.slices;
+                    dd[0] = (T)s;
+                    for (int sl = 1; sl < M.slices; ++sl) dd[sl] = T(0);
+                }
             }
             __syncthreads();
         }
@@ -65,111 +72,309 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
 }
 
 // ------------------------------------------------------------------------------ closure
-// Per cell, once per stage (one thread per cell in FP64, warps for the band sums):
-//  * n, u, T, q, P_12 from the raw sums (Eq. macro_def);
-//  * nbar over the stored FM band (Eq. fm, n = 0 outside the domain), chi = chi_SET(pi sigma^3
-//    nbar / 6) (Eqs. chi, chi_ret), or chi at the local density;
-//  * the J1 gradients by the five-point stencils (two halo cells each side are recomputed),
-//    mu, Pr, tau (Eqs. viscosity, prandtl, tau), the covariant strain, the Shakhov coefficient;
-//  * the per-axis equilibrium vectors g_R, g_2, g_3 (Sec. III.C) by their recurrences;
-//  * at the two wall items, the wall density n_w from zero net mass flux (diffuse walls).
-// Output: the FP64 closure record and the per-cell collision record in the populations'
-// precision, [20 scalars | g_R | g_2 | g_3].
-__host__ __device__ inline size_t closure_smem_bytes(int max_cells, int max_union, int tsize) {
-    const size_t CH = (size_t)max_cells + 4;
-    return (CH * kSums + 9 * CH + 32) * sizeof(double) + ((size_t)max_cells * 4 * kMaxE + max_union) * tsize + 16;
+// Per cell, once per stage.  A cell item covers up to kClosureCells own cells and the two
+// stencil cells on each side ("reach", at most 32 cells); one lane per reach cell for the
+// macroscopic fields, so that no arithmetic is spread thinly over lanes:
+//  * n, u, T (Eq. macro_def) of every reach cell from the FP64 raw sums, in the wide type
+//    (FP64, or double-float for FP32 populations); q and P_12 of the own cells;
+//  * warps 1..3 meanwhile sum the FM bands (Eq. fm, n = 0 outside the domain) from the slice
+//    densities staged in shared memory; chi = chi_SET(pi sigma^3 nbar / 6) (Eqs. chi, chi_ret),
+//    or chi at the local density;
+//  * the J1 gradients (Eq. j1) as stencils of logarithms of ratios to the own cell, exact
+//    because the stencil weights sum to zero:  sum_q w_q ln(n_q^2 chi_q T_q) = sum_q w_q
+//    [2 log1p(dn_q / n) + log1p(dchi_q / chi) + log1p(dT_q / T)], the differences taken in the
+//    wide type; velocity gradients from wide differences;
+//  * mu, Pr, tau (Eqs. viscosity, prandtl, tau), the covariant strain and the Shakhov
+//    coefficient; the recurrences of the expansion coefficients of the equilibria (Sec. III.C;
+//    warp = axis, lane = cell) and the per-axis vectors g_2, g_R, g_3 (whole block).
+// With write_ca the FP64 closure record (n, u, T, q, P_12, chi, nbar) is written as well (the
+// moments and closure queries; not needed by the stage itself).
+// Wall items (kind 1 + side, part): the block sums the outgoing flux of one part of the momenta
+// at one wall; the stage kernel forms n_w from the parts (diffuse walls, zero net mass flux).
+// Output: the per-cell collision record in the populations' precision, [20 scalars | g_2 | g_R
+// | g_3].
+__host__ __device__ inline int closure_tab_elems(int nR, int n2, int n3) {
+    return 4 * kMaxE + 2 + (nR + n2 + n3) * kMaxE + 2 * nR + n2 + n3;
+}
+// dynamic shared memory: [staged band rows | tables | band-union densities]
+__host__ __device__ inline size_t closure_smem_bytes(int nR, int n2, int n3, int max_union, int wst_elems, int tsize) {
+    return (size_t)wst_elems * tsize + ((size_t)closure_tab_elems(nR, n2, n3) + (size_t)max_union) * tsize + 16;
+}
+
+// Position q of the five-point derivative stencil of cell c (the stencils of stencil5).
+template <typename R>
+__device__ __forceinline__ void stencil5_at(int c, int N, int q, int& cell, R& w) {
+    const R k = R(1) / R(12);
+    if (c >= 2 && c <= N - 3) {
+        cell = c - 2 + q;
+        w = q == 0 ? k : q == 1 ? R(-8) * k : q == 2 ? R(0) : q == 3 ? R(8) * k : -k;
+    } else if (c == 0) {
+        cell = q;
+        w = q == 0 ? R(-25) * k : q == 1 ? R(48) * k : q == 2 ? R(-36) * k : q == 3 ? R(16) * k : R(-3) * k;
+    } else if (c == 1) {
+        cell = q;
+        w = q == 0 ? R(-3) * k : q == 1 ? R(-10) * k : q == 2 ? R(18) * k : q == 3 ? R(-6) * k : k;
+    } else if (c == N - 2) {
+        cell = N - 1 - q;
+        w = q == 0 ? R(3) * k : q == 1 ? R(10) * k : q == 2 ? R(-18) * k : q == 3 ? R(6) * k : -k;
+    } else {
+        cell = N - 1 - q;
+        w = q == 0 ? R(25) * k : q == 1 ? R(-48) * k : q == 2 ? R(36) * k : q == 3 ? R(-16) * k : R(3) * k;
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
+__device__ __forceinline__ T inst_param(double d, float f) {
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
+    using W = Wide<T>;
+    __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells, wide
+    __shared__ T s_chi[32], snb[32];               // reach cells: chi, band density
+    __shared__ int sblo[32], scnt[32];             // reach cells: first band column, stored extent
+    __shared__ T sq[4][32];                        // own cells: q1, q2, q3, P_12
+    __shared__ T ecs[kClosureCells][4][kMaxE];     // own cells: expansion coefficients
+    __shared__ T red[4];
+    __shared__ T sgp[5][kClosureCells][5];        // gradient terms per own cell and stencil position
+    __shared__ __align__(8) uint64_t cbar;         // completion of the band-row copy
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5, NT = blockDim.x;
-    const int CH = A.max_cells + 4;
-    double* ssum = reinterpret_cast<double*>(smem_raw);  // [CH][13] raw sums of the cells in reach
-    double* cb = ssum + CH * kSums;                       // [9][CH]: n u0 u1 u2 T chi phi1 phi2 nbar
-    double* red = cb + 9 * CH;                            // [32]
-    T* ec = reinterpret_cast<T*>(red + 32);               // [max_cells][4][kMaxE]
-    T* nbuf = ec + (size_t)A.max_cells * 4 * kMaxE;
-    const T* tabT = reinterpret_cast<const T*>(A.tabT);   // the tables in the populations' precision
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
     const T* band = reinterpret_cast<const T*>(A.band);
+    const T* dens = reinterpret_cast<const T*>(A.dens);
     const T* fin_all = reinterpret_cast<const T*>(A.f_in);
+    const T* geoT = reinterpret_cast<const T*>(A.geoT);
     T* rec_all = reinterpret_cast<T*>(A.rec);
-    const double* tab = A.tab;
-    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Np = M.Np, QR = nR / 2;
+    T* nwp = reinterpret_cast<T*>(A.nwp);
+    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Np = M.Np, QR = nR / 2, slices = A.slices;
+    // staged band rows, then the tables in the populations' precision
+    T* wst = reinterpret_cast<T*>(smem_raw);
+    T* ha = wst + A.wst_elems;
+    T* hb = ha + kMaxE;
+    T* ihb = hb + kMaxE + 1;  // 1 / hb
+    T* h0t = ihb + kMaxE + 1;
+    T* GR = h0t + kMaxE;
+    T* G2 = GR + nR * kMaxE;
+    T* G3 = G2 + n2 * kMaxE;
+    T* pRt = G3 + n3 * kMaxE;
+    T* wRt = pRt + nR;
+    T* w2t = wRt + nR;
+    T* w3t = w2t + n2;
+    T* nbuf = ha + closure_tab_elems(nR, n2, n3);  // densities of the band union of an item
+    {
+        const T* tabT = reinterpret_cast<const T*>(A.tabT);
+        for (int e = tid; e < kMaxE; e += NT) {
+            ha[e] = tabT[M.o_ha + e];
+            h0t[e] = tabT[M.o_h0 + e];
+        }
+        for (int e = tid; e <= kMaxE; e += NT) {
+            hb[e] = tabT[M.o_hb + e];
+            ihb[e] = hb[e] != T(0) ? T(1) / hb[e] : T(0);
+        }
+        if (tid == 0) {
+            mbar_init(&cbar, 1);
+            fence_mbar_init();
+        }
+        for (int e = tid; e < nR * kMaxE; e += NT) GR[e] = tabT[M.o_GR + e];
+        for (int e = tid; e < n2 * kMaxE; e += NT) G2[e] = tabT[M.o_G2 + e];
+        for (int e = tid; e < n3 * kMaxE; e += NT) G3[e] = tabT[M.o_G3 + e];
+        for (int e = tid; e < nR; e += NT) {
+            pRt[e] = tabT[M.o_pR + e];
+            wRt[e] = tabT[M.o_wR + e];
+        }
+        for (int e = tid; e < n2; e += NT) w2t[e] = tabT[M.o_w2 + e];
+        for (int e = tid; e < n3; e += NT) w3t[e] = tabT[M.o_w3 + e];
+        __syncthreads();
+    }
+    uint32_t phase = 0;
     const int nit = *A.n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const int4 w = A.items[it];
         const InstDev I = A.inst[w.x];
-        const int c0 = w.y, cnt = w.z, N = I.n_cells;
-        // cells whose closure the gradients need: two on each side, and the five cells next to a
-        // wall for the one-sided stencils (nh <= max(cnt + 4, 5) <= max_cells + 4)
-        const int h0 = max(0, min(c0 - 2, N - 5)), h1 = min(N, max(c0 + cnt + 2, 5)), nh = h1 - h0;
-        const double* S = A.sums + (long long)I.cell_off * A.slices * kSums;
-        double* ca = A.ca + (long long)I.cell_off * kCA;
-        // ---- 1. raw sums of the cells in reach (summed over the momentum slices in a fixed
-        // order) and the densities of the union of their FM bands
-        for (int e = tid; e < nh * kSums; e += NT) {
-            const int t = e / kSums, q = e % kSums;
-            const double* src = S + (long long)(h0 + t) * A.slices * kSums + q;
-            double v = 0.0;
-            for (int sl = 0; sl < A.slices; ++sl) v += src[sl * kSums];
-            ssum[t * kSums + q] = v;
-        }
-        int jlo = 0, jhi = -1;
-        if (!I.chi_local) {
-            jlo = A.band_lo[I.cell_off + h0];
-            jhi = min(N - 1, A.band_lo[I.cell_off + h1 - 1] + I.band_w - 1);
-            const int nu = min(jhi - jlo + 1, A.max_union);
-            for (int j = tid; j < nu; j += NT) {
-                const double* src = S + (long long)(jlo + j) * A.slices * kSums;
-                double nj = 0.0;
-                for (int sl = 0; sl < A.slices; ++sl) nj += src[sl * kSums];
-                nbuf[j] = (T)nj;
+        const int N = I.n_cells;
+        if (w.w != 0) {
+            // ---- one part of the outgoing flux through a wall: sum_out |p_R| w vhat_wall
+            const int side = w.w - 1, part = w.z, P = A.wall_parts;
+            const int mlo = (int)((long long)Np * part / P), mhi = (int)((long long)Np * (part + 1) / P);
+            const T* fin = fin_all + I.f_off;
+            const long long st = side == 0 ? (long long)Np : -(long long)Np;
+            const long long base = side == 0 ? 0LL : (long long)(N - 1) * Np;
+            T acc = T(0);
+            for (int m0 = mlo + tid; m0 < mhi; m0 += 4 * NT) {
+                // four momenta per pass so that their sixteen loads are in flight together
+                T fv[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int m = min(m0 + u * NT, mhi - 1);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) fv[u][r] = fin[base + m + r * st];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int m = m0 + u * NT;
+                    if (m >= mhi) continue;
+                    const int k = m / (nR * n2), rem = m % (nR * n2), i = rem / n2, j = rem % n2;
+                    const T pr = pRt[i];
+                    if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
+                    const T wm = wRt[i] * w2t[j] * w3t[k], iw = T(1) / wm;
+                    const T f0 = fv[u][0], f1 = fv[u][1], f2 = fv[u][2], f3 = fv[u][3];
+                    const T g1 = T(4) * f0 - T(6) * f1 + T(4) * f2 - f3;
+                    const T g2 = T(10) * f0 - T(20) * f1 + T(15) * f2 - T(4) * f3;
+                    const T vh = weno5(f2 * iw, f1 * iw, f0 * iw, g1 * iw, g2 * iw);
+                    acc += fabs(pr) * wm * vh;
+                }
             }
+            acc = warp_sum(acc);
+            if (lane == 0) red[warp] = acc;
+            __syncthreads();
+            if (tid == 0) nwp[((long long)w.x * 2 + side) * P + part] = (red[0] + red[1]) + (red[2] + red[3]);
+            __syncthreads();
+            continue;
+        }
+        const int c0 = w.y, cnt = w.z;
+        // reach: the own cells, two on each side, and the five cells next to a wall
+        const int h0 = max(0, min(c0 - 2, N - 5)), h1 = min(N, max(c0 + cnt + 2, 5)), nh = h1 - h0;
+        const double* S = A.sums + (long long)I.cell_off * slices * kSums;
+        double* ca = A.ca + (long long)I.cell_off * kCA;
+        const int rs = A.rec_stride;
+        T* rec = rec_all + (long long)I.cell_off * rs;
+        // ---- 1. every global load of the item at once: the raw sums of the reach cells and the
+        // geometry of the own cells (warp 0, lane per cell), the band rows of the reach cells
+        // (bulk copies of their stored extents, issued by warp 0) and the densities of the union
+        // of the bands (all threads)
+        double s[kSums];
+        T geo0 = T(1), geo1 = T(0);
+        if (warp == 0 && lane < nh) {
+            const double* src = S + (long long)(h0 + lane) * slices * kSums;
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) s[q] = src[q];
+            for (int sl = 1; sl < slices; ++sl)
+#pragma unroll
+                for (int q = 0; q < kSums; ++q) s[q] += src[sl * kSums + q];
+        }
+        if (warp == 0 && lane < cnt) {
+            const T* gc = geoT + (long long)(I.cell_off + c0 + lane) * kGeo;
+            geo0 = gc[0];
+            geo1 = gc[1];
+        }
+        int jlo = 0, nu = 0;
+        const bool staged = !I.chi_local && nh * I.band_w <= A.wst_elems;
+        if (!I.chi_local) {
+            const int2* bl = reinterpret_cast<const int2*>(A.band_lo) + I.cell_off;
+            const int2 first = bl[h0], last = bl[h1 - 1];
+            jlo = first.x;
+            // columns grow with the row, and extents are rounded up by at most 3
+            const int jhi = min(N - 1, last.x + last.y - 1 + 3);
+            nu = min(jhi - jlo + 1, A.max_union);
+            if (warp == 0) {
+                int2 mine = make_int2(0, 0);
+                if (lane < nh) mine = bl[h0 + lane];
+                if (lane < nh) {
+                    sblo[lane] = mine.x;
+                    scnt[lane] = mine.y;
+                }
+                if (staged) {
+                    // one bulk copy per row, of its stored extent (a multiple of 16 bytes)
+                    int bytes = lane < nh ? mine.y * (int)sizeof(T) : 0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        mbar_expect_tx(&cbar, (uint32_t)bytes);
+                    }
+                    __syncwarp();
+                    if (lane < nh && mine.y > 0)
+                        bulk_g2s(wst + (long long)lane * I.band_w, band + I.band_off + (long long)(h0 + lane) * I.band_w,
+                                 (uint32_t)(mine.y * sizeof(T)), &cbar);
+                }
+            }
+            const T* nd = dens + ((long long)I.cell_off + jlo) * slices;
+            for (int j0 = tid; j0 < nu; j0 += 4 * NT) {
+                // four loads in flight per thread
+                T v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = min(j0 + u * NT, nu - 1);
+                    v[u] = nd[(long long)j * slices];
+                    for (int sl = 1; sl < slices; ++sl) v[u] += nd[(long long)j * slices + sl];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u * NT < nu) nbuf[j0 + u * NT] = v[u];
+            }
+        }
+        if (staged) {
+            const bool ok = mbar_wait_bounded(&cbar, phase);
+            // every thread takes the same exit: a block-wide vote on the outcome
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(A.err, 2);
+                mbar_wait_bounded(&cbar, phase);  // bounded wait for the copy still in flight
+                return;
+            }
+            phase ^= 1u;
         }
         __syncthreads();
-        // ---- 2. n, u, T (Eq. macro_def) per cell in reach; q and P_12 of the own cells
-        for (int t = tid; t < nh; t += NT) {
-            const int c = h0 + t;
-            const double* s = ssum + t * kSums;
-            const double n = s[0], in = 1.0 / n;
-            const double u0 = s[1] * in, u1 = s[2] * in, u2 = s[3] * in;
-            const double tr = s[4] + s[5] + s[6];
-            const double uu = u0 * u0 + u1 * u1 + u2 * u2;
-            const double Tc = (tr - n * uu) * in * (1.0 / 3.0);
-            cb[0 * CH + t] = n;
-            cb[1 * CH + t] = u0;
-            cb[2 * CH + t] = u1;
-            cb[3 * CH + t] = u2;
-            cb[4 * CH + t] = Tc;
-            if (I.chi_local) {
-                cb[5 * CH + t] = chi_cs(I.etafac * n);
-                cb[8 * CH + t] = n;
+        // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells;
+        // warps 1..3: FM band sums of the reach cells from shared memory
+        if (warp == 0) {
+            if (lane < nh) {
+                const int c = h0 + lane;
+                const W n = w_from(s[0], (T*)nullptr);
+                const W u0 = w_div(w_from(s[1], (T*)nullptr), n);
+                const W u1 = w_div(w_from(s[2], (T*)nullptr), n);
+                const W u2 = w_div(w_from(s[3], (T*)nullptr), n);
+                const W tr = w_add(w_add(w_from(s[4], (T*)nullptr), w_from(s[5], (T*)nullptr)), w_from(s[6], (T*)nullptr));
+                const W uu = w_add(w_add(w_mul(u0, u0), w_mul(u1, u1)), w_mul(u2, u2));
+                const W Tc = w_div(w_sub(tr, w_mul(n, uu)), w_scale(n, T(3)));
+                sw_n[lane] = n;
+                sw_u[0][lane] = u0;
+                sw_u[1][lane] = u1;
+                sw_u[2][lane] = u2;
+                sw_T[lane] = Tc;
+                if (c >= c0 && c < c0 + cnt) {
+                    // q and P_12 in the populations' precision (they enter only the Shakhov
+                    // factor and the diagnostics)
+                    const T tn = w_hi(n), t0 = w_hi(u0), t1 = w_hi(u1), t2 = w_hi(u2), ttr = w_hi(tr), tuu = w_hi(uu);
+                    const T s4 = (T)s[4], s5 = (T)s[5], s6 = (T)s[6], s7 = (T)s[7], s8 = (T)s[8], s9 = (T)s[9];
+                    const T m0 = s4 * t0 + s7 * t1 + s8 * t2;
+                    const T m1 = s7 * t0 + s5 * t1 + s9 * t2;
+                    const T m2 = s8 * t0 + s9 * t1 + s6 * t2;
+                    sq[0][c - c0] = T(0.5) * ((T)s[10] - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
+                    sq[1][c - c0] = T(0.5) * ((T)s[11] - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
+                    sq[2][c - c0] = T(0.5) * ((T)s[12] - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
+                    sq[3][c - c0] = s7 - tn * t0 * t1;
+                    if (A.write_ca) {
+                        // the FP64 closure record (queries only)
+                        const double dn = s[0], in = 1.0 / dn;
+                        const double v0 = s[1] * in, v1 = s[2] * in, v2 = s[3] * in;
+                        const double dtr = s[4] + s[5] + s[6];
+                        const double vv = v0 * v0 + v1 * v1 + v2 * v2;
+                        const double dT = (dtr - dn * vv) * in * (1.0 / 3.0);
+                        const double d0 = s[4] * v0 + s[7] * v1 + s[8] * v2;
+                        const double d1 = s[7] * v0 + s[5] * v1 + s[9] * v2;
+                        const double d2 = s[8] * v0 + s[9] * v1 + s[6] * v2;
+                        double* r = ca + (long long)c * kCA;
+                        r[0] = dn;
+                        r[1] = v0;
+                        r[2] = v1;
+                        r[3] = v2;
+                        r[4] = dT;
+                        r[5] = 0.5 * (s[10] - 2.0 * d0 - v0 * dtr + 2.0 * dn * vv * v0);
+                        r[6] = 0.5 * (s[11] - 2.0 * d1 - v1 * dtr + 2.0 * dn * vv * v1);
+                        r[7] = 0.5 * (s[12] - 2.0 * d2 - v2 * dtr + 2.0 * dn * vv * v2);
+                        r[8] = s[7] - dn * v0 * v1;  // P_12
+                        r[11] = 0.0;
+                    }
+                }
             }
-            if (c >= c0 && c < c0 + cnt) {
-                const double m0 = s[4] * u0 + s[7] * u1 + s[8] * u2;
-                const double m1 = s[7] * u0 + s[5] * u1 + s[9] * u2;
-                const double m2 = s[8] * u0 + s[9] * u1 + s[6] * u2;
-                double* r = ca + (long long)c * kCA;
-                r[0] = n;
-                r[1] = u0;
-                r[2] = u1;
-                r[3] = u2;
-                r[4] = Tc;
-                r[5] = 0.5 * (s[10] - 2.0 * m0 - u0 * tr + 2.0 * n * uu * u0);
-                r[6] = 0.5 * (s[11] - 2.0 * m1 - u1 * tr + 2.0 * n * uu * u1);
-                r[7] = 0.5 * (s[12] - 2.0 * m2 - u2 * tr + 2.0 * n * uu * u2);
-                r[8] = s[7] - n * u0 * u1;  // P_12
-                r[11] = 0.0;
-            }
-        }
-        // ---- 3. Fischer-Methfessel density (Eq. fm) and chi (Eqs. chi, chi_ret): a warp per cell
-        if (!I.chi_local) {
-            for (int t = warp; t < nh; t += nwarps) {
+        } else if (!I.chi_local) {
+            for (int t = warp - 1; t < nh; t += 3) {
                 const int c = h0 + t;
-                const int lo = A.band_lo[I.cell_off + c];
-                const int kmax = min(I.band_w, jhi - lo + 1);
-                const T* Wr = band + I.band_off + (long long)c * I.band_w;
+                const int lo = sblo[t];
+                const int kmax = min(min(scnt[t], N - lo), nu - (lo - jlo));
+                const T* Wr = staged ? wst + (long long)t * I.band_w : band + I.band_off + (long long)c * I.band_w;
                 const T* nb = nbuf + (lo - jlo);
                 T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
                 int k = lane;
@@ -180,190 +385,194 @@ __global__ void __launch_bounds__(256) closure_kernel(ClosureArgs A, MomSet M) {
                     a3 += Wr[k + 96] * nb[k + 96];
                 }
                 for (; k < kmax; k += 32) a0 += Wr[k] * nb[k];
-                const T acc = warp_sum((a0 + a1) + (a2 + a3));
-                if (lane == 0) {
-                    cb[8 * CH + t] = (double)acc;
-                    cb[5 * CH + t] = chi_cs(I.etafac * (double)acc);
-                }
+                const T tot = warp_sum((a0 + a1) + (a2 + a3));
+                if (lane == 0) snb[t] = tot;
             }
         }
         __syncthreads();
-        for (int t = tid; t < nh; t += NT) {
-            const double n = cb[t], Tc = cb[4 * CH + t], chi = cb[5 * CH + t];
-            cb[6 * CH + t] = log(n * n * chi * Tc);
-            cb[7 * CH + t] = log(Tc);
+        // ---- 3. chi of the reach cells (warp 0); the gradient terms, one thread per own cell and
+        // stencil position (logarithms of ratios to the own cell, differences in the wide type)
+        if (warp == 0 && lane < nh) {
+            // chi in the wide type, rounded once: J1 scales with b rho chi, and near finely
+            // resolved walls J1 is large enough that a few roundings of chi show in the RHS
+            const T etafac = inst_param<T>(I.etafac, I.f_etafac);
+            const W eta = w_scale(w_from_t(I.chi_local ? w_hi(sw_n[lane]) : snb[lane]), etafac);
+            const W om = w_sub(w_from_t(T(1)), eta);
+            const W om3 = w_mul(w_mul(om, om), om);
+            s_chi[lane] = w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
         }
         __syncthreads();
-        // ---- 4. own cells: warp job 0 = gradients, transport, strain (Eqs. j1, viscosity,
-        // prandtl, tau); jobs 1..4 = expansion coefficients of the equilibria (Sec. III.C)
-        const int rs = A.rec_stride;
-        T* rec = rec_all + (long long)I.cell_off * rs;
-        for (int job = warp; job < 5; job += nwarps) {
-            for (int t = lane; t < cnt; t += 32) {
-                const int c = c0 + t, lt = c - h0;
-                const double n = cb[lt], u0 = cb[CH + lt], u1 = cb[2 * CH + lt], u2 = cb[3 * CH + lt];
-                const double Tc = cb[4 * CH + lt], chi = cb[5 * CH + lt];
-                if (job == 0) {
-                    int idx[5];
-                    double sw[5];
-                    stencil5(c, N, idx, sw);
-                    const double* gc = A.geo + (long long)(I.cell_off + c) * kGeo;
-                    const double R = gc[0], sc = gc[1] / I.ds;
-                    double X = 0.0, Y = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
-                    for (int q = 0; q < 5; ++q) {
-                        const int k = idx[q] - h0;
-                        X += sw[q] * cb[6 * CH + k];
-                        Y += sw[q] * cb[7 * CH + k];
-                        d0 += sw[q] * cb[1 * CH + k];
-                        d1 += sw[q] * cb[2 * CH + k];
-                        d2 += sw[q] * cb[3 * CH + k];
-                    }
-                    X *= sc;
-                    Y *= sc;
-                    d0 *= sc;
-                    d1 *= sc;
-                    d2 *= sc;
-                    // transport, strain and Shakhov coefficient in the populations' precision
-                    // (they are stored in it); FP64 above only for the gradients of logarithms
-                    using C = T;
-                    const C cn = (C)n, cT = (C)Tc, cchi = (C)chi, iR = (C)(1.0 / R);
-                    const C cu0 = (C)u0, cu1 = (C)u1, cu2 = (C)u2, sg = (C)I.sigma;
-                    const C br = (C)I.bfac * cn, x = br * cchi;
-                    const C pi = C(3.14159265358979323846);
-                    const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
-                                 (C(1) / cchi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
-                    const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
-                                 (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
-                    const C itau = cn * cT / mu;
-                    C S11, S22, S01, S02, div;
-                    const C cd0 = (C)d0, cd1 = (C)d1, cd2 = (C)d2;
-                    if (I.geometry == 0) {
-                        S11 = cu0 * iR;
-                        S22 = C(0);
-                        S01 = C(0.5) * (cd1 - cu1 * iR);
-                        S02 = C(0.5) * cd2;
-                        div = cd0 + cu0 * iR;
-                    } else {
-                        S11 = S22 = cu0 * iR;
-                        S01 = C(0.5) * (cd1 - cu1 * iR);
-                        S02 = C(0.5) * (cd2 - cu2 * iR);
-                        div = cd0 + C(2) * cu0 * iR;
-                    }
-                    const double* rc = ca + (long long)c * kCA;
-                    T* ct = rec + (long long)c * rs;
-                    const C iT = C(1) / cT;
-                    ct[0] = cn;
-                    ct[1] = cu0;
-                    ct[2] = cu1;
-                    ct[3] = cu2;
-                    ct[4] = iT;
-                    ct[5] = itau;
-                    ct[6] = (C(1) - Pr) * iT * iT / cn;
-                    ct[7] = (T)rc[5];
-                    ct[8] = (T)rc[6];
-                    ct[9] = (T)rc[7];
-                    ct[10] = x;
-                    ct[11] = (T)X;
-                    ct[12] = (T)Y;
-                    ct[13] = cd0;
-                    ct[14] = S11;
-                    ct[15] = S22;
-                    ct[16] = S01;
-                    ct[17] = S02;
-                    ct[18] = T(0);
-                    ct[19] = div;
-                    ca[(long long)c * kCA + 9] = chi;
-                    ca[(long long)c * kCA + 10] = cb[8 * CH + lt];
-                } else if (job <= 2) {
-                    // half range, half line of sign s (job 1: +, job 2: -), v = s u_R:
-                    //   e_0 = h_0 (1 + erf(v/sqrt(2T)))/2,
-                    //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
-                    //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)]
-                    // (in the populations' precision)
-                    using C = T;
-                    T* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
-                    const T* ha = tabT + M.o_ha;
-                    const T* hb = tabT + M.o_hb;
-                    const T* h0t = tabT + M.o_h0;
-                    for (int l = 0; l < kMaxE; ++l) e[l] = C(0);
-                    const C cT = (C)Tc, v = job == 1 ? (C)u0 : -(C)u0;
-                    const C G0 = exp(-v * v / (C(2) * cT)) / sqrt(C(6.283185307179586477) * cT);
-                    e[0] = h0t[0] * C(0.5) * (C(1) + erf(v / sqrt(C(2) * cT)));
-                    C run = C(0);
-                    for (int l = 0; l < M.NR; ++l) {
-                        const C em1 = l ? e[l - 1] : C(0);
-                        const C bl = l ? hb[l] : C(0);
-                        const C val = (v - ha[l]) * e[l] + (cT - C(1)) * bl * em1 +
-                                      cT * h0t[l] * (G0 - run * C(0.39894228040143267794));
-                        e[l + 1] = val / hb[l + 1];
-                        run += h0t[l] * e[l];
-                    }
-                } else {
-                    // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                    using C = T;
-                    T* e = ec + ((long long)t * 4 + (job - 1)) * kMaxE;
-                    for (int l = 0; l < kMaxE; ++l) e[l] = C(0);
-                    const C u = job == 3 ? (C)u1 : (C)u2, cT = (C)Tc;
-                    const int Nax = job == 3 ? M.N2 : M.N3;
-                    e[0] = C(1);
-                    if (Nax >= 1) e[1] = u;
-                    for (int l = 1; l < Nax; ++l) e[l + 1] = u * e[l] + C(l) * (cT - C(1)) * e[l - 1];
-                }
+        for (int e = tid; e < cnt * 5; e += NT) {
+            const int t = e / 5, q = e % 5, c = c0 + t, lt = c - h0;
+            int cq;
+            T wq;
+            stencil5_at<T>(c, N, q, cq, wq);
+            const int k = cq - h0;
+            const W nw = sw_n[lt], Tw = sw_T[lt];
+            const T lT = log1p(ratio_fast(w_hi(w_sub(sw_T[k], Tw)), w_hi(Tw)));
+            const T ln = log1p(ratio_fast(w_hi(w_sub(sw_n[k], nw)), w_hi(nw)));
+            // ln chi_q - ln chi_c from the packing-fraction difference alone, since
+            // ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of chi itself)
+            const T etaf = inst_param<T>(I.etafac, I.f_etafac);
+            const T dnb = I.chi_local ? w_hi(w_sub(sw_n[k], nw)) : snb[k] - snb[lt];
+            const T etac = etaf * (I.chi_local ? w_hi(nw) : snb[lt]), deta = etaf * dnb;
+            const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
+            sgp[0][t][q] = wq * (T(2) * ln + lchi + lT);
+            sgp[1][t][q] = wq * lT;
+            sgp[2][t][q] = wq * w_hi(w_sub(sw_u[0][k], sw_u[0][lt]));
+            sgp[3][t][q] = wq * w_hi(w_sub(sw_u[1][k], sw_u[1][lt]));
+            sgp[4][t][q] = wq * w_hi(w_sub(sw_u[2][k], sw_u[2][lt]));
+        }
+        __syncthreads();
+        // transport, strain and Shakhov coefficient, one thread per own cell
+        if (tid < cnt) {
+            using C = T;
+            const int t = tid, c = c0 + t, lt = c - h0;
+            const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
+            const C in = C(1) / cn, iT = C(1) / cT, ichi = C(1) / cchi;
+            C gsum[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) gsum[v] = (sgp[v][t][0] + sgp[v][t][1]) + (sgp[v][t][2] + sgp[v][t][3]) + sgp[v][t][4];
+            const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
+            const C X = gsum[0] * sc, Y = gsum[1] * sc;
+            const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
+            const C iR = C(1) / geo0;
+            const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
+            const C sg = inst_param<C>(I.sigma, I.f_sigma);
+            const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
+            const C pi = C(3.14159265358979323846);
+            const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
+                         (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
+            const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
+                         (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
+            C S11, S22, S01, S02, div;
+            if (I.geometry == 0) {
+                S11 = cu0 * iR;
+                S22 = C(0);
+                S01 = C(0.5) * (cd1 - cu1 * iR);
+                S02 = C(0.5) * cd2;
+                div = cd0 + cu0 * iR;
+            } else {
+                S11 = S22 = cu0 * iR;
+                S01 = C(0.5) * (cd1 - cu1 * iR);
+                S02 = C(0.5) * (cd2 - cu2 * iR);
+                div = cd0 + C(2) * cu0 * iR;
             }
+            T* ct = rec + (long long)c * rs;
+            ct[0] = cn;
+            ct[1] = cu0;
+            ct[2] = cu1;
+            ct[3] = cu2;
+            ct[4] = iT;
+            ct[5] = cn * cT / mu;
+            ct[6] = (C(1) - Pr) * iT * iT * in;
+            ct[7] = sq[0][t];
+            ct[8] = sq[1][t];
+            ct[9] = sq[2][t];
+            ct[10] = x;
+            ct[11] = X;
+            ct[12] = Y;
+            ct[13] = cd0;
+            ct[14] = S11;
+            ct[15] = S22;
+            ct[16] = S01;
+            ct[17] = S02;
+            ct[18] = T(0);
+            ct[19] = div;
+            if (A.write_ca) {
+                ca[(long long)c * kCA + 9] = (double)cchi;
+                ca[(long long)c * kCA + 10] = I.chi_local ? (double)cn : (double)snb[lt];
+            }
+        }
+        __syncthreads();
+        // ---- 4. expansion coefficients of the discrete equilibria (Sec. III.C): warp = axis
+        // half (0: half range +, 1: half range -, 2: axis 2, 3: axis 3), lane = own cell
+        for (int t = lane; t < cnt; t += 32) {
+            using C = T;
+            C e[kMaxE + 1];
+#pragma unroll
+            for (int l = 0; l <= kMaxE; ++l) e[l] = C(0);
+            const int lt = c0 + t - h0;
+            const C cT = w_hi(sw_T[lt]);
+            const C tm1 = w_hi(w_sub(sw_T[lt], w_from_t(C(1))));  // T - 1 without cancellation
+            if (warp < 2) {
+                // half range, half line of sign s (warp 0: +, warp 1: -), v = s u_R.  The
+                // recurrence of the coefficients,
+                //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
+                //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
+                //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
+                // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1:
+                // r_0 = h_0 / 2, r_l = 0 for l >= 1), where every term is small and nothing
+                // cancels: with D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) /
+                // sqrt T, z = v / sqrt(2T), and h_0(0) r_0 = 1,
+                //   d_0 = h_0 erf(z) / 2,
+                //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
+                //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
+                //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
+                const C ur = w_hi(sw_u[0][lt]);
+                const C v = warp == 0 ? ur : -ur;
+                const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
+                const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
+                const C is2pi = C(0.39894228040143267794);
+                const C r0 = h0t[0] * C(0.5);
+                C d[kMaxE + 1];
+#pragma unroll
+                for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
+                d[0] = r0 * erf(z);
+                C run = C(0);  // sum_{k<l} h_k(0) d_k
+#pragma unroll
+                for (int l = 0; l < kMaxE; ++l) {
+                    if (l < M.NR) {
+                        C val;
+                        if (l == 0) {
+                            val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
+                        } else {
+                            const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
+                            val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
+                        }
+                        run += h0t[l] * d[l];
+                        d[l + 1] = val * ihb[l + 1];
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l <= kMaxE; ++l) e[l] = d[l];
+                e[0] += r0;
+            } else {
+                // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
+                const C u = w_hi(sw_u[warp == 2 ? 1 : 2][lt]);
+                const int Nax = warp == 2 ? M.N2 : M.N3;
+                e[0] = C(1);
+                e[1] = Nax >= 1 ? u : C(0);
+#pragma unroll
+                for (int l = 1; l < kMaxE; ++l)
+                    if (l < Nax) e[l + 1] = u * e[l] + C(l) * tm1 * e[l - 1];
+            }
+#pragma unroll
+            for (int l = 0; l < kMaxE; ++l) ecs[t][warp][l] = e[l];
         }
         __syncthreads();
         // ---- 5. per-axis equilibrium vectors of the own cells, in the populations' precision
         const int ng = nR + n2 + n3;
         for (int e = tid; e < cnt * ng; e += NT) {
             const int t = e / ng, k = e % ng;
-            const T* e4 = ec + (long long)t * 4 * kMaxE;
             T acc = T(0);
             int dst;
             if (k < nR) {
-                const T* eh = e4 + (k >= QR ? kMaxE : 0);
-                for (int l = 0; l <= M.NR; ++l) acc += tabT[M.o_GR + k * kMaxE + l] * eh[l];
+                const T* eh = ecs[t][k >= QR ? 1 : 0];
+                for (int l = 0; l <= M.NR; ++l) acc += GR[k * kMaxE + l] * eh[l];
                 dst = rec_off_gR(n2) + k;
             } else if (k < nR + n2) {
                 const int j = k - nR;
-                for (int l = 0; l <= M.N2; ++l) acc += tabT[M.o_G2 + j * kMaxE + l] * e4[2 * kMaxE + l];
+                for (int l = 0; l <= M.N2; ++l) acc += G2[j * kMaxE + l] * ecs[t][2][l];
                 dst = rec_off_g2() + j;
             } else {
                 const int j = k - nR - n2;
-                for (int l = 0; l <= M.N3; ++l) acc += tabT[M.o_G3 + j * kMaxE + l] * e4[3 * kMaxE + l];
+                for (int l = 0; l <= M.N3; ++l) acc += G3[j * kMaxE + l] * ecs[t][3][l];
                 dst = rec_off_g3(nR, n2) + j;
             }
             rec[(long long)(c0 + t) * rs + dst] = acc;
         }
-        // ---- 6. wall densities (diffuse walls): n_w = sum_out |p_R| w vhat_wall / sum_in |p_R| g_wall
-        const T* fin = fin_all + I.f_off;
-        for (int side = 0; side < 2; ++side) {
-            const bool here = side == 0 ? (c0 == 0) : (c0 + cnt == N);
-            if (!here) continue;
-            double acc = 0.0;
-            for (int m = tid; m < Np; m += NT) {
-                const int k = m / (nR * n2), rem = m % (nR * n2), i = rem / n2, j = rem % n2;
-                const T pr = (T)tab[M.o_pR + i];
-                if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
-                const T wm = (T)tab[M.o_wR + i] * (T)tab[M.o_w2 + j] * (T)tab[M.o_w3 + k], iw = T(1) / wm;
-                const long long b = side == 0 ? (long long)m : (long long)(N - 1) * Np + m;
-                const long long st = side == 0 ? (long long)Np : -(long long)Np;
-                const T f0 = fin[b], f1 = fin[b + st], f2 = fin[b + 2 * st], f3 = fin[b + 3 * st];
-                const T g1 = T(4) * f0 - T(6) * f1 + T(4) * f2 - f3;
-                const T g2 = T(10) * f0 - T(20) * f1 + T(15) * f2 - T(4) * f3;
-                const T vh = weno5(f2 * iw, f1 * iw, f0 * iw, g1 * iw, g2 * iw);
-                acc += (double)(fabs(pr) * wm * vh);
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) red[warp] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                double tot = 0.0;
-                for (int ww = 0; ww < nwarps; ++ww) tot += red[ww];
-                A.nw[w.x * 2 + side] = tot / I.nw_den[side];
-            }
-            __syncthreads();
-        }
-        __syncthreads();
+        __syncthreads();  // shared arrays are reused by the next item
     }
 }
 
@@ -423,27 +632,44 @@ __global__ void residual_kernel(const double* __restrict__ sums, int slices, con
 
 // ------------------------------------------------------------------------------ launchers
 template <typename T>
-void launch_moments(const T* f, double* sums, const int4* items, const int* n_items, int grid, const InstDev* inst,
-                    const double* tab, const MomSet& M, cudaStream_t s) {
-    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, items, n_items, inst, tab, M);
+void launch_moments(const T* f, double* sums, T* dens, const int4* items, const int* n_items, int grid,
+                    const InstDev* inst, const double* tab, const MomSet& M, cudaStream_t s) {
+    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, dens, items, n_items, inst, tab, M);
+}
+
+// Slice densities from restored raw sums.
+template <typename T>
+__global__ void dens_kernel(const double* __restrict__ sums, T* __restrict__ dens, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dens[i] = (T)sums[i * kSums];
+}
+
+template <typename T>
+void launch_dens_from_sums(const double* sums, T* dens, long long n, cudaStream_t s) {
+    const long long g = (n + 255) / 256;
+    dens_kernel<T><<<(int)(g < 4096 ? (g > 0 ? g : 1) : 4096), 256, 0, s>>>(sums, dens, n);
 }
 
 template <typename T>
 void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(closure_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 32 * 1024) cudaFuncSetAttribute(closure_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     closure_kernel<T><<<grid, threads, smem, s>>>(A, M);
 }
 
-size_t closure_smem(int max_cells, int max_union, int tsize) { return closure_smem_bytes(max_cells, max_union, tsize); }
+size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize) {
+    return closure_smem_bytes(nR, n2, n3, max_union, wst_elems, tsize);
+}
 
 void launch_residual(const double* sums, int slices, const InstDev* inst, const double* geo, double* prev, double* out,
                      int n_inst, int save, cudaStream_t s) {
     residual_kernel<<<n_inst < 1024 ? n_inst : 1024, 256, 0, s>>>(sums, slices, inst, geo, prev, out, n_inst, save);
 }
 
-template void launch_moments<float>(const float*, double*, const int4*, const int*, int, const InstDev*,
+template void launch_dens_from_sums<float>(const double*, float*, long long, cudaStream_t);
+template void launch_dens_from_sums<double>(const double*, double*, long long, cudaStream_t);
+template void launch_moments<float>(const float*, double*, float*, const int4*, const int*, int, const InstDev*,
                                     const double*, const MomSet&, cudaStream_t);
-template void launch_moments<double>(const double*, double*, const int4*, const int*, int, const InstDev*,
+template void launch_moments<double>(const double*, double*, double*, const int4*, const int*, int, const InstDev*,
                                      const double*, const MomSet&, cudaStream_t);
 template void launch_closure<float>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
 template void launch_closure<double>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);

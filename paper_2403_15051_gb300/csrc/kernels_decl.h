@@ -50,13 +50,16 @@ struct StreamCfg {
 };
 
 template <typename T>
-void launch_moments(const T* f, double* sums, const int4* items, const int* n_items, int grid, const InstDev* inst,
+void launch_moments(const T* f, double* sums, T* dens, const int4* items, const int* n_items, int grid, const InstDev* inst,
                     const double* tab, const MomSet& M, cudaStream_t s);
+
+template <typename T>
+void launch_dens_from_sums(const double* sums, T* dens, long long n, cudaStream_t s);
 
 template <typename T>
 void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s);
 
-size_t closure_smem(int max_cells, int max_union, int tsize);
+size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize);
 
 
 #define FDLB_STREAM_DECL(T, G)                                                                             \

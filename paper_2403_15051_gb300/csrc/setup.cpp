@@ -441,6 +441,9 @@ FMBand fm_band(int geometry, const Grid& g, double sigma) {
         hi[i] = std::max(h, lo);
         b.width = std::max(b.width, hi[i] - lo + 1);
     }
+    b.width = (b.width + 3) / 4 * 4;  // rows of 16-byte multiples (bulk copies of row extents)
+    b.cnt.assign(N, 0);
+    for (int i = 0; i < N; ++i) b.cnt[i] = std::min(b.width, (hi[i] - b.lo[i] + 1 + 3) / 4 * 4);
     b.W.assign((size_t)N * b.width, 0.0);
     const double norm = 3.0 / (4.0 * kPi * sigma * sigma * sigma);
     const double full = 4.0 / 3.0 * kPi * sigma * sigma * sigma;

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     T* sgw = sw_3 + n3;            // [2][nR + n2 + n3]: inner and outer wall Maxwellian per axis
     T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
     T* red = reinterpret_cast<T*>(smem_raw + P.red);  // [cell][warp][16] warp sums
+    __shared__ T snw[2];                               // wall densities of the item's instance
     const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
     T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
@@ -210,16 +211,24 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             for (int e = tid; e < Be * rs; e += NT) cellT[e] = rsrc[e];
         }
 
-        // ---- 2. geometry of the tile and the wall densities (overlapping the copy)
-        const double* gwi = A.gw + (long long)wi.x * 2 * gwstride;
-        for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = (T)gwi[e];
+        // ---- 2. geometry of the tile, the wall Maxwellians and the wall densities from the
+        // parts of the outgoing fluxes (overlapping the copy)
+        const T* gwi = reinterpret_cast<const T*>(A.gwT) + (long long)wi.x * 2 * gwstride;
+        for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = gwi[e];
         for (int c = tid; c < Be; c += NT) {
-            const double* g = A.geo + (long long)(I.cell_off + c0 + c) * kGeo;
-            sgeo[c * 3 + 0] = (T)g[2];
-            sgeo[c * 3 + 1] = (T)g[3];
-            sgeo[c * 3 + 2] = (T)g[4];
+            const T* g = reinterpret_cast<const T*>(A.geoT) + (long long)(I.cell_off + c0 + c) * kGeo;
+            sgeo[c * 3 + 0] = g[2];
+            sgeo[c * 3 + 1] = g[3];
+            sgeo[c * 3 + 2] = g[4];
         }
-        const T nwL = (T)A.nw[wi.x * 2], nwR = (T)A.nw[wi.x * 2 + 1];
+        if (tid < 2) {
+            const T* pp = reinterpret_cast<const T*>(A.nwp) + ((long long)wi.x * 2 + tid) * A.wall_parts;
+            T sum = T(0);
+            for (int p = 0; p < A.wall_parts; ++p) sum += pp[p];
+            const T iden = sizeof(T) == 4 ? (T)(tid ? I.f_nw_iden[1] : I.f_nw_iden[0])
+                                          : (T)(tid ? I.nw_iden[1] : I.nw_iden[0]);
+            snw[tid] = sum * iden;
+        }
 
         // ---- wait for the staged cells
         if (A.use_bulk) {
@@ -233,6 +242,8 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             phase ^= 1u;
         }
         __syncthreads();
+
+        const T nwL = snw[0], nwR = snw[1];
 
         // ---- 3. ghost rows at the walls
         const T* gwL = sgw;
@@ -317,7 +328,8 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             }
         }
 
-        const T dt = (T)I.dt, ca_ = (T)A.a, cb_ = (T)A.b;
+        const T dt = sizeof(T) == 4 ? (T)I.f_dt : (T)I.dt;
+        const T ca_ = sizeof(T) == 4 ? (T)A.fa : (T)A.a, cb_ = sizeof(T) == 4 ? (T)A.fb : (T)A.b;
         for (int cl = 0; cl < Be; ++cl) {
             const int c = c0 + cl;
             const T* ct = cellT + cl * rs;
@@ -494,7 +506,9 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                 const int cl = e / kSums, q = e % kSums;
                 double s = 0.0;
                 for (int ww = 0; ww < nwarps; ++ww) s += (double)red[(cl * nwarps + ww) * 16 + q];
-                A.sums_out[((long long)(I.cell_off + c0 + cl) * M.slices + sl) * kSums + q] = s;
+                const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
+                A.sums_out[cs * kSums + q] = s;
+                if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
             }
         }
         __syncthreads();  // the next item overwrites the staged rows, the records and the sums
