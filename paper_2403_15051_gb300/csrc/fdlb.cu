@@ -24,7 +24,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
-    size_t f[3], sums[3], dens[3], ca, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
+    size_t f[3], sums[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err,
         rprev, rout, total;
 };
@@ -54,7 +54,7 @@ struct Solver {
     void* f[3] = {nullptr, nullptr, nullptr};
     double* sums[3] = {nullptr, nullptr, nullptr};
     void* dens[3] = {nullptr, nullptr, nullptr};
-    void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr;
+    void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr, *cw = nullptr;
     void* rec = nullptr;
     void* tabT = nullptr;
     double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *rprev = nullptr,
@@ -189,6 +189,7 @@ Layout make_layout(const Solver& S) {
     for (int b = 0; b < 3; ++b) L.sums[b] = take((size_t)S.total_cells * S.n3 * kSums * sizeof(double));
     for (int b = 0; b < 3; ++b) L.dens[b] = take((size_t)S.total_cells * S.n3 * S.tsize);
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
+    L.cw = take((size_t)S.total_cells * 2 * S.tsize);
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
     L.tabT = take(S.tab_h.size() * S.tsize);
@@ -483,7 +484,7 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.sums = S.sums[buf];
     A.dens = S.dens[buf];
     A.f_in = S.f[buf];
-    A.ca = S.ca;
+    A.cw = S.cw;
     A.rec = S.rec;
     A.rec_stride = record_stride(S.nR, S.n2, S.n3);
     A.nwp = S.nwp;
@@ -497,7 +498,6 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.slices = S.M.slices;
     A.max_union = S.max_union;
     A.wall_parts = kWallParts;
-    A.write_ca = write_ca;
     A.wst_elems = S.closure_wst;
     A.err = S.err;
     if (S.precision == FDLB_FP32)
@@ -505,6 +505,14 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     else
         launch_closure<double>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
     S.launches++;
+    if (write_ca) {
+        // the FP64 closure record for the queries (not part of the stage)
+        if (S.precision == FDLB_FP32)
+            launch_ca<float>(S.sums[buf], S.cw, S.ca, S.M.slices, S.total_cells, S.stream);
+        else
+            launch_ca<double>(S.sums[buf], S.cw, S.ca, S.M.slices, S.total_cells, S.stream);
+        S.launches++;
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -729,6 +737,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.citems = (int4*)(R.ws + L.citems);
     R.n_citems = (int*)(R.ws + L.n_citems);
     R.nwp = (void*)(R.ws + L.nwp);
+    R.cw = (void*)(R.ws + L.cw);
     R.geoT = (void*)(R.ws + L.geoT);
     R.gwT = (void*)(R.ws + L.gwT);
     R.err = (int*)(R.ws + L.err);

@@ -87,7 +87,7 @@ struct ClosureArgs {
     const double* sums;
     const void* dens;              // per-slice densities (T), [cell][slice], for the FM bands
     const void* f_in;              // populations (T), for the wall fluxes
-    double* ca;                    // FP64 closure records (written with write_ca)
+    void* cw;                      // [cell][2] chi and nbar of the stage (T), for the queries
     void* rec;                     // per-cell collision records (T)
     int rec_stride;
     void* nwp;                     // [instance][2][kWallParts] outgoing wall fluxes (T)
@@ -101,7 +101,6 @@ struct ClosureArgs {
     int slices;
     int max_union;                 // capacity of the shared density buffer
     int wall_parts;
-    int write_ca;
     int wst_elems;                 // capacity of the staged band rows (elements)
     int* err;                      // set when a bulk copy never completes
 };

@@ -87,8 +87,8 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
 //  * mu, Pr, tau (Eqs. viscosity, prandtl, tau), the covariant strain and the Shakhov
 //    coefficient; the recurrences of the expansion coefficients of the equilibria (Sec. III.C;
 //    warp = axis, lane = cell) and the per-axis vectors g_2, g_R, g_3 (whole block).
-// With write_ca the FP64 closure record (n, u, T, q, P_12, chi, nbar) is written as well (the
-// moments and closure queries; not needed by the stage itself).
+// chi and nbar of the own cells also go to a small side buffer, from which ca_kernel forms the
+// FP64 closure record of the moments and closure queries.
 // Wall items (kind 1 + side, part): the block sums the outgoing flux of one part of the momenta
 // at one wall; the stage kernel forms n_w from the parts (diffuse walls, zero net mass flux).
 // Output: the per-cell collision record in the populations' precision, [20 scalars | g_2 | g_R
@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
         // reach: the own cells, two on each side, and the five cells next to a wall
         const int h0 = max(0, min(c0 - 2, N - 5)), h1 = min(N, max(c0 + cnt + 2, 5)), nh = h1 - h0;
         const double* S = A.sums + (long long)I.cell_off * slices * kSums;
-        double* ca = A.ca + (long long)I.cell_off * kCA;
         const int rs = A.rec_stride;
         T* rec = rec_all + (long long)I.cell_off * rs;
         // ---- 1. every global load of the item at once: the raw sums of the reach cells and the
@@ -345,28 +344,6 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
                     sq[1][c - c0] = T(0.5) * ((T)s[11] - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
                     sq[2][c - c0] = T(0.5) * ((T)s[12] - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
                     sq[3][c - c0] = s7 - tn * t0 * t1;
-                    if (A.write_ca) {
-                        // the FP64 closure record (queries only)
-                        const double dn = s[0], in = 1.0 / dn;
-                        const double v0 = s[1] * in, v1 = s[2] * in, v2 = s[3] * in;
-                        const double dtr = s[4] + s[5] + s[6];
-                        const double vv = v0 * v0 + v1 * v1 + v2 * v2;
-                        const double dT = (dtr - dn * vv) * in * (1.0 / 3.0);
-                        const double d0 = s[4] * v0 + s[7] * v1 + s[8] * v2;
-                        const double d1 = s[7] * v0 + s[5] * v1 + s[9] * v2;
-                        const double d2 = s[8] * v0 + s[9] * v1 + s[6] * v2;
-                        double* r = ca + (long long)c * kCA;
-                        r[0] = dn;
-                        r[1] = v0;
-                        r[2] = v1;
-                        r[3] = v2;
-                        r[4] = dT;
-                        r[5] = 0.5 * (s[10] - 2.0 * d0 - v0 * dtr + 2.0 * dn * vv * v0);
-                        r[6] = 0.5 * (s[11] - 2.0 * d1 - v1 * dtr + 2.0 * dn * vv * v1);
-                        r[7] = 0.5 * (s[12] - 2.0 * d2 - v2 * dtr + 2.0 * dn * vv * v2);
-                        r[8] = s[7] - dn * v0 * v1;  // P_12
-                        r[11] = 0.0;
-                    }
                 }
             }
         } else if (!I.chi_local) {
@@ -390,165 +367,167 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
             }
         }
         __syncthreads();
-        // ---- 3. chi of the reach cells (warp 0); the gradient terms, one thread per own cell and
-        // stencil position (logarithms of ratios to the own cell, differences in the wide type)
-        if (warp == 0 && lane < nh) {
-            // chi in the wide type, rounded once: J1 scales with b rho chi, and near finely
-            // resolved walls J1 is large enough that a few roundings of chi show in the RHS
-            const T etafac = inst_param<T>(I.etafac, I.f_etafac);
-            const W eta = w_scale(w_from_t(I.chi_local ? w_hi(sw_n[lane]) : snb[lane]), etafac);
-            const W om = w_sub(w_from_t(T(1)), eta);
-            const W om3 = w_mul(w_mul(om, om), om);
-            s_chi[lane] = w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
-        }
-        __syncthreads();
-        for (int e = tid; e < cnt * 5; e += NT) {
-            const int t = e / 5, q = e % 5, c = c0 + t, lt = c - h0;
-            int cq;
-            T wq;
-            stencil5_at<T>(c, N, q, cq, wq);
-            const int k = cq - h0;
-            const W nw = sw_n[lt], Tw = sw_T[lt];
-            const T lT = log1p(ratio_fast(w_hi(w_sub(sw_T[k], Tw)), w_hi(Tw)));
-            const T ln = log1p(ratio_fast(w_hi(w_sub(sw_n[k], nw)), w_hi(nw)));
-            // ln chi_q - ln chi_c from the packing-fraction difference alone, since
-            // ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of chi itself)
+        // ---- 3. two concurrent chains.  Warp 0: chi of the reach cells, the gradient terms (one
+        // lane per own cell and stencil position: logarithms of ratios to the own cell, differences
+        // in the wide type), then transport, strain and Shakhov coefficient (lane per own cell).
+        // Warps 1 and 2: the expansion coefficients of the equilibria (Sec. III.C), lane per
+        // (own cell, axis half): warp 1 the half-range axis (+ and -), warp 2 the axes 2 and 3.
+        if (warp == 0) {
+            if (lane < nh) {
+                // chi in the wide type, rounded once: J1 scales with b rho chi, and near finely
+                // resolved walls J1 is large enough that a few roundings of chi show in the RHS
+                const T etafac = inst_param<T>(I.etafac, I.f_etafac);
+                const W eta = w_scale(w_from_t(I.chi_local ? w_hi(sw_n[lane]) : snb[lane]), etafac);
+                const W om = w_sub(w_from_t(T(1)), eta);
+                const W om3 = w_mul(w_mul(om, om), om);
+                s_chi[lane] = w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
+            }
+            __syncwarp();
             const T etaf = inst_param<T>(I.etafac, I.f_etafac);
-            const T dnb = I.chi_local ? w_hi(w_sub(sw_n[k], nw)) : snb[k] - snb[lt];
-            const T etac = etaf * (I.chi_local ? w_hi(nw) : snb[lt]), deta = etaf * dnb;
-            const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
-            sgp[0][t][q] = wq * (T(2) * ln + lchi + lT);
-            sgp[1][t][q] = wq * lT;
-            sgp[2][t][q] = wq * w_hi(w_sub(sw_u[0][k], sw_u[0][lt]));
-            sgp[3][t][q] = wq * w_hi(w_sub(sw_u[1][k], sw_u[1][lt]));
-            sgp[4][t][q] = wq * w_hi(w_sub(sw_u[2][k], sw_u[2][lt]));
-        }
-        __syncthreads();
-        // transport, strain and Shakhov coefficient, one thread per own cell
-        if (tid < cnt) {
-            using C = T;
-            const int t = tid, c = c0 + t, lt = c - h0;
-            const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
-            const C in = C(1) / cn, iT = C(1) / cT, ichi = C(1) / cchi;
-            C gsum[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) gsum[v] = (sgp[v][t][0] + sgp[v][t][1]) + (sgp[v][t][2] + sgp[v][t][3]) + sgp[v][t][4];
-            const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
-            const C X = gsum[0] * sc, Y = gsum[1] * sc;
-            const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
-            const C iR = C(1) / geo0;
-            const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
-            const C sg = inst_param<C>(I.sigma, I.f_sigma);
-            const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
-            const C pi = C(3.14159265358979323846);
-            const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
-                         (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
-            const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
-                         (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
-            C S11, S22, S01, S02, div;
-            if (I.geometry == 0) {
-                S11 = cu0 * iR;
-                S22 = C(0);
-                S01 = C(0.5) * (cd1 - cu1 * iR);
-                S02 = C(0.5) * cd2;
-                div = cd0 + cu0 * iR;
-            } else {
-                S11 = S22 = cu0 * iR;
-                S01 = C(0.5) * (cd1 - cu1 * iR);
-                S02 = C(0.5) * (cd2 - cu2 * iR);
-                div = cd0 + C(2) * cu0 * iR;
+            for (int e = lane; e < cnt * 5; e += 32) {
+                const int t = e / 5, q = e % 5, c = c0 + t, lt = c - h0;
+                int cq;
+                T wq;
+                stencil5_at<T>(c, N, q, cq, wq);
+                const int k = cq - h0;
+                const W nw = sw_n[lt], Tw = sw_T[lt];
+                const T lT = log1p(ratio_fast(w_hi(w_sub(sw_T[k], Tw)), w_hi(Tw)));
+                const T ln = log1p(ratio_fast(w_hi(w_sub(sw_n[k], nw)), w_hi(nw)));
+                // ln chi_q - ln chi_c from the packing-fraction difference alone, since
+                // ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of chi itself)
+                const T dnb = I.chi_local ? w_hi(w_sub(sw_n[k], nw)) : snb[k] - snb[lt];
+                const T etac = etaf * (I.chi_local ? w_hi(nw) : snb[lt]), deta = etaf * dnb;
+                const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
+                sgp[0][t][q] = wq * (T(2) * ln + lchi + lT);
+                sgp[1][t][q] = wq * lT;
+                sgp[2][t][q] = wq * w_hi(w_sub(sw_u[0][k], sw_u[0][lt]));
+                sgp[3][t][q] = wq * w_hi(w_sub(sw_u[1][k], sw_u[1][lt]));
+                sgp[4][t][q] = wq * w_hi(w_sub(sw_u[2][k], sw_u[2][lt]));
             }
-            T* ct = rec + (long long)c * rs;
-            ct[0] = cn;
-            ct[1] = cu0;
-            ct[2] = cu1;
-            ct[3] = cu2;
-            ct[4] = iT;
-            ct[5] = cn * cT / mu;
-            ct[6] = (C(1) - Pr) * iT * iT * in;
-            ct[7] = sq[0][t];
-            ct[8] = sq[1][t];
-            ct[9] = sq[2][t];
-            ct[10] = x;
-            ct[11] = X;
-            ct[12] = Y;
-            ct[13] = cd0;
-            ct[14] = S11;
-            ct[15] = S22;
-            ct[16] = S01;
-            ct[17] = S02;
-            ct[18] = T(0);
-            ct[19] = div;
-            if (A.write_ca) {
-                ca[(long long)c * kCA + 9] = (double)cchi;
-                ca[(long long)c * kCA + 10] = I.chi_local ? (double)cn : (double)snb[lt];
+            __syncwarp();
+            if (lane < cnt) {
+                using C = T;
+                const int t = lane, c = c0 + t, lt = c - h0;
+                const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
+                const C in = C(1) / cn, iT = C(1) / cT, ichi = C(1) / cchi;
+                C gsum[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v)
+                    gsum[v] = (sgp[v][t][0] + sgp[v][t][1]) + (sgp[v][t][2] + sgp[v][t][3]) + sgp[v][t][4];
+                const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
+                const C X = gsum[0] * sc, Y = gsum[1] * sc;
+                const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
+                const C iR = C(1) / geo0;
+                const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
+                const C sg = inst_param<C>(I.sigma, I.f_sigma);
+                const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
+                const C pi = C(3.14159265358979323846);
+                const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
+                             (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
+                const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
+                             (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
+                C S11, S22, S01, S02, div;
+                if (I.geometry == 0) {
+                    S11 = cu0 * iR;
+                    S22 = C(0);
+                    S01 = C(0.5) * (cd1 - cu1 * iR);
+                    S02 = C(0.5) * cd2;
+                    div = cd0 + cu0 * iR;
+                } else {
+                    S11 = S22 = cu0 * iR;
+                    S01 = C(0.5) * (cd1 - cu1 * iR);
+                    S02 = C(0.5) * (cd2 - cu2 * iR);
+                    div = cd0 + C(2) * cu0 * iR;
+                }
+                T* ct = rec + (long long)c * rs;
+                ct[0] = cn;
+                ct[1] = cu0;
+                ct[2] = cu1;
+                ct[3] = cu2;
+                ct[4] = iT;
+                ct[5] = cn * cT / mu;
+                ct[6] = (C(1) - Pr) * iT * iT * in;
+                ct[7] = sq[0][t];
+                ct[8] = sq[1][t];
+                ct[9] = sq[2][t];
+                ct[10] = x;
+                ct[11] = X;
+                ct[12] = Y;
+                ct[13] = cd0;
+                ct[14] = S11;
+                ct[15] = S22;
+                ct[16] = S01;
+                ct[17] = S02;
+                ct[18] = T(0);
+                ct[19] = div;
+                T* cw = reinterpret_cast<T*>(A.cw) + (long long)(I.cell_off + c) * 2;
+                cw[0] = cchi;
+                cw[1] = I.chi_local ? cn : snb[lt];
             }
-        }
-        __syncthreads();
-        // ---- 4. expansion coefficients of the discrete equilibria (Sec. III.C): warp = axis
-        // half (0: half range +, 1: half range -, 2: axis 2, 3: axis 3), lane = own cell
-        for (int t = lane; t < cnt; t += 32) {
+        } else if (warp <= 2) {
             using C = T;
-            C e[kMaxE + 1];
+            for (int e = lane; e < 2 * cnt; e += 32) {
+                const int t = e % cnt, job = 2 * (warp - 1) + e / cnt, lt = c0 + t - h0;
+                C ev[kMaxE + 1];
 #pragma unroll
-            for (int l = 0; l <= kMaxE; ++l) e[l] = C(0);
-            const int lt = c0 + t - h0;
-            const C cT = w_hi(sw_T[lt]);
-            const C tm1 = w_hi(w_sub(sw_T[lt], w_from_t(C(1))));  // T - 1 without cancellation
-            if (warp < 2) {
-                // half range, half line of sign s (warp 0: +, warp 1: -), v = s u_R.  The
-                // recurrence of the coefficients,
-                //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
-                //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
-                //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
-                // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1:
-                // r_0 = h_0 / 2, r_l = 0 for l >= 1), where every term is small and nothing
-                // cancels: with D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) /
-                // sqrt T, z = v / sqrt(2T), and h_0(0) r_0 = 1,
-                //   d_0 = h_0 erf(z) / 2,
-                //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
-                //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
-                //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
-                const C ur = w_hi(sw_u[0][lt]);
-                const C v = warp == 0 ? ur : -ur;
-                const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
-                const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
-                const C is2pi = C(0.39894228040143267794);
-                const C r0 = h0t[0] * C(0.5);
-                C d[kMaxE + 1];
+                for (int l = 0; l <= kMaxE; ++l) ev[l] = C(0);
+                const C cT = w_hi(sw_T[lt]);
+                const C tm1 = w_hi(w_sub(sw_T[lt], w_from_t(C(1))));  // T - 1 without cancellation
+                if (job < 2) {
+                    // half range, half line of sign s (job 0: +, 1: -), v = s u_R.  The
+                    // recurrence of the coefficients,
+                    //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
+                    //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
+                    //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
+                    // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1:
+                    // r_0 = h_0 / 2, r_l = 0 for l >= 1), where every term is small and nothing
+                    // cancels: with D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) /
+                    // sqrt T, z = v / sqrt(2T), and h_0(0) r_0 = 1,
+                    //   d_0 = h_0 erf(z) / 2,
+                    //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
+                    //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
+                    //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
+                    const C ur = w_hi(sw_u[0][lt]);
+                    const C v = job == 0 ? ur : -ur;
+                    const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
+                    const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
+                    const C is2pi = C(0.39894228040143267794);
+                    const C r0 = h0t[0] * C(0.5);
+                    C d[kMaxE + 1];
 #pragma unroll
-                for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
-                d[0] = r0 * erf(z);
-                C run = C(0);  // sum_{k<l} h_k(0) d_k
+                    for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
+                    d[0] = r0 * erf(z);
+                    C run = C(0);  // sum_{k<l} h_k(0) d_k
 #pragma unroll
-                for (int l = 0; l < kMaxE; ++l) {
-                    if (l < M.NR) {
-                        C val;
-                        if (l == 0) {
-                            val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
-                        } else {
-                            const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
-                            val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
+                    for (int l = 0; l < kMaxE; ++l) {
+                        if (l < M.NR) {
+                            C val;
+                            if (l == 0) {
+                                val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
+                            } else {
+                                const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
+                                val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
+                            }
+                            run += h0t[l] * d[l];
+                            d[l + 1] = val * ihb[l + 1];
                         }
-                        run += h0t[l] * d[l];
-                        d[l + 1] = val * ihb[l + 1];
                     }
+#pragma unroll
+                    for (int l = 0; l <= kMaxE; ++l) ev[l] = d[l];
+                    ev[0] += r0;
+                } else {
+                    // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
+                    const C u = w_hi(sw_u[job == 2 ? 1 : 2][lt]);
+                    const int Nax = job == 2 ? M.N2 : M.N3;
+                    ev[0] = C(1);
+                    ev[1] = Nax >= 1 ? u : C(0);
+#pragma unroll
+                    for (int l = 1; l < kMaxE; ++l)
+                        if (l < Nax) ev[l + 1] = u * ev[l] + C(l) * tm1 * ev[l - 1];
                 }
 #pragma unroll
-                for (int l = 0; l <= kMaxE; ++l) e[l] = d[l];
-                e[0] += r0;
-            } else {
-                // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                const C u = w_hi(sw_u[warp == 2 ? 1 : 2][lt]);
-                const int Nax = warp == 2 ? M.N2 : M.N3;
-                e[0] = C(1);
-                e[1] = Nax >= 1 ? u : C(0);
-#pragma unroll
-                for (int l = 1; l < kMaxE; ++l)
-                    if (l < Nax) e[l + 1] = u * e[l] + C(l) * tm1 * e[l - 1];
+                for (int l = 0; l < kMaxE; ++l) ecs[t][job][l] = ev[l];
             }
-#pragma unroll
-            for (int l = 0; l < kMaxE; ++l) ecs[t][warp][l] = e[l];
         }
         __syncthreads();
         // ---- 5. per-axis equilibrium vectors of the own cells, in the populations' precision
@@ -574,6 +553,49 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
         }
         __syncthreads();  // shared arrays are reused by the next item
     }
+}
+
+// ------------------------------------------------------------------------------ queries
+// The FP64 closure record of every cell of the active instances (moments and closure queries,
+// not the stage): n, u, T, q, P_12 (Eq. macro_def) from the raw sums in FP64, chi and nbar from
+// the closure's side buffer.
+template <typename T>
+__global__ void ca_kernel(const double* __restrict__ sums, const void* cwv, double* __restrict__ ca, int slices,
+                          int total_cells) {
+    const T* cw = reinterpret_cast<const T*>(cwv);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total_cells; c += gridDim.x * blockDim.x) {
+        double s[kSums];
+        for (int q = 0; q < kSums; ++q) s[q] = 0.0;
+        for (int sl = 0; sl < slices; ++sl)
+            for (int q = 0; q < kSums; ++q) s[q] += sums[((long long)c * slices + sl) * kSums + q];
+        const double n = s[0], in = 1.0 / n;
+        const double u0 = s[1] * in, u1 = s[2] * in, u2 = s[3] * in;
+        const double tr = s[4] + s[5] + s[6];
+        const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+        const double Tc = (tr - n * uu) * in * (1.0 / 3.0);
+        const double m0 = s[4] * u0 + s[7] * u1 + s[8] * u2;
+        const double m1 = s[7] * u0 + s[5] * u1 + s[9] * u2;
+        const double m2 = s[8] * u0 + s[9] * u1 + s[6] * u2;
+        double* r = ca + (long long)c * kCA;
+        r[0] = n;
+        r[1] = u0;
+        r[2] = u1;
+        r[3] = u2;
+        r[4] = Tc;
+        r[5] = 0.5 * (s[10] - 2.0 * m0 - u0 * tr + 2.0 * n * uu * u0);
+        r[6] = 0.5 * (s[11] - 2.0 * m1 - u1 * tr + 2.0 * n * uu * u1);
+        r[7] = 0.5 * (s[12] - 2.0 * m2 - u2 * tr + 2.0 * n * uu * u2);
+        r[8] = s[7] - n * u0 * u1;  // P_12
+        r[9] = (double)cw[2 * (long long)c];
+        r[10] = (double)cw[2 * (long long)c + 1];
+        r[11] = 0.0;
+    }
+}
+
+template <typename T>
+void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s) {
+    const int g = (total_cells + 255) / 256;
+    ca_kernel<T><<<g < 2048 ? (g > 0 ? g : 1) : 2048, 256, 0, s>>>(sums, cw, ca, slices, total_cells);
 }
 
 // ------------------------------------------------------------------------------ stream
@@ -665,6 +687,8 @@ void launch_residual(const double* sums, int slices, const InstDev* inst, const 
     residual_kernel<<<n_inst < 1024 ? n_inst : 1024, 256, 0, s>>>(sums, slices, inst, geo, prev, out, n_inst, save);
 }
 
+template void launch_ca<float>(const double*, const void*, double*, int, int, cudaStream_t);
+template void launch_ca<double>(const double*, const void*, double*, int, int, cudaStream_t);
 template void launch_dens_from_sums<float>(const double*, float*, long long, cudaStream_t);
 template void launch_dens_from_sums<double>(const double*, double*, long long, cudaStream_t);
 template void launch_moments<float>(const float*, double*, float*, const int4*, const int*, int, const InstDev*,
