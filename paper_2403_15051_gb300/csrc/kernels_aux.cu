@@ -551,6 +551,20 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
             }
             rec[(long long)(c0 + t) * rs + dst] = acc;
         }
+        __syncthreads();
+        // ---- 6. discrete mass of the stored equilibrium: the rounded vectors need not sum to
+        // exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
+        // would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is
+        // divided by the wide-precision product of the sums of the stored vectors.
+        if (tid < cnt) {
+            const int lt = c0 + tid - h0;
+            T* ct = rec + (long long)(c0 + tid) * rs;
+            W sR = w_from_t(T(0)), s2 = w_from_t(T(0)), s3 = w_from_t(T(0));
+            for (int k = 0; k < nR; ++k) sR = w_add(sR, w_from_t(ct[rec_off_gR(n2) + k]));
+            for (int j = 0; j < n2; ++j) s2 = w_add(s2, w_from_t(ct[rec_off_g2() + j]));
+            for (int j = 0; j < n3; ++j) s3 = w_add(s3, w_from_t(ct[rec_off_g3(nR, n2) + j]));
+            ct[0] = w_hi(w_div(sw_n[lt], w_mul(w_mul(sR, s2), s3)));
+        }
         __syncthreads();  // shared arrays are reused by the next item
     }
 }

@@ -454,15 +454,18 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
                     }
                     const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
                     if (A.mode == 0) {
-                        T fnv[VW];
+                        // a f_n + b (f + dt L) with a = 1 - b, written as f_n + b ((f - f_n) + dt L):
+                        // exactly affine whatever the rounding of b (in FP32, fl(1/3) + fl(2/3)
+                        // exceeds one by 3e-8, which would scale the state by that much every step)
                         if (ca_ != T(0)) {
+                            T fnv[VW];
                             ldg_vec<T, VW>(f_n + gidx, fnv);
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) out[e] = fnv[e] + cb_ * ((fv[e] - fnv[e]) + dt * out[e]);
                         } else {
 #pragma unroll
-                            for (int e = 0; e < VW; ++e) fnv[e] = T(0);
+                            for (int e = 0; e < VW; ++e) out[e] = fv[e] + dt * out[e];
                         }
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) out[e] = ca_ * fnv[e] + cb_ * (fv[e] + dt * out[e]);
                     }
                     st_vec<T, VW>(f_out + gidx, out);
                     // raw sums: power sums over the vector's p_2, then the 13 moments
