@@ -270,7 +270,10 @@ int fdlb_nn_loss_grad(fdlb_nn_handle h, const float* raw_params_host, const floa
 int fdlb_nn_train_step(fdlb_nn_handle h, const float* raw_params_host, const float* targets_host, int batch,
                        float lr, float* loss);
 /* Predict the profiles of one instance of `solver` from its parameters and seed its state with
- * them (decode the outputs as above, then fdlb_init_from_moments). */
+ * them (decode the outputs as above, then fdlb_init_from_moments).  The density and heat-flux
+ * profiles are rescaled together so that the seed carries the instance's total mass (that of its
+ * uniform start): the walls conserve mass, so the steady state depends on it.  The solver's
+ * stream is synchronised (two mass reads). */
 int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const float* raw_params_host);
 
 /* ----------------------------------------------------------------------- no device allocation

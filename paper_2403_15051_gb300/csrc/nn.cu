@@ -532,6 +532,21 @@ int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const
         T[x] = Tin * std::max(0.05, 1.0 + 0.1 * (double)o[2]);
         qR[x] = 0.01 * info.n0 * Tin * std::sqrt(Tin) * (double)o[3];
     }
+    // The walls conserve mass, so the steady state depends on the total mass: the seed must carry
+    // the instance's own mass (that of its uniform start).  The seeded populations are linear in
+    // (n, q_R) at fixed u_2 and T, so scaling both profiles scales the mass exactly.
+    double m_uniform = 0.0, m_seed = 0.0;
+    rc = fdlb_init_uniform(solver, instance, 0.0, 0.0);
+    if (!rc) rc = fdlb_get_diagnostics(solver, instance, &m_uniform, nullptr, nullptr);
+    if (!rc) rc = fdlb_init_from_moments(solver, instance, nn.data(), u2.data(), T.data(), qR.data(), n->P);
+    if (!rc) rc = fdlb_get_diagnostics(solver, instance, &m_seed, nullptr, nullptr);
+    if (rc) return rc;
+    if (!(m_seed > 0.0) || !(m_uniform > 0.0)) return FDLB_ENAN;
+    const double lam = m_uniform / m_seed;
+    for (int x = 0; x < n->P; ++x) {
+        nn[x] *= lam;
+        qR[x] *= lam;
+    }
     return fdlb_init_from_moments(solver, instance, nn.data(), u2.data(), T.data(), qR.data(), n->P);
 }
 

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2403_15051_gb300 import build as fbuild
+from paper_2403_15051_gb300 import fdlb
 from paper_2403_15051_gb300 import warmstart as ws
 from paper_2403_15051_gb300 import workloads as wl
 
@@ -28,6 +29,14 @@ def test_trained_network_reduces_steps_to_steady():
     assert rc == 0, (rc, res)
     net, losses = ws.train(raw, tg, epochs=300, batch=16, lr=2e-3, width=32, modes=6, layers=3, hidden=64)
     assert losses[-1] < 0.2 * losses[0]
+    # the seed carries each instance's own total mass (the walls conserve it)
+    S = fdlb.Solver(eval_ds)
+    m_uniform = [S.diagnostics(q)[1] for q in range(len(eval_ds))]
+    for q, d in enumerate(eval_ds):
+        net.warm_start(S, q, ws.raw_parameters(d))
+    m_seed = [S.diagnostics(q)[1] for q in range(len(eval_ds))]
+    S.close()
+    assert np.allclose(m_seed, m_uniform, rtol=1e-5), (m_seed, m_uniform)
     cold, _, rc1 = ws.steps_to_steady(eval_ds, None, tol=1e-6, max_steps=60_000, check_every=100)
     warm, _, rc2 = ws.steps_to_steady(eval_ds, net, tol=1e-6, max_steps=60_000, check_every=100)
     assert rc1 == 0 and rc2 == 0
