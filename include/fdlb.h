@@ -206,6 +206,12 @@ const char* fdlb_error_string(int code);
 int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads);
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
 
+/* Programmatic dependent launch of the closure and stage kernels (default on): each may start
+ * while its predecessor in the stream finishes, loading its constant tables, and waits for the
+ * predecessor's completion before it reads anything the predecessor writes.  Results are the same
+ * bit for bit either way; 0 turns it off (ordinary stream-ordered launches). */
+int fdlb_set_programmatic_launch(fdlb_handle h, int enable);
+
 /* Own cells per closure work item (1..28; default 4).  A closure item also recomputes the
  * macroscopic fields of two stencil cells on each side, so larger items repeat less work and
  * smaller items spread the latency-bound closure over more SMs.  FDLB_EINVAL outside the

@@ -50,6 +50,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
     return false;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream is still running: it does only work that reads
+// nothing the predecessor writes (constant tables into shared memory), then pdl_wait(), which
+// returns once the predecessor grid has completed and its memory is visible.  pdl_trigger() lets
+// the successor be scheduled as soon as every block of this grid has started.  Both are no-ops
+// for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ T ldg_t(const T* p) {
     return __ldg(p);

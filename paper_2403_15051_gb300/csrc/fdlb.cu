@@ -85,6 +85,7 @@ struct Solver {
     int graph_steps = 20;
     // per-kernel timing (events around each launch, direct launches)
     bool timing = false;
+    int programmatic = 1;  // closure and stage kernels overlap their prologues with the predecessor
     cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
     double t_stream_ms = 0.0, t_closure_ms = 0.0;
     int64_t n_stream_t = 0, n_closure_t = 0;
@@ -500,6 +501,7 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.wall_parts = kWallParts;
     A.wst_elems = S.closure_wst;
     A.err = S.err;
+    A.programmatic = S.programmatic;
     if (S.precision == FDLB_FP32)
         launch_closure<float>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
     else
@@ -569,6 +571,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.mode = mode;
     A.B = S.B;
     A.use_bulk = S.use_bulk;
+    A.programmatic = S.programmatic;
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
@@ -1296,6 +1299,17 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
     if (slice_k) *slice_k = S->KS;
     if (threads) *threads = S->threads;
     return rc;
+}
+
+int fdlb_set_programmatic_launch(fdlb_handle h, int enable) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    S->programmatic = enable ? 1 : 0;
+    if (S->gexec) {
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+    }
+    return FDLB_OK;
 }
 
 int fdlb_set_closure_cells(fdlb_handle h, int cells) {

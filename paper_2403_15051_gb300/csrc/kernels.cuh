@@ -81,6 +81,7 @@ struct StageArgs {
     int mode;                      // 0: RK stage; 1: write L(f_in) to f_out
     int B;                         // cells per tile
     int use_bulk;                  // stage the tile with cp.async.bulk
+    int programmatic;              // launched with programmatic stream serialization
 };
 
 struct ClosureArgs {
@@ -102,6 +103,7 @@ struct ClosureArgs {
     int max_union;                 // capacity of the shared density buffer
     int wall_parts;
     int wst_elems;                 // capacity of the staged band rows (elements)
+    int programmatic;              // launched with programmatic stream serialization
     int* err;                      // set when a bulk copy never completes
 };
 

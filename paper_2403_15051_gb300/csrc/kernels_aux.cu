@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
         for (int e = tid; e < n3; e += NT) w3t[e] = tabT[M.o_w3 + e];
         __syncthreads();
     }
+    pdl_trigger();
+    pdl_wait();  // everything below reads what the previous kernels wrote
     uint32_t phase = 0;
     const int nit = *A.n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
@@ -689,7 +691,7 @@ void launch_dens_from_sums(const double* sums, T* dens, long long n, cudaStream_
 template <typename T>
 void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {
     if (smem > 32 * 1024) cudaFuncSetAttribute(closure_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    closure_kernel<T><<<grid, threads, smem, s>>>(A, M);
+    launch_maybe_programmatic(closure_kernel<T>, grid, threads, smem, s, A.programmatic, A, M);
 }
 
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize) {

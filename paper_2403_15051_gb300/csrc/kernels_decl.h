@@ -16,6 +16,24 @@ inline __host__ __device__ int rec_off_g2() { return kCellScalars; }
 inline __host__ __device__ int rec_off_gR(int n2) { return kCellScalars + n2; }
 inline __host__ __device__ int rec_off_g3(int nR, int n2) { return kCellScalars + n2 + nR; }
 
+// Launch with programmatic stream serialization when `programmatic` (see pdl_wait), else the
+// ordinary way.
+template <typename... Args>
+inline cudaError_t launch_maybe_programmatic(void (*kern)(Args...), int grid, int threads, size_t smem, cudaStream_t s,
+                                             int programmatic, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = programmatic ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct StreamSmem {
     int fs, rec, tabs, geo, red, total;
 };

@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     if (GEOM == 1)
         for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = (T)tab[M.o_K3 + e];
     __syncthreads();
+    pdl_trigger();
+    pdl_wait();  // everything below reads what the previous kernels wrote
 
     uint32_t phase = 0;
     const int nit = *A.n_items;
@@ -523,8 +525,7 @@ cudaError_t launch_stream_t(const StageArgs& A, const MomSet& M, int grid, int t
     auto kern = stream_kernel<T, GEOM, VW, NV, NR_, N2_, N3_>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, threads, smem, s>>>(A, M);
-    return cudaGetLastError();
+    return launch_maybe_programmatic(kern, grid, threads, smem, s, A.programmatic, A, M);
 }
 
 // Instantiations: generic shapes (VW 1, 2, 4 for float; 1, 2 for double) and the compile-time

@@ -91,6 +91,7 @@ def load_library():
         "fdlb_error_string": (ctypes.c_char_p, [c_int]),
         "fdlb_set_tiling": (c_int, [H, c_int, c_int, c_int]),
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
+        "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_autotune": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_launch_count": (c_int64, [H]),
         "fdlb_set_graph_steps": (c_int, [H, c_int]),
@@ -292,6 +293,9 @@ class Solver:
 
     def set_tiling(self, cells=0, slice_k=0, threads=0):
         _check(self._L.fdlb_set_tiling(self._h, cells, slice_k, threads), "fdlb_set_tiling")
+
+    def set_programmatic_launch(self, enable):
+        _check(self._L.fdlb_set_programmatic_launch(self._h, 1 if enable else 0), "fdlb_set_programmatic_launch")
 
     def set_closure_cells(self, cells):
         _check(self._L.fdlb_set_closure_cells(self._h, cells), "fdlb_set_closure_cells")
