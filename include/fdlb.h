@@ -212,7 +212,7 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
  * bit for bit either way; 0 turns it off (ordinary stream-ordered launches). */
 int fdlb_set_programmatic_launch(fdlb_handle h, int enable);
 
-/* Own cells per closure work item (1..28; default 4).  A closure item also recomputes the
+/* Own cells per closure work item (1..28; default 2 on the cylinder, 4 on the sphere).  A closure item also recomputes the
  * macroscopic fields of two stencil cells on each side, so larger items repeat less work and
  * smaller items spread the latency-bound closure over more SMs.  FDLB_EINVAL outside the
  * range. */

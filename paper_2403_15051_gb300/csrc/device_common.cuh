@@ -146,11 +146,17 @@ __device__ __forceinline__ Wide<float> w_scale(Wide<float> a, float c) {
     const float e = fmaf(a.lo, c, fmaf(a.hi, c, -p));
     return w_norm(p, e);
 }
-// a / b: a first quotient, the remainder a - q1 b in double-float, a correction
+// a / b: a first quotient, the remainder a - q1 b in double-float, a correction.  The two
+// quotients need only single-precision accuracy (the remainder is exact to the double-float
+// level), so they are the fast ones.
 __device__ __forceinline__ Wide<float> w_div(Wide<float> a, Wide<float> b) {
-    const float q1 = a.hi / b.hi;
+    const float q1 = __fdividef(a.hi, b.hi);
     const Wide<float> r = w_sub(a, w_scale(b, q1));
-    return w_norm(q1, r.hi / b.hi);
+    return w_norm(q1, __fdividef(r.hi, b.hi));
+}
+__device__ __forceinline__ Wide<double> w_shfl_xor(Wide<double> a, int o) { return {__shfl_xor_sync(0xffffffffu, a.v, o)}; }
+__device__ __forceinline__ Wide<float> w_shfl_xor(Wide<float> a, int o) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
 template <typename T>

@@ -561,6 +561,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.n_items = S.n_sitems;
     A.inst = S.inst_d;
     A.tab = S.tab;
+    A.tabT = S.tabT;
     A.geoT = S.geoT;
     A.gwT = S.gwT;
     A.err = S.err;
@@ -807,6 +808,8 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     // default tiling (the fastest of a sweep on GB300; fdlb_autotune refines it per workload):
     // whole cells per block, 4 cells per tile (cylinder, 256 threads) or 8 (sphere, 512 threads)
     rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, 256) : configure_tiling(R, 8, R.n3, 512);
+    R.closure_cells = R.geometry == FDLB_CYL ? 2 : 4;  // the fastest closure items with overlapped launches
+    if (!rc) rc = upload_items(R);
     for (int q = 0; q < n && !rc; ++q) rc = fdlb_init_uniform(reinterpret_cast<fdlb_handle>(S.get()), q, 0.0, 0.0);
     if (rc) {
         if (R.own_ws) cudaFree(R.ws);

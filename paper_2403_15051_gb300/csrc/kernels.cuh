@@ -72,6 +72,7 @@ struct StageArgs {
     const int* n_items;
     const InstDev* inst;
     const double* tab;
+    const void* tabT;              // the same tables in T
     const void* geoT;              // [cell][kGeo] in T
     const void* gwT;               // [instance][2][nR + n2 + n3] wall Maxwellians per axis, in T
     int* err;

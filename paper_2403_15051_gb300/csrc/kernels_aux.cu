@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
                 using C = T;
                 const int t = lane, c = c0 + t, lt = c - h0;
                 const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
-                const C in = C(1) / cn, iT = C(1) / cT, ichi = C(1) / cchi;
+                const C in = ratio_fast(C(1), cn), iT = ratio_fast(C(1), cT), ichi = ratio_fast(C(1), cchi);
                 C gsum[5];
 #pragma unroll
                 for (int v = 0; v < 5; ++v)
@@ -419,15 +419,15 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
                 const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
                 const C X = gsum[0] * sc, Y = gsum[1] * sc;
                 const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
-                const C iR = C(1) / geo0;
+                const C iR = ratio_fast(C(1), geo0);
                 const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
                 const C sg = inst_param<C>(I.sigma, I.f_sigma);
                 const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
                 const C pi = C(3.14159265358979323846);
-                const C mu = C(5) / (C(16) * sg * sg) * sqrt(cT / pi) *
+                const C mu = ratio_fast(C(5), C(16) * sg * sg) * sqrt(cT * C(0.31830988618379067154)) *
                              (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
-                const C Pr = C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x) /
-                             (C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
+                const C Pr = ratio_fast(C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x),
+                                        C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
                 C S11, S22, S01, S02, div;
                 if (I.geometry == 0) {
                     S11 = cu0 * iR;
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
                 ct[2] = cu1;
                 ct[3] = cu2;
                 ct[4] = iT;
-                ct[5] = cn * cT / mu;
+                ct[5] = ratio_fast(cn * cT, mu);
                 ct[6] = (C(1) - Pr) * iT * iT * in;
                 ct[7] = sq[0][t];
                 ct[8] = sq[1][t];
@@ -557,15 +557,24 @@ __global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
         // ---- 6. discrete mass of the stored equilibrium: the rounded vectors need not sum to
         // exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
         // would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is
-        // divided by the wide-precision product of the sums of the stored vectors.
-        if (tid < cnt) {
-            const int lt = c0 + tid - h0;
-            T* ct = rec + (long long)(c0 + tid) * rs;
-            W sR = w_from_t(T(0)), s2 = w_from_t(T(0)), s3 = w_from_t(T(0));
-            for (int k = 0; k < nR; ++k) sR = w_add(sR, w_from_t(ct[rec_off_gR(n2) + k]));
-            for (int j = 0; j < n2; ++j) s2 = w_add(s2, w_from_t(ct[rec_off_g2() + j]));
-            for (int j = 0; j < n3; ++j) s3 = w_add(s3, w_from_t(ct[rec_off_g3(nR, n2) + j]));
-            ct[0] = w_hi(w_div(sw_n[lt], w_mul(w_mul(sR, s2), s3)));
+        // divided by the wide-precision product of the sums of the stored vectors (a warp per own
+        // cell, a butterfly of wide sums: every lane ends with the same value).
+        for (int t = warp; t < cnt; t += NT / 32) {
+            T* ct = rec + (long long)(c0 + t) * rs;
+            W s3w[3] = {w_from_t(T(0)), w_from_t(T(0)), w_from_t(T(0))};
+            for (int k = lane; k < ng; k += 32) {
+                const int a = k < nR ? 0 : (k < nR + n2 ? 1 : 2);
+                const int src = a == 0 ? rec_off_gR(n2) + k : (a == 1 ? rec_off_g2() + k - nR : rec_off_g3(nR, n2) + k - nR - n2);
+                const W g = w_from_t(ct[src]);
+                s3w[0] = a == 0 ? w_add(s3w[0], g) : s3w[0];
+                s3w[1] = a == 1 ? w_add(s3w[1], g) : s3w[1];
+                s3w[2] = a == 2 ? w_add(s3w[2], g) : s3w[2];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
+            if (lane == 0) ct[0] = w_hi(w_div(sw_n[c0 + t - h0], w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
         }
         __syncthreads();  // shared arrays are reused by the next item
     }

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
     T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
     const T* __restrict__ rec_all = reinterpret_cast<const T*>(A.rec);
-    const double* __restrict__ tab = A.tab;
+    const T* __restrict__ tab = reinterpret_cast<const T*>(A.tabT);  // tables in T: no conversions
     const int gwstride = nR + n2 + n3;
 
     if (tid == 0) {
@@ -157,24 +157,24 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         fence_mbar_init();
     }
     for (int e = tid; e < nR; e += NT) {
-        sp_R[e] = (T)tab[M.o_pR + e];
-        sw_R[e] = (T)tab[M.o_wR + e];
+        sp_R[e] = tab[M.o_pR + e];
+        sw_R[e] = tab[M.o_wR + e];
     }
     for (int e = tid; e < n2; e += NT) {
-        sp_2[e] = (T)tab[M.o_p2 + e];
-        sw_2[e] = (T)tab[M.o_w2 + e];
+        sp_2[e] = tab[M.o_p2 + e];
+        sw_2[e] = tab[M.o_w2 + e];
     }
     for (int e = tid; e < n3; e += NT) {
-        sp_3[e] = (T)tab[M.o_p3 + e];
-        sw_3[e] = (T)tab[M.o_w3 + e];
+        sp_3[e] = tab[M.o_p3 + e];
+        sw_3[e] = tab[M.o_w3 + e];
     }
-    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * (nR + 1) + e % nR] = (T)tab[M.o_KR + e];
+    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * (nR + 1) + e % nR] = tab[M.o_KR + e];
     for (int e = tid; e < n2 * n2; e += NT) {
         const int j = e / n2, b = e % n2;
-        sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = (T)tab[M.o_K2 + e];
+        sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = tab[M.o_K2 + e];
     }
     if (GEOM == 1)
-        for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = (T)tab[M.o_K3 + e];
+        for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = tab[M.o_K3 + e];
     __syncthreads();
     pdl_trigger();
     pdl_wait();  // everything below reads what the previous kernels wrote
@@ -506,11 +506,19 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
         }
         __syncthreads();
         if (A.mode == 0) {
-            // FP64 sums over the warps in a fixed order
+            // FP64 sums over the warps: the conversions first (independent), then a fixed pairwise
+            // tree (the FP64 pipe is slow on this part: a chain of adds would be the tail of the item)
             for (int e = tid; e < Be * kSums; e += NT) {
                 const int cl = e / kSums, q = e % kSums;
-                double s = 0.0;
-                for (int ww = 0; ww < nwarps; ++ww) s += (double)red[(cl * nwarps + ww) * 16 + q];
+                constexpr int kW = 16;  // at most 512 threads
+                double v[kW];
+#pragma unroll
+                for (int ww = 0; ww < kW; ++ww) v[ww] = ww < nwarps ? (double)red[(cl * nwarps + ww) * 16 + q] : 0.0;
+#pragma unroll
+                for (int h = kW / 2; h > 0; h >>= 1)
+#pragma unroll
+                    for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
+                const double s = v[0];
                 const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
                 A.sums_out[cs * kSums + q] = s;
                 if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
