@@ -206,6 +206,14 @@ const char* fdlb_error_string(int code);
 int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads);
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
 
+/* The K^h contraction of the curvature force on the tensor cores (default off): an
+ * nR x nR by nR x (n2 KS) product per cell in split TF32 (K = Kh + Kl, f = fh + fl; three
+ * TF32 products with FP32 accumulation, FP32-level accuracy) with mma.sync m16n8k8, for FP32
+ * populations on the 16 x 8 x 8 and 24 x 12 x 12 quadratures; elsewhere the CUDA-core path
+ * stays.  *in_use (may be NULL) tells whether it applies to this handle.  On GB300 these
+ * contractions are too small to pay for the splitting: the default is the CUDA-core path. */
+int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use);
+
 /* Programmatic dependent launch of the closure and stage kernels (default on): each may start
  * while its predecessor in the stream finishes, loading its constant tables, and waits for the
  * predecessor's completion before it reads anything the predecessor writes.  Results are the same

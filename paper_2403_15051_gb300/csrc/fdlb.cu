@@ -86,6 +86,8 @@ struct Solver {
     // per-kernel timing (events around each launch, direct launches)
     bool timing = false;
     int programmatic = 1;  // closure and stage kernels overlap their prologues with the predecessor
+    int tensor = 0;        // K^h contraction on the tensor cores where available
+    int mma_on = 0;        // ... and in use for the current tiling
     cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
     double t_stream_ms = 0.0, t_closure_ms = 0.0;
     int64_t n_stream_t = 0, n_closure_t = 0;
@@ -425,9 +427,10 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
     S.scfg = cfg;
     S.threads = nt;
+    S.mma_on = S.tensor && cfg.spec && cfg.vw == 4 && S.tsize == 4 && S.nR % 8 == 0;
     // shrink the tile until it fits in shared memory
     for (;;) {
-        StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize);
+        StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize, S.mma_on ? 1 : 0);
         if ((size_t)P.total <= S.smem_optin || S.B <= 2) {
             S.smem_stream = P.total;
             break;
@@ -573,6 +576,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.B = S.B;
     A.use_bulk = S.use_bulk;
     A.programmatic = S.programmatic;
+    A.mma = S.mma_on;
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
@@ -1301,6 +1305,15 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
     if (cells_per_tile) *cells_per_tile = S->B;
     if (slice_k) *slice_k = S->KS;
     if (threads) *threads = S->threads;
+    return rc;
+}
+
+int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    S->tensor = enable ? 1 : 0;
+    const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
+    if (in_use) *in_use = S->mma_on;
     return rc;
 }
 

@@ -83,6 +83,7 @@ struct StageArgs {
     int B;                         // cells per tile
     int use_bulk;                  // stage the tile with cp.async.bulk
     int programmatic;              // launched with programmatic stream serialization
+    int mma;                       // K^h contraction on the tensor cores (FP32 compile-time shapes)
 };
 
 struct ClosureArgs {

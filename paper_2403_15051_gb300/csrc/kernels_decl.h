@@ -35,14 +35,15 @@ inline cudaError_t launch_maybe_programmatic(void (*kern)(Args...), int grid, in
 }
 
 struct StreamSmem {
-    int fs, rec, tabs, geo, red, total;
+    int fs, rec, tabs, geo, red, kr, total;
 };
 
 // Shared-memory plan of the stream kernel (byte offsets), shared with the host: the staged rows
 // of cells c0-3 .. c0+B+2, the tile's collision records, the tables (radial nodes and weights,
 // K^h with row stride nR+1, K_2 in the vector-swizzled order, K_3 with row stride n3+1, wall
 // Maxwellians), the cell geometry and the per-warp partial sums.
-__host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize) {
+__host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize,
+                                                       int mma = 0) {
     auto al = [](long long x) { return (int)((x + 15) & ~15LL); };
     StreamSmem s;
     int off = 16;  // mbarrier
@@ -56,6 +57,8 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
     off += al((long long)B * 3 * tsize);
     s.red = off;
     off += al((long long)B * nwarps * 16 * tsize);
+    s.kr = off;  // K^h f of the tile's own cells (tensor-core path)
+    if (mma) off += al((long long)B * Ms * tsize);
     s.total = off;
     return s;
 }

@@ -127,7 +127,11 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     const int n2v = n2 / VW;               // vectors per (k, i) row
     const int Vs = Ms / VW;                // vectors per slice
     const int rs = record_stride(nR, n2, n3);
-    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T));
+    // K^h contraction on the tensor cores (split TF32): available for the FP32 compile-time
+    // shapes, used when the host asks for it
+    constexpr bool kMMA = sizeof(T) == 4 && NR_ > 0 && NR_ % 8 == 0 && VW == 4;
+    const bool use_mma = kMMA && A.mma;
+    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T), use_mma ? 1 : 0);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);  // rows: cells c0-3 .. c0+B+2
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     T* sgw = sw_3 + n3;            // [2][nR + n2 + n3]: inner and outer wall Maxwellian per axis
     T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
     T* red = reinterpret_cast<T*>(smem_raw + P.red);  // [cell][warp][16] warp sums
+    T* skrf = reinterpret_cast<T*>(smem_raw + P.kr);   // [cell][k][i][j] K^h f of the own cells
     __shared__ T snw[2];                               // wall densities of the item's instance
     const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
     const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
@@ -281,6 +286,59 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             __syncthreads();
         }
 
+        // ---- 3b. tensor cores: (K^h f)[i][(k, j)] = sum_a K^h[i][a] f[k][a][j] for the own cells,
+        // a GEMM of the nR x nR matrix with the cell's nR x (n2 KS) slice, in split TF32
+        // (K = Kh + Kl, f = fh + fl; Kh fh + Kh fl + Kl fh with FP32 accumulation: FP32-level
+        // products), n-tiles of 8 columns spread over the warps, results to shared memory.
+        if constexpr (kMMA) {
+          if (use_mma) {
+            constexpr int MT = (NR_ + 15) / 16, KT = NR_ / 8;
+            const int g = lane >> 2, tg = lane & 3;
+            uint32_t ah[MT][KT][4], alo[MT][KT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int ks = 0; ks < KT; ++ks)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = mt * 16 + g + ((q & 1) ? 8 : 0), cidx = ks * 8 + tg + ((q & 2) ? 4 : 0);
+                        const float x = r < NR_ ? sKR[r * (NR_ + 1) + cidx] : 0.f;
+                        ah[mt][ks][q] = to_tf32(x);
+                        alo[mt][ks][q] = to_tf32(x - __uint_as_float(ah[mt][ks][q]));
+                    }
+            const int ncol = n2 * KS, ntc = ncol / 8;
+            for (int tt = warp; tt < Be * ntc; tt += nwarps) {
+                const int cl = tt / ntc, nt = tt % ntc;
+                const int colb = nt * 8 + g;  // this lane's B column (k, j)
+                const T* bsrc = fs + (long long)(cl + 3) * Ms + ((colb / n2) * nR) * n2 + colb % n2;
+                float acc[MT][4];
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < KT; ++ks) {
+                    const float x0 = bsrc[(ks * 8 + tg) * n2], x1 = bsrc[(ks * 8 + tg + 4) * n2];
+                    const uint32_t bh0 = to_tf32(x0), bh1 = to_tf32(x1);
+                    const uint32_t bl0 = to_tf32(x0 - __uint_as_float(bh0)), bl1 = to_tf32(x1 - __uint_as_float(bh1));
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        mma_tf32(acc[mt], alo[mt][ks], bh0, bh1);
+                        mma_tf32(acc[mt], ah[mt][ks], bl0, bl1);
+                        mma_tf32(acc[mt], ah[mt][ks], bh0, bh1);
+                    }
+                }
+                T* dst = skrf + (long long)cl * Ms;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = mt * 16 + g + ((q & 2) ? 8 : 0), cc = nt * 8 + 2 * tg + (q & 1);
+                        if (r < NR_) dst[((cc / n2) * nR + r) * n2 + cc % n2] = acc[mt][q];
+                    }
+            }
+            __syncthreads();
+          }
+        }
+
         // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
         int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
         T pr_[NV], p3_[NV];
@@ -387,15 +445,19 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
 #pragma unroll
                     for (int e = 0; e < VW; ++e) KRf[e] = K2f[e] = K3f[e] = T(0);
                     {
-                        const T* col = fc + kk * nR * n2 + jb * VW;
-                        const T* kr = sKR + i * (nR + 1);
+                        if (kMMA && use_mma) {
+                            ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
+                        } else {
+                            const T* col = fc + kk * nR * n2 + jb * VW;
+                            const T* kr = sKR + i * (nR + 1);
 #pragma unroll 8
-                        for (int a = 0; a < nR; ++a) {
-                            T cv[VW];
-                            ld_vec<T, VW>(col + a * n2, cv);
-                            const T kv = kr[a];
+                            for (int a = 0; a < nR; ++a) {
+                                T cv[VW];
+                                ld_vec<T, VW>(col + a * n2, cv);
+                                const T kv = kr[a];
 #pragma unroll
-                            for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                                for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                            }
                         }
                         const T* row = fc + (kk * nR + i) * n2;
 #pragma unroll 4

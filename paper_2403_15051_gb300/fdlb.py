@@ -92,6 +92,7 @@ def load_library():
         "fdlb_set_tiling": (c_int, [H, c_int, c_int, c_int]),
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
+        "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_autotune": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_launch_count": (c_int64, [H]),
         "fdlb_set_graph_steps": (c_int, [H, c_int]),
@@ -293,6 +294,12 @@ class Solver:
 
     def set_tiling(self, cells=0, slice_k=0, threads=0):
         _check(self._L.fdlb_set_tiling(self._h, cells, slice_k, threads), "fdlb_set_tiling")
+
+    def set_tensor_contraction(self, enable):
+        used = c_int()
+        _check(self._L.fdlb_set_tensor_contraction(self._h, 1 if enable else 0, byref(used)),
+               "fdlb_set_tensor_contraction")
+        return bool(used.value)
 
     def set_programmatic_launch(self, enable):
         _check(self._L.fdlb_set_programmatic_launch(self._h, 1 if enable else 0), "fdlb_set_programmatic_launch")

@@ -252,3 +252,18 @@ def test_programmatic_launch_is_bit_identical():
         S.step(30)
         out.append(S.get_f())
     assert np.array_equal(out[0], out[1])
+
+
+def test_tensor_core_contraction_matches_oracle():
+    """The split-TF32 tensor-core K^h contraction (FP32, 16 x 8 x 8 quadrature at full size): the
+    RHS and ten steps against the FP64 oracle within the FP32 tolerances."""
+    d = wl.fourier_cyl_1024()
+    P, f0, S = _pair(d, seed=21, amp=0.02)
+    assert S.set_tensor_contraction(True)
+    L = S.eval_rhs()
+    L_or = osolver.rhs(f0, P)
+    assert np.max(np.abs(L - L_or)) / np.max(np.abs(L_or)) <= RHS_TOL["fp32"]
+    S.step(10)
+    f_or = osolver.run(f0, P, 10)
+    errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
+    assert max(errs.values()) <= TOL["fp32"], errs
