@@ -269,7 +269,7 @@ int plan_solver(const fdlb_params* ps, int n, Solver& S) {
         S.total_cells += N;
         S.f_elems += align_up((size_t)N * S.Np, falign);
         S.band_elems += (size_t)N * S.setup[q].band.width;
-        S.max_sitems += ((N + 3) / 4) * S.n3;
+        S.max_sitems += (N / 2 + 1) * S.n3;  // tiles of at least two cells, at most n3 slices
         S.max_citems += N + 2 * kWallParts;  // room for one-cell closure items, + the wall items
     }
     S.active.assign(n, 1);
@@ -336,7 +336,15 @@ int upload_items(Solver& S) {
     const int slices = S.n3 / S.KS;
     for (int q : order) {
         const int N = S.setup[q].p.n_cells;
-        const int nt = (N + S.B - 1) / S.B;
+        int nt = (N + S.B - 1) / S.B;
+        if (S.n_inst == 1 && S.n_sm > 0) {
+            // one instance: a multiple of the SM count of tiles (one or more full waves; every
+            // SM gets the same number of tiles), tile sizes differing by at most one cell, the
+            // larger first, as long as tiles keep at least two cells
+            const int per_wave = S.n_sm;
+            const int r = (nt * slices + per_wave - 1) / per_wave * per_wave / slices;
+            if (r >= nt && r * slices % per_wave == 0 && N / r >= 2) nt = r;
+        }
         const int base = N / nt, rem = N % nt;
         int c0 = 0;
         for (int t = 0; t < nt; ++t) {
