@@ -1,0 +1,55 @@
+"""The replica bookkeeping of bench.py on two ranks of the gloo backend (host cores): the timing
+is the maximum over the ranks, the whole-job rate counts every rank's work, and the comparison
+arm runs on rank 0 alone while the other ranks exit without work."""
+import io
+import json
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    w, r, _ = bench.dist_setup()
+    assert (w, r) == (world, rank)
+    ms = bench.max_over_ranks(10.0 + rank, w)
+    rate = bench.job_rate(1000, 5, w, ms)
+    bench.barrier(w)
+    buf = io.StringIO()
+    args = bench.argparse.Namespace(workload="couette_cyl_64", steps=1, warmup=0, gpus=world, no_cpu_baseline=True)
+    with redirect_stdout(buf):
+        rc = bench.run_reference(args)
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as fh:
+        json.dump({"ms": ms, "rate": rate, "rc": rc, "stdout": buf.getvalue()}, fh)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    mp.start_processes(_rank, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
+    r0 = json.load(open(tmp_path / "rank0.json"))
+    r1 = json.load(open(tmp_path / "rank1.json"))
+    assert r0["ms"] == r1["ms"] == 11.0  # the slowest rank
+    assert r0["rate"] == pytest.approx(1000 * 5 * 2 / 11.0e-3)
+    assert r0["rc"] == r1["rc"] == 0
+    assert r1["stdout"] == ""  # the comparison arm runs on rank 0 only
+    line = json.loads(r0["stdout"].strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
