@@ -3,13 +3,15 @@
 steps per second) on the cylindrical Fourier-flow workload (1024 stretched cells, 16 x 8 x 8 =
 1024 momenta, FP32 populations with FP64 moment sums).
 
-One timed step = one SSP-RK3 step of the whole instance (3 closure + 3 fused-stage launches,
-replayed from a one-step CUDA graph), with L2 flushed (256 MB write) before every timed step
-because the 4 MB population arrays would otherwise stay L2-resident.  Device time from CUDA
+One timed step = one SSP-RK3 step of the whole instance: one launch of the persistent step
+kernel (per stage and tile the closure and the fused stage, grid barriers between stages) where
+it applies, else 3 closure + 3 fused-stage launches replayed from a one-step CUDA graph; L2 is
+flushed (256 MB write) before every timed step because the 4 MB population arrays would
+otherwise stay L2-resident.  Device time from CUDA
 events on the solver's stream; max over ranks (one independent replica per GPU: weak scaling).
 
-Also reported: the fused-stage kernel against its roofline (it is bound by FP32 arithmetic
-issue: algorithmic flops per launch / its event-timed duration against the FP32 CUDA-core peak;
+Also reported: the dominant kernel against its roofline (it is bound by FP32 arithmetic issue:
+algorithmic flops per launch / its event-timed duration against the FP32 CUDA-core peak;
 the HBM view of the same launch for context), the end-to-end rate through the C ABI with host
 buffers, the FP64 CPU oracle timed on the host cores (`cpu_baseline`), SM clocks sampled during
 the run.
@@ -38,8 +40,8 @@ METRIC = "node-velocity updates/s"
 UNIT = "updates/s"
 L2_FLUSH_BYTES = 256 << 20
 REF_BUDGET_S = 120.0
-KERNEL_SOURCES = ["paper_2403_15051_gb300/csrc/stream_kernel.cuh", "paper_2403_15051_gb300/csrc/device_common.cuh",
-                  "paper_2403_15051_gb300/csrc/kernels_decl.h"]
+KERNEL_SOURCES = ["paper_2403_15051_gb300/csrc/" + f for f in (
+    "step_kernel.cuh", "stream_kernel.cuh", "closure_item.cuh", "device_common.cuh", "kernels_decl.h", "kernels.cuh")]
 
 
 def accept_kn(kn, eta0):
@@ -96,16 +98,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name):
-    """DRAM bytes per fused-stage launch from the committed ncu summary, if it was taken on
-    the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "stream_kernel_traffic.json")
+def recorded_traffic(workload_name, kernel):
+    """DRAM bytes per launch of `kernel` on the workload from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except Exception:
         return None
-    ent = rec.get(workload_name)
+    ent = rec.get(workload_name + ":" + kernel)
     if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
     return float(ent["dram_bytes_per_launch"])
@@ -230,14 +232,16 @@ def cpu_baseline(ds, budget_s=15.0):
                       f"({el:.1f} s, numpy FP64, one thread)"}
 
 
-def bench_config(args, ds, world, flush_needed):
+def bench_config(args, ds, world, flush_needed, persistent=False):
     d = ds[0]
     units = units_per_step(ds)
     return {"workload": args.workload, "instances": len(ds), "n_cells": sum(x["n_cells"] for x in ds),
             "n_momenta": 2 * d["Q_R"] * d["Q_2"] * d["Q_3"], "precision": d["precision"],
             "updates_per_step": units,
             "l2": "flushed by a 256 MB write before every timed step" if flush_needed else "inputs larger than L2",
-            "graph": "one-step CUDA graph per timed step", "parallelism": f"{world} independent replicas"}
+            "launch": ("one persistent step-kernel launch per timed step" if persistent
+                       else "one-step CUDA graph per timed step"),
+            "parallelism": f"{world} independent replicas"}
 
 
 def needs_flush(ds):
@@ -293,6 +297,7 @@ def run_ours(args):
     fbuild.build()
     ds = workload(args.workload)
     S = fdlb.Solver(ds)
+    persistent = S.set_persistent_step(None)  # the library's default scheduling
     S.set_graph_steps(1)
     stream = torch.cuda.ExternalStream(S.stream_handle())
     units = units_per_step(ds)
@@ -349,13 +354,16 @@ def run_ours(args):
     ms_max = max_over_ranks(ms, world)
     value = job_rate(units, args.steps, world, ms_max)
 
-    # ---- fused-stage kernel timing over K more steps (events around every launch)
+    # ---- kernel timing over K more steps (events around every launch): the persistent step
+    # kernel where it is in use, else the closure and fused-stage kernels
     S.set_kernel_timing(True)
     S.kernel_times()
+    S.step_kernel_times()
     for k in range(args.steps):
         l2_flush(k)
         S.step(1)
     stream_ms, n_stream, closure_ms, n_closure = S.kernel_times()
+    step_ms, n_step_launch, n_step_steps = S.step_kernel_times()
     S.set_kernel_timing(False)
     clocks = sampler.stop()
 
@@ -393,29 +401,39 @@ def run_ours(args):
     e2e = {"value": units * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
            "d2h_bytes_per_step": d2h // e2e_steps}
 
-    # ---- roofline of the fused-stage kernel.  It is bound by FP32 arithmetic issue, not by
-    # HBM: achieved = algorithmic flops per launch / event-timed launch duration, against the
-    # FP32 CUDA-core peak from the unit counts and the sampled SM clock.  The HBM view (8 population
-    # passes per SSP-RK3 step -> 8/3 per launch, against the measured copy bandwidth) is kept for
-    # context.
+    # ---- roofline of the dominant kernel: the persistent step kernel (one launch per timed step:
+    # three stages, each with its closure) or else the fused-stage kernel (one stage per launch).
+    # It is bound by FP32 arithmetic issue, not by HBM: achieved = algorithmic flops per launch /
+    # event-timed launch duration, against the FP32 CUDA-core peak from the unit counts and the
+    # sampled SM clock.  The HBM view (8 population passes per SSP-RK3 step, against the measured
+    # copy bandwidth) is kept for context.
     hbm_peak, peak_kind = measured_peaks()
-    avg_stream_ms = stream_ms / max(n_stream, 1)
     d0 = ds[0]
     nR, n2, n3 = 2 * d0["Q_R"], d0["Q_2"], d0["Q_3"]
     fpu = alg_flops_per_update(d0["geometry"], nR, n2, n3)
-    alg_flops = fpu * units
+    if persistent and n_step_launch:
+        kernel = "step_kernel"
+        stages_per_launch = 3.0 * n_step_steps / n_step_launch
+        avg_ms = step_ms / n_step_launch
+    else:
+        kernel = "stream_kernel"
+        stages_per_launch = 1.0
+        avg_ms = stream_ms / max(n_stream, 1)
+    alg_flops = fpu * units * stages_per_launch
     sm_mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
     alu_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    achieved = alg_flops / (avg_stream_ms * 1e-3) / 1e12
-    alg_bytes = 8.0 / 3.0 * state_bytes
-    hbm_achieved = alg_bytes / (avg_stream_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload)
+    achieved = alg_flops / (avg_ms * 1e-3) / 1e12
+    alg_bytes = 8.0 / 3.0 * state_bytes * stages_per_launch
+    hbm_achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload, kernel)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz,
-                "kernel": "stream_kernel", "alg_flops_per_update": fpu, "alg_flops_per_launch": alg_flops,
-                "avg_launch_ms": avg_stream_ms, "closure_avg_launch_ms": closure_ms / max(n_closure, 1),
+                "kernel": kernel, "alg_flops_per_update": fpu, "stages_per_launch": stages_per_launch,
+                "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
                 "hbm_view": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                              "alg_bytes_per_launch": alg_bytes, "peak_source": peak_kind}}
+    if not persistent:
+        roofline["closure_avg_launch_ms"] = closure_ms / max(n_closure, 1)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -425,7 +443,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if tsize == 4 else "f64", "data": "synthetic",
-                "config": bench_config(args, ds, world, flush_needed),
+                "config": bench_config(args, ds, world, flush_needed, persistent),
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "hot_l2_value": hot_value}
         print(json.dumps(line))

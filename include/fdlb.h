@@ -214,6 +214,18 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
  * contractions are too small to pay for the splitting: the default is the CUDA-core path. */
 int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use);
 
+/* Whole SSP-RK3 steps in one persistent launch (default off): each block owns tiles of cells
+ * for the launch and runs, per stage, the closure of its own cells into shared memory and the
+ * stage, with a grid-wide barrier between stages (cooperative launch, every wait bounded: a
+ * barrier that does not complete within 1 s sets the error flag, reported as FDLB_ETIMEOUT by
+ * fdlb_get_diagnostics).  The results are those of the closure and stage kernels, bit for bit.
+ * It applies to the 16 x 8 x 8 and 24 x 12 x 12 quadratures with one momentum slice when the
+ * grid fits on the device at once; elsewhere, and in kernel-timing mode, the two launches per
+ * stage stay.  enable < 0 only reports; *in_use (may be NULL) tells whether it applies to this
+ * handle.  This scheduling is an implementation choice of this library; the paper describes the
+ * method, not launches. */
+int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use);
+
 /* Programmatic dependent launch of the closure and stage kernels (default on): each may start
  * while its predecessor in the stream finishes, loading its constant tables, and waits for the
  * predecessor's completion before it reads anything the predecessor writes.  Results are the same
@@ -235,8 +247,11 @@ int fdlb_set_graph_steps(fdlb_handle h, int steps);
 /* Per-kernel timing.  When on, fdlb_step launches the kernels directly (no graph) and brackets
  * every closure and streaming launch with CUDA events on the solver's stream; fdlb_kernel_times
  * returns the accumulated durations (ms) and launch counts since the last call and clears them.
- * Any output pointer may be NULL. */
+ * Where the persistent step kernel is in use (fdlb_set_persistent_step), its launches are timed
+ * instead and fdlb_step_kernel_times returns their accumulated duration (ms), the number of
+ * launches and the steps they ran.  Any output pointer may be NULL. */
 int fdlb_set_kernel_timing(fdlb_handle h, int on);
+int fdlb_step_kernel_times(fdlb_handle h, double* ms, int64_t* launches, int64_t* steps);
 int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, double* closure_ms,
                       int64_t* n_closure);
 

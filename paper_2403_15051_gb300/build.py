@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlb_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["fdlb.cu", "kernels_aux.cu", "stream_float_0.cu", "stream_float_1.cu", "stream_double_0.cu",
-              "stream_double_1.cu", "noalloc.cu", "nn.cu"]
+              "stream_double_1.cu", "step_float_0.cu", "step_float_1.cu", "step_double_0.cu", "step_double_1.cu",
+              "noalloc.cu", "nn.cu"]
 CPP_SOURCES = ["setup.cpp"]
 
 
@@ -49,7 +50,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-                         "-diag-suppress", "549,1886", "-c", s, "-o", o])
+                         "-diag-suppress", "549,1886,177", "-c", s, "-o", o])
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src + ".o")

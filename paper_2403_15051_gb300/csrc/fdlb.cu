@@ -25,7 +25,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
     size_t f[3], sums[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
-        n_citems, nwp, err,
+        n_citems, nwp, err, gbar,
         rprev, rout, total;
 };
 
@@ -64,6 +64,7 @@ struct Solver {
     int* band_lo = nullptr;
     int4 *sitems = nullptr, *citems = nullptr;
     int *n_sitems = nullptr, *n_citems = nullptr, *err = nullptr;
+    unsigned* gbar = nullptr;
     std::vector<double> tab_h;
     MomSet M{};
     // tiling of the stream kernel
@@ -88,8 +89,14 @@ struct Solver {
     int programmatic = 1;  // closure and stage kernels overlap their prologues with the predecessor
     int tensor = 0;        // K^h contraction on the tensor cores where available
     int mma_on = 0;        // ... and in use for the current tiling
+    // persistent step kernel (closure + stage per tile, grid barriers between stages)
+    int fused = 0;         // use it where the configuration allows (off by default: slower on GB300)
+    int fused_on = 0;      // ... and in use for the current tiling
+    int grid_step = 0, step_wst = 0, step_clo_off = 0, max_tile = 0;
+    size_t smem_step = 0;
     cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
-    double t_stream_ms = 0.0, t_closure_ms = 0.0;
+    double t_stream_ms = 0.0, t_closure_ms = 0.0, t_step_ms = 0.0;
+    int64_t n_step_t = 0, n_step_steps = 0;
     int64_t n_stream_t = 0, n_closure_t = 0;
 };
 
@@ -209,6 +216,7 @@ Layout make_layout(const Solver& S) {
     L.n_citems = take(sizeof(int));
     L.nwp = take((size_t)S.n_inst * 2 * kWallParts * S.tsize);
     L.err = take(sizeof(int));
+    L.gbar = take(64);  // grid barrier counter of the persistent step kernel
     L.rprev = take((size_t)S.total_cells * 4 * sizeof(double));
     L.rout = take((size_t)S.n_inst * 10 * sizeof(double));
     L.total = off;
@@ -326,6 +334,48 @@ void fill_inst(Solver& S, int q) {
 
 // Work lists: stream items (instance, first cell, cells, slice) over the active instances,
 // tiles of 3..B cells, largest instances first; closure items (instance, first cell, cells).
+cudaError_t launch_step_dispatch(const Solver& S, const StepArgs* P, int* blocks_per_sm) {
+    const int g = S.geometry;
+    if (S.precision == FDLB_FP32)
+        return g == FDLB_CYL ? launch_step_float_0(S.scfg, P, S.M, S.grid_step, S.threads, S.smem_step, S.stream, blocks_per_sm)
+                             : launch_step_float_1(S.scfg, P, S.M, S.grid_step, S.threads, S.smem_step, S.stream, blocks_per_sm);
+    return g == FDLB_CYL ? launch_step_double_0(S.scfg, P, S.M, S.grid_step, S.threads, S.smem_step, S.stream, blocks_per_sm)
+                         : launch_step_double_1(S.scfg, P, S.M, S.grid_step, S.threads, S.smem_step, S.stream, blocks_per_sm);
+}
+
+// Whether the persistent step kernel runs the current configuration, and its launch shape: the
+// compile-time shapes, one momentum slice, the bulk staging, tiles within the closure's reach,
+// at least one warp beyond the closure's four, and a co-resident grid (every block owns the
+// tiles it + k grid for the whole launch).
+int plan_step_kernel(Solver& S, int n_items) {
+    S.fused_on = 0;
+    S.grid_step = 0;
+    if (!S.fused || !S.scfg.spec || S.M.slices != 1 || !S.use_bulk || S.threads < 5 * 32 || S.max_tile < 1 ||
+        S.max_tile > kClosureCells || n_items < 1)
+        return FDLB_OK;
+    // shared memory: the stage's plan, then [staged band rows | closure tables | band-union
+    // densities]; static shared memory of the closure (< 16 KB) stays below the opt-in limit
+    const size_t clo_off = (S.smem_stream + 15) / 16 * 16;
+    const size_t base = clo_off + closure_smem(S.nR, S.n2, S.n3, S.max_union, 0, (int)S.tsize);
+    const size_t limit = S.smem_optin > 16384 ? S.smem_optin - 16384 : 0;
+    if (base > limit) return FDLB_OK;
+    int wst = 0;
+    for (int q = 0; q < S.n_inst; ++q)
+        wst = std::max(wst, std::min(S.setup[q].p.n_cells, S.max_tile + 4) * S.setup[q].band.width);
+    wst = (int)std::min<size_t>((size_t)wst, (limit - base) / S.tsize);
+    S.step_wst = wst;
+    S.step_clo_off = (int)clo_off;
+    S.smem_step = clo_off + closure_smem(S.nR, S.n2, S.n3, S.max_union, wst, (int)S.tsize);
+    int bps = 0;
+    if (launch_step_dispatch(S, nullptr, &bps) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        return FDLB_OK;
+    }
+    S.grid_step = std::min(n_items, bps * S.n_sm);
+    S.fused_on = 1;
+    return FDLB_OK;
+}
+
 int upload_items(Solver& S) {
     std::vector<int> order;
     for (int q = 0; q < S.n_inst; ++q)
@@ -364,17 +414,24 @@ int upload_items(Solver& S) {
     FDLB_CUDA(cudaMemcpyAsync(S.n_sitems, &ns, sizeof(int), cudaMemcpyHostToDevice, S.stream));
     FDLB_CUDA(cudaMemcpyAsync(S.n_citems, &nc, sizeof(int), cudaMemcpyHostToDevice, S.stream));
     FDLB_CUDA(cudaStreamSynchronize(S.stream));  // host vectors go out of scope
-    // closure shared memory: the tables and the union of the FM bands of one item's reach
+    // closure shared memory: the tables and the union of the FM bands of one item's reach (the
+    // closure kernel's items and, for the persistent step kernel, the tiles)
     int max_union = 1;
-    for (const int4& w : ci) {
-        if (w.w != 0) continue;
+    S.max_tile = 0;
+    auto reach_union = [&](const int4& w) {
         const InstanceSetup& I = S.setup[w.x];
-        if (I.band.width == 0) continue;
+        if (I.band.width == 0) return;
         const int N = I.p.n_cells;
         const int h0 = std::max(0, std::min(w.y - 2, N - 5)), h1 = std::min(N, std::max(w.y + w.z + 2, 5));
         const int lo = I.band.lo[h0];
         const int hi = std::min(N - 1, I.band.lo[h1 - 1] + I.band.cnt[h1 - 1] - 1 + 3);
         max_union = std::max(max_union, hi - lo + 1);
+    };
+    for (const int4& w : ci)
+        if (w.w == 0) reach_union(w);
+    for (const int4& w : si) {
+        reach_union(w);
+        S.max_tile = std::max(S.max_tile, w.z);
     }
     S.max_union = max_union;
     // staged band rows of one item's reach (at most closure_cells + 4 rows); instances whose rows
@@ -389,7 +446,7 @@ int upload_items(Solver& S) {
     S.closure_smem = closure_smem(S.nR, S.n2, S.n3, max_union, wst, (int)S.tsize);
     S.grid_closure = std::max(1, std::min(nc, S.n_sm * 8));
     S.grid_stream = std::max(1, ns);
-    return FDLB_OK;
+    return plan_step_kernel(S, ns);
 }
 
 int launch_moments_all(Solver& S, int buf);
@@ -682,9 +739,79 @@ int ensure_graph(Solver& S) {
     return cuda_status(e);
 }
 
+// n whole steps in one launch of the persistent step kernel (barrier counter cleared first).
+int launch_steps_fused(Solver& S, int64_t n) {
+    StepArgs P{};
+    StageArgs& A = P.st;
+    A.rec = S.rec;
+    A.rec_stride = record_stride(S.nR, S.n2, S.n3);
+    A.nwp = S.nwp;
+    A.wall_parts = kWallParts;
+    A.items = S.sitems;
+    A.n_items = S.n_sitems;
+    A.inst = S.inst_d;
+    A.tab = S.tab;
+    A.tabT = S.tabT;
+    A.geoT = S.geoT;
+    A.gwT = S.gwT;
+    A.err = S.err;
+    A.mode = 0;
+    A.B = S.B;
+    A.use_bulk = S.use_bulk;
+    A.mma = S.mma_on;
+    ClosureArgs& C = P.cl;
+    C.cw = S.cw;
+    C.rec = S.rec;
+    C.rec_stride = A.rec_stride;
+    C.nwp = S.nwp;
+    C.items = S.sitems;
+    C.n_items = S.n_sitems;
+    C.inst = S.inst_d;
+    C.band = S.band;
+    C.band_lo = S.band_lo;
+    C.tabT = S.tabT;
+    C.geoT = S.geoT;
+    C.slices = S.M.slices;
+    C.max_union = S.max_union;
+    C.wall_parts = kWallParts;
+    C.wst_elems = S.step_wst;
+    C.err = S.err;
+    for (int b = 0; b < 3; ++b) {
+        P.f[b] = S.f[b];
+        P.sums[b] = S.sums[b];
+        P.dens[b] = S.dens[b];
+    }
+    P.bar = S.gbar;
+    P.n_steps = (int)n;
+    P.clo_off = S.step_clo_off;
+    FDLB_CUDA(cudaMemsetAsync(S.gbar, 0, sizeof(unsigned), S.stream));
+    S.launches++;
+    if (!S.timing) return cuda_status(launch_step_dispatch(S, &P, nullptr));
+    FDLB_CUDA(cudaEventRecord(S.tev[0], S.stream));
+    const int rc = cuda_status(launch_step_dispatch(S, &P, nullptr));
+    if (rc) return rc;
+    FDLB_CUDA(cudaEventRecord(S.tev[1], S.stream));
+    FDLB_CUDA(cudaEventSynchronize(S.tev[1]));
+    float m = 0.f;
+    FDLB_CUDA(cudaEventElapsedTime(&m, S.tev[0], S.tev[1]));
+    S.t_step_ms += m;
+    S.n_step_t++;
+    S.n_step_steps += n;
+    return FDLB_OK;
+}
+
 int do_steps(Solver& S, int64_t n) {
     const int64_t before = S.launches;
     int64_t done = 0;
+    if (S.fused_on) {
+        constexpr int64_t kMaxStepsPerLaunch = 1 << 12;
+        while (done < n) {
+            const int64_t k = std::min(n - done, kMaxStepsPerLaunch);
+            const int rc = launch_steps_fused(S, k);
+            if (rc) return rc;
+            done += k;
+        }
+    }
     if (n >= S.graph_steps && !S.timing) {
         int rc = ensure_graph(S);
         if (rc) return rc;
@@ -757,6 +884,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.geoT = (void*)(R.ws + L.geoT);
     R.gwT = (void*)(R.ws + L.gwT);
     R.err = (int*)(R.ws + L.err);
+    R.gbar = (unsigned*)(R.ws + L.gbar);
     R.rprev = (double*)(R.ws + L.rprev);
     R.rout = (double*)(R.ws + L.rout);
     FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
@@ -1325,6 +1453,19 @@ int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) {
     return rc;
 }
 
+int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (enable < 0) {  // query only
+        if (in_use) *in_use = S->fused_on;
+        return FDLB_OK;
+    }
+    S->fused = enable ? 1 : 0;
+    const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
+    if (in_use) *in_use = S->fused_on;
+    return rc;
+}
+
 int fdlb_set_programmatic_launch(fdlb_handle h, int enable) {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
@@ -1381,6 +1522,17 @@ int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, doubl
     if (n_closure) *n_closure = S->n_closure_t;
     S->t_stream_ms = S->t_closure_ms = 0.0;
     S->n_stream_t = S->n_closure_t = 0;
+    return FDLB_OK;
+}
+
+int fdlb_step_kernel_times(fdlb_handle h, double* ms, int64_t* launches, int64_t* steps) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (ms) *ms = S->t_step_ms;
+    if (launches) *launches = S->n_step_t;
+    if (steps) *steps = S->n_step_steps;
+    S->t_step_ms = 0.0;
+    S->n_step_t = S->n_step_steps = 0;
     return FDLB_OK;
 }
 

@@ -109,4 +109,15 @@ struct ClosureArgs {
     int* err;                      // set when a bulk copy never completes
 };
 
+struct StepArgs {
+    StageArgs st;                  // the stage fields; buffers and coefficients set per stage
+    ClosureArgs cl;                // the closure fields; sums, densities, populations set per stage
+    void* f[3];                    // f^n (and f^{n+1}), f1, f2
+    double* sums[3];
+    void* dens[3];
+    unsigned int* bar;             // grid barrier counter (zero at launch)
+    int n_steps;
+    int clo_off;                   // byte offset of the closure's shared memory
+};
+
 }  // namespace fdlb

@@ -5,6 +5,7 @@
 #include "device_common.cuh"
 #include "kernels.cuh"
 #include "kernels_decl.h"
+#include "closure_item.cuh"
 
 namespace fdlb {
 
@@ -72,511 +73,49 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
 }
 
 // ------------------------------------------------------------------------------ closure
-// Per cell, once per stage.  A cell item covers up to kClosureCells own cells and the two
-// stencil cells on each side ("reach", at most 32 cells); one lane per reach cell for the
-// macroscopic fields, so that no arithmetic is spread thinly over lanes:
-//  * n, u, T (Eq. macro_def) of every reach cell from the FP64 raw sums, in the wide type
-//    (FP64, or double-float for FP32 populations); q and P_12 of the own cells;
-//  * warps 1..3 meanwhile sum the FM bands (Eq. fm, n = 0 outside the domain) from the slice
-//    densities staged in shared memory; chi = chi_SET(pi sigma^3 nbar / 6) (Eqs. chi, chi_ret),
-//    or chi at the local density;
-//  * the J1 gradients (Eq. j1) as stencils of logarithms of ratios to the own cell, exact
-//    because the stencil weights sum to zero:  sum_q w_q ln(n_q^2 chi_q T_q) = sum_q w_q
-//    [2 log1p(dn_q / n) + log1p(dchi_q / chi) + log1p(dT_q / T)], the differences taken in the
-//    wide type; velocity gradients from wide differences;
-//  * mu, Pr, tau (Eqs. viscosity, prandtl, tau), the covariant strain and the Shakhov
-//    coefficient; the recurrences of the expansion coefficients of the equilibria (Sec. III.C;
-//    warp = axis, lane = cell) and the per-axis vectors g_2, g_R, g_3 (whole block).
-// chi and nbar of the own cells also go to a small side buffer, from which ca_kernel forms the
-// FP64 closure record of the moments and closure queries.
-// Wall items (kind 1 + side, part): the block sums the outgoing flux of one part of the momenta
-// at one wall; the stage kernel forms n_w from the parts (diffuse walls, zero net mass flux).
-// Output: the per-cell collision record in the populations' precision, [20 scalars | g_2 | g_R
-// | g_3].
-__host__ __device__ inline int closure_tab_elems(int nR, int n2, int n3) {
-    return 4 * kMaxE + 2 + (nR + n2 + n3) * kMaxE + 2 * nR + n2 + n3;
-}
-// dynamic shared memory: [staged band rows | tables | band-union densities]
-__host__ __device__ inline size_t closure_smem_bytes(int nR, int n2, int n3, int max_union, int wst_elems, int tsize) {
-    return (size_t)wst_elems * tsize + ((size_t)closure_tab_elems(nR, n2, n3) + (size_t)max_union) * tsize + 16;
-}
-
-// Position q of the five-point derivative stencil of cell c (the stencils of stencil5).
-template <typename R>
-__device__ __forceinline__ void stencil5_at(int c, int N, int q, int& cell, R& w) {
-    const R k = R(1) / R(12);
-    if (c >= 2 && c <= N - 3) {
-        cell = c - 2 + q;
-        w = q == 0 ? k : q == 1 ? R(-8) * k : q == 2 ? R(0) : q == 3 ? R(8) * k : -k;
-    } else if (c == 0) {
-        cell = q;
-        w = q == 0 ? R(-25) * k : q == 1 ? R(48) * k : q == 2 ? R(-36) * k : q == 3 ? R(16) * k : R(-3) * k;
-    } else if (c == 1) {
-        cell = q;
-        w = q == 0 ? R(-3) * k : q == 1 ? R(-10) * k : q == 2 ? R(18) * k : q == 3 ? R(-6) * k : k;
-    } else if (c == N - 2) {
-        cell = N - 1 - q;
-        w = q == 0 ? R(3) * k : q == 1 ? R(10) * k : q == 2 ? R(-18) * k : q == 3 ? R(6) * k : -k;
-    } else {
-        cell = N - 1 - q;
-        w = q == 0 ? R(25) * k : q == 1 ? R(-48) * k : q == 2 ? R(36) * k : q == 3 ? R(-16) * k : R(3) * k;
-    }
-}
-
+// The closure kernel: items of own cells (closure_cells in closure_item.cuh) and wall items
+// (kind 1 + side, part): the block sums the outgoing flux of one part of the momenta at one
+// wall; the stage kernel forms n_w from the parts (diffuse walls, zero net mass flux).
 template <typename T>
-__device__ __forceinline__ T inst_param(double d, float f) {
-    if constexpr (sizeof(T) == 4) return f;
-    else return d;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) closure_kernel(ClosureArgs A, MomSet M) {
-    using W = Wide<T>;
-    __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells, wide
-    __shared__ T s_chi[32], snb[32];               // reach cells: chi, band density
-    __shared__ int sblo[32], scnt[32];             // reach cells: first band column, stored extent
-    __shared__ T sq[4][32];                        // own cells: q1, q2, q3, P_12
-    __shared__ T ecs[kClosureCells][4][kMaxE];     // own cells: expansion coefficients
-    __shared__ T red[4];
-    __shared__ T sgp[5][kClosureCells][5];        // gradient terms per own cell and stencil position
-    __shared__ __align__(8) uint64_t cbar;         // completion of the band-row copy
+__global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A, MomSet M) {
+    __shared__ T red[kClosureWarps];
+    __shared__ __align__(8) uint64_t cbar;  // completion of the band-row copy
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
-    const T* band = reinterpret_cast<const T*>(A.band);
-    const T* dens = reinterpret_cast<const T*>(A.dens);
-    const T* fin_all = reinterpret_cast<const T*>(A.f_in);
-    const T* geoT = reinterpret_cast<const T*>(A.geoT);
-    T* rec_all = reinterpret_cast<T*>(A.rec);
-    T* nwp = reinterpret_cast<T*>(A.nwp);
-    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Np = M.Np, QR = nR / 2, slices = A.slices;
-    // staged band rows, then the tables in the populations' precision
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // staged band rows, then the tables in the populations' precision, then the band-union
+    // densities of an item
     T* wst = reinterpret_cast<T*>(smem_raw);
-    T* ha = wst + A.wst_elems;
-    T* hb = ha + kMaxE;
-    T* ihb = hb + kMaxE + 1;  // 1 / hb
-    T* h0t = ihb + kMaxE + 1;
-    T* GR = h0t + kMaxE;
-    T* G2 = GR + nR * kMaxE;
-    T* G3 = G2 + n2 * kMaxE;
-    T* pRt = G3 + n3 * kMaxE;
-    T* wRt = pRt + nR;
-    T* w2t = wRt + nR;
-    T* w3t = w2t + n2;
-    T* nbuf = ha + closure_tab_elems(nR, n2, n3);  // densities of the band union of an item
-    {
-        const T* tabT = reinterpret_cast<const T*>(A.tabT);
-        for (int e = tid; e < kMaxE; e += NT) {
-            ha[e] = tabT[M.o_ha + e];
-            h0t[e] = tabT[M.o_h0 + e];
-        }
-        for (int e = tid; e <= kMaxE; e += NT) {
-            hb[e] = tabT[M.o_hb + e];
-            ihb[e] = hb[e] != T(0) ? T(1) / hb[e] : T(0);
-        }
-        if (tid == 0) {
-            mbar_init(&cbar, 1);
-            fence_mbar_init();
-        }
-        for (int e = tid; e < nR * kMaxE; e += NT) GR[e] = tabT[M.o_GR + e];
-        for (int e = tid; e < n2 * kMaxE; e += NT) G2[e] = tabT[M.o_G2 + e];
-        for (int e = tid; e < n3 * kMaxE; e += NT) G3[e] = tabT[M.o_G3 + e];
-        for (int e = tid; e < nR; e += NT) {
-            pRt[e] = tabT[M.o_pR + e];
-            wRt[e] = tabT[M.o_wR + e];
-        }
-        for (int e = tid; e < n2; e += NT) w2t[e] = tabT[M.o_w2 + e];
-        for (int e = tid; e < n3; e += NT) w3t[e] = tabT[M.o_w3 + e];
-        __syncthreads();
+    T* tabs = wst + A.wst_elems;
+    const ClosureTabs<T> tb = closure_tables<T>(tabs, A.tabT, M, tid, blockDim.x);
+    T* nbuf = tabs + closure_tab_elems(M.nR, M.n2, M.n3);
+    if (tid == 0) {
+        mbar_init(&cbar, 1);
+        fence_mbar_init();
     }
+    __syncthreads();
     pdl_trigger();
     pdl_wait();  // everything below reads what the previous kernels wrote
+    const T* fin_all = reinterpret_cast<const T*>(A.f_in);
+    T* rec_all = reinterpret_cast<T*>(A.rec);
+    T* nwp = reinterpret_cast<T*>(A.nwp);
     uint32_t phase = 0;
     const int nit = *A.n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const int4 w = A.items[it];
         const InstDev I = A.inst[w.x];
-        const int N = I.n_cells;
         if (w.w != 0) {
-            // ---- one part of the outgoing flux through a wall: sum_out |p_R| w vhat_wall
+            // ---- one part of the outgoing flux through a wall
             const int side = w.w - 1, part = w.z, P = A.wall_parts;
-            const int mlo = (int)((long long)Np * part / P), mhi = (int)((long long)Np * (part + 1) / P);
-            const T* fin = fin_all + I.f_off;
-            const long long st = side == 0 ? (long long)Np : -(long long)Np;
-            const long long base = side == 0 ? 0LL : (long long)(N - 1) * Np;
-            T acc = T(0);
-            for (int m0 = mlo + tid; m0 < mhi; m0 += 4 * NT) {
-                // four momenta per pass so that their sixteen loads are in flight together
-                T fv[4][4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int m = min(m0 + u * NT, mhi - 1);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) fv[u][r] = fin[base + m + r * st];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int m = m0 + u * NT;
-                    if (m >= mhi) continue;
-                    const int k = m / (nR * n2), rem = m % (nR * n2), i = rem / n2, j = rem % n2;
-                    const T pr = pRt[i];
-                    if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
-                    const T wm = wRt[i] * w2t[j] * w3t[k], iw = T(1) / wm;
-                    const T f0 = fv[u][0], f1 = fv[u][1], f2 = fv[u][2], f3 = fv[u][3];
-                    const T g1 = T(4) * f0 - T(6) * f1 + T(4) * f2 - f3;
-                    const T g2 = T(10) * f0 - T(20) * f1 + T(15) * f2 - T(4) * f3;
-                    const T vh = weno5(f2 * iw, f1 * iw, f0 * iw, g1 * iw, g2 * iw);
-                    acc += fabs(pr) * wm * vh;
-                }
-            }
+            T acc = wall_flux_partial<T>(fin_all + I.f_off, M, tb, I.n_cells, side, part, P, tid);
             acc = warp_sum(acc);
             if (lane == 0) red[warp] = acc;
             __syncthreads();
-            if (tid == 0) nwp[((long long)w.x * 2 + side) * P + part] = (red[0] + red[1]) + (red[2] + red[3]);
+            if (tid == 0) nwp[((long long)w.x * 2 + side) * P + part] = wall_part_sum(red);
             __syncthreads();
             continue;
         }
-        const int c0 = w.y, cnt = w.z;
-        // reach: the own cells, two on each side, and the five cells next to a wall
-        const int h0 = max(0, min(c0 - 2, N - 5)), h1 = min(N, max(c0 + cnt + 2, 5)), nh = h1 - h0;
-        const double* S = A.sums + (long long)I.cell_off * slices * kSums;
-        const int rs = A.rec_stride;
-        T* rec = rec_all + (long long)I.cell_off * rs;
-        // ---- 1. every global load of the item at once: the raw sums of the reach cells and the
-        // geometry of the own cells (warp 0, lane per cell), the band rows of the reach cells
-        // (bulk copies of their stored extents, issued by warp 0) and the densities of the union
-        // of the bands (all threads)
-        double s[kSums];
-        T geo0 = T(1), geo1 = T(0);
-        if (warp == 0 && lane < nh) {
-            const double* src = S + (long long)(h0 + lane) * slices * kSums;
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) s[q] = src[q];
-            for (int sl = 1; sl < slices; ++sl)
-#pragma unroll
-                for (int q = 0; q < kSums; ++q) s[q] += src[sl * kSums + q];
-        }
-        if (warp == 0 && lane < cnt) {
-            const T* gc = geoT + (long long)(I.cell_off + c0 + lane) * kGeo;
-            geo0 = gc[0];
-            geo1 = gc[1];
-        }
-        int jlo = 0, nu = 0;
-        const bool staged = !I.chi_local && nh * I.band_w <= A.wst_elems;
-        if (!I.chi_local) {
-            const int2* bl = reinterpret_cast<const int2*>(A.band_lo) + I.cell_off;
-            const int2 first = bl[h0], last = bl[h1 - 1];
-            jlo = first.x;
-            // columns grow with the row, and extents are rounded up by at most 3
-            const int jhi = min(N - 1, last.x + last.y - 1 + 3);
-            nu = min(jhi - jlo + 1, A.max_union);
-            if (warp == 0) {
-                int2 mine = make_int2(0, 0);
-                if (lane < nh) mine = bl[h0 + lane];
-                if (lane < nh) {
-                    sblo[lane] = mine.x;
-                    scnt[lane] = mine.y;
-                }
-                if (staged) {
-                    // one bulk copy per row, of its stored extent (a multiple of 16 bytes)
-                    int bytes = lane < nh ? mine.y * (int)sizeof(T) : 0;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
-                    if (lane == 0) {
-                        fence_proxy_async();
-                        mbar_expect_tx(&cbar, (uint32_t)bytes);
-                    }
-                    __syncwarp();
-                    if (lane < nh && mine.y > 0)
-                        bulk_g2s(wst + (long long)lane * I.band_w, band + I.band_off + (long long)(h0 + lane) * I.band_w,
-                                 (uint32_t)(mine.y * sizeof(T)), &cbar);
-                }
-            }
-            const T* nd = dens + ((long long)I.cell_off + jlo) * slices;
-            for (int j0 = tid; j0 < nu; j0 += 4 * NT) {
-                // four loads in flight per thread
-                T v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = min(j0 + u * NT, nu - 1);
-                    v[u] = nd[(long long)j * slices];
-                    for (int sl = 1; sl < slices; ++sl) v[u] += nd[(long long)j * slices + sl];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (j0 + u * NT < nu) nbuf[j0 + u * NT] = v[u];
-            }
-        }
-        if (staged) {
-            const bool ok = mbar_wait_bounded(&cbar, phase);
-            // every thread takes the same exit: a block-wide vote on the outcome
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicOr(A.err, 2);
-                mbar_wait_bounded(&cbar, phase);  // bounded wait for the copy still in flight
-                return;
-            }
-            phase ^= 1u;
-        }
-        __syncthreads();
-        // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells;
-        // warps 1..3: FM band sums of the reach cells from shared memory
-        if (warp == 0) {
-            if (lane < nh) {
-                const int c = h0 + lane;
-                const W n = w_from(s[0], (T*)nullptr);
-                const W u0 = w_div(w_from(s[1], (T*)nullptr), n);
-                const W u1 = w_div(w_from(s[2], (T*)nullptr), n);
-                const W u2 = w_div(w_from(s[3], (T*)nullptr), n);
-                const W tr = w_add(w_add(w_from(s[4], (T*)nullptr), w_from(s[5], (T*)nullptr)), w_from(s[6], (T*)nullptr));
-                const W uu = w_add(w_add(w_mul(u0, u0), w_mul(u1, u1)), w_mul(u2, u2));
-                const W Tc = w_div(w_sub(tr, w_mul(n, uu)), w_scale(n, T(3)));
-                sw_n[lane] = n;
-                sw_u[0][lane] = u0;
-                sw_u[1][lane] = u1;
-                sw_u[2][lane] = u2;
-                sw_T[lane] = Tc;
-                if (c >= c0 && c < c0 + cnt) {
-                    // q and P_12 in the populations' precision (they enter only the Shakhov
-                    // factor and the diagnostics)
-                    const T tn = w_hi(n), t0 = w_hi(u0), t1 = w_hi(u1), t2 = w_hi(u2), ttr = w_hi(tr), tuu = w_hi(uu);
-                    const T s4 = (T)s[4], s5 = (T)s[5], s6 = (T)s[6], s7 = (T)s[7], s8 = (T)s[8], s9 = (T)s[9];
-                    const T m0 = s4 * t0 + s7 * t1 + s8 * t2;
-                    const T m1 = s7 * t0 + s5 * t1 + s9 * t2;
-                    const T m2 = s8 * t0 + s9 * t1 + s6 * t2;
-                    sq[0][c - c0] = T(0.5) * ((T)s[10] - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
-                    sq[1][c - c0] = T(0.5) * ((T)s[11] - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
-                    sq[2][c - c0] = T(0.5) * ((T)s[12] - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
-                    sq[3][c - c0] = s7 - tn * t0 * t1;
-                }
-            }
-        } else if (!I.chi_local) {
-            for (int t = warp - 1; t < nh; t += 3) {
-                const int c = h0 + t;
-                const int lo = sblo[t];
-                const int kmax = min(min(scnt[t], N - lo), nu - (lo - jlo));
-                const T* Wr = staged ? wst + (long long)t * I.band_w : band + I.band_off + (long long)c * I.band_w;
-                const T* nb = nbuf + (lo - jlo);
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-                int k = lane;
-                for (; k + 96 < kmax; k += 128) {
-                    a0 += Wr[k] * nb[k];
-                    a1 += Wr[k + 32] * nb[k + 32];
-                    a2 += Wr[k + 64] * nb[k + 64];
-                    a3 += Wr[k + 96] * nb[k + 96];
-                }
-                for (; k < kmax; k += 32) a0 += Wr[k] * nb[k];
-                const T tot = warp_sum((a0 + a1) + (a2 + a3));
-                if (lane == 0) snb[t] = tot;
-            }
-        }
-        __syncthreads();
-        // ---- 3. two concurrent chains.  Warp 0: chi of the reach cells, the gradient terms (one
-        // lane per own cell and stencil position: logarithms of ratios to the own cell, differences
-        // in the wide type), then transport, strain and Shakhov coefficient (lane per own cell).
-        // Warps 1 and 2: the expansion coefficients of the equilibria (Sec. III.C), lane per
-        // (own cell, axis half): warp 1 the half-range axis (+ and -), warp 2 the axes 2 and 3.
-        if (warp == 0) {
-            if (lane < nh) {
-                // chi in the wide type, rounded once: J1 scales with b rho chi, and near finely
-                // resolved walls J1 is large enough that a few roundings of chi show in the RHS
-                const T etafac = inst_param<T>(I.etafac, I.f_etafac);
-                const W eta = w_scale(w_from_t(I.chi_local ? w_hi(sw_n[lane]) : snb[lane]), etafac);
-                const W om = w_sub(w_from_t(T(1)), eta);
-                const W om3 = w_mul(w_mul(om, om), om);
-                s_chi[lane] = w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
-            }
-            __syncwarp();
-            const T etaf = inst_param<T>(I.etafac, I.f_etafac);
-            for (int e = lane; e < cnt * 5; e += 32) {
-                const int t = e / 5, q = e % 5, c = c0 + t, lt = c - h0;
-                int cq;
-                T wq;
-                stencil5_at<T>(c, N, q, cq, wq);
-                const int k = cq - h0;
-                const W nw = sw_n[lt], Tw = sw_T[lt];
-                const T lT = log1p(ratio_fast(w_hi(w_sub(sw_T[k], Tw)), w_hi(Tw)));
-                const T ln = log1p(ratio_fast(w_hi(w_sub(sw_n[k], nw)), w_hi(nw)));
-                // ln chi_q - ln chi_c from the packing-fraction difference alone, since
-                // ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of chi itself)
-                const T dnb = I.chi_local ? w_hi(w_sub(sw_n[k], nw)) : snb[k] - snb[lt];
-                const T etac = etaf * (I.chi_local ? w_hi(nw) : snb[lt]), deta = etaf * dnb;
-                const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
-                sgp[0][t][q] = wq * (T(2) * ln + lchi + lT);
-                sgp[1][t][q] = wq * lT;
-                sgp[2][t][q] = wq * w_hi(w_sub(sw_u[0][k], sw_u[0][lt]));
-                sgp[3][t][q] = wq * w_hi(w_sub(sw_u[1][k], sw_u[1][lt]));
-                sgp[4][t][q] = wq * w_hi(w_sub(sw_u[2][k], sw_u[2][lt]));
-            }
-            __syncwarp();
-            if (lane < cnt) {
-                using C = T;
-                const int t = lane, c = c0 + t, lt = c - h0;
-                const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
-                const C in = ratio_fast(C(1), cn), iT = ratio_fast(C(1), cT), ichi = ratio_fast(C(1), cchi);
-                C gsum[5];
-#pragma unroll
-                for (int v = 0; v < 5; ++v)
-                    gsum[v] = (sgp[v][t][0] + sgp[v][t][1]) + (sgp[v][t][2] + sgp[v][t][3]) + sgp[v][t][4];
-                const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
-                const C X = gsum[0] * sc, Y = gsum[1] * sc;
-                const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
-                const C iR = ratio_fast(C(1), geo0);
-                const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
-                const C sg = inst_param<C>(I.sigma, I.f_sigma);
-                const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
-                const C pi = C(3.14159265358979323846);
-                const C mu = ratio_fast(C(5), C(16) * sg * sg) * sqrt(cT * C(0.31830988618379067154)) *
-                             (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
-                const C Pr = ratio_fast(C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x),
-                                        C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
-                C S11, S22, S01, S02, div;
-                if (I.geometry == 0) {
-                    S11 = cu0 * iR;
-                    S22 = C(0);
-                    S01 = C(0.5) * (cd1 - cu1 * iR);
-                    S02 = C(0.5) * cd2;
-                    div = cd0 + cu0 * iR;
-                } else {
-                    S11 = S22 = cu0 * iR;
-                    S01 = C(0.5) * (cd1 - cu1 * iR);
-                    S02 = C(0.5) * (cd2 - cu2 * iR);
-                    div = cd0 + C(2) * cu0 * iR;
-                }
-                T* ct = rec + (long long)c * rs;
-                ct[0] = cn;
-                ct[1] = cu0;
-                ct[2] = cu1;
-                ct[3] = cu2;
-                ct[4] = iT;
-                ct[5] = ratio_fast(cn * cT, mu);
-                ct[6] = (C(1) - Pr) * iT * iT * in;
-                ct[7] = sq[0][t];
-                ct[8] = sq[1][t];
-                ct[9] = sq[2][t];
-                ct[10] = x;
-                ct[11] = X;
-                ct[12] = Y;
-                ct[13] = cd0;
-                ct[14] = S11;
-                ct[15] = S22;
-                ct[16] = S01;
-                ct[17] = S02;
-                ct[18] = T(0);
-                ct[19] = div;
-                T* cw = reinterpret_cast<T*>(A.cw) + (long long)(I.cell_off + c) * 2;
-                cw[0] = cchi;
-                cw[1] = I.chi_local ? cn : snb[lt];
-            }
-        } else if (warp <= 2) {
-            using C = T;
-            for (int e = lane; e < 2 * cnt; e += 32) {
-                const int t = e % cnt, job = 2 * (warp - 1) + e / cnt, lt = c0 + t - h0;
-                C ev[kMaxE + 1];
-#pragma unroll
-                for (int l = 0; l <= kMaxE; ++l) ev[l] = C(0);
-                const C cT = w_hi(sw_T[lt]);
-                const C tm1 = w_hi(w_sub(sw_T[lt], w_from_t(C(1))));  // T - 1 without cancellation
-                if (job < 2) {
-                    // half range, half line of sign s (job 0: +, 1: -), v = s u_R.  The
-                    // recurrence of the coefficients,
-                    //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
-                    //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
-                    //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
-                    // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1:
-                    // r_0 = h_0 / 2, r_l = 0 for l >= 1), where every term is small and nothing
-                    // cancels: with D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) /
-                    // sqrt T, z = v / sqrt(2T), and h_0(0) r_0 = 1,
-                    //   d_0 = h_0 erf(z) / 2,
-                    //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
-                    //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
-                    //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
-                    const C ur = w_hi(sw_u[0][lt]);
-                    const C v = job == 0 ? ur : -ur;
-                    const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
-                    const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
-                    const C is2pi = C(0.39894228040143267794);
-                    const C r0 = h0t[0] * C(0.5);
-                    C d[kMaxE + 1];
-#pragma unroll
-                    for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
-                    d[0] = r0 * erf(z);
-                    C run = C(0);  // sum_{k<l} h_k(0) d_k
-#pragma unroll
-                    for (int l = 0; l < kMaxE; ++l) {
-                        if (l < M.NR) {
-                            C val;
-                            if (l == 0) {
-                                val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
-                            } else {
-                                const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
-                                val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
-                            }
-                            run += h0t[l] * d[l];
-                            d[l + 1] = val * ihb[l + 1];
-                        }
-                    }
-#pragma unroll
-                    for (int l = 0; l <= kMaxE; ++l) ev[l] = d[l];
-                    ev[0] += r0;
-                } else {
-                    // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                    const C u = w_hi(sw_u[job == 2 ? 1 : 2][lt]);
-                    const int Nax = job == 2 ? M.N2 : M.N3;
-                    ev[0] = C(1);
-                    ev[1] = Nax >= 1 ? u : C(0);
-#pragma unroll
-                    for (int l = 1; l < kMaxE; ++l)
-                        if (l < Nax) ev[l + 1] = u * ev[l] + C(l) * tm1 * ev[l - 1];
-                }
-#pragma unroll
-                for (int l = 0; l < kMaxE; ++l) ecs[t][job][l] = ev[l];
-            }
-        }
-        __syncthreads();
-        // ---- 5. per-axis equilibrium vectors of the own cells, in the populations' precision
-        const int ng = nR + n2 + n3;
-        for (int e = tid; e < cnt * ng; e += NT) {
-            const int t = e / ng, k = e % ng;
-            T acc = T(0);
-            int dst;
-            if (k < nR) {
-                const T* eh = ecs[t][k >= QR ? 1 : 0];
-                for (int l = 0; l <= M.NR; ++l) acc += GR[k * kMaxE + l] * eh[l];
-                dst = rec_off_gR(n2) + k;
-            } else if (k < nR + n2) {
-                const int j = k - nR;
-                for (int l = 0; l <= M.N2; ++l) acc += G2[j * kMaxE + l] * ecs[t][2][l];
-                dst = rec_off_g2() + j;
-            } else {
-                const int j = k - nR - n2;
-                for (int l = 0; l <= M.N3; ++l) acc += G3[j * kMaxE + l] * ecs[t][3][l];
-                dst = rec_off_g3(nR, n2) + j;
-            }
-            rec[(long long)(c0 + t) * rs + dst] = acc;
-        }
-        __syncthreads();
-        // ---- 6. discrete mass of the stored equilibrium: the rounded vectors need not sum to
-        // exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
-        // would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is
-        // divided by the wide-precision product of the sums of the stored vectors (a warp per own
-        // cell, a butterfly of wide sums: every lane ends with the same value).
-        for (int t = warp; t < cnt; t += NT / 32) {
-            T* ct = rec + (long long)(c0 + t) * rs;
-            W s3w[3] = {w_from_t(T(0)), w_from_t(T(0)), w_from_t(T(0))};
-            for (int k = lane; k < ng; k += 32) {
-                const int a = k < nR ? 0 : (k < nR + n2 ? 1 : 2);
-                const int src = a == 0 ? rec_off_gR(n2) + k : (a == 1 ? rec_off_g2() + k - nR : rec_off_g3(nR, n2) + k - nR - n2);
-                const W g = w_from_t(ct[src]);
-                s3w[0] = a == 0 ? w_add(s3w[0], g) : s3w[0];
-                s3w[1] = a == 1 ? w_add(s3w[1], g) : s3w[1];
-                s3w[2] = a == 2 ? w_add(s3w[2], g) : s3w[2];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
-            if (lane == 0) ct[0] = w_hi(w_div(sw_n[c0 + t - h0], w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
-        }
-        __syncthreads();  // shared arrays are reused by the next item
+        T* recb = rec_all + (long long)(I.cell_off + w.y) * A.rec_stride;
+        if (!closure_cells<T>(A, M, tb, I, w.y, w.z, recb, wst, nbuf, &cbar, phase, NoExtra{})) return;
     }
 }
 

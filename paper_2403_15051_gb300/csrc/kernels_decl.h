@@ -95,6 +95,15 @@ FDLB_STREAM_DECL(double, 0)
 FDLB_STREAM_DECL(double, 1)
 #undef FDLB_STREAM_DECL
 
+#define FDLB_STEP_DECL(T, G)                                                                                   \
+    cudaError_t launch_step_##T##_##G(const StreamCfg& cfg, const StepArgs* S, const MomSet& M, int grid,     \
+                                      int threads, size_t smem, cudaStream_t s, int* blocks_per_sm);
+FDLB_STEP_DECL(float, 0)
+FDLB_STEP_DECL(float, 1)
+FDLB_STEP_DECL(double, 0)
+FDLB_STEP_DECL(double, 1)
+#undef FDLB_STEP_DECL
+
 void launch_residual(const double* sums, int slices, const InstDev* inst, const double* geo, double* prev, double* out,
                      int n_inst, int save, cudaStream_t s);
 

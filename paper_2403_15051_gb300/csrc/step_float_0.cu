@@ -1,0 +1,6 @@
+// Instantiation of the persistent step kernel for float populations, geometry 0 (0 cylinder, 1 sphere).
+#include "step_kernel.cuh"
+
+namespace fdlb {
+FDLB_STEP_INSTANCE(float, 0)
+}  // namespace fdlb

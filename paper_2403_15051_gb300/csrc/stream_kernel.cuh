@@ -73,6 +73,27 @@ __device__ __forceinline__ void ldg_vec(const T* p, T (&o)[VW]) {
     }
 }
 
+// The same through L2 only (data written earlier in the same launch by other blocks).
+template <typename T, int VW>
+__device__ __forceinline__ void ldcg_vec(const T* p, T (&o)[VW]) {
+    if constexpr (sizeof(T) == 4 && VW == 4) {
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 2) {
+        const float2 x = __ldcg(reinterpret_cast<const float2*>(p));
+        o[0] = x.x; o[1] = x.y;
+    } else if constexpr (sizeof(T) == 8 && VW >= 2) {
+#pragma unroll
+        for (int h = 0; h < VW / 2; ++h) {
+            const double2 x = __ldcg(reinterpret_cast<const double2*>(p + 2 * h));
+            o[2 * h] = x.x; o[2 * h + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) o[e] = __ldcg(p + e);
+    }
+}
+
 template <typename T, int VW>
 __device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
     if constexpr (sizeof(T) == 4 && VW == 4) {
@@ -115,48 +136,55 @@ __device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
     return w1 + __shfl_xor_sync(0xffffffffu, w1, 1);
 }
 
-// NR_, N2_, N3_: compile-time axis sizes (0: taken from M at run time).
-template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
-__global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int NT = blockDim.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
-    const int nR = NR_ ? NR_ : M.nR, n2 = N2_ ? N2_ : M.n2, n3 = N3_ ? N3_ : M.n3;
-    const int KS = GEOM == 1 ? n3 : M.KS;  // the sphere couples every axis: one slice
-    const int Ms = nR * n2 * KS, Np = nR * n2 * n3;
-    const int n2v = n2 / VW;               // vectors per (k, i) row
-    const int Vs = Ms / VW;                // vectors per slice
-    const int rs = record_stride(nR, n2, n3);
-    // K^h contraction on the tensor cores (split TF32): available for the FP32 compile-time
-    // shapes, used when the host asks for it
-    constexpr bool kMMA = sizeof(T) == 4 && NR_ > 0 && NR_ % 8 == 0 && VW == 4;
-    const bool use_mma = kMMA && A.mma;
-    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T), use_mma ? 1 : 0);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-    T* fs = reinterpret_cast<T*>(smem_raw + P.fs);  // rows: cells c0-3 .. c0+B+2
-    T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);
-    T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);  // K_2 swizzled (vector loads: first, aligned):
-                                                       // [e][b / VW][j / VW][b % VW], j = (j / VW) VW + e
-    T* sKR = sK2 + n2 * n2;        // K^h, row stride nR + 1
-    T* sK3 = sKR + nR * (nR + 1);  // K_3, row stride n3 + 1
-    T* sp_R = sK3 + n3 * (n3 + 1);
-    T* sp_2 = sp_R + nR;
-    T* sp_3 = sp_2 + n2;
-    T* sw_R = sp_3 + n3;
-    T* sw_2 = sw_R + nR;
-    T* sw_3 = sw_2 + n2;
-    T* sgw = sw_3 + n3;            // [2][nR + n2 + n3]: inner and outer wall Maxwellian per axis
-    T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);
-    T* red = reinterpret_cast<T*>(smem_raw + P.red);  // [cell][warp][16] warp sums
-    T* skrf = reinterpret_cast<T*>(smem_raw + P.kr);   // [cell][k][i][j] K^h f of the own cells
-    __shared__ T snw[2];                               // wall densities of the item's instance
-    const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);
-    const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);
-    T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);
-    const T* __restrict__ rec_all = reinterpret_cast<const T*>(A.rec);
-    const T* __restrict__ tab = reinterpret_cast<const T*>(A.tabT);  // tables in T: no conversions
-    const int gwstride = nR + n2 + n3;
+// Local names of the stage's dimensions and of its shared-memory plan (StreamSmem): fs the
+// staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sK2 K_2 in the vector-swizzled
+// order [e][b / VW][j / VW][b % VW] (first: aligned vector loads), sKR K^h with row stride nR+1,
+// sK3 K_3 with row stride n3+1, nodes and weights, sgw the inner and outer wall Maxwellians per
+// axis [2][nR + n2 + n3], sgeo the tile's geometry, red the per-warp sums [cell][warp][16], skrf
+// K^h f of the own cells (tensor-core path).  NR_, N2_, N3_: compile-time axis sizes (0: taken
+// from M at run time).  The sphere couples every axis: one slice (KS = n3).
+#define FDLB_STREAM_LAYOUT                                                                                       \
+    extern __shared__ __align__(16) unsigned char smem_raw[];                                                    \
+    const int NT = blockDim.x;                                                                                   \
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;                             \
+    const int nR = NR_ ? NR_ : M.nR, n2 = N2_ ? N2_ : M.n2, n3 = N3_ ? N3_ : M.n3;                               \
+    const int KS = GEOM == 1 ? n3 : M.KS;                                                                        \
+    const int Ms = nR * n2 * KS, Np = nR * n2 * n3;                                                              \
+    const int n2v = n2 / VW;                                                                                     \
+    const int Vs = Ms / VW;                                                                                      \
+    const int rs = record_stride(nR, n2, n3);                                                                    \
+    constexpr bool kMMA = sizeof(T) == 4 && NR_ > 0 && NR_ % 8 == 0 && VW == 4;                                  \
+    const bool use_mma = kMMA && A.mma;                                                                          \
+    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T), use_mma ? 1 : 0);         \
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                                                       \
+    T* fs = reinterpret_cast<T*>(smem_raw + P.fs);                                                               \
+    T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);                                                           \
+    T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);                                                            \
+    T* sKR = sK2 + n2 * n2;                                                                                      \
+    T* sK3 = sKR + nR * (nR + 1);                                                                                \
+    T* sp_R = sK3 + n3 * (n3 + 1);                                                                               \
+    T* sp_2 = sp_R + nR;                                                                                         \
+    T* sp_3 = sp_2 + n2;                                                                                         \
+    T* sw_R = sp_3 + n3;                                                                                         \
+    T* sw_2 = sw_R + nR;                                                                                         \
+    T* sw_3 = sw_2 + n2;                                                                                         \
+    T* sgw = sw_3 + n3;                                                                                          \
+    T* sgeo = reinterpret_cast<T*>(smem_raw + P.geo);                                                            \
+    T* red = reinterpret_cast<T*>(smem_raw + P.red);                                                             \
+    T* skrf = reinterpret_cast<T*>(smem_raw + P.kr);                                                             \
+    const T* __restrict__ f_in = reinterpret_cast<const T*>(A.f_in);                                             \
+    const T* __restrict__ f_n = reinterpret_cast<const T*>(A.f_n);                                               \
+    T* __restrict__ f_out = reinterpret_cast<T*>(A.f_out);                                                       \
+    const T* __restrict__ rec_all = reinterpret_cast<const T*>(A.rec);                                           \
+    const T* __restrict__ tab = reinterpret_cast<const T*>(A.tabT);                                              \
+    const int gwstride = nR + n2 + n3;                                                                           \
+    (void)0
 
+// Tables of the stage (nodes, weights, K matrices) into shared memory and the copy barrier;
+// the caller synchronises.
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+__device__ __forceinline__ void stream_tables(const StageArgs& A, const MomSet& M) {
+    FDLB_STREAM_LAYOUT;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -180,198 +208,265 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     }
     if (GEOM == 1)
         for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = tab[M.o_K3 + e];
-    __syncthreads();
-    pdl_trigger();
-    pdl_wait();  // everything below reads what the previous kernels wrote
+}
 
-    uint32_t phase = 0;
-    const int nit = *A.n_items;
-    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
-        const int4 wi = A.items[it];
-        const InstDev I = A.inst[wi.x];
-        const int N = I.n_cells, c0 = wi.y, Be = wi.z, sl = wi.w;
-        const T* fin = f_in + I.f_off;
-        const long long slice_off = (long long)sl * Ms;
-        const int lo = c0 >= 3 ? c0 - 3 : 0;
-        const int hi = min(c0 + Be + 3, N);  // staged cells [lo, hi)
-        T* const frow0 = fs + (long long)(lo - c0 + 3) * Ms;
-        const T* rsrc = rec_all + (long long)(I.cell_off + c0) * rs;
-
-        // ---- 1. stage the cells (this slice) and the tile's collision records
-        if (A.use_bulk) {
-            if (tid == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + Be * rs) * sizeof(T)));
-                if (M.slices == 1) {
-                    bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
-                } else {
-                    for (int cc = lo; cc < hi; ++cc)
-                        bulk_g2s(frow0 + (long long)(cc - lo) * Ms, fin + (long long)cc * Np + slice_off,
-                                 (uint32_t)(Ms * sizeof(T)), bar);
-                }
-                bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
+// Staging of a work item: the cells c0-3 .. c0+Be+2 of its slice and, when `records`, the
+// tile's collision records (the bulk engine, completion on the copy barrier; else plain loads).
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+__device__ __forceinline__ void stream_issue(const StageArgs& A, const MomSet& M, int4 wi, const InstDev& I,
+                                             bool records) {
+    FDLB_STREAM_LAYOUT;
+    const int N = I.n_cells, c0 = wi.y, Be = wi.z, sl = wi.w;
+    const T* fin = f_in + I.f_off;
+    const long long slice_off = (long long)sl * Ms;
+    const int lo = c0 >= 3 ? c0 - 3 : 0;
+    const int hi = min(c0 + Be + 3, N);  // staged cells [lo, hi)
+    T* const frow0 = fs + (long long)(lo - c0 + 3) * Ms;
+    const T* rsrc = rec_all + (long long)(I.cell_off + c0) * rs;
+    // ---- 1. stage the cells (this slice) and the tile's collision records
+    if (A.use_bulk) {
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + (records ? Be * rs : 0)) * sizeof(T)));
+            if (M.slices == 1) {
+                bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
+            } else {
+                for (int cc = lo; cc < hi; ++cc)
+                    bulk_g2s(frow0 + (long long)(cc - lo) * Ms, fin + (long long)cc * Np + slice_off,
+                             (uint32_t)(Ms * sizeof(T)), bar);
             }
-        } else {
-            for (int cc = lo; cc < hi; ++cc)
-                for (int e = tid; e < Ms; e += NT)
-                    frow0[(long long)(cc - lo) * Ms + e] = ldg_t(fin + (long long)cc * Np + slice_off + e);
+            if (records) bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
+        }
+    } else {
+        for (int cc = lo; cc < hi; ++cc)
+            for (int e = tid; e < Ms; e += NT)
+                frow0[(long long)(cc - lo) * Ms + e] = ldg_t(fin + (long long)cc * Np + slice_off + e);
+        if (records)
             for (int e = tid; e < Be * rs; e += NT) cellT[e] = rsrc[e];
-        }
+    }
+}
 
-        // ---- 2. geometry of the tile, the wall Maxwellians and the wall densities from the
-        // parts of the outgoing fluxes (overlapping the copy)
-        const T* gwi = reinterpret_cast<const T*>(A.gwT) + (long long)wi.x * 2 * gwstride;
-        for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = gwi[e];
-        for (int c = tid; c < Be; c += NT) {
-            const T* g = reinterpret_cast<const T*>(A.geoT) + (long long)(I.cell_off + c0 + c) * kGeo;
-            sgeo[c * 3 + 0] = g[2];
-            sgeo[c * 3 + 1] = g[3];
-            sgeo[c * 3 + 2] = g[4];
-        }
-        if (tid < 2) {
-            const T* pp = reinterpret_cast<const T*>(A.nwp) + ((long long)wi.x * 2 + tid) * A.wall_parts;
-            T sum = T(0);
-            for (int p = 0; p < A.wall_parts; ++p) sum += pp[p];
-            const T iden = sizeof(T) == 4 ? (T)(tid ? I.f_nw_iden[1] : I.f_nw_iden[0])
-                                          : (T)(tid ? I.nw_iden[1] : I.nw_iden[0]);
-            snw[tid] = sum * iden;
-        }
+// Geometry of the tile and the instance's wall Maxwellians into shared memory.
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+__device__ __forceinline__ void stream_statics(const StageArgs& A, const MomSet& M, int4 wi, const InstDev& I) {
+    FDLB_STREAM_LAYOUT;
+    const int c0 = wi.y, Be = wi.z;
+    const T* gwi = reinterpret_cast<const T*>(A.gwT) + (long long)wi.x * 2 * gwstride;
+    for (int e = tid; e < 2 * gwstride; e += NT) sgw[e] = gwi[e];
+    for (int c = tid; c < Be; c += NT) {
+        const T* g = reinterpret_cast<const T*>(A.geoT) + (long long)(I.cell_off + c0 + c) * kGeo;
+        sgeo[c * 3 + 0] = g[2];
+        sgeo[c * 3 + 1] = g[3];
+        sgeo[c * 3 + 2] = g[4];
+    }
+}
 
-        // ---- wait for the staged cells
-        if (A.use_bulk) {
-            const bool ok = mbar_wait_bounded(bar, phase);
-            // every thread takes the same exit: a block-wide vote on the outcome
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicOr(A.err, 1);
-                mbar_wait_bounded(bar, phase);  // bounded wait for the copy still in flight
-                return;
+// Completion of the staged copy; false (on every thread, A.err set) when it never completes.
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+__device__ __forceinline__ bool stream_wait(const StageArgs& A, const MomSet& M, uint32_t& phase) {
+    FDLB_STREAM_LAYOUT;
+    // ---- wait for the staged cells
+    if (A.use_bulk) {
+        const bool ok = mbar_wait_bounded(bar, phase);
+        // every thread takes the same exit: a block-wide vote on the outcome
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(A.err, 1);
+            mbar_wait_bounded(bar, phase);  // bounded wait for the copy still in flight
+            return false;
+        }
+        phase ^= 1u;
+    }
+    return true;
+}
+
+// Steps 3-5 of the item on the staged cells and records: ghost rows, the populations of the
+// new stage, their raw sums.  nwL, nwR: the wall densities of the item's instance.
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_, bool kCoherent = false>
+__device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet& M, int4 wi, const InstDev& I,
+                                               T nwL, T nwR) {
+    FDLB_STREAM_LAYOUT;
+    const int N = I.n_cells, c0 = wi.y, Be = wi.z, sl = wi.w;
+    const long long slice_off = (long long)sl * Ms;
+    // ---- 3. ghost rows: the tile's stencils span cells c0-3 .. c0+Be+2 (rows 0 .. Be+5, row =
+    // cell - c0 + 3); the cells outside the domain among them (-2, -1 and N, N+1) hold n_w times
+    // the wall Maxwellian for directions into the domain, the cubic extrapolation of the four
+    // cells next to the wall for directions out of it.  Tiles near a wall need them whether or
+    // not they touch it (a tile of two cells starting at cell 2 reaches cell -1).
+    const T* gwL = sgw;
+    const T* gwR = sgw + gwstride;
+    const bool ghL = c0 < 3, ghR = c0 + Be + 2 >= N;
+    if (ghL || ghR) {
+        for (int ml = tid; ml < Ms; ml += NT) {
+            const int kk = ml / (nR * n2), rem = ml % (nR * n2), i = rem / n2, j = rem % n2;
+            const int k = sl * KS + kk;
+            const T pr = sp_R[i];
+            if (ghL) {
+                T g1, g2;
+                if (pr > T(0)) {
+                    g1 = g2 = nwL * gwL[i] * gwL[nR + j] * gwL[nR + n2 + k];
+                } else {
+                    const T* r0 = fs + (long long)(3 - c0) * Ms + ml;  // cell 0
+                    wall_ghosts(r0[0], r0[Ms], r0[2 * Ms], r0[3 * Ms], g1, g2);
+                }
+                fs[(long long)(2 - c0) * Ms + ml] = g1;                 // cell -1
+                if (c0 <= 1) fs[(long long)(1 - c0) * Ms + ml] = g2;    // cell -2
             }
-            phase ^= 1u;
+            if (ghR) {
+                T g1, g2;
+                if (pr < T(0)) {
+                    g1 = g2 = nwR * gwR[i] * gwR[nR + j] * gwR[nR + n2 + k];
+                } else {
+                    const T* r0 = fs + (long long)(N - 1 - c0 + 3) * Ms + ml;  // cell N-1
+                    wall_ghosts(r0[0], r0[-Ms], r0[-2 * Ms], r0[-3 * Ms], g1, g2);
+                }
+                fs[(long long)(N - c0 + 3) * Ms + ml] = g1;                           // cell N
+                if (N + 1 <= c0 + Be + 2) fs[(long long)(N + 1 - c0 + 3) * Ms + ml] = g2;  // cell N+1
+            }
         }
         __syncthreads();
+    }
 
-        const T nwL = snw[0], nwR = snw[1];
-
-        // ---- 3. ghost rows at the walls
-        const T* gwL = sgw;
-        const T* gwR = sgw + gwstride;
-        if (c0 == 0 || c0 + Be == N) {
-            for (int ml = tid; ml < Ms; ml += NT) {
-                const int kk = ml / (nR * n2), rem = ml % (nR * n2), i = rem / n2, j = rem % n2;
-                const int k = sl * KS + kk;
-                const T pr = sp_R[i];
-                if (c0 == 0) {
-                    T g1, g2;
-                    if (pr > T(0)) {
-                        g1 = g2 = nwL * gwL[i] * gwL[nR + j] * gwL[nR + n2 + k];
-                    } else {
-                        const T* r0 = fs + 3 * Ms + ml;
-                        wall_ghosts(r0[0], r0[Ms], r0[2 * Ms], r0[3 * Ms], g1, g2);
-                    }
-                    fs[2 * Ms + ml] = g1;  // cell -1
-                    fs[1 * Ms + ml] = g2;  // cell -2
+    // ---- 3b. tensor cores: (K^h f)[i][(k, j)] = sum_a K^h[i][a] f[k][a][j] for the own cells,
+    // a GEMM of the nR x nR matrix with the cell's nR x (n2 KS) slice, in split TF32
+    // (K = Kh + Kl, f = fh + fl; Kh fh + Kh fl + Kl fh with FP32 accumulation: FP32-level
+    // products), n-tiles of 8 columns spread over the warps, results to shared memory.
+    if constexpr (kMMA) {
+      if (use_mma) {
+        constexpr int MT = (NR_ + 15) / 16, KT = NR_ / 8;
+        const int g = lane >> 2, tg = lane & 3;
+        uint32_t ah[MT][KT][4], alo[MT][KT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < KT; ++ks)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = mt * 16 + g + ((q & 1) ? 8 : 0), cidx = ks * 8 + tg + ((q & 2) ? 4 : 0);
+                    const float x = r < NR_ ? sKR[r * (NR_ + 1) + cidx] : 0.f;
+                    ah[mt][ks][q] = to_tf32(x);
+                    alo[mt][ks][q] = to_tf32(x - __uint_as_float(ah[mt][ks][q]));
                 }
-                if (c0 + Be == N) {
-                    T g1, g2;
-                    if (pr < T(0)) {
-                        g1 = g2 = nwR * gwR[i] * gwR[nR + j] * gwR[nR + n2 + k];
-                    } else {
-                        const T* r0 = fs + (long long)(N - 1 - c0 + 3) * Ms + ml;
-                        wall_ghosts(r0[0], r0[-Ms], r0[-2 * Ms], r0[-3 * Ms], g1, g2);
-                    }
-                    fs[(long long)(N - c0 + 3) * Ms + ml] = g1;      // cell N
-                    fs[(long long)(N + 1 - c0 + 3) * Ms + ml] = g2;  // cell N+1
+        const int ncol = n2 * KS, ntc = ncol / 8;
+        for (int tt = warp; tt < Be * ntc; tt += nwarps) {
+            const int cl = tt / ntc, nt = tt % ntc;
+            const int colb = nt * 8 + g;  // this lane's B column (k, j)
+            const T* bsrc = fs + (long long)(cl + 3) * Ms + ((colb / n2) * nR) * n2 + colb % n2;
+            float acc[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < KT; ++ks) {
+                const float x0 = bsrc[(ks * 8 + tg) * n2], x1 = bsrc[(ks * 8 + tg + 4) * n2];
+                const uint32_t bh0 = to_tf32(x0), bh1 = to_tf32(x1);
+                const uint32_t bl0 = to_tf32(x0 - __uint_as_float(bh0)), bl1 = to_tf32(x1 - __uint_as_float(bh1));
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma_tf32(acc[mt], alo[mt][ks], bh0, bh1);
+                    mma_tf32(acc[mt], ah[mt][ks], bl0, bl1);
+                    mma_tf32(acc[mt], ah[mt][ks], bh0, bh1);
                 }
             }
-            __syncthreads();
-        }
-
-        // ---- 3b. tensor cores: (K^h f)[i][(k, j)] = sum_a K^h[i][a] f[k][a][j] for the own cells,
-        // a GEMM of the nR x nR matrix with the cell's nR x (n2 KS) slice, in split TF32
-        // (K = Kh + Kl, f = fh + fl; Kh fh + Kh fl + Kl fh with FP32 accumulation: FP32-level
-        // products), n-tiles of 8 columns spread over the warps, results to shared memory.
-        if constexpr (kMMA) {
-          if (use_mma) {
-            constexpr int MT = (NR_ + 15) / 16, KT = NR_ / 8;
-            const int g = lane >> 2, tg = lane & 3;
-            uint32_t ah[MT][KT][4], alo[MT][KT][4];
+            T* dst = skrf + (long long)cl * Ms;
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-                for (int ks = 0; ks < KT; ++ks)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = mt * 16 + g + ((q & 1) ? 8 : 0), cidx = ks * 8 + tg + ((q & 2) ? 4 : 0);
-                        const float x = r < NR_ ? sKR[r * (NR_ + 1) + cidx] : 0.f;
-                        ah[mt][ks][q] = to_tf32(x);
-                        alo[mt][ks][q] = to_tf32(x - __uint_as_float(ah[mt][ks][q]));
-                    }
-            const int ncol = n2 * KS, ntc = ncol / 8;
-            for (int tt = warp; tt < Be * ntc; tt += nwarps) {
-                const int cl = tt / ntc, nt = tt % ntc;
-                const int colb = nt * 8 + g;  // this lane's B column (k, j)
-                const T* bsrc = fs + (long long)(cl + 3) * Ms + ((colb / n2) * nR) * n2 + colb % n2;
-                float acc[MT][4];
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
-#pragma unroll
-                for (int ks = 0; ks < KT; ++ks) {
-                    const float x0 = bsrc[(ks * 8 + tg) * n2], x1 = bsrc[(ks * 8 + tg + 4) * n2];
-                    const uint32_t bh0 = to_tf32(x0), bh1 = to_tf32(x1);
-                    const uint32_t bl0 = to_tf32(x0 - __uint_as_float(bh0)), bl1 = to_tf32(x1 - __uint_as_float(bh1));
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        mma_tf32(acc[mt], alo[mt][ks], bh0, bh1);
-                        mma_tf32(acc[mt], ah[mt][ks], bl0, bl1);
-                        mma_tf32(acc[mt], ah[mt][ks], bh0, bh1);
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const int r = mt * 16 + g + ((q & 2) ? 8 : 0), cc = nt * 8 + 2 * tg + (q & 1);
+                    if (r < NR_) dst[((cc / n2) * nR + r) * n2 + cc % n2] = acc[mt][q];
                 }
-                T* dst = skrf + (long long)cl * Ms;
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = mt * 16 + g + ((q & 2) ? 8 : 0), cc = nt * 8 + 2 * tg + (q & 1);
-                        if (r < NR_) dst[((cc / n2) * nR + r) * n2 + cc % n2] = acc[mt][q];
-                    }
-            }
-            __syncthreads();
-          }
         }
+        __syncthreads();
+      }
+    }
 
-        // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
-        int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
-        T pr_[NV], p3_[NV];
-        T wm_[NV][VW], iw_[NV][VW], p2_[NV][VW], vl_[NV][VW];
+    // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
+    int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
+    T pr_[NV], p3_[NV];
+    T wm_[NV][VW], iw_[NV][VW], p2_[NV][VW], vl_[NV][VW];
 #pragma unroll
-        for (int g = 0; g < NV; ++g) {
-            const int v = tid + g * NT;
-            vcode[g] = -1;
-            pr_[g] = p3_[g] = T(0);
+    for (int g = 0; g < NV; ++g) {
+        const int v = tid + g * NT;
+        vcode[g] = -1;
+        pr_[g] = p3_[g] = T(0);
 #pragma unroll
-            for (int e = 0; e < VW; ++e) wm_[g][e] = iw_[g][e] = p2_[g][e] = vl_[g][e] = T(0);
-            if (v < Vs) {
-                const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
-                const int k = sl * KS + kk;
-                vcode[g] = (kk << 20) | (i << 10) | jb;
-                const T pr = sp_R[i];
-                pr_[g] = pr;
-                p3_[g] = sp_3[k];
-                const T wik = sw_R[i] * sw_3[k];
+        for (int e = 0; e < VW; ++e) wm_[g][e] = iw_[g][e] = p2_[g][e] = vl_[g][e] = T(0);
+        if (v < Vs) {
+            const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
+            const int k = sl * KS + kk;
+            vcode[g] = (kk << 20) | (i << 10) | jb;
+            const T pr = sp_R[i];
+            pr_[g] = pr;
+            p3_[g] = sp_3[k];
+            const T wik = sw_R[i] * sw_3[k];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const int j = jb * VW + e;
+                p2_[g][e] = sp_2[j];
+                wm_[g][e] = wik * sw_2[j];
+                iw_[g][e] = T(1) / wm_[g][e];
+            }
+            if (c0 == 0 && pr > T(0)) {
+                const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e] * iw_[g][e];
+            } else {
+                // rows of cells c0-3..c0+1 (p_R > 0) or c0+2..c0-2 (p_R < 0)
+                const T* b = fs + (long long)(pr > T(0) ? 0 : 5) * Ms + v * VW;
+                const int s = pr > T(0) ? Ms : -Ms;
+                T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
+                ld_vec<T, VW>(b, r0);
+                ld_vec<T, VW>(b + s, r1);
+                ld_vec<T, VW>(b + 2 * s, r2);
+                ld_vec<T, VW>(b + 3 * s, r3);
+                ld_vec<T, VW>(b + 4 * s, r4);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
-                    const int j = jb * VW + e;
-                    p2_[g][e] = sp_2[j];
-                    wm_[g][e] = wik * sw_2[j];
-                    iw_[g][e] = T(1) / wm_[g][e];
+                    const T iw = iw_[g][e];
+                    vl_[g][e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
                 }
-                if (c0 == 0 && pr > T(0)) {
-                    const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
+            }
+        }
+    }
+
+    const T dt = sizeof(T) == 4 ? (T)I.f_dt : (T)I.dt;
+    const T ca_ = sizeof(T) == 4 ? (T)A.fa : (T)A.a, cb_ = sizeof(T) == 4 ? (T)A.fb : (T)A.b;
+    for (int cl = 0; cl < Be; ++cl) {
+        const int c = c0 + cl;
+        const T* ct = cellT + cl * rs;
+        T sc[20];
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e] * iw_[g][e];
+        for (int q = 0; q < 20; q += 4) {
+            T t4[4];
+            ld_vec<T, 4>(ct + q, t4);
+            sc[q] = t4[0]; sc[q + 1] = t4[1]; sc[q + 2] = t4[2]; sc[q + 3] = t4[3];
+        }
+        const T n = sc[0], u0 = sc[1], u1 = sc[2], u2 = sc[3], iT = sc[4], itau = sc[5], cS = sc[6];
+        const T q0 = sc[7], q1 = sc[8], q2 = sc[9], brchi = sc[10], X = sc[11], Y = sc[12];
+        const T S00 = sc[13], S11 = sc[14], S22 = sc[15], S01 = sc[16], S02 = sc[17], dv = sc[19];
+        const T* g2c = ct + rec_off_g2();
+        const T* gRc = ct + rec_off_gR(n2);
+        const T* g3c = ct + rec_off_g3(nR, n2);
+        const T Ap = sgeo[cl * 3 + 0], Am = sgeo[cl * 3 + 1], kf = sgeo[cl * 3 + 2];
+        const T* fc = fs + (long long)(cl + 3) * Ms;  // row of cell c
+        T acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = T(0);
+#pragma unroll
+        for (int g = 0; g < NV; ++g) {
+            const int cd = vcode[g];
+            if (cd >= 0) {
+                const int kk = cd >> 20, i = (cd >> 10) & 1023, jb = cd & 1023;
+                const int k = sl * KS + kk;
+                const int vb = ((kk * nR + i) * n2v + jb) * VW;  // element offset in the slice
+                const T pr = pr_[g], p3v = p3_[g];
+                // advection: WENO5 value at the right face, upwind by sign(p_R)
+                T vr[VW];
+                if (c == N - 1 && pr < T(0)) {
+                    const T gik = nwR * gwR[i] * gwR[nR + n2 + k];
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e] * iw_[g][e];
                 } else {
-                    // rows of cells c0-3..c0+1 (p_R > 0) or c0+2..c0-2 (p_R < 0)
-                    const T* b = fs + (long long)(pr > T(0) ? 0 : 5) * Ms + v * VW;
+                    const T* b = fc + (pr > T(0) ? -2 * Ms : 3 * Ms) + vb;
                     const int s = pr > T(0) ? Ms : -Ms;
                     T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
                     ld_vec<T, VW>(b, r0);
@@ -382,213 +477,194 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
                         const T iw = iw_[g][e];
-                        vl_[g][e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                        vr[e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
                     }
                 }
-            }
-        }
-
-        const T dt = sizeof(T) == 4 ? (T)I.f_dt : (T)I.dt;
-        const T ca_ = sizeof(T) == 4 ? (T)A.fa : (T)A.a, cb_ = sizeof(T) == 4 ? (T)A.fb : (T)A.b;
-        for (int cl = 0; cl < Be; ++cl) {
-            const int c = c0 + cl;
-            const T* ct = cellT + cl * rs;
-            T sc[20];
+                // curvature force: K^h along i (one column shared by the vector), K_2 along j
+                T KRf[VW], K2f[VW], K3f[VW];
 #pragma unroll
-            for (int q = 0; q < 20; q += 4) {
-                T t4[4];
-                ld_vec<T, 4>(ct + q, t4);
-                sc[q] = t4[0]; sc[q + 1] = t4[1]; sc[q + 2] = t4[2]; sc[q + 3] = t4[3];
-            }
-            const T n = sc[0], u0 = sc[1], u1 = sc[2], u2 = sc[3], iT = sc[4], itau = sc[5], cS = sc[6];
-            const T q0 = sc[7], q1 = sc[8], q2 = sc[9], brchi = sc[10], X = sc[11], Y = sc[12];
-            const T S00 = sc[13], S11 = sc[14], S22 = sc[15], S01 = sc[16], S02 = sc[17], dv = sc[19];
-            const T* g2c = ct + rec_off_g2();
-            const T* gRc = ct + rec_off_gR(n2);
-            const T* g3c = ct + rec_off_g3(nR, n2);
-            const T Ap = sgeo[cl * 3 + 0], Am = sgeo[cl * 3 + 1], kf = sgeo[cl * 3 + 2];
-            const T* fc = fs + (long long)(cl + 3) * Ms;  // row of cell c
-            T acc[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = T(0);
-#pragma unroll
-            for (int g = 0; g < NV; ++g) {
-                const int cd = vcode[g];
-                if (cd >= 0) {
-                    const int kk = cd >> 20, i = (cd >> 10) & 1023, jb = cd & 1023;
-                    const int k = sl * KS + kk;
-                    const int vb = ((kk * nR + i) * n2v + jb) * VW;  // element offset in the slice
-                    const T pr = pr_[g], p3v = p3_[g];
-                    // advection: WENO5 value at the right face, upwind by sign(p_R)
-                    T vr[VW];
-                    if (c == N - 1 && pr < T(0)) {
-                        const T gik = nwR * gwR[i] * gwR[nR + n2 + k];
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e] * iw_[g][e];
+                for (int e = 0; e < VW; ++e) KRf[e] = K2f[e] = K3f[e] = T(0);
+                {
+                    if (kMMA && use_mma) {
+                        ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
                     } else {
-                        const T* b = fc + (pr > T(0) ? -2 * Ms : 3 * Ms) + vb;
-                        const int s = pr > T(0) ? Ms : -Ms;
-                        T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
-                        ld_vec<T, VW>(b, r0);
-                        ld_vec<T, VW>(b + s, r1);
-                        ld_vec<T, VW>(b + 2 * s, r2);
-                        ld_vec<T, VW>(b + 3 * s, r3);
-                        ld_vec<T, VW>(b + 4 * s, r4);
+                        const T* col = fc + kk * nR * n2 + jb * VW;
+                        const T* kr = sKR + i * (nR + 1);
+#pragma unroll 8
+                        for (int a = 0; a < nR; ++a) {
+                            T cv[VW];
+                            ld_vec<T, VW>(col + a * n2, cv);
+                            const T kv = kr[a];
+#pragma unroll
+                            for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                        }
+                    }
+                    const T* row = fc + (kk * nR + i) * n2;
+#pragma unroll 4
+                    for (int b4 = 0; b4 < n2v; ++b4) {
+                        T rv[VW];
+                        ld_vec<T, VW>(row + b4 * VW, rv);
 #pragma unroll
                         for (int e = 0; e < VW; ++e) {
-                            const T iw = iw_[g][e];
-                            vr[e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                            T kq[VW];
+                            ld_vec<T, VW>(sK2 + ((e * n2v + b4) * n2v + jb) * VW, kq);
+#pragma unroll
+                            for (int t = 0; t < VW; ++t) K2f[e] += kq[t] * rv[t];
                         }
                     }
-                    // curvature force: K^h along i (one column shared by the vector), K_2 along j
-                    T KRf[VW], K2f[VW], K3f[VW];
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) KRf[e] = K2f[e] = K3f[e] = T(0);
-                    {
-                        if (kMMA && use_mma) {
-                            ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
-                        } else {
-                            const T* col = fc + kk * nR * n2 + jb * VW;
-                            const T* kr = sKR + i * (nR + 1);
-#pragma unroll 8
-                            for (int a = 0; a < nR; ++a) {
-                                T cv[VW];
-                                ld_vec<T, VW>(col + a * n2, cv);
-                                const T kv = kr[a];
-#pragma unroll
-                                for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
-                            }
-                        }
-                        const T* row = fc + (kk * nR + i) * n2;
+                    if (GEOM == 1) {
+                        const T* k3 = sK3 + k * (n3 + 1);
+                        const T* c3 = fc + i * n2 + jb * VW;
 #pragma unroll 4
-                        for (int b4 = 0; b4 < n2v; ++b4) {
-                            T rv[VW];
-                            ld_vec<T, VW>(row + b4 * VW, rv);
+                        for (int b = 0; b < n3; ++b) {
+                            T cv[VW];
+                            ld_vec<T, VW>(c3 + b * nR * n2, cv);
+                            const T kv = k3[b];
 #pragma unroll
-                            for (int e = 0; e < VW; ++e) {
-                                T kq[VW];
-                                ld_vec<T, VW>(sK2 + ((e * n2v + b4) * n2v + jb) * VW, kq);
-#pragma unroll
-                                for (int t = 0; t < VW; ++t) K2f[e] += kq[t] * rv[t];
-                            }
-                        }
-                        if (GEOM == 1) {
-                            const T* k3 = sK3 + k * (n3 + 1);
-                            const T* c3 = fc + i * n2 + jb * VW;
-#pragma unroll 4
-                            for (int b = 0; b < n3; ++b) {
-                                T cv[VW];
-                                ld_vec<T, VW>(c3 + b * nR * n2, cv);
-                                const T kv = k3[b];
-#pragma unroll
-                                for (int e = 0; e < VW; ++e) K3f[e] += kv * cv[e];
-                            }
+                            for (int e = 0; e < VW; ++e) K3f[e] += kv * cv[e];
                         }
                     }
-                    // collision: -(f - f^S)/tau + J1[f^MB]; terms without j shared by the vector
-                    T fv[VW], g2v[VW];
-                    ld_vec<T, VW>(fc + vb, fv);
-                    ld_vec<T, VW>(g2c + jb * VW, g2v);
-                    const T x0 = pr - u0, x2 = p3v - u2;
-                    const T xsA = x0 * x0 + x2 * x2, xqA = x0 * q0 + x2 * q2;
-                    const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
-                    const T fmbA = n * gRc[i] * g3c[k];
-                    const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
-                    T out[VW];
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        const T p2v = p2_[g][e];
-                        const T adv = pr * wm_[g][e] * (Ap * vr[e] - Am * vl_[g][e]);
-                        vl_[g][e] = vr[e];
-                        T frc;
-                        if (GEOM == 0) {
-                            frc = kf * (p2v * p2v * KRf[e] - pr * K2f[e]);
-                        } else {
-                            frc = (kf * p2v * p2v + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
-                        }
-                        const T x1 = p2v - u1;
-                        const T xs = xsA + x1 * x1;
-                        const T xq = xqA + x1 * q1;
-                        const T fmb = fmbA * g2v[e];
-                        const T z2 = T(0.5) * xs * iT;
-                        const T strain = iT * (stA + x1 * x1 * S11 + T(2) * x0 * x1 * S01);
-                        const T j1 = -brchi * (x0 * (X + T(0.6) * (z2 - T(2.5)) * Y) + T(0.4) * (strain + (z2 - T(2.5)) * dv));
-                        const T fS = fmb * (T(1) + cS * (T(0.2) * xs * iT - T(1)) * xq);
-                        out[e] = -adv - frc - (fv[e] - fS) * itau + fmb * j1;
-                    }
-                    const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
-                    if (A.mode == 0) {
-                        // a f_n + b (f + dt L) with a = 1 - b, written as f_n + b ((f - f_n) + dt L):
-                        // exactly affine whatever the rounding of b (in FP32, fl(1/3) + fl(2/3)
-                        // exceeds one by 3e-8, which would scale the state by that much every step)
-                        if (ca_ != T(0)) {
-                            T fnv[VW];
-                            ldg_vec<T, VW>(f_n + gidx, fnv);
-#pragma unroll
-                            for (int e = 0; e < VW; ++e) out[e] = fnv[e] + cb_ * ((fv[e] - fnv[e]) + dt * out[e]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < VW; ++e) out[e] = fv[e] + dt * out[e];
-                        }
-                    }
-                    st_vec<T, VW>(f_out + gidx, out);
-                    // raw sums: power sums over the vector's p_2, then the 13 moments
-                    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        const T p2v = p2_[g][e];
-                        const T o1 = out[e] * p2v, o2 = o1 * p2v;
-                        s0 += out[e];
-                        s1 += o1;
-                        s2 += o2;
-                        s3 += o2 * p2v;
-                    }
-                    const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
-                    const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
-                    acc[0] += s0;
-                    acc[1] += prs0;
-                    acc[2] += s1;
-                    acc[3] += p3s0;
-                    acc[4] += pr * prs0;
-                    acc[5] += s2;
-                    acc[6] += p3v * p3s0;
-                    acc[7] += pr * s1;
-                    acc[8] += pr * p3s0;
-                    acc[9] += p3v * s1;
-                    acc[10] += pr * e10;
-                    acc[11] += rr * s1 + s3;
-                    acc[12] += p3v * e10;
                 }
-            }
-            // ---- 5. warp sums of the 13 raw moments of this cell (lane L holds sum L/2)
-            if (A.mode == 0) {
-                const T s = warp_sum16_transposed(acc, lane);
-                if (!(lane & 1) && (lane >> 1) < kSums) red[(cl * nwarps + warp) * 16 + (lane >> 1)] = s;
+                // collision: -(f - f^S)/tau + J1[f^MB]; terms without j shared by the vector
+                T fv[VW], g2v[VW];
+                ld_vec<T, VW>(fc + vb, fv);
+                ld_vec<T, VW>(g2c + jb * VW, g2v);
+                const T x0 = pr - u0, x2 = p3v - u2;
+                const T xsA = x0 * x0 + x2 * x2, xqA = x0 * q0 + x2 * q2;
+                const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
+                const T fmbA = n * gRc[i] * g3c[k];
+                const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
+                T out[VW];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const T p2v = p2_[g][e];
+                    const T adv = pr * wm_[g][e] * (Ap * vr[e] - Am * vl_[g][e]);
+                    vl_[g][e] = vr[e];
+                    T frc;
+                    if (GEOM == 0) {
+                        frc = kf * (p2v * p2v * KRf[e] - pr * K2f[e]);
+                    } else {
+                        frc = (kf * p2v * p2v + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
+                    }
+                    const T x1 = p2v - u1;
+                    const T xs = xsA + x1 * x1;
+                    const T xq = xqA + x1 * q1;
+                    const T fmb = fmbA * g2v[e];
+                    const T z2 = T(0.5) * xs * iT;
+                    const T strain = iT * (stA + x1 * x1 * S11 + T(2) * x0 * x1 * S01);
+                    const T j1 = -brchi * (x0 * (X + T(0.6) * (z2 - T(2.5)) * Y) + T(0.4) * (strain + (z2 - T(2.5)) * dv));
+                    const T fS = fmb * (T(1) + cS * (T(0.2) * xs * iT - T(1)) * xq);
+                    out[e] = -adv - frc - (fv[e] - fS) * itau + fmb * j1;
+                }
+                const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
+                if (A.mode == 0) {
+                    // a f_n + b (f + dt L) with a = 1 - b, written as f_n + b ((f - f_n) + dt L):
+                    // exactly affine whatever the rounding of b (in FP32, fl(1/3) + fl(2/3)
+                    // exceeds one by 3e-8, which would scale the state by that much every step)
+                    if (ca_ != T(0)) {
+                        T fnv[VW];
+                        // f_n: read-only for the stage kernel; written earlier in the same launch for the
+                // persistent step kernel, which reads it coherently (L2)
+                if constexpr (kCoherent)
+                    ldcg_vec<T, VW>(f_n + gidx, fnv);
+                else
+                    ldg_vec<T, VW>(f_n + gidx, fnv);
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) out[e] = fnv[e] + cb_ * ((fv[e] - fnv[e]) + dt * out[e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VW; ++e) out[e] = fv[e] + dt * out[e];
+                    }
+                }
+                st_vec<T, VW>(f_out + gidx, out);
+                // raw sums: power sums over the vector's p_2, then the 13 moments
+                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                    const T p2v = p2_[g][e];
+                    const T o1 = out[e] * p2v, o2 = o1 * p2v;
+                    s0 += out[e];
+                    s1 += o1;
+                    s2 += o2;
+                    s3 += o2 * p2v;
+                }
+                const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
+                const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
+                acc[0] += s0;
+                acc[1] += prs0;
+                acc[2] += s1;
+                acc[3] += p3s0;
+                acc[4] += pr * prs0;
+                acc[5] += s2;
+                acc[6] += p3v * p3s0;
+                acc[7] += pr * s1;
+                acc[8] += pr * p3s0;
+                acc[9] += p3v * s1;
+                acc[10] += pr * e10;
+                acc[11] += rr * s1 + s3;
+                acc[12] += p3v * e10;
             }
         }
-        __syncthreads();
+        // ---- 5. warp sums of the 13 raw moments of this cell (lane L holds sum L/2)
         if (A.mode == 0) {
-            // FP64 sums over the warps: the conversions first (independent), then a fixed pairwise
-            // tree (the FP64 pipe is slow on this part: a chain of adds would be the tail of the item)
-            for (int e = tid; e < Be * kSums; e += NT) {
-                const int cl = e / kSums, q = e % kSums;
-                constexpr int kW = 16;  // at most 512 threads
-                double v[kW];
-#pragma unroll
-                for (int ww = 0; ww < kW; ++ww) v[ww] = ww < nwarps ? (double)red[(cl * nwarps + ww) * 16 + q] : 0.0;
-#pragma unroll
-                for (int h = kW / 2; h > 0; h >>= 1)
-#pragma unroll
-                    for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
-                const double s = v[0];
-                const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
-                A.sums_out[cs * kSums + q] = s;
-                if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
-            }
+            const T s = warp_sum16_transposed(acc, lane);
+            if (!(lane & 1) && (lane >> 1) < kSums) red[(cl * nwarps + warp) * 16 + (lane >> 1)] = s;
         }
-        __syncthreads();  // the next item overwrites the staged rows, the records and the sums
+    }
+    __syncthreads();
+    if (A.mode == 0) {
+        // FP64 sums over the warps: the conversions first (independent), then a fixed pairwise
+        // tree (the FP64 pipe is slow on this part: a chain of adds would be the tail of the item)
+        for (int e = tid; e < Be * kSums; e += NT) {
+            const int cl = e / kSums, q = e % kSums;
+            constexpr int kW = 16;  // at most 512 threads
+            double v[kW];
+#pragma unroll
+            for (int ww = 0; ww < kW; ++ww) v[ww] = ww < nwarps ? (double)red[(cl * nwarps + ww) * 16 + q] : 0.0;
+#pragma unroll
+            for (int h = kW / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
+            const double s = v[0];
+            const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
+            A.sums_out[cs * kSums + q] = s;
+            if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
+        }
+    }
+    __syncthreads();  // the next item overwrites the staged rows, the records and the sums
+}
+
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+__global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
+    __shared__ T snw[2];  // wall densities of the item's instance
+    const int tid = threadIdx.x;
+    stream_tables<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
+    __syncthreads();
+    pdl_trigger();
+    pdl_wait();  // everything below reads what the previous kernels wrote
+    uint32_t phase = 0;
+    const int nit = *A.n_items;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const int4 wi = A.items[it];
+        const InstDev I = A.inst[wi.x];
+        stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, true);
+        // geometry, wall Maxwellians and the wall densities from the parts of the outgoing
+        // fluxes, overlapping the copy
+        stream_statics<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I);
+        if (tid < 2) {
+            const T* pp = reinterpret_cast<const T*>(A.nwp) + ((long long)wi.x * 2 + tid) * A.wall_parts;
+            T sum = T(0);
+            for (int p = 0; p < A.wall_parts; ++p) sum += pp[p];
+            const T iden = sizeof(T) == 4 ? (T)(tid ? I.f_nw_iden[1] : I.f_nw_iden[0])
+                                          : (T)(tid ? I.nw_iden[1] : I.nw_iden[0]);
+            snw[tid] = sum * iden;
+        }
+        if (!stream_wait<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, phase)) return;
+        __syncthreads();
+        stream_compute<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, snw[0], snw[1]);
     }
 }
+
 
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
 cudaError_t launch_stream_t(const StageArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {

@@ -93,6 +93,8 @@ def load_library():
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
+        "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
+        "fdlb_step_kernel_times": (c_int, [H, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
         "fdlb_autotune": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_launch_count": (c_int64, [H]),
         "fdlb_set_graph_steps": (c_int, [H, c_int]),
@@ -301,6 +303,14 @@ class Solver:
                "fdlb_set_tensor_contraction")
         return bool(used.value)
 
+    def set_persistent_step(self, enable):
+        """Whole steps in one persistent launch (default off); returns whether it applies to
+        this handle.  enable=None only reports."""
+        used = c_int()
+        flag = -1 if enable is None else (1 if enable else 0)
+        _check(self._L.fdlb_set_persistent_step(self._h, flag, byref(used)), "fdlb_set_persistent_step")
+        return bool(used.value)
+
     def set_programmatic_launch(self, enable):
         _check(self._L.fdlb_set_programmatic_launch(self._h, 1 if enable else 0), "fdlb_set_programmatic_launch")
 
@@ -326,6 +336,12 @@ class Solver:
         sm, ns, cm, nc = c_double(), c_int64(), c_double(), c_int64()
         _check(self._L.fdlb_kernel_times(self._h, byref(sm), byref(ns), byref(cm), byref(nc)), "fdlb_kernel_times")
         return sm.value, ns.value, cm.value, nc.value
+
+    def step_kernel_times(self):
+        """(persistent step-kernel ms, launches, steps) accumulated since the last call."""
+        ms, nl, ns = c_double(), c_int64(), c_int64()
+        _check(self._L.fdlb_step_kernel_times(self._h, byref(ms), byref(nl), byref(ns)), "fdlb_step_kernel_times")
+        return ms.value, nl.value, ns.value
 
     def stream_handle(self):
         s = c_void_p()

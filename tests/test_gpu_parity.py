@@ -77,9 +77,10 @@ def test_twenty_steps_match_oracle(precision, name, geom, beta):
         assert np.max(np.abs(S.get_f() - f_or)) <= 1e-10 * np.max(np.abs(f_or))
 
 
-@pytest.mark.parametrize("tiling", [(4, 1, 0), (8, 2, 0), (16, 4, 0), (32, 1, 512), (5, 4, 128)])
+@pytest.mark.parametrize("tiling", [(4, 1, 0), (8, 2, 0), (16, 4, 0), (32, 1, 512), (5, 4, 128), (2, 1, 0), (2, 4, 0)])
 def test_tilings_agree(tiling):
-    # ragged tails (53 cells), different tile sizes, slice widths and block sizes
+    # ragged tails (53 cells), different tile sizes, slice widths and block sizes; tiles of two
+    # cells (and one) whose stencils reach ghost cells of a wall they do not touch
     d = small_case(precision="fp64", n_cells=53, u_wall=(0.2, 0.0))
     P, f0, S = _pair(d, seed=9)
     ref = fdlb.Solver(d)
