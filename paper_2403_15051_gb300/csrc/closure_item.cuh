@@ -116,15 +116,16 @@ __device__ ClosureTabs<T> closure_tables(T* base, const void* tabTv, const MomSe
 
 // One thread's share of part `part` (of P) of the outgoing flux through a wall (side 0: inner,
 // 1: outer): the sum over the outgoing momenta of |p_R| w vhat, vhat the WENO5 value at the
-// wall face from the wall cell, its neighbour and the cubic extrapolation outside.  `tl` is the
-// thread's index in a block of kClosureThreads threads, whose order of the sums this follows.
+// wall face from the wall cell, its neighbour and the cubic extrapolation outside.  `wall` points
+// at the populations of the wall cell (cell 0 or N-1), `st` is the step to the next cell inward
+// (the rows may be in global or shared memory).  `tl` is the thread's index in a block of
+// kClosureThreads threads, whose order of the sums this follows.
 template <typename T>
-__device__ T wall_flux_partial(const T* fin, const MomSet& M, const ClosureTabs<T>& tb, int N, int side, int part, int P,
-                               int tl) {
+__device__ T wall_flux_partial(const T* wall, long long st, const MomSet& M, const ClosureTabs<T>& tb, int side, int part,
+                               int P, int tl) {
     const int Np = M.Np, nR = M.nR, n2 = M.n2, NT = kClosureThreads;
     const int mlo = (int)((long long)Np * part / P), mhi = (int)((long long)Np * (part + 1) / P);
-    const long long st = side == 0 ? (long long)Np : -(long long)Np;
-    const long long base = side == 0 ? 0LL : (long long)(N - 1) * Np;
+    const long long base = 0;
     T acc = T(0);
     for (int m0 = mlo + tl; m0 < mhi; m0 += 4 * NT) {
         // four momenta per pass so that their sixteen loads are in flight together
@@ -133,7 +134,7 @@ __device__ T wall_flux_partial(const T* fin, const MomSet& M, const ClosureTabs<
         for (int u = 0; u < 4; ++u) {
             const int m = min(m0 + u * NT, mhi - 1);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) fv[u][r] = fin[base + m + r * st];
+            for (int r = 0; r < 4; ++r) fv[u][r] = wall[base + m + r * st];
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -162,17 +163,22 @@ __device__ __forceinline__ T wall_part_sum(const T* r) {
 struct NoExtra {
     __device__ void operator()(int, int) const {}
 };
+struct NoAfterLoads {
+    __device__ void operator()() const {}
+};
 
 // Closure of the own cells [c0, c0 + cnt) of one instance (cnt <= kClosureCells): the collision
 // records go to `recb` (the record of cell c0, stride A.rec_stride), chi and nbar to A.cw.
 // Every thread of the block calls it (it holds block barriers); the block has at least
 // kClosureWarps warps, and warps beyond them run extra(w, nw) (the w-th of nw such warps)
-// while warps 0..2 run the chains of step 3.  `wst` holds A.wst_elems staged band elements, `nbuf`
+// while warps 0..2 run the chains of step 3; every thread runs after_loads() once the item's
+// global loads are issued.  `wst` holds A.wst_elems staged band elements, `nbuf`
 // A.max_union densities.  Returns false on every thread when the band-row copy never
 // completed (A.err is set).
-template <typename T, typename Extra>
+template <typename T, typename Extra, typename AfterLoads>
 __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const ClosureTabs<T>& tb, const InstDev& I, int c0,
-                              int cnt, T* recb, T* wst, T* nbuf, uint64_t* cbar, uint32_t& phase, const Extra& extra) {
+                              int cnt, T* recb, T* wst, T* nbuf, uint64_t* cbar, uint32_t& phase, const Extra& extra,
+                              const AfterLoads& after_loads) {
     using W = Wide<T>;
     __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells, wide
     __shared__ T s_chi[32], snb[32];               // reach cells: chi, band density
@@ -256,6 +262,7 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
                 if (j0 + u * NT < nu) nbuf[j0 + u * NT] = v[u];
         }
     }
+    after_loads();
     if (staged) {
         const bool ok = mbar_wait_bounded(cbar, phase);
         // every thread takes the same exit: a block-wide vote on the outcome
@@ -267,8 +274,8 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
         phase ^= 1u;
     }
     __syncthreads();
-    // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells;
-    // warps 1..3: FM band sums of the reach cells from shared memory
+    // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells; the other
+    // warps: FM band sums of the reach cells from shared memory
     if (warp == 0) {
         if (lane < nh) {
             const int c = h0 + lane;
@@ -298,8 +305,9 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
                 sq[3][c - c0] = s7 - tn * t0 * t1;
             }
         }
-    } else if (!I.chi_local && warp < kClosureWarps) {
-        for (int t = warp - 1; t < nh; t += kClosureWarps - 1) {
+    } else if (!I.chi_local) {
+        // one warp per row, every warp but the first (the row's sum does not depend on which)
+        for (int t = warp - 1; t < nh; t += NT / 32 - 1) {
             const int c = h0 + t;
             const int lo = sblo[t];
             const int kmax = min(min(scnt[t], N - lo), nu - (lo - jlo));

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
         if (w.w != 0) {
             // ---- one part of the outgoing flux through a wall
             const int side = w.w - 1, part = w.z, P = A.wall_parts;
-            T acc = wall_flux_partial<T>(fin_all + I.f_off, M, tb, I.n_cells, side, part, P, tid);
+            const T* wall = fin_all + I.f_off + (side == 0 ? 0LL : (long long)(I.n_cells - 1) * M.Np);
+            T acc = wall_flux_partial<T>(wall, side == 0 ? (long long)M.Np : -(long long)M.Np, M, tb, side, part, P, tid);
             acc = warp_sum(acc);
             if (lane == 0) red[warp] = acc;
             __syncthreads();
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
             continue;
         }
         T* recb = rec_all + (long long)(I.cell_off + w.y) * A.rec_stride;
-        if (!closure_cells<T>(A, M, tb, I, w.y, w.z, recb, wst, nbuf, &cbar, phase, NoExtra{})) return;
+        if (!closure_cells<T>(A, M, tb, I, w.y, w.z, recb, wst, nbuf, &cbar, phase, NoExtra{}, NoAfterLoads{})) return;
     }
 }
 

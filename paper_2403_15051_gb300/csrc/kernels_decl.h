@@ -34,6 +34,12 @@ inline cudaError_t launch_maybe_programmatic(void (*kern)(Args...), int grid, in
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Row stride of K^h in the stage kernel's shared memory: a multiple of four elements (16-byte
+// vector loads of a row) whose rows fall on distinct banks for the rows a quarter warp reads.
+inline __host__ __device__ int kr_stride(int nR) { return (nR + 3) / 4 * 4 + 4; }
+// Elements from the start of the tables to K^h: K_2, padded to 16 bytes.
+inline __host__ __device__ int kr_offset(int n2, int tsize) { return (n2 * n2 * tsize + 15) / 16 * 16 / tsize; }
+
 struct StreamSmem {
     int fs, rec, tabs, geo, red, kr, total;
 };
@@ -52,7 +58,8 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
     s.rec = off;
     off += al((long long)B * record_stride(nR, n2, n3) * tsize);
     s.tabs = off;
-    off += al((long long)(2 * (nR + n2 + n3) + nR * (nR + 1) + n2 * n2 + n3 * (n3 + 1) + 2 * (nR + n2 + n3)) * tsize);
+    off += al((long long)(2 * (nR + n2 + n3) + nR * kr_stride(nR) + kr_offset(n2, tsize) + n3 * (n3 + 1) +
+                          2 * (nR + n2 + n3)) * tsize);
     s.geo = off;
     off += al((long long)B * 3 * tsize);
     s.red = off;

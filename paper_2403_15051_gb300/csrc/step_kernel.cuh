@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
     const StreamSmem P = stream_smem_plan(S.st.B, nR * n2 * KS, nR, n2, n3, (int)(blockDim.x >> 5), (int)sizeof(T),
                                           (sizeof(T) == 4 && S.st.mma) ? 1 : 0);
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);
+    T* fs = reinterpret_cast<T*>(smem_raw + P.fs);
+    uint64_t* sbar = reinterpret_cast<uint64_t*>(smem_raw);  // the stage's copy barrier
+    const int Ms = nR * n2 * KS;
     // closure region: [staged band rows | tables | band-union densities]
     T* wst = reinterpret_cast<T*>(smem_raw + S.clo_off);
     T* ctab = wst + S.cl.wst_elems;
@@ -116,29 +119,53 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
                     return;
                 }
             }
-            const T* fin_all = reinterpret_cast<const T*>(S.f[in]);
             for (int it = blockIdx.x; it < nit; it += gridDim.x) {
                 const int4 wi = A.items[it];
                 const InstDev I = A.inst[wi.x];
                 const int N = I.n_cells;
                 // tiles whose stencils reach a wall's ghost cells need that wall's density
                 const bool wl = wi.y < 3, wr = wi.y + wi.z + 2 >= N;
-                // 1. the rows of the stage input (the records come from the closure below)
-                stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, false);
                 // 2. the closure of the own cells; the extra warps sum the wall fluxes for a tile
                 // near a wall: virtual warp (side, part, w) of the closure kernel's block
-                const T* fin = fin_all + I.f_off;
+                // the four cells next to a wall are among the tile's staged rows (row = cell - c0 + 3):
+                // the extra warps wait for the staged copy (bounded) and read them there
                 auto walls = [&](int w, int nw) {
-                    const int ns = (wl ? 1 : 0) + (wr ? 1 : 0);
-                    for (int v = w; v < ns * kWallParts * kClosureWarps; v += nw) {
-                        const int side = (wl && v < kWallParts * kClosureWarps) ? 0 : 1;
-                        const int r = v % (kWallParts * kClosureWarps), part = r / kClosureWarps, vw = r % kClosureWarps;
-                        T acc = wall_flux_partial<T>(fin, M, tb, N, side, part, kWallParts, vw * 32 + lane);
-                        acc = warp_sum(acc);
-                        if (lane == 0) wred[side][part][vw] = acc;
+                    if (!mbar_wait_bounded(sbar, sphase)) {
+                        if (lane == 0) atomicOr(A.err, 1);  // the stage's own wait reports it too
+                        return;
+                    }
+                    const int nv = ((wl ? 1 : 0) + (wr ? 1 : 0)) * kWallParts * kClosureWarps;
+                    // four virtual warps at a time: independent chains in flight together
+                    for (int v0 = w; v0 < nv; v0 += 4 * nw) {
+                        T acc[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int v = v0 + u * nw;
+                            acc[u] = T(0);
+                            if (v < nv) {
+                                const int side = (wl && v < kWallParts * kClosureWarps) ? 0 : 1;
+                                const int r = v % (kWallParts * kClosureWarps), part = r / kClosureWarps;
+                                const T* wall = fs + (long long)((side == 0 ? 0 : N - 1) - wi.y + 3) * Ms;
+                                acc[u] = wall_flux_partial<T>(wall, side == 0 ? (long long)Ms : -(long long)Ms, M, tb, side,
+                                                              part, kWallParts, (r % kClosureWarps) * 32 + lane);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int v = v0 + u * nw;
+                            if (v < nv) {  // warp-uniform
+                                const int side = (wl && v < kWallParts * kClosureWarps) ? 0 : 1;
+                                const int r = v % (kWallParts * kClosureWarps);
+                                const T a = warp_sum(acc[u]);
+                                if (lane == 0) wred[side][r / kClosureWarps][r % kClosureWarps] = a;
+                            }
+                        }
                     }
                 };
-                if (!closure_cells<T>(C, M, tb, I, wi.y, wi.z, cellT, wst, nbuf, &cbar, cphase, walls)) {
+                // 1. the rows of the stage input, requested after the closure's loads (the
+                // records come from the closure)
+                auto rows = [&]() { stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, false); };
+                if (!closure_cells<T>(C, M, tb, I, wi.y, wi.z, cellT, wst, nbuf, &cbar, cphase, walls, rows)) {
                     stream_wait<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, sphase);  // the rows still in flight
                     return;
                 }

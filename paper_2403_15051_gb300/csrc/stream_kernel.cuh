@@ -138,7 +138,7 @@ __device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
 
 // Local names of the stage's dimensions and of its shared-memory plan (StreamSmem): fs the
 // staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sK2 K_2 in the vector-swizzled
-// order [e][b / VW][j / VW][b % VW] (first: aligned vector loads), sKR K^h with row stride nR+1,
+// order [e][b / VW][j / VW][b % VW] (first: aligned vector loads), sKR K^h with row stride krs,
 // sK3 K_3 with row stride n3+1, nodes and weights, sgw the inner and outer wall Maxwellians per
 // axis [2][nR + n2 + n3], sgeo the tile's geometry, red the per-warp sums [cell][warp][16], skrf
 // K^h f of the own cells (tensor-core path).  NR_, N2_, N3_: compile-time axis sizes (0: taken
@@ -160,8 +160,9 @@ __device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);                                                               \
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);                                                           \
     T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);                                                            \
-    T* sKR = sK2 + n2 * n2;                                                                                      \
-    T* sK3 = sKR + nR * (nR + 1);                                                                                \
+    const int krs = kr_stride(nR);                                                                               \
+    T* sKR = sK2 + kr_offset(n2, (int)sizeof(T));                                                                \
+    T* sK3 = sKR + nR * krs;                                                                                     \
     T* sp_R = sK3 + n3 * (n3 + 1);                                                                               \
     T* sp_2 = sp_R + nR;                                                                                         \
     T* sp_3 = sp_2 + n2;                                                                                         \
@@ -201,7 +202,7 @@ __device__ __forceinline__ void stream_tables(const StageArgs& A, const MomSet& 
         sp_3[e] = tab[M.o_p3 + e];
         sw_3[e] = tab[M.o_w3 + e];
     }
-    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * (nR + 1) + e % nR] = tab[M.o_KR + e];
+    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * krs + e % nR] = tab[M.o_KR + e];
     for (int e = tid; e < n2 * n2; e += NT) {
         const int j = e / n2, b = e % n2;
         sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = tab[M.o_K2 + e];
@@ -342,7 +343,7 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int r = mt * 16 + g + ((q & 1) ? 8 : 0), cidx = ks * 8 + tg + ((q & 2) ? 4 : 0);
-                    const float x = r < NR_ ? sKR[r * (NR_ + 1) + cidx] : 0.f;
+                    const float x = r < NR_ ? sKR[r * krs + cidx] : 0.f;
                     ah[mt][ks][q] = to_tf32(x);
                     alo[mt][ks][q] = to_tf32(x - __uint_as_float(ah[mt][ks][q]));
                 }
@@ -443,6 +444,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
         const T n = sc[0], u0 = sc[1], u1 = sc[2], u2 = sc[3], iT = sc[4], itau = sc[5], cS = sc[6];
         const T q0 = sc[7], q1 = sc[8], q2 = sc[9], brchi = sc[10], X = sc[11], Y = sc[12];
         const T S00 = sc[13], S11 = sc[14], S22 = sc[15], S01 = sc[16], S02 = sc[17], dv = sc[19];
+        // collision terms of the cell that do not depend on the momentum (see below)
+        const T hiT = T(0.5) * iT, fiT = T(0.2) * iT, nbr = -brchi;
+        const T g1c = T(2) * iT * S01, J2c = T(0.4) * iT * S11, F3 = cS * fiT * q1;
         const T* g2c = ct + rec_off_g2();
         const T* gRc = ct + rec_off_gR(n2);
         const T* g3c = ct + rec_off_g3(nR, n2);
@@ -489,14 +493,30 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                         ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
                     } else {
                         const T* col = fc + kk * nR * n2 + jb * VW;
-                        const T* kr = sKR + i * (nR + 1);
-#pragma unroll 8
-                        for (int a = 0; a < nR; ++a) {
-                            T cv[VW];
-                            ld_vec<T, VW>(col + a * n2, cv);
-                            const T kv = kr[a];
+                        const T* kr = sKR + i * krs;
+                        if constexpr (sizeof(T) == 4 && NR_ > 0 && NR_ % 4 == 0) {
+                            // four entries of the K^h row per vector load
+#pragma unroll 2
+                            for (int a4 = 0; a4 < NR_; a4 += 4) {
+                                T kq[4];
+                                ld_vec<T, 4>(kr + a4, kq);
 #pragma unroll
-                            for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                                for (int t = 0; t < 4; ++t) {
+                                    T cv[VW];
+                                    ld_vec<T, VW>(col + (a4 + t) * n2, cv);
+#pragma unroll
+                                    for (int e = 0; e < VW; ++e) KRf[e] += kq[t] * cv[e];
+                                }
+                            }
+                        } else {
+#pragma unroll 8
+                            for (int a = 0; a < nR; ++a) {
+                                T cv[VW];
+                                ld_vec<T, VW>(col + a * n2, cv);
+                                const T kv = kr[a];
+#pragma unroll
+                                for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                            }
                         }
                     }
                     const T* row = fc + (kk * nR + i) * n2;
@@ -525,7 +545,11 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                         }
                     }
                 }
-                // collision: -(f - f^S)/tau + J1[f^MB]; terms without j shared by the vector
+                // collision: -(f - f^S)/tau + J1[f^MB] (Eqs. j0, j1).  With x = p - u and
+                // x1 = p_2 - u_2 the only coordinate that varies along the vector, the Shakhov
+                // factor f^S / f^MB = 1 + c_S (|x|^2 / (5 T) - 1) x.q is a cubic in x1 and J1 / f^MB
+                // (which holds |x|^2 / (2T) - 5/2 and the strain x.S.x / T) a quadratic: their
+                // coefficients are formed once per vector, then two Horner evaluations per momentum.
                 T fv[VW], g2v[VW];
                 ld_vec<T, VW>(fc + vb, fv);
                 ld_vec<T, VW>(g2c + jb * VW, g2v);
@@ -534,6 +558,12 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
                 const T fmbA = n * gRc[i] * g3c[k];
                 const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
+                const T Yd = T(0.6) * x0 * Y + T(0.4) * dv;
+                const T J0 = nbr * (x0 * X + Yd * (hiT * xsA - T(2.5)) + T(0.4) * iT * stA);
+                const T J1 = nbr * T(0.4) * g1c * x0;
+                const T J2 = nbr * (Yd * hiT + J2c);
+                const T b0 = fiT * xsA - T(1), cb0 = cS * b0;
+                const T F0 = T(1) + cb0 * xqA, F1 = cb0 * q1, F2 = cS * fiT * xqA;
                 T out[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
@@ -547,13 +577,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                         frc = (kf * p2v * p2v + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
                     }
                     const T x1 = p2v - u1;
-                    const T xs = xsA + x1 * x1;
-                    const T xq = xqA + x1 * q1;
                     const T fmb = fmbA * g2v[e];
-                    const T z2 = T(0.5) * xs * iT;
-                    const T strain = iT * (stA + x1 * x1 * S11 + T(2) * x0 * x1 * S01);
-                    const T j1 = -brchi * (x0 * (X + T(0.6) * (z2 - T(2.5)) * Y) + T(0.4) * (strain + (z2 - T(2.5)) * dv));
-                    const T fS = fmb * (T(1) + cS * (T(0.2) * xs * iT - T(1)) * xq);
+                    const T fS = fmb * (((F3 * x1 + F2) * x1 + F1) * x1 + F0);
+                    const T j1 = (J2 * x1 + J1) * x1 + J0;
                     out[e] = -adv - frc - (fv[e] - fS) * itau + fmb * j1;
                 }
                 const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
