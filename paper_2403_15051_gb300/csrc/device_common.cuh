@@ -107,6 +107,31 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     return ratio_fast(a0 * r0 + a1 * r1 + a2 * r2, T(6) * (a0 + a1 + a2));
 }
 
+// The same reconstruction written on the window in ascending cell order, w0..w4, for either
+// upwind direction: sigma = +1 gives weno5(w0, .., w4) (value at the right face of w2's cell,
+// from the left), sigma = -1 gives weno5(w4, .., w0) (left face, from the right).  The three
+// smoothness indicators belong to the left, centre and right stencils whatever the direction,
+// and every candidate value is (D_k + 12 w2 -+ 3 sigma t_k) / 2 with D_k the stencil's second
+// difference and t_k the first-difference part of its indicator, so the value is
+// w2 + sum_k a_k X_k / (12 sum_k a_k), X_k = D_k +- 3 sigma t_k.  The linear weights follow the
+// direction: (dL, dC, dR) = (0.1, 0.6, 0.3) or (0.3, 0.6, 0.1); s3 = 3 sigma.  Indicators are
+// taken four times over (4 eps + 13/3 D^2 + t^2): the normalised weights are unchanged.
+template <typename T>
+__device__ __forceinline__ T weno5_sym(T w0, T w1, T w2, T w3, T w4, T s3, T dL, T dR) {
+    const T d0 = w1 - w0, d1 = w2 - w1, d2 = w3 - w2, d3 = w4 - w3;
+    const T D1 = d1 - d0, D2 = d2 - d1, D3 = d3 - d2;
+    const T tL = T(3) * d1 - d0, tC = -(d1 + d2), tR = d3 - T(3) * d2;
+    const T c = T(13.0 / 3.0), e4 = T(4e-6);
+    const T EL = tL * tL + (c * D1 * D1 + e4);
+    const T EC = tC * tC + (c * D2 * D2 + e4);
+    const T ER = tR * tR + (c * D3 * D3 + e4);
+    const T m = fmin(EL, fmin(EC, ER));
+    const T sL = ratio_fast(m, EL), sC = ratio_fast(m, EC), sR = ratio_fast(m, ER);
+    const T aL = dL * sL * sL, aC = T(0.6) * sC * sC, aR = dR * sR * sR;
+    const T XL = D1 + s3 * tL, XC = D2 - s3 * tC, XR = D3 - s3 * tR;
+    return w2 + ratio_fast(aL * XL + aC * XC + aR * XR, T(12) * (aL + aC + aR));
+}
+
 // ---- wide accumulators: plain FP64 for FP64 populations; for FP32 populations a double-float
 // (hi + lo, about 44 significant bits) on the FP32 pipe, because FP64 arithmetic on GB300 costs
 // 64 cycles per dependent operation and about 440 per division.  The error-free transformations

@@ -411,19 +411,19 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 #pragma unroll
                 for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e] * iw_[g][e];
             } else {
-                // rows of cells c0-3..c0+1 (p_R > 0) or c0+2..c0-2 (p_R < 0)
-                const T* b = fs + (long long)(pr > T(0) ? 0 : 5) * Ms + v * VW;
-                const int s = pr > T(0) ? Ms : -Ms;
+                // rows of cells c0-3..c0+1 (p_R > 0) or c0-2..c0+2 (p_R < 0), ascending
+                const T* b = fs + (long long)(pr > T(0) ? 0 : 1) * Ms + v * VW;
+                const T s3 = pr > T(0) ? T(3) : T(-3), dL = pr > T(0) ? T(0.1) : T(0.3), dR = pr > T(0) ? T(0.3) : T(0.1);
                 T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
                 ld_vec<T, VW>(b, r0);
-                ld_vec<T, VW>(b + s, r1);
-                ld_vec<T, VW>(b + 2 * s, r2);
-                ld_vec<T, VW>(b + 3 * s, r3);
-                ld_vec<T, VW>(b + 4 * s, r4);
+                ld_vec<T, VW>(b + Ms, r1);
+                ld_vec<T, VW>(b + 2 * Ms, r2);
+                ld_vec<T, VW>(b + 3 * Ms, r3);
+                ld_vec<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     const T iw = iw_[g][e];
-                    vl_[g][e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                    vl_[g][e] = weno5_sym(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw, s3, dL, dR);
                 }
             }
         }
@@ -470,18 +470,20 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 #pragma unroll
                     for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e] * iw_[g][e];
                 } else {
-                    const T* b = fc + (pr > T(0) ? -2 * Ms : 3 * Ms) + vb;
-                    const int s = pr > T(0) ? Ms : -Ms;
+                    // rows of cells c-2..c+2 (p_R > 0) or c-1..c+3 (p_R < 0), ascending
+                    const T* b = fc + (pr > T(0) ? -2 * Ms : -Ms) + vb;
+                    const T s3 = pr > T(0) ? T(3) : T(-3), dL = pr > T(0) ? T(0.1) : T(0.3);
+                    const T dR = pr > T(0) ? T(0.3) : T(0.1);
                     T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
                     ld_vec<T, VW>(b, r0);
-                    ld_vec<T, VW>(b + s, r1);
-                    ld_vec<T, VW>(b + 2 * s, r2);
-                    ld_vec<T, VW>(b + 3 * s, r3);
-                    ld_vec<T, VW>(b + 4 * s, r4);
+                    ld_vec<T, VW>(b + Ms, r1);
+                    ld_vec<T, VW>(b + 2 * Ms, r2);
+                    ld_vec<T, VW>(b + 3 * Ms, r3);
+                    ld_vec<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
                     for (int e = 0; e < VW; ++e) {
                         const T iw = iw_[g][e];
-                        vr[e] = weno5(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw);
+                        vr[e] = weno5_sym(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw, s3, dL, dR);
                     }
                 }
                 // curvature force: K^h along i (one column shared by the vector), K_2 along j
