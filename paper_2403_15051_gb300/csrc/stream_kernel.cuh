@@ -641,19 +641,32 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
     }
     __syncthreads();
     if (A.mode == 0) {
-        // FP64 sums over the warps: the conversions first (independent), then a fixed pairwise
-        // tree (the FP64 pipe is slow on this part: a chain of adds would be the tail of the item)
+        // sums over the warps in a fixed pairwise tree, to FP64.  FP32 partials: a double-float
+        // tree (error-free first level, ~44 bits after), converted once (exact); the FP64 pipe is
+        // slow on this part and the sums are the tail of every item.  FP64 partials: FP64.
         for (int e = tid; e < Be * kSums; e += NT) {
             const int cl = e / kSums, q = e % kSums;
             constexpr int kW = 16;  // at most 512 threads
-            double v[kW];
+            double s;
+            if constexpr (sizeof(T) == 4) {
+                Wide<float> v[kW];
 #pragma unroll
-            for (int ww = 0; ww < kW; ++ww) v[ww] = ww < nwarps ? (double)red[(cl * nwarps + ww) * 16 + q] : 0.0;
+                for (int ww = 0; ww < kW; ++ww) v[ww] = w_from_t(ww < nwarps ? (float)red[(cl * nwarps + ww) * 16 + q] : 0.f);
 #pragma unroll
-            for (int h = kW / 2; h > 0; h >>= 1)
+                for (int h = kW / 2; h > 0; h >>= 1)
 #pragma unroll
-                for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
-            const double s = v[0];
+                    for (int ww = 0; ww < h; ++ww) v[ww] = w_add(v[ww], v[ww + h]);
+                s = (double)v[0].hi + (double)v[0].lo;
+            } else {
+                double v[kW];
+#pragma unroll
+                for (int ww = 0; ww < kW; ++ww) v[ww] = ww < nwarps ? (double)red[(cl * nwarps + ww) * 16 + q] : 0.0;
+#pragma unroll
+                for (int h = kW / 2; h > 0; h >>= 1)
+#pragma unroll
+                    for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
+                s = v[0];
+            }
             const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
             A.sums_out[cs * kSums + q] = s;
             if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
