@@ -201,15 +201,32 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
     // geometry of the own cells (warp 0, lane per cell), the band rows of the reach cells
     // (bulk copies of their stored extents, issued by warp 0) and the densities of the union
     // of the bands (all threads)
-    double s[kSums];
+    // the raw sums in the wide type: FP64, or for FP32 populations the double-float pairs the
+    // stage kernel stores beside them (no FP64 arithmetic here)
+    W sv[kSums];
     T geo0 = T(1), geo1 = T(0);
     if (warp == 0 && lane < nh) {
-        const double* src = S + (long long)(h0 + lane) * slices * kSums;
+        if constexpr (sizeof(T) == 4) {
+            const float2* src = reinterpret_cast<const float2*>(A.sumsw) + ((long long)I.cell_off + h0 + lane) * slices * kSums;
 #pragma unroll
-        for (int q = 0; q < kSums; ++q) s[q] = src[q];
-        for (int sl = 1; sl < slices; ++sl)
+            for (int q = 0; q < kSums; ++q) {
+                const float2 p = src[q];
+                sv[q] = W{p.x, p.y};
+            }
+            for (int sl = 1; sl < slices; ++sl)
 #pragma unroll
-            for (int q = 0; q < kSums; ++q) s[q] += src[sl * kSums + q];
+                for (int q = 0; q < kSums; ++q) {
+                    const float2 p = src[sl * kSums + q];
+                    sv[q] = w_add(sv[q], W{p.x, p.y});
+                }
+        } else {
+            const double* src = S + (long long)(h0 + lane) * slices * kSums;
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) sv[q] = w_from(src[q], (T*)nullptr);
+            for (int sl = 1; sl < slices; ++sl)
+#pragma unroll
+                for (int q = 0; q < kSums; ++q) sv[q] = w_add(sv[q], w_from(src[sl * kSums + q], (T*)nullptr));
+        }
     }
     if (warp == 0 && lane < cnt) {
         const T* gc = geoT + (long long)(I.cell_off + c0 + lane) * kGeo;
@@ -279,11 +296,11 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
     if (warp == 0) {
         if (lane < nh) {
             const int c = h0 + lane;
-            const W n = w_from(s[0], (T*)nullptr);
-            const W u0 = w_div(w_from(s[1], (T*)nullptr), n);
-            const W u1 = w_div(w_from(s[2], (T*)nullptr), n);
-            const W u2 = w_div(w_from(s[3], (T*)nullptr), n);
-            const W tr = w_add(w_add(w_from(s[4], (T*)nullptr), w_from(s[5], (T*)nullptr)), w_from(s[6], (T*)nullptr));
+            const W n = sv[0];
+            const W u0 = w_div(sv[1], n);
+            const W u1 = w_div(sv[2], n);
+            const W u2 = w_div(sv[3], n);
+            const W tr = w_add(w_add(sv[4], sv[5]), sv[6]);
             const W uu = w_add(w_add(w_mul(u0, u0), w_mul(u1, u1)), w_mul(u2, u2));
             const W Tc = w_div(w_sub(tr, w_mul(n, uu)), w_scale(n, T(3)));
             sw_n[lane] = n;
@@ -295,13 +312,13 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
                 // q and P_12 in the populations' precision (they enter only the Shakhov
                 // factor and the diagnostics)
                 const T tn = w_hi(n), t0 = w_hi(u0), t1 = w_hi(u1), t2 = w_hi(u2), ttr = w_hi(tr), tuu = w_hi(uu);
-                const T s4 = (T)s[4], s5 = (T)s[5], s6 = (T)s[6], s7 = (T)s[7], s8 = (T)s[8], s9 = (T)s[9];
+                const T s4 = w_hi(sv[4]), s5 = w_hi(sv[5]), s6 = w_hi(sv[6]), s7 = w_hi(sv[7]), s8 = w_hi(sv[8]), s9 = w_hi(sv[9]);
                 const T m0 = s4 * t0 + s7 * t1 + s8 * t2;
                 const T m1 = s7 * t0 + s5 * t1 + s9 * t2;
                 const T m2 = s8 * t0 + s9 * t1 + s6 * t2;
-                sq[0][c - c0] = T(0.5) * ((T)s[10] - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
-                sq[1][c - c0] = T(0.5) * ((T)s[11] - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
-                sq[2][c - c0] = T(0.5) * ((T)s[12] - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
+                sq[0][c - c0] = T(0.5) * (w_hi(sv[10]) - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
+                sq[1][c - c0] = T(0.5) * (w_hi(sv[11]) - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
+                sq[2][c - c0] = T(0.5) * (w_hi(sv[12]) - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
                 sq[3][c - c0] = s7 - tn * t0 * t1;
             }
         }

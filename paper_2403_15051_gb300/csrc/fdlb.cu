@@ -24,7 +24,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Byte layout of all device state, computed identically for sizing and carving.
 struct Layout {
-    size_t f[3], sums[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
+    size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
         rprev, rout, total;
 };
@@ -53,6 +53,7 @@ struct Solver {
     Layout lay{};
     void* f[3] = {nullptr, nullptr, nullptr};
     double* sums[3] = {nullptr, nullptr, nullptr};
+    void* sumsw[3] = {nullptr, nullptr, nullptr};
     void* dens[3] = {nullptr, nullptr, nullptr};
     void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr, *cw = nullptr;
     void* rec = nullptr;
@@ -197,6 +198,8 @@ Layout make_layout(const Solver& S) {
     };
     for (int b = 0; b < 3; ++b) L.f[b] = take(S.f_elems * S.tsize);
     for (int b = 0; b < 3; ++b) L.sums[b] = take((size_t)S.total_cells * S.n3 * kSums * sizeof(double));
+    // double-float pairs of the sums for the FP32 closure
+    for (int b = 0; b < 3; ++b) L.sumsw[b] = take(S.tsize == 4 ? (size_t)S.total_cells * S.n3 * kSums * 8 : 0);
     for (int b = 0; b < 3; ++b) L.dens[b] = take((size_t)S.total_cells * S.n3 * S.tsize);
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
     L.cw = take((size_t)S.total_cells * 2 * S.tsize);
@@ -538,12 +541,16 @@ void from_device_layout(const Solver& S, const std::vector<T>& src, double* dst,
 
 int launch_moments_all(Solver& S, int buf) {
     const int nc = S.max_citems;
-    if (S.precision == FDLB_FP32)
+    if (S.precision == FDLB_FP32) {
         launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.citems, S.n_citems, std::max(1, std::min(nc, S.n_sm * 8)),
                               S.inst_d, S.tab, S.M, S.stream);
-    else
+        // the double-float pairs the FP32 closure reads
+        launch_sums_pairs(S.sums[buf], S.sumsw[buf], (long long)S.total_cells * S.M.slices * kSums, S.stream);
+        S.launches++;
+    } else {
         launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], S.citems, S.n_citems,
                                std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
+    }
     S.launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -551,6 +558,7 @@ int launch_moments_all(Solver& S, int buf) {
 int launch_closure_buf(Solver& S, int buf, int write_ca) {
     ClosureArgs A{};
     A.sums = S.sums[buf];
+    A.sumsw = S.sumsw[buf];
     A.dens = S.dens[buf];
     A.f_in = S.f[buf];
     A.cw = S.cw;
@@ -624,6 +632,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.nwp = S.nwp;
     A.wall_parts = kWallParts;
     A.sums_out = S.sums[out];
+    A.sumsw_out = S.sumsw[out];
     A.dens_out = S.dens[out];
     A.items = S.sitems;
     A.n_items = S.n_sitems;
@@ -779,6 +788,7 @@ int launch_steps_fused(Solver& S, int64_t n) {
     for (int b = 0; b < 3; ++b) {
         P.f[b] = S.f[b];
         P.sums[b] = S.sums[b];
+        P.sumsw[b] = S.sumsw[b];
         P.dens[b] = S.dens[b];
     }
     P.bar = S.gbar;
@@ -864,6 +874,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     for (int b = 0; b < 3; ++b) {
         R.f[b] = R.ws + L.f[b];
         R.sums[b] = (double*)(R.ws + L.sums[b]);
+        R.sumsw[b] = (void*)(R.ws + L.sumsw[b]);
         R.dens[b] = (void*)(R.ws + L.dens[b]);
     }
     R.ca = (double*)(R.ws + L.ca);
@@ -1370,8 +1381,10 @@ int fdlb_load(fdlb_handle h, const char* path) {
     S->prev_valid = false;
     if (recompute) return fdlb::launch_moments_all(*S, 0);
     const long long nd = (long long)S->total_cells * S->M.slices;
-    if (S->precision == FDLB_FP32)
+    if (S->precision == FDLB_FP32) {
         fdlb::launch_dens_from_sums<float>(S->sums[0], (float*)S->dens[0], nd, S->stream);
+        fdlb::launch_sums_pairs(S->sums[0], S->sumsw[0], nd * fdlb::kSums, S->stream);
+    }
     else
         fdlb::launch_dens_from_sums<double>(S->sums[0], (double*)S->dens[0], nd, S->stream);
     return fdlb::cuda_status(cudaGetLastError());

@@ -67,6 +67,7 @@ struct StageArgs {
     int rec_stride;
     const void* nwp;               // [instance][2][kWallParts] outgoing wall fluxes of f_in (T)
     double* sums_out;              // raw sums of f_out
+    void* sumsw_out;               // the same as double-float pairs (FP32 populations), [cell][slice][13]
     void* dens_out;                // per-slice densities of f_out (T), [cell][slice]
     const int4* items;             // (instance, first cell, cells, slice)
     const int* n_items;
@@ -88,6 +89,7 @@ struct StageArgs {
 
 struct ClosureArgs {
     const double* sums;
+    const void* sumsw;             // the raw sums as double-float pairs (FP32 populations)
     const void* dens;              // per-slice densities (T), [cell][slice], for the FM bands
     const void* f_in;              // populations (T), for the wall fluxes
     void* cw;                      // [cell][2] chi and nbar of the stage (T), for the queries
@@ -114,6 +116,7 @@ struct StepArgs {
     ClosureArgs cl;                // the closure fields; sums, densities, populations set per stage
     void* f[3];                    // f^n (and f^{n+1}), f1, f2
     double* sums[3];
+    void* sumsw[3];
     void* dens[3];
     unsigned int* bar;             // grid barrier counter (zero at launch)
     int n_steps;

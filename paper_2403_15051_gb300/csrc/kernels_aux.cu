@@ -231,6 +231,21 @@ __global__ void dens_kernel(const double* __restrict__ sums, T* __restrict__ den
         dens[i] = (T)sums[i * kSums];
 }
 
+// Double-float pairs (hi = fl(s), lo = fl(s - hi)) of FP64 raw sums: the closure's input for
+// FP32 populations, where the stage kernel does not write them (set-up, restored checkpoints).
+__global__ void sums_pairs_kernel(const double* __restrict__ sums, float2* __restrict__ sw, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = sums[i];
+        const float hi = __double2float_rn(v);
+        sw[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
+void launch_sums_pairs(const double* sums, void* sw, long long n, cudaStream_t s) {
+    const long long g = (n + 255) / 256;
+    sums_pairs_kernel<<<(int)(g < 4096 ? (g > 0 ? g : 1) : 4096), 256, 0, s>>>(sums, reinterpret_cast<float2*>(sw), n);
+}
+
 template <typename T>
 void launch_dens_from_sums(const double* sums, T* dens, long long n, cudaStream_t s) {
     const long long g = (n + 255) / 256;

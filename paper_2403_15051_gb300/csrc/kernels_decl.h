@@ -84,6 +84,8 @@ void launch_moments(const T* f, double* sums, T* dens, const int4* items, const 
 template <typename T>
 void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s);
 
+void launch_sums_pairs(const double* sums, void* sw, long long n, cudaStream_t s);
+
 template <typename T>
 void launch_dens_from_sums(const double* sums, T* dens, long long n, cudaStream_t s);
 

@@ -104,12 +104,14 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
             A.f_n = S.f[0];
             A.f_out = S.f[out];
             A.sums_out = S.sums[out];
+            A.sumsw_out = S.sumsw[out];
             A.dens_out = S.dens[out];
             A.a = a;
             A.b = b;
             A.fa = (float)a;
             A.fb = (float)b;
             C.sums = S.sums[in];
+            C.sumsw = S.sumsw[in];
             C.dens = S.dens[in];
             C.f_in = S.f[in];
             if (step > 0 || stage > 0) {

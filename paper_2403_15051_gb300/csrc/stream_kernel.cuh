@@ -657,6 +657,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 #pragma unroll
                     for (int ww = 0; ww < h; ++ww) v[ww] = w_add(v[ww], v[ww + h]);
                 s = (double)v[0].hi + (double)v[0].lo;
+                // the pair itself for the closure (its split of s: hi = fl(s), lo = s - hi)
+                const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
+                reinterpret_cast<float2*>(A.sumsw_out)[cs * kSums + q] = make_float2(v[0].hi, v[0].lo);
             } else {
                 double v[kW];
 #pragma unroll
