@@ -226,6 +226,16 @@ int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use);
  * method, not launches. */
 int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use);
 
+/* Test hooks of the bounded device waits (both 0 in use).  tx_extra_bytes (0..65536): every
+ * staged copy of the stage kernel waits for that many bytes more than it copies, so its bounded
+ * wait on the copy barrier runs out; barrier_extra (0..65536): every grid barrier of the
+ * persistent step kernel waits for that many arrivals more than the grid makes, so its 1 s wait
+ * runs out.  In both cases the blocks set the error flag and leave without faulting: the next
+ * fdlb_get_diagnostics returns FDLB_ETIMEOUT and the state of the interrupted step is
+ * undefined.  fdlb_clear_error clears the flag (the handle stays usable; set a state again). */
+int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra);
+int fdlb_clear_error(fdlb_handle h);
+
 /* Programmatic dependent launch of the closure and stage kernels (default on): each may start
  * while its predecessor in the stream finishes, loading its constant tables, and waits for the
  * predecessor's completion before it reads anything the predecessor writes.  Results are the same

@@ -42,11 +42,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: each try_wait suspends for a hardware-chosen interval, so 2^22 tries end
-// within seconds.  Returns false if the phase never completed.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after 1 s of global time (a copy completes in microseconds), or after
+// 2^22 tries (each suspends for a hardware-chosen interval) whichever comes first.  Returns false
+// if the phase never completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
-    for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int it = 1; it < (1 << 22); ++it) {
         if (mbar_try_wait(bar, phase)) return true;
+        if ((it & 63) == 0 && global_ns() - t0 > 1000000000ull) return false;
+    }
     return false;
 }
 

@@ -92,6 +92,7 @@ struct Solver {
     int mma_on = 0;        // ... and in use for the current tiling
     // persistent step kernel (closure + stage per tile, grid barriers between stages)
     int fused = 0;         // use it where the configuration allows (off by default: slower on GB300)
+    int test_tx_extra = 0, test_bar_extra = 0;  // test hooks of the bounded waits (0 in use)
     int fused_on = 0;      // ... and in use for the current tiling
     int grid_step = 0, step_wst = 0, step_clo_off = 0, max_tile = 0;
     size_t smem_step = 0;
@@ -651,6 +652,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.use_bulk = S.use_bulk;
     A.programmatic = S.programmatic;
     A.mma = S.mma_on;
+    A.tx_extra = S.test_tx_extra;
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
@@ -794,6 +796,8 @@ int launch_steps_fused(Solver& S, int64_t n) {
     P.bar = S.gbar;
     P.n_steps = (int)n;
     P.clo_off = S.step_clo_off;
+    P.bar_extra = S.test_bar_extra;
+    A.tx_extra = S.test_tx_extra;
     FDLB_CUDA(cudaMemsetAsync(S.gbar, 0, sizeof(unsigned), S.stream));
     S.launches++;
     if (!S.timing) return cuda_status(launch_step_dispatch(S, &P, nullptr));
@@ -1477,6 +1481,26 @@ int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use) {
     const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
     if (in_use) *in_use = S->fused_on;
     return rc;
+}
+
+int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra) {
+    Solver* S = SOL(h);
+    if (!S || tx_extra_bytes < 0 || tx_extra_bytes > 65536 || barrier_extra < 0 || barrier_extra > 65536) return FDLB_EINVAL;
+    S->test_tx_extra = tx_extra_bytes;
+    S->test_bar_extra = barrier_extra;
+    if (S->gexec) {
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+    }
+    return FDLB_OK;
+}
+
+int fdlb_clear_error(fdlb_handle h) {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    FDLB_CUDA(cudaMemsetAsync(S->err, 0, sizeof(int), S->stream));
+    FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    return FDLB_OK;
 }
 
 int fdlb_set_programmatic_launch(fdlb_handle h, int enable) {

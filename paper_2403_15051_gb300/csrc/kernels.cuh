@@ -85,6 +85,7 @@ struct StageArgs {
     int use_bulk;                  // stage the tile with cp.async.bulk
     int programmatic;              // launched with programmatic stream serialization
     int mma;                       // K^h contraction on the tensor cores (FP32 compile-time shapes)
+    int tx_extra;                  // test hook: bytes the staged-copy barrier waits for beyond the copy
 };
 
 struct ClosureArgs {
@@ -121,6 +122,7 @@ struct StepArgs {
     unsigned int* bar;             // grid barrier counter (zero at launch)
     int n_steps;
     int clo_off;                   // byte offset of the closure's shared memory
+    int bar_extra;                 // test hook: arrivals every grid barrier waits for beyond the grid
 };
 
 }  // namespace fdlb

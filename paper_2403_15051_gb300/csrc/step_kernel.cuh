@@ -29,11 +29,6 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 // Generic-proxy global stores of this thread become visible to the bulk-copy engine's reads.
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -116,7 +111,7 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
             C.f_in = S.f[in];
             if (step > 0 || stage > 0) {
                 ++nbar;
-                if (!grid_barrier(S.bar, nbar * gridDim.x)) {
+                if (!grid_barrier(S.bar, nbar * gridDim.x + (unsigned)S.bar_extra)) {
                     if (tid == 0) atomicOr(A.err, 4);
                     return;
                 }

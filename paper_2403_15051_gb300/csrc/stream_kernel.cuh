@@ -228,7 +228,7 @@ __device__ __forceinline__ void stream_issue(const StageArgs& A, const MomSet& M
     if (A.use_bulk) {
         if (tid == 0) {
             fence_proxy_async();
-            mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + (records ? Be * rs : 0)) * sizeof(T)));
+            mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + (records ? Be * rs : 0)) * sizeof(T)) + (uint32_t)A.tx_extra);
             if (M.slices == 1) {
                 bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
             } else {

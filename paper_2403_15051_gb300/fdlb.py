@@ -94,6 +94,8 @@ def load_library():
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
+        "fdlb_set_wait_test": (c_int, [H, c_int, c_int]),
+        "fdlb_clear_error": (c_int, [H]),
         "fdlb_step_kernel_times": (c_int, [H, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
         "fdlb_autotune": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_launch_count": (c_int64, [H]),
@@ -310,6 +312,13 @@ class Solver:
         flag = -1 if enable is None else (1 if enable else 0)
         _check(self._L.fdlb_set_persistent_step(self._h, flag, byref(used)), "fdlb_set_persistent_step")
         return bool(used.value)
+
+    def set_wait_test(self, tx_extra_bytes=0, barrier_extra=0):
+        """Test hooks that make the bounded device waits run out (0, 0 in use)."""
+        _check(self._L.fdlb_set_wait_test(self._h, tx_extra_bytes, barrier_extra), "fdlb_set_wait_test")
+
+    def clear_error(self):
+        _check(self._L.fdlb_clear_error(self._h), "fdlb_clear_error")
 
     def set_programmatic_launch(self, enable):
         _check(self._L.fdlb_set_programmatic_launch(self._h, 1 if enable else 0), "fdlb_set_programmatic_launch")
