@@ -289,8 +289,9 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
             return false;
         }
         phase ^= 1u;
+    } else {
+        __syncthreads();  // staged: the vote above is the barrier
     }
-    __syncthreads();
     // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells; the other
     // warps: FM band sums of the reach cells from shared memory
     if (warp == 0) {

@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
                     const T iden = sizeof(T) == 4 ? (T)I.f_nw_iden[side] : (T)I.nw_iden[side];
                     nw[side] = sum * iden;
                 }
+                // (the wait ends with a block-wide vote: the barrier after the copy and the statics)
                 if (!stream_wait<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, sphase)) return;
-                __syncthreads();
                 // 3. the stage
                 stream_compute<T, GEOM, VW, NV, NR_, N2_, N3_, true>(A, M, wi, I, nw[0], nw[1]);
             }

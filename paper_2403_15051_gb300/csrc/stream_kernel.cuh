@@ -262,7 +262,9 @@ __device__ __forceinline__ void stream_statics(const StageArgs& A, const MomSet&
     }
 }
 
-// Completion of the staged copy; false (on every thread, A.err set) when it never completes.
+// Completion of the staged copy; false (on every thread, A.err set) when it never completes.  With
+// the bulk engine the outcome is voted on block-wide, which is also the block's barrier after the
+// copy; the plain-load path needs a barrier of its own.
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
 __device__ __forceinline__ bool stream_wait(const StageArgs& A, const MomSet& M, uint32_t& phase) {
     FDLB_STREAM_LAYOUT;
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
             snw[tid] = sum * iden;
         }
         if (!stream_wait<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, phase)) return;
-        __syncthreads();
+        if (!A.use_bulk) __syncthreads();  // the bulk path's wait ends with a block-wide vote
         stream_compute<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, snw[0], snw[1]);
     }
 }
