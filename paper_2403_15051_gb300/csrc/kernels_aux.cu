@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
         fence_mbar_init();
     }
     __syncthreads();
-    pdl_trigger();
     pdl_wait();  // everything below reads what the previous kernels wrote
+    // the successor (the stage kernel) may start now: it requests the rows of the stage input,
+    // written by the kernel this one has just waited for
+    pdl_trigger();
     const T* fin_all = reinterpret_cast<const T*>(A.f_in);
     T* rec_all = reinterpret_cast<T*>(A.rec);
     T* nwp = reinterpret_cast<T*>(A.nwp);

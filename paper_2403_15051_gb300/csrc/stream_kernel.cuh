@@ -213,9 +213,11 @@ __device__ __forceinline__ void stream_tables(const StageArgs& A, const MomSet& 
 
 // Staging of a work item: the cells c0-3 .. c0+Be+2 of its slice and, when `records`, the
 // tile's collision records (the bulk engine, completion on the copy barrier; else plain loads).
+// With the bulk engine the two can be requested apart: part 1 expects the whole item and copies
+// the rows, part 2 copies the records, part 3 does both.
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
 __device__ __forceinline__ void stream_issue(const StageArgs& A, const MomSet& M, int4 wi, const InstDev& I,
-                                             bool records) {
+                                             bool records, int part = 3) {
     FDLB_STREAM_LAYOUT;
     const int N = I.n_cells, c0 = wi.y, Be = wi.z, sl = wi.w;
     const T* fin = f_in + I.f_off;
@@ -227,16 +229,18 @@ __device__ __forceinline__ void stream_issue(const StageArgs& A, const MomSet& M
     // ---- 1. stage the cells (this slice) and the tile's collision records
     if (A.use_bulk) {
         if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + (records ? Be * rs : 0)) * sizeof(T)) + (uint32_t)A.tx_extra);
-            if (M.slices == 1) {
-                bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
-            } else {
-                for (int cc = lo; cc < hi; ++cc)
-                    bulk_g2s(frow0 + (long long)(cc - lo) * Ms, fin + (long long)cc * Np + slice_off,
-                             (uint32_t)(Ms * sizeof(T)), bar);
+            if (part & 1) {
+                fence_proxy_async();
+                mbar_expect_tx(bar, (uint32_t)(((hi - lo) * Ms + (records ? Be * rs : 0)) * sizeof(T)) + (uint32_t)A.tx_extra);
+                if (M.slices == 1) {
+                    bulk_g2s(frow0, fin + (long long)lo * Np, (uint32_t)((hi - lo) * Np * sizeof(T)), bar);
+                } else {
+                    for (int cc = lo; cc < hi; ++cc)
+                        bulk_g2s(frow0 + (long long)(cc - lo) * Ms, fin + (long long)cc * Np + slice_off,
+                                 (uint32_t)(Ms * sizeof(T)), bar);
+                }
             }
-            if (records) bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
+            if (records && (part & 2)) bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
         }
     } else {
         for (int cc = lo; cc < hi; ++cc)
@@ -685,15 +689,24 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     __shared__ T snw[2];  // wall densities of the item's instance
     const int tid = threadIdx.x;
     stream_tables<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
+    // The rows of the first item are requested before the wait: they are the output of the stage
+    // kernel two launches back, complete once the closure kernel in between has passed its own
+    // wait, which it does before it lets this kernel start.  The records (the closure's output)
+    // follow the wait.
+    const int nit = *A.n_items;
+    const bool early = A.use_bulk && blockIdx.x < nit;
+    if (early) {
+        const int4 wi = A.items[blockIdx.x];
+        stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, A.inst[wi.x], true, 1);
+    }
     __syncthreads();
     pdl_trigger();
     pdl_wait();  // everything below reads what the previous kernels wrote
     uint32_t phase = 0;
-    const int nit = *A.n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const int4 wi = A.items[it];
         const InstDev I = A.inst[wi.x];
-        stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, true);
+        stream_issue<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I, true, (early && it == blockIdx.x) ? 2 : 3);
         // geometry, wall Maxwellians and the wall densities from the parts of the outgoing
         // fluxes, overlapping the copy
         stream_statics<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M, wi, I);
