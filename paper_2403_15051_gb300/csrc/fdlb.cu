@@ -1111,8 +1111,13 @@ int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) {
 int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
-    int rc = fdlb::launch_closure_buf(*S, 0, 1);
-    if (rc) return rc;
+    // n, u, T, q, P_12 come from the FP64 raw sums of the current state alone (the closure's chi
+    // and nbar, columns the query does not return, are not needed): the record kernel only
+    if (S->precision == FDLB_FP32)
+        fdlb::launch_ca<float>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream);
+    else
+        fdlb::launch_ca<double>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream);
+    FDLB_CUDA(cudaGetLastError());
     const int N = S->setup[instance].p.n_cells;
     const double* src = S->ca + (size_t)S->cell_off[instance] * fdlb::kCA;
     FDLB_CUDA(cudaMemcpy2DAsync(out, FDLB_NMOM * sizeof(double), src, fdlb::kCA * sizeof(double),
