@@ -963,7 +963,11 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     // default tiling (the fastest of a sweep on GB300; fdlb_autotune refines it per workload):
     // whole cells per block, 4 cells per tile (cylinder, 256 threads) or 8 (sphere, 512 threads)
     rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, 256) : configure_tiling(R, 8, R.n3, 512);
-    R.closure_cells = R.geometry == FDLB_CYL ? 2 : 4;  // the fastest closure items with overlapped launches
+    // closure items: few cells each where the whole closure is one short latency-bound launch (2 on
+    // the cylinder, 4 on the sphere, with overlapped launches), 8 where items outnumber the blocks
+    // that fit on the device several times over (batches, long instances: throughput-bound)
+    R.closure_cells = R.geometry == FDLB_CYL ? 2 : 4;
+    if (R.total_cells / R.closure_cells > R.n_sm * 8) R.closure_cells = 8;
     if (!rc) rc = upload_items(R);
     for (int q = 0; q < n && !rc; ++q) rc = fdlb_init_uniform(reinterpret_cast<fdlb_handle>(S.get()), q, 0.0, 0.0);
     if (rc) {
