@@ -543,13 +543,11 @@ void from_device_layout(const Solver& S, const std::vector<T>& src, double* dst,
 int launch_moments_all(Solver& S, int buf) {
     const int nc = S.max_citems;
     if (S.precision == FDLB_FP32) {
-        launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.citems, S.n_citems, std::max(1, std::min(nc, S.n_sm * 8)),
-                              S.inst_d, S.tab, S.M, S.stream);
-        // the double-float pairs the FP32 closure reads
-        launch_sums_pairs(S.sums[buf], S.sumsw[buf], (long long)S.total_cells * S.M.slices * kSums, S.stream);
-        S.launches++;
+        // the FP64 sums and the double-float pairs the FP32 closure reads
+        launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.sumsw[buf], S.citems, S.n_citems,
+                              std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
     } else {
-        launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], S.citems, S.n_citems,
+        launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], nullptr, S.citems, S.n_citems,
                                std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
     }
     S.launches++;

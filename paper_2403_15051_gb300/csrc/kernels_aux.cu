@@ -14,7 +14,7 @@ namespace fdlb {
 // of the partial-sum array, the other slices are cleared.
 template <typename T>
 __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sums, T* __restrict__ dens,
-                               const int4* __restrict__ items,
+                               float2* __restrict__ sumsw, const int4* __restrict__ items,
                                const int* __restrict__ n_items, const InstDev* __restrict__ inst,
                                const double* __restrict__ tab, MomSet M) {
     __shared__ double red[kMaxRed][kSums];
@@ -58,9 +58,15 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
             if (threadIdx.x < kSums) {
                 double s = 0.0;
                 for (int ww = 0; ww < nw; ++ww) s += red[ww][threadIdx.x];
-                double* dst = sums + ((long long)(I.cell_off + c) * M.slices) * kSums;
+                const long long base = ((long long)(I.cell_off + c) * M.slices) * kSums;
+                double* dst = sums + base;
                 dst[threadIdx.x] = s;
                 for (int sl = 1; sl < M.slices; ++sl) dst[sl * kSums + threadIdx.x] = 0.0;
+                if (sumsw) {  // the double-float pairs of the FP32 closure
+                    const float hi = __double2float_rn(s);
+                    sumsw[base + threadIdx.x] = make_float2(hi, __double2float_rn(s - (double)hi));
+                    for (int sl = 1; sl < M.slices; ++sl) sumsw[base + sl * kSums + threadIdx.x] = make_float2(0.f, 0.f);
+                }
                 if (threadIdx.x == 0) {
                     T* dd = dens + (long long)(I.cell_off + c) * M.slices;
                     dd[0] = (T)s;
@@ -221,9 +227,9 @@ __global__ void residual_kernel(const double* __restrict__ sums, int slices, con
 
 // ------------------------------------------------------------------------------ launchers
 template <typename T>
-void launch_moments(const T* f, double* sums, T* dens, const int4* items, const int* n_items, int grid,
+void launch_moments(const T* f, double* sums, T* dens, void* sumsw, const int4* items, const int* n_items, int grid,
                     const InstDev* inst, const double* tab, const MomSet& M, cudaStream_t s) {
-    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, dens, items, n_items, inst, tab, M);
+    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, dens, reinterpret_cast<float2*>(sumsw), items, n_items, inst, tab, M);
 }
 
 // Slice densities from restored raw sums.
@@ -273,9 +279,9 @@ template void launch_ca<float>(const double*, const void*, double*, int, int, cu
 template void launch_ca<double>(const double*, const void*, double*, int, int, cudaStream_t);
 template void launch_dens_from_sums<float>(const double*, float*, long long, cudaStream_t);
 template void launch_dens_from_sums<double>(const double*, double*, long long, cudaStream_t);
-template void launch_moments<float>(const float*, double*, float*, const int4*, const int*, int, const InstDev*,
+template void launch_moments<float>(const float*, double*, float*, void*, const int4*, const int*, int, const InstDev*,
                                     const double*, const MomSet&, cudaStream_t);
-template void launch_moments<double>(const double*, double*, double*, const int4*, const int*, int, const InstDev*,
+template void launch_moments<double>(const double*, double*, double*, void*, const int4*, const int*, int, const InstDev*,
                                      const double*, const MomSet&, cudaStream_t);
 template void launch_closure<float>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
 template void launch_closure<double>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);

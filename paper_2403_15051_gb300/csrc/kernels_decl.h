@@ -78,7 +78,7 @@ struct StreamCfg {
 };
 
 template <typename T>
-void launch_moments(const T* f, double* sums, T* dens, const int4* items, const int* n_items, int grid, const InstDev* inst,
+void launch_moments(const T* f, double* sums, T* dens, void* sumsw, const int4* items, const int* n_items, int grid, const InstDev* inst,
                     const double* tab, const MomSet& M, cudaStream_t s);
 
 template <typename T>
