@@ -76,6 +76,21 @@ def batch_instances(accept, n=512, seed=0, n_lo=128, n_hi=2048):
     return out
 
 
+def layering_instances(geometry, precision="fp32", cells_per_sigma=24, Q=(4, 4, 4), etas=(0.01, 0.1, 0.2),
+                       radii=(1.0, 3.0, 5.0), confinements=(4.0, 7.0, 10.0)):
+    """Dense hard-sphere gas at rest between coaxial cylinders or concentric spheres at T_w = 1 (the
+    appendix on the stationary gas): sigma = 1, inner radius R_L, outer R_L + C, mean reduced density
+    eta0; every combination, in the order eta0, R_L, C."""
+    out = []
+    for eta0 in etas:
+        for rl in radii:
+            for c in confinements:
+                out.append(dict(geometry=geometry, R_in=rl, R_out=rl + c, sigma=1.0, n_cells=int(round(c * cells_per_sigma)),
+                                beta=0.0, Q_R=Q[0], Q_2=Q[1], Q_3=Q[2], eta0=eta0, T_wall=(1.0, 1.0), u_wall=(0.0, 0.0),
+                                dt=None, precision=precision, chi_model=0))
+    return out
+
+
 def perturbation(shape, seed, amplitude=0.05):
     """Seeded multiplicative perturbation 1 + amplitude * U[-1, 1] of the given shape."""
     rng = np.random.default_rng(seed)
