@@ -91,6 +91,21 @@ def layering_instances(geometry, precision="fp32", cells_per_sigma=24, Q=(4, 4, 
     return out
 
 
+def heatflux_instances(geometry, precision="fp64", cells_per_sigma=24, Q=(4, 4, 4), etas=(0.01, 0.1, 0.2),
+                       radii=(1.0, 2.0, 5.0, 10.0, 20.0, 50.0), confinement=4.0, dT=0.1):
+    """Fourier flow between coaxial cylinders or concentric spheres at rest with wall temperatures
+    1 and 1 + dT (the comparison of the two geometries' heat fluxes): sigma = 1, inner radius R_L,
+    outer R_L + C; every (eta0, R_L) combination in that order."""
+    out = []
+    for eta0 in etas:
+        for rl in radii:
+            out.append(dict(geometry=geometry, R_in=rl, R_out=rl + confinement, sigma=1.0,
+                            n_cells=int(round(confinement * cells_per_sigma)), beta=0.0, Q_R=Q[0], Q_2=Q[1], Q_3=Q[2],
+                            eta0=eta0, T_wall=(1.0, 1.0 + dT), u_wall=(0.0, 0.0), dt=None, precision=precision,
+                            chi_model=0))
+    return out
+
+
 def perturbation(shape, seed, amplitude=0.05):
     """Seeded multiplicative perturbation 1 + amplitude * U[-1, 1] of the given shape."""
     rng = np.random.default_rng(seed)
