@@ -91,10 +91,17 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the timed kernels' code: the sources with comments removed and whitespace collapsed
+    (a change of prose leaves the recorded counters valid, any change of code does not)."""
+    import re
+
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, p)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
