@@ -5,7 +5,8 @@
 //                      The passive-or-outermost axis k is outermost inside a cell so that a
 //                      momentum slice (a range of k) is one contiguous run per cell.
 //   sums[cell][slice][13]  FP64 raw quadrature sums (Eq. mom_quad) of the populations,
-//                      one partial per momentum slice (summed by the consumer in a fixed order).
+//                      one partial per momentum slice (summed by the consumer in a fixed order);
+//                      for FP32 populations also as double-float pairs (float2), the closure's input.
 //   dens[cell][slice]  the slice densities (sum 0) in the populations' precision, read by the
 //                      FM band sums.
 //   ca[cell][12]       FP64 closure record: n, u1, u2, u3, T, q1, q2, q3, P12, chi, nbar, 0.
@@ -19,6 +20,8 @@
 //                     with metric factors (Sec. II.B/C), the curvature force with the K matrices
 //                     (Sec. III.B), the Shakhov + J1 collision, the RK combination, the store, and
 //                     the raw sums of the new populations (epilogue).
+// Or, optionally, whole steps in one cooperative launch (step_kernel.cuh): the same closure and
+// stage code per tile, grid barriers between stages.
 #pragma once
 
 #include <cuda_runtime.h>

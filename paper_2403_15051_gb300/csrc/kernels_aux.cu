@@ -11,7 +11,8 @@ namespace fdlb {
 
 // ------------------------------------------------------------------------------ moments
 // Raw quadrature sums (Eq. mom_quad) of the populations of whole cells; written into slice 0
-// of the partial-sum array, the other slices are cleared.
+// of the partial-sum array, the other slices are cleared; for FP32 populations also the
+// double-float pairs of the sums (sumsw, the closure's input).
 template <typename T>
 __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sums, T* __restrict__ dens,
                                float2* __restrict__ sumsw, const int4* __restrict__ items,

@@ -2,15 +2,19 @@
 //
 // Per work item (instance, first cell c0, cells Be, slice sl):
 //  1. the TMA engine copies the populations of cells c0-3 .. c0+Be+2 (this slice) and the
-//     tile's collision records (written by the closure kernel) into shared memory;
+//     tile's collision records (written by the closure kernel) into shared memory (a block's
+//     first rows before its dependency wait, the records after it);
 //  2. meanwhile the block loads the cell geometry and the wall densities;
-//  3. ghost rows at a wall: incoming directions carry n_w times the wall Maxwellian, outgoing
-//     directions the cubic extrapolation of the four cells next to the wall;
+//  3. ghost rows where the tile's stencils leave the domain: incoming directions carry n_w times
+//     the wall Maxwellian, outgoing directions the cubic extrapolation of the four cells next to
+//     the wall;
 //  4. per population: WENO5 face values of f/w upwinded by sign(p_R), conservative advection
 //     with the face areas and cell volume (Sec. II.B/C), the curvature force with the K matrices
 //     (Sec. III.B), the Shakhov + J1 collision (Eqs. j0, j1), the RK combination and the store;
 //  5. the 13 raw sums of the new populations per cell: per-thread partials, a transposing warp
-//     reduction in the populations' precision, FP64 across the warps at the end of the item.
+//     reduction in the populations' precision, across the warps at the end of the item in a
+//     fixed tree (double-float for FP32 populations, FP64 for FP64), stored as FP64 sums and, for
+//     FP32 populations, as the double-float pairs the closure reads.
 //
 // Thread mapping: a "vector" is VW momenta with the same (k, i) and consecutive j, which are
 // contiguous in the [k][i][j] layout.  A thread owns up to NV vectors for the whole kernel, so
