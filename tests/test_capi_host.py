@@ -112,3 +112,27 @@ def test_default_time_step_matches_oracle_rule(lib):
     chi0 = float(omodel.chi_set(d["eta0"]))
     tau = float(omodel.relaxation_time(P.n0, 1.2, chi0, P.sigma))
     assert P.dt == pytest.approx(min(0.4 * dr / (np.abs(P.pR).max() * np.sqrt(1.2)), 0.5 * tau), rel=1e-14)
+
+
+@pytest.mark.parametrize("maker", ["layering", "heatflux"])
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_sweep_workloads_pass_host_validation(lib, maker, geometry):
+    """The gas-at-rest and heat-flux sweeps are valid batches for the library's set-up."""
+    import ctypes
+
+    from paper_2403_15051_gb300 import workloads as wl
+    ds = (wl.layering_instances if maker == "layering" else wl.heatflux_instances)(geometry)
+    p = (fdlb.Params * len(ds))(*[fdlb.make_params(d) for d in ds])
+    nb = ctypes.c_size_t()
+    assert lib.fdlb_workspace_bytes(p, len(ds), ctypes.byref(nb)) == 0 and nb.value > 0
+
+
+def test_handle_calls_reject_a_null_handle(lib):
+    import ctypes
+    null = ctypes.c_void_p(0)
+    d, n1, n2 = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    used = ctypes.c_int()
+    assert lib.fdlb_set_persistent_step(null, 1, ctypes.byref(used)) == 1
+    assert lib.fdlb_set_wait_test(null, 0, 0) == 1
+    assert lib.fdlb_clear_error(null) == 1
+    assert lib.fdlb_step_kernel_times(null, ctypes.byref(d), ctypes.byref(n1), ctypes.byref(n2)) == 1
