@@ -250,3 +250,23 @@ def test_fourier_flow_radial_heat_flux_constant_times_R():
     Rq = P.grid.R_c * m["q"][:, 0]
     assert np.all(Rq > 0)  # heat flows outwards from the hot inner wall
     assert (Rq.max() - Rq.min()) / Rq.mean() < 0.02
+
+
+@pytest.mark.slow
+def test_fourier_flow_radial_heat_flux_constant_times_R_squared():
+    """Steady Fourier flow between concentric spheres: with the gas at rest the energy balance
+    reduces to d(R^2 q_R)/dR = 0, so R^2 q_R is constant across the gap (Sec. IV.B, geometry
+    comparison) and q_R falls off as R^-2.  A spherical metric factor taken as the cylinder's (one
+    power of R) would give R q_R constant instead, which this rejects.  The first and last three
+    cells hold the Knudsen layers and the one-sided wall stencils and are left out."""
+    P = S.make_problem(geo.SPH, 1.0, 2.0, 24, 4, 4, 4, eta0=0.1, Kn=0.1, T_wall=(1.1, 0.9))
+    f = S.uniform_state(P)
+    f = S.run(f, P, int(round(12.0 / P.dt)))
+    m = S.moments(f, P)
+    R, qR = P.grid.R_c[3:-3], m["q"][3:-3, 0]
+    assert np.all(qR > 0)
+    R2q, Rq = R ** 2 * qR, R * qR
+    assert (R2q.max() - R2q.min()) / R2q.mean() < 0.01
+    assert (Rq.max() - Rq.min()) / Rq.mean() > 0.2
+    slope = np.polyfit(np.log(R), np.log(qR), 1)[0]
+    assert slope == pytest.approx(-2.0, abs=0.02)
