@@ -237,6 +237,13 @@ def test_couette_profile_is_A_R_plus_B_over_R_in_the_dilute_small_Kn_limit():
     assert fit_res < 2e-3 * uw
     assert lin_res > 5 * fit_res  # the curvature of the profile is resolved
     assert A == pytest.approx(A0, rel=0.25) and B == pytest.approx(B0, rel=0.25)
+    # the emergent shear viscosity: away from the Knudsen layers the kinetic shear stress is the
+    # Newton law P_R2 = -mu R d(u_phi/R)/dR with mu = tau P_i from the Eq. viscosity coefficient
+    m = S.moments(f, P)
+    chi = model.chi_set(model.eta_of_n(m["n"], P.sigma))
+    mu = model.viscosity(m["n"], m["T"], chi, P.sigma)
+    ratio = (m["P01"] / (-mu * (S.d_dR(uphi, P.grid) - uphi / Rc)))[8:16]
+    assert np.all(np.abs(ratio - 1) < 0.01), ratio
 
 
 @pytest.mark.slow
@@ -270,3 +277,19 @@ def test_fourier_flow_radial_heat_flux_constant_times_R_squared():
     assert (Rq.max() - Rq.min()) / Rq.mean() > 0.2
     slope = np.polyfit(np.log(R), np.log(qR), 1)[0]
     assert slope == pytest.approx(-2.0, abs=0.02)
+
+
+@pytest.mark.slow
+def test_fourier_flow_conductivity_in_the_dilute_small_Kn_limit():
+    """The emergent thermal conductivity of the Shakhov model (Sec. II): in a dilute gas at
+    Kn = 0.05 the steady radial heat flux between cylinders follows Fourier's law q_R = -lambda
+    dT/dR with lambda = (5/2) tau P_i / Pr (Eq. viscosity, second line; Pr -> 2/3) in the cells
+    away from the Knudsen layers.  A Shakhov correction dropped (Pr = 1) or of the wrong sign
+    changes lambda by a third or more."""
+    P = S.make_problem(geo.CYL, 1.0, 2.0, 24, 4, 4, 4, eta0=0.001, Kn=0.05, T_wall=(1.1, 0.9))
+    f = S.run(S.uniform_state(P), P, int(round(12.0 / P.dt)))
+    m = S.moments(f, P)
+    chi = model.chi_set(model.eta_of_n(m["n"], P.sigma))
+    lam = model.conductivity(m["n"], m["T"], chi, P.sigma)
+    ratio = (m["q"][:, 0] / (-lam * S.d_dR(m["T"], P.grid)))[8:16]
+    assert np.all(np.abs(ratio - 1) < 0.015), ratio
