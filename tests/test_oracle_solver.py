@@ -53,6 +53,34 @@ def test_collision_and_force_conserve_mass_per_cell(g):
     assert np.all(np.abs(d["force"].sum((1, 2, 3))) <= 1e-13 * scale)
 
 
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+@pytest.mark.parametrize("chi_model", [S.SET_LOCAL, S.RET_FM])
+def test_collision_momentum_and_energy_moments(g, chi_model):
+    """Gaussian moments of the collision term (Eqs. shakhov, j1) on a perturbed state.  The
+    Shakhov part conserves momentum and energy; the first-order Enskog term J1 transfers
+    momentum -P_c X along R only (P_c = b rho chi n T, the non-ideal part of the pressure;
+    X = d ln(n^2 chi T)/dR, so -grad P_c for the local chi) and does the work -P_c div u (the
+    Y term and the (zeta^2 - 5/2) div u term carry neither).  The degree-5 energy moment of the
+    Shakhov correction is exact from Q = 6 (expansion order 5) on."""
+    P = S.make_problem(g, 1.0, 2.0, 16, 6, 6, 6, eta0=0.2, Kn=0.05, T_wall=(1.0, 1.3), chi_model=chi_model,
+                       u_wall=((0.2, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    f = _perturbed(P, seed=3, amp=0.1)
+    _, d = S.rhs(f, P, details=True)
+    C, cl = d["coll"], d["closure"]
+    ax = (1, 2, 3)
+    p = S.momentum_axes(P)
+    u = cl["u"]
+    xi = [p[a][None] - u[:, a][:, None, None, None] for a in range(3)]
+    Pc = cl["br"] * cl["chi"] * cl["n"] * cl["T"]
+    scale = np.abs(C).sum(ax)
+    mom = [(C * p[a]).sum(ax) for a in range(3)]
+    energy = (C * 0.5 * (xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2)).sum(ax)
+    assert np.max(np.abs(Pc * cl["X"]) / scale) > 0.1 and np.max(np.abs(Pc * cl["div"]) / scale) > 0.1
+    assert np.all(np.abs(mom[0] + Pc * cl["X"]) <= 1e-13 * scale)
+    assert np.all(np.abs(mom[1]) <= 1e-13 * scale) and np.all(np.abs(mom[2]) <= 1e-13 * scale)
+    assert np.all(np.abs(energy + Pc * cl["div"]) <= 1e-13 * scale)
+
+
 def test_mirror_symmetry_of_wall_speed():
     # u_w -> -u_w flips u_phi and q_phi and leaves n, T, q_R unchanged
     kw = dict(eta0=0.1, Kn=0.1)
