@@ -81,6 +81,37 @@ def test_collision_momentum_and_energy_moments(g, chi_model):
     assert np.all(np.abs(energy + Pc * cl["div"]) <= 1e-13 * scale)
 
 
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+@pytest.mark.parametrize("Q", [3, 5])
+def test_force_momentum_and_energy_moments(g, Q):
+    """Momentum moments of the curvature term (Secs. II.B, II.C), integrated by parts in momentum
+    space: with kappa = (A_+ - A_-)/V (1/R on the cylinder, 2/R on the sphere) the force term F
+    (entering the RHS as -F) has radial moment -kappa M_22 (cylinder) or -kappa (M_22 + M_33)/2
+    (sphere), the centrifugal pressure, and tangential moments kappa M_R2 (cylinder) or
+    kappa M_R2 / 2 and kappa M_R3 / 2 (sphere), the curvature part of the angular-momentum
+    balance; its energy moment is zero.  This holds on any nodal state, since the derivative
+    matrices are exact on the polynomials involved (stretched grid, perturbed state)."""
+    P = S.make_problem(g, 1.0, 2.0, 16, Q, Q, Q, eta0=0.2, Kn=0.05, beta=1.0, T_wall=(1.0, 1.3),
+                       u_wall=((0.2, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    f = _perturbed(P, seed=3, amp=0.1)
+    F = S.force(f, P)
+    ax = (1, 2, 3)
+    p = S.momentum_axes(P)
+    k = P.grid.kappa
+    M = lambda a, b: (f * p[a] * p[b]).sum(ax)
+    mom = [(F * p[a]).sum(ax) for a in range(3)]
+    energy = (F * 0.5 * (p[0] ** 2 + p[1] ** 2 + p[2] ** 2)).sum(ax)
+    if g == geo.CYL:
+        want = [-k * M(1, 1), k * M(0, 1), np.zeros_like(k)]
+    else:
+        want = [-0.5 * k * (M(1, 1) + M(2, 2)), 0.5 * k * M(0, 1), 0.5 * k * M(0, 2)]
+    scale = np.abs(F).sum(ax)
+    assert np.min(np.abs(want[1]) / scale) > 1e-4
+    for a in range(3):
+        assert np.all(np.abs(mom[a] - want[a]) <= 1e-13 * scale), a
+    assert np.all(np.abs(energy) <= 1e-13 * scale)
+
+
 def test_mirror_symmetry_of_wall_speed():
     # u_w -> -u_w flips u_phi and q_phi and leaves n, T, q_R unchanged
     kw = dict(eta0=0.1, Kn=0.1)
