@@ -303,6 +303,9 @@ def test_couette_profile_is_A_R_plus_B_over_R_in_the_dilute_small_Kn_limit():
     mu = model.viscosity(m["n"], m["T"], chi, P.sigma)
     ratio = (m["P01"] / (-mu * (S.d_dR(uphi, P.grid) - uphi / Rc)))[8:16]
     assert np.all(np.abs(ratio - 1) < 0.01), ratio
+    # torque balance: J1 carries no phi-momentum, so R^2 P_R2 is constant across the gap
+    R2P = (Rc ** 2 * m["P01"])[3:-3]
+    assert (R2P.max() - R2P.min()) / abs(R2P.mean()) < 0.01
 
 
 @pytest.mark.slow
@@ -352,3 +355,45 @@ def test_fourier_flow_conductivity_in_the_dilute_small_Kn_limit():
     lam = model.conductivity(m["n"], m["T"], chi, P.sigma)
     ratio = (m["q"][:, 0] / (-lam * S.d_dR(m["T"], P.grid)))[8:16]
     assert np.all(np.abs(ratio - 1) < 0.015), ratio
+
+
+# ----------------------------------------------------------------------------- convergence orders
+def _observed_orders(errors):
+    e = np.asarray(errors)
+    return np.log2(e[:-1] / e[1:])
+
+
+@pytest.mark.parametrize("upwind", [+1, -1])
+def test_weno5_flux_difference_converges_at_fifth_order(upwind):
+    """Finite-difference WENO5-JS on point values (Sec. III.A, A8 reading): the difference of the
+    reconstructed face values over h approximates the derivative to O(h^5) on a smooth profile
+    without critical points, upwind from either side."""
+    def err(N):
+        h = 1.0 / N
+        x = (np.arange(-3, N + 3) + 0.5) * h
+        g = np.exp(x) + 0.5 * np.sin(3 * x)
+        i = np.arange(3, N + 3)
+        if upwind > 0:
+            right = S.weno5(g[i - 2], g[i - 1], g[i], g[i + 1], g[i + 2])
+            left = S.weno5(g[i - 3], g[i - 2], g[i - 1], g[i], g[i + 1])
+        else:
+            right = S.weno5(g[i + 3], g[i + 2], g[i + 1], g[i], g[i - 1])
+            left = S.weno5(g[i + 2], g[i + 1], g[i], g[i - 1], g[i - 2])
+        exact = np.exp(x[i]) + 1.5 * np.cos(3 * x[i])
+        return np.max(np.abs((right - left) / h - exact))
+    orders = _observed_orders([err(N) for N in (20, 40, 80, 160)])
+    assert np.all(orders[1:] > 4.7), orders
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_radial_gradients_converge_at_fourth_order(beta):
+    """The closure's radial derivative (fourth-order central differences in the mapped coordinate,
+    one-sided five-point stencils in the two cells by each wall; Sec. III.A, A9 reading) on a
+    uniform and a stretched grid: O(h^4) in the max norm over every cell."""
+    def err(N):
+        G = geo.make_grid(geo.CYL, 1.0, 2.0, 0.01, N, beta)
+        R = G.R_c
+        exact = np.exp(R) * (np.sin(2 * R) + 2 * np.cos(2 * R))
+        return np.max(np.abs(S.d_dR(np.exp(R) * np.sin(2 * R), G) - exact))
+    orders = _observed_orders([err(N) for N in (16, 32, 64, 128)])
+    assert np.all(orders > 3.8), orders
