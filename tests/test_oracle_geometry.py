@@ -3,7 +3,7 @@ import math
 
 import numpy as np
 import pytest
-from scipy.integrate import quad
+from scipy.special import elliprd, elliprf, elliprj
 
 from oracle import geometry as geo
 
@@ -34,17 +34,21 @@ def test_lens_volume_special_cases():
 
 
 def _ellK(k):
-    return quad(lambda t: 1 / math.sqrt(1 - k * k * math.sin(t) ** 2), 0, math.pi / 2, epsabs=1e-15, epsrel=1e-14)[0]
+    """Complete elliptic integral of the first kind in Carlson's form, K = R_F(0, 1 - k^2, 1)."""
+    return float(elliprf(0.0, 1.0 - k * k, 1.0))
 
 
 def _ellE(k):
-    return quad(lambda t: math.sqrt(1 - k * k * math.sin(t) ** 2), 0, math.pi / 2, epsabs=1e-15, epsrel=1e-14)[0]
+    """Second kind: E = R_F(0, 1 - k^2, 1) - (k^2 / 3) R_D(0, 1 - k^2, 1)."""
+    m = k * k
+    return float(elliprf(0.0, 1.0 - m, 1.0) - m / 3.0 * elliprd(0.0, 1.0 - m, 1.0))
 
 
 def _ellPi(k, a2):
-    # int_0^1 dz / ((1 - a2 z^2) sqrt(1 - z^2) sqrt(1 - k^2 z^2)), z = sin t
-    return quad(lambda t: 1 / ((1 - a2 * math.sin(t) ** 2) * math.sqrt(1 - k * k * math.sin(t) ** 2)),
-                0, math.pi / 2, epsabs=1e-15, epsrel=1e-14, limit=200)[0]
+    """Third kind, int_0^{pi/2} dt / ((1 - a2 sin^2 t) sqrt(1 - k^2 sin^2 t))
+    = R_F(0, 1 - k^2, 1) + (a2 / 3) R_J(0, 1 - k^2, 1, 1 - a2)."""
+    m = k * k
+    return float(elliprf(0.0, 1.0 - m, 1.0) + a2 / 3.0 * elliprj(0.0, 1.0 - m, 1.0, 1.0 - a2))
 
 
 def paper_sphere_cylinder_volume(r, R, b):
