@@ -114,7 +114,9 @@ int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out);
 /* Many independent instances advanced together by one set of launches (the batched sweep):
  * all instances share the geometry kind, Q_R, Q_2, Q_3, the expansion orders and the
  * precision; everything else (size, radii, Kn, eta0, walls, dt) may differ.  Instance ids are
- * 0..n_instances-1 in the order given. */
+ * 0..n_instances-1 in the order given.  Errors as fdlb_create, and FDLB_EINVAL when the batch's
+ * total cells, work items or stored FM band entries exceed 2^31 - 1 (the device tables index
+ * them with 32-bit integers; about 5000 instances of 1024 stretched cells reach the band limit). */
 int fdlb_batch_create(const fdlb_params* ps, int n_instances, void* cuda_stream, fdlb_handle* out);
 
 /* Device bytes needed by fdlb_create_in for these instances. */

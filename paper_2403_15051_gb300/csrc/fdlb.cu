@@ -274,16 +274,26 @@ int plan_solver(const fdlb_params* ps, int n, Solver& S) {
     S.max_sitems = 0;
     S.max_citems = 0;
     const size_t falign = kAlign / S.tsize;
+    // cell indices, work-item counts and the FM band offsets are 32-bit in the device tables:
+    // a batch whose totals pass 2^31 - 1 (e.g. ~5000 instances of 1024 stretched cells, whose
+    // bands hold ~4.3e5 entries each) is rejected here instead of wrapping
+    const long long kIntMax = 2147483647LL;
+    long long cells = 0, sitems = 0, citems = 0;
     for (int q = 0; q < n; ++q) {
         const int N = S.setup[q].p.n_cells;
-        S.cell_off[q] = S.total_cells;
+        S.cell_off[q] = (int)cells;
         S.f_off[q] = (long long)S.f_elems;
-        S.total_cells += N;
+        cells += N;
         S.f_elems += align_up((size_t)N * S.Np, falign);
         S.band_elems += (size_t)N * S.setup[q].band.width;
-        S.max_sitems += (N / 2 + 1) * S.n3;  // tiles of at least two cells, at most n3 slices
-        S.max_citems += N + 2 * kWallParts;  // room for one-cell closure items, + the wall items
+        sitems += (long long)(N / 2 + 1) * S.n3;  // tiles of at least two cells, at most n3 slices
+        citems += (long long)N + 2 * kWallParts;  // room for one-cell closure items, + the wall items
+        if (cells > kIntMax || sitems > kIntMax || citems > kIntMax || S.band_elems > (size_t)kIntMax)
+            return FDLB_EINVAL;
     }
+    S.total_cells = (int)cells;
+    S.max_sitems = (int)sitems;
+    S.max_citems = (int)citems;
     S.active.assign(n, 1);
     S.inst_steps.assign(n, 0);
     S.last_res.assign(n, -1.0);
