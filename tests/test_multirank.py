@@ -33,7 +33,7 @@ def _rank(rank, world, port, out_dir):
     rate = bench.job_rate(1000, 5, w, ms)
     bench.barrier(w)
     buf = io.StringIO()
-    args = bench.argparse.Namespace(workload="couette_cyl_64", steps=1, warmup=0, gpus=world, no_cpu_baseline=True)
+    args = bench.argparse.Namespace(workload="couette_cyl_64", steps=2, warmup=3, gpus=world, no_cpu_baseline=True)
     with redirect_stdout(buf):
         rc = bench.run_reference(args)
     with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as fh:
@@ -53,3 +53,12 @@ def test_two_gloo_ranks(tmp_path):
     assert r1["stdout"] == ""  # the comparison arm runs on rank 0 only
     line = json.loads(r0["stdout"].strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    # the rest of the one-line contract of the comparison arm
+    assert line["metric"] == "node-velocity updates/s" and line["unit"] == "updates/s"
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None and line["dtype"] == "f64"
+    assert line["steps"] == 2 and line["warmup"] == 3 and line["ms_per_step"] > 0
+    assert line["config"]["workload"] == "couette_cyl_64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
