@@ -45,9 +45,9 @@ struct StreamSmem {
 };
 
 // Shared-memory plan of the stream kernel (byte offsets), shared with the host: the staged rows
-// of cells c0-3 .. c0+B+2, the tile's collision records, the tables (radial nodes and weights,
-// K^h with row stride nR+1, K_2 in the vector-swizzled order, K_3 with row stride n3+1, wall
-// Maxwellians), the cell geometry and the per-warp partial sums.
+// of cells c0-3 .. c0+B+2, the tile's collision records, the tables (K_2 in the vector-swizzled
+// order, then K^h with row stride kr_stride(nR), K_3 with row stride n3+1, the nodes and weights,
+// the wall Maxwellians), the cell geometry and the per-warp partial sums.
 __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize,
                                                        int mma = 0) {
     auto al = [](long long x) { return (int)((x + 15) & ~15LL); };
