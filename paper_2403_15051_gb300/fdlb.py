@@ -151,6 +151,8 @@ def make_params(d: dict) -> Params:
     p.sigma = float(d.get("sigma") or 0.0)
     p.chi_model = int(d.get("chi_model", CHI_RET_FM))
     prec = d.get("precision", "fp64")
+    if prec not in ("fp32", "fp64", FP32, FP64):
+        raise ValueError(f"precision must be 'fp32' or 'fp64', not {prec!r}")
     p.precision = FP32 if prec in ("fp32", FP32) else FP64
     p.dt = float(d.get("dt") or 0.0)
     p.cfl = float(d.get("cfl") or 0.0)

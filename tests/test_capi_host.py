@@ -136,3 +136,12 @@ def test_handle_calls_reject_a_null_handle(lib):
     assert lib.fdlb_set_wait_test(null, 0, 0) == 1
     assert lib.fdlb_clear_error(null) == 1
     assert lib.fdlb_step_kernel_times(null, ctypes.byref(d), ctypes.byref(n1), ctypes.byref(n2)) == 1
+
+
+def test_params_marshalling_rejects_an_unknown_precision():
+    d = small_case()
+    assert fdlb.make_params(dict(d, precision="fp32")).precision == fdlb.FP32
+    assert fdlb.make_params(dict(d, precision="fp64")).precision == fdlb.FP64
+    for bad in ("bf16", "f32", "FP32", 2):
+        with pytest.raises(ValueError):
+            fdlb.make_params(dict(d, precision=bad))
