@@ -108,7 +108,9 @@ typedef struct fdlb_solver* fdlb_handle;
  * cudaStream_t; NULL makes the handle create (and later destroy) a private blocking stream, so
  * that the step can be captured into a CUDA graph.  The state is left at the uniform equilibrium
  * (fdlb_init_uniform with defaults).  Errors: FDLB_EINVAL for a parameter outside the ranges
- * above or C = L/sigma < 3; FDLB_ENOGPU / FDLB_ECUDA / FDLB_ENOMEM from the device. */
+ * above, C = L/sigma < 3, or a Fischer-Methfessel band (cells x stored band width) of more than
+ * 2^31 - 1 entries; FDLB_ENOMEM when the host set-up runs out of memory; FDLB_ENOGPU /
+ * FDLB_ECUDA / FDLB_ENOMEM from the device. */
 int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out);
 
 /* Many independent instances advanced together by one set of launches (the batched sweep):
@@ -362,7 +364,8 @@ int fdlb_grid(int geometry, double R_in, double R_out, double sigma, int n_cells
               double* R_c, double* R_f, double* V, double* kappa);
 
 /* Fischer-Methfessel weights (Eq. fm, App. A) as a dense row-major n_cells x n_cells matrix:
- * nbar_i = sum_j W[i][j] n_j with n = 0 outside the computational domain. */
+ * nbar_i = sum_j W[i][j] n_j with n = 0 outside the computational domain.  FDLB_EINVAL for the
+ * arguments fdlb_grid rejects or a band of more than 2^31 - 1 entries, as fdlb_create. */
 int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n_cells,
                     double beta, double* W);
 

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
+#include <stdexcept>
 #include <vector>
 
 #include "internal.h"
@@ -228,7 +230,7 @@ Layout make_layout(const Solver& S) {
 }
 
 // Host-side plan of one handle: validation, quadrature, per-instance set-up, sizes.
-int plan_solver(const fdlb_params* ps, int n, Solver& S) {
+int plan_solver_body(const fdlb_params* ps, int n, Solver& S) {
     if (!ps || n < 1) return FDLB_EINVAL;
     const fdlb_params& p0 = ps[0];
     for (int q = 0; q < n; ++q) {
@@ -298,6 +300,18 @@ int plan_solver(const fdlb_params* ps, int n, Solver& S) {
     S.inst_steps.assign(n, 0);
     S.last_res.assign(n, -1.0);
     return FDLB_OK;
+}
+
+// The plan's host tables are std::vectors: a failed host allocation becomes FDLB_ENOMEM, so no
+// C++ exception leaves the C ABI.
+int plan_solver(const fdlb_params* ps, int n, Solver& S) {
+    try {
+        return plan_solver_body(ps, n, S);
+    } catch (const std::bad_alloc&) {
+        return FDLB_ENOMEM;
+    } catch (const std::length_error&) {
+        return FDLB_ENOMEM;
+    }
 }
 
 // Wall Maxwellians per axis and the incoming-flux normaliser of the diffuse wall.

@@ -60,7 +60,10 @@ struct FMBand {
     std::vector<int> cnt;          // stored nonzero extent of each row (a multiple of 4, <= width)
     std::vector<double> W;         // [N][width], zero padded
 };
-FMBand fm_band(int geometry, const Grid& g, double sigma);
+// Fischer-Methfessel weights of every cell over the cells its ball reaches (Eq. fm, App. A).
+// FDLB_EINVAL, before the weights are allocated, when the band would hold more than 2^31 - 1
+// entries (the device tables index it with 32-bit offsets).
+int fm_band(int geometry, const Grid& g, double sigma, FMBand& b);
 
 // ------------------------------------------------------------------ validated instance
 struct InstanceSetup {

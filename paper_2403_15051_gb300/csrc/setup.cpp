@@ -426,8 +426,8 @@ double cylinder_volume_inside(double r, double d, double Rp, const GL01& gl) {
 
 }  // namespace
 
-FMBand fm_band(int geometry, const Grid& g, double sigma) {
-    FMBand b;
+int fm_band(int geometry, const Grid& g, double sigma, FMBand& b) {
+    b = FMBand();
     const int N = g.N;
     b.lo.assign(N, 0);
     std::vector<int> hi(N, 0);
@@ -442,6 +442,7 @@ FMBand fm_band(int geometry, const Grid& g, double sigma) {
         b.width = std::max(b.width, hi[i] - lo + 1);
     }
     b.width = (b.width + 3) / 4 * 4;  // rows of 16-byte multiples (bulk copies of row extents)
+    if ((long long)N * b.width > 2147483647LL) return FDLB_EINVAL;
     b.cnt.assign(N, 0);
     for (int i = 0; i < N; ++i) b.cnt[i] = std::min(b.width, (hi[i] - b.lo[i] + 1 + 3) / 4 * 4);
     b.W.assign((size_t)N * b.width, 0.0);
@@ -463,7 +464,7 @@ FMBand fm_band(int geometry, const Grid& g, double sigma) {
             prev = next;
         }
     }
-    return b;
+    return FDLB_OK;
 }
 
 // ------------------------------------------------------------------------ validation
@@ -525,7 +526,7 @@ int build_instance(const fdlb_params& p_in, const AxisRule& aR, InstanceSetup& o
         const double cfl = p.cfl > 0.0 ? p.cfl : 0.4;
         out.dt = std::min(cfl * dr / (pmax * std::sqrt(Tmax)), 0.5 * tau);
     }
-    if (p.chi_model == FDLB_CHI_RET_FM) out.band = fm_band(p.geometry, out.grid, out.sigma);
+    if (p.chi_model == FDLB_CHI_RET_FM) return fm_band(p.geometry, out.grid, out.sigma, out.band);
     return FDLB_OK;
 }
 
@@ -583,7 +584,9 @@ int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n
     if ((geometry != FDLB_CYL && geometry != FDLB_SPH) || n_cells < 8 || !(R_out - R_in > sigma) || !(sigma > 0) || !W)
         return FDLB_EINVAL;
     fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
-    fdlb::FMBand b = fdlb::fm_band(geometry, g, sigma);
+    fdlb::FMBand b;
+    const int rc = fdlb::fm_band(geometry, g, sigma, b);
+    if (rc) return rc;
     std::memset(W, 0, sizeof(double) * (size_t)n_cells * n_cells);
     for (int i = 0; i < n_cells; ++i)
         for (int k = 0; k < b.width && b.lo[i] + k < n_cells; ++k)

@@ -145,3 +145,17 @@ def test_params_marshalling_rejects_an_unknown_precision():
     for bad in ("bf16", "f32", "FP32", 2):
         with pytest.raises(ValueError):
             fdlb.make_params(dict(d, precision=bad))
+
+
+def test_fm_band_beyond_32_bit_offsets_is_rejected_before_allocation(lib):
+    """65536 cells across a gap of three diameters: every ball reaches two thirds of the cells, so
+    the Fischer-Methfessel band would hold 2.9e9 entries (23 GB), more than the device tables'
+    32-bit offsets address.  The set-up refuses it with FDLB_EINVAL before allocating; with the
+    local chi (no band) the same grid plans normally."""
+    import ctypes
+    nb = ctypes.c_size_t()
+    base = dict(small_case(), R_in=1.0, R_out=4.0, n_cells=65536, sigma=1.0, Kn=None, Q_R=2, Q_2=2, Q_3=2)
+    p = (fdlb.Params * 1)(fdlb.make_params(dict(base, chi_model=fdlb.CHI_RET_FM)))
+    assert lib.fdlb_workspace_bytes(p, 1, ctypes.byref(nb)) == 1  # FDLB_EINVAL
+    p = (fdlb.Params * 1)(fdlb.make_params(dict(base, chi_model=fdlb.CHI_SET_LOCAL)))
+    assert lib.fdlb_workspace_bytes(p, 1, ctypes.byref(nb)) == 0 and nb.value > 0
