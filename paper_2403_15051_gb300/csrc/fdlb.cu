@@ -8,8 +8,6 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
-#include <new>
-#include <stdexcept>
 #include <vector>
 
 #include "internal.h"
@@ -302,16 +300,8 @@ int plan_solver_body(const fdlb_params* ps, int n, Solver& S) {
     return FDLB_OK;
 }
 
-// The plan's host tables are std::vectors: a failed host allocation becomes FDLB_ENOMEM, so no
-// C++ exception leaves the C ABI.
 int plan_solver(const fdlb_params* ps, int n, Solver& S) {
-    try {
-        return plan_solver_body(ps, n, S);
-    } catch (const std::bad_alloc&) {
-        return FDLB_ENOMEM;
-    } catch (const std::length_error&) {
-        return FDLB_ENOMEM;
-    }
+    return host_guard([&] { return plan_solver_body(ps, n, S); });
 }
 
 // Wall Maxwellians per axis and the incoming-flux normaliser of the diffuse wall.

@@ -3,12 +3,27 @@
 #pragma once
 
 #include <cstdint>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
 #include "../../include/fdlb.h"
 
 namespace fdlb {
+
+// Runs a host step whose tables are std::vectors and reports a failed host allocation as
+// FDLB_ENOMEM: no C++ exception leaves the C ABI.
+template <class F>
+int host_guard(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return FDLB_ENOMEM;
+    } catch (const std::length_error&) {
+        return FDLB_ENOMEM;
+    }
+}
 
 constexpr int kMaxQ = 24;          // largest quadrature order per axis
 constexpr int kMaxN = 7;           // largest equilibrium expansion order handled on the device

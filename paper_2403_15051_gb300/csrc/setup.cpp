@@ -572,26 +572,30 @@ int fdlb_grid(int geometry, double R_in, double R_out, double sigma, int n_cells
               double* R_f, double* V, double* kappa) {
     if ((geometry != FDLB_CYL && geometry != FDLB_SPH) || n_cells < 8 || !(R_out - R_in > sigma) || !(sigma > 0))
         return FDLB_EINVAL;
-    fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
-    if (R_c) std::memcpy(R_c, g.R_c.data(), n_cells * sizeof(double));
-    if (R_f) std::memcpy(R_f, g.R_f.data(), (n_cells + 1) * sizeof(double));
-    if (V) std::memcpy(V, g.V_c.data(), n_cells * sizeof(double));
-    if (kappa) std::memcpy(kappa, g.kappa.data(), n_cells * sizeof(double));
-    return FDLB_OK;
+    return fdlb::host_guard([&] {
+        fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
+        if (R_c) std::memcpy(R_c, g.R_c.data(), n_cells * sizeof(double));
+        if (R_f) std::memcpy(R_f, g.R_f.data(), (n_cells + 1) * sizeof(double));
+        if (V) std::memcpy(V, g.V_c.data(), n_cells * sizeof(double));
+        if (kappa) std::memcpy(kappa, g.kappa.data(), n_cells * sizeof(double));
+        return FDLB_OK;
+    });
 }
 
 int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n_cells, double beta, double* W) {
     if ((geometry != FDLB_CYL && geometry != FDLB_SPH) || n_cells < 8 || !(R_out - R_in > sigma) || !(sigma > 0) || !W)
         return FDLB_EINVAL;
-    fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
-    fdlb::FMBand b;
-    const int rc = fdlb::fm_band(geometry, g, sigma, b);
-    if (rc) return rc;
-    std::memset(W, 0, sizeof(double) * (size_t)n_cells * n_cells);
-    for (int i = 0; i < n_cells; ++i)
-        for (int k = 0; k < b.width && b.lo[i] + k < n_cells; ++k)
-            W[(size_t)i * n_cells + b.lo[i] + k] = b.W[(size_t)i * b.width + k];
-    return FDLB_OK;
+    return fdlb::host_guard([&] {
+        fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
+        fdlb::FMBand b;
+        const int rc = fdlb::fm_band(geometry, g, sigma, b);
+        if (rc) return rc;
+        std::memset(W, 0, sizeof(double) * (size_t)n_cells * n_cells);
+        for (int i = 0; i < n_cells; ++i)
+            for (int k = 0; k < b.width && b.lo[i] + k < n_cells; ++k)
+                W[(size_t)i * n_cells + b.lo[i] + k] = b.W[(size_t)i * b.width + k];
+        return FDLB_OK;
+    });
 }
 
 }  // extern "C"
