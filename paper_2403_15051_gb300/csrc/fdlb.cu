@@ -228,7 +228,7 @@ Layout make_layout(const Solver& S) {
 }
 
 // Host-side plan of one handle: validation, quadrature, per-instance set-up, sizes.
-int plan_solver_body(const fdlb_params* ps, int n, Solver& S) {
+int plan_solver(const fdlb_params* ps, int n, Solver& S) try {
     if (!ps || n < 1) return FDLB_EINVAL;
     const fdlb_params& p0 = ps[0];
     for (int q = 0; q < n; ++q) {
@@ -298,11 +298,8 @@ int plan_solver_body(const fdlb_params* ps, int n, Solver& S) {
     S.inst_steps.assign(n, 0);
     S.last_res.assign(n, -1.0);
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int plan_solver(const fdlb_params* ps, int n, Solver& S) {
-    return host_guard([&] { return plan_solver_body(ps, n, S); });
-}
 
 // Wall Maxwellians per axis and the incoming-flux normaliser of the diffuse wall.
 void wall_tables(const Solver& S, int q, double* out, double* den) {
@@ -1000,13 +997,13 @@ static Solver* SOL(fdlb_handle h) { return reinterpret_cast<Solver*>(h); }
 
 extern "C" {
 
-int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out) {
+int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out) try {
     return fdlb::solver_create(p, 1, cuda_stream, nullptr, 0, out);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_batch_create(const fdlb_params* ps, int n_instances, void* cuda_stream, fdlb_handle* out) {
+int fdlb_batch_create(const fdlb_params* ps, int n_instances, void* cuda_stream, fdlb_handle* out) try {
     return fdlb::solver_create(ps, n_instances, cuda_stream, nullptr, 0, out);
-}
+} FDLB_HOST_CATCH
 
 int fdlb_workspace_bytes(const fdlb_params* ps, int n_instances, size_t* bytes) {
     if (!bytes) return FDLB_EINVAL;
@@ -1018,10 +1015,10 @@ int fdlb_workspace_bytes(const fdlb_params* ps, int n_instances, size_t* bytes) 
 }
 
 int fdlb_create_in(const fdlb_params* ps, int n_instances, void* cuda_stream, void* workspace, size_t workspace_bytes,
-                   fdlb_handle* out) {
+                   fdlb_handle* out) try {
     if (!workspace) return FDLB_EINVAL;
     return fdlb::solver_create(ps, n_instances, cuda_stream, workspace, workspace_bytes, out);
-}
+} FDLB_HOST_CATCH
 
 void fdlb_destroy(fdlb_handle h) {
     Solver* S = SOL(h);
@@ -1036,7 +1033,7 @@ void fdlb_destroy(fdlb_handle h) {
     delete S;
 }
 
-int fdlb_set_wall(fdlb_handle h, int instance, int side, double T_w, double u_tangential) {
+int fdlb_set_wall(fdlb_handle h, int instance, int side, double T_w, double u_tangential) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || (side != 0 && side != 1)) return FDLB_EINVAL;
     if (!(T_w > 0.0) || !std::isfinite(u_tangential)) return FDLB_EINVAL;
@@ -1054,9 +1051,9 @@ int fdlb_set_wall(fdlb_handle h, int instance, int side, double T_w, double u_ta
                               cudaMemcpyHostToDevice, S->stream));
     FDLB_CUDA(cudaStreamSynchronize(S->stream));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_init_uniform(fdlb_handle h, int instance, double n0, double T0) {
+int fdlb_init_uniform(fdlb_handle h, int instance, double n0, double T0) try {
     Solver* S = SOL(h);
     if (!S || instance >= S->n_inst) return FDLB_EINVAL;
     if (instance < 0) {
@@ -1073,10 +1070,10 @@ int fdlb_init_uniform(fdlb_handle h, int instance, double n0, double T0) {
     std::vector<double> n(N, nn), u(N, 0.0), T(N, TT), q(N, 0.0), f;
     fdlb::seed_state(*S, instance, n, u, T, q, f);
     return fdlb::upload_state(*S, instance, f.data());
-}
+} FDLB_HOST_CATCH
 
 int fdlb_init_from_moments(fdlb_handle h, int instance, const double* n, const double* u2, const double* T,
-                           const double* qR, int n_points) {
+                           const double* qR, int n_points) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || n_points < 2 || !n || !u2 || !T || !qR) return FDLB_EINVAL;
     for (int k = 0; k < n_points; ++k)
@@ -1096,35 +1093,35 @@ int fdlb_init_from_moments(fdlb_handle h, int instance, const double* n, const d
     }
     fdlb::seed_state(*S, instance, cn, cu, cT, cq, f);
     return fdlb::upload_state(*S, instance, f.data());
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_f(fdlb_handle h, int instance, const double* f_host) {
+int fdlb_set_f(fdlb_handle h, int instance, const double* f_host) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !f_host) return FDLB_EINVAL;
     return fdlb::upload_state(*S, instance, f_host);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_f(fdlb_handle h, int instance, double* f_host) {
+int fdlb_get_f(fdlb_handle h, int instance, double* f_host) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !f_host) return FDLB_EINVAL;
     return fdlb::download_buf(*S, instance, 0, f_host);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_step(fdlb_handle h, int64_t n_steps) {
+int fdlb_step(fdlb_handle h, int64_t n_steps) try {
     Solver* S = SOL(h);
     if (!S || n_steps < 0) return FDLB_EINVAL;
     return fdlb::do_steps(*S, n_steps);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) {
+int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !L_host) return FDLB_EINVAL;
     int rc = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1);
     if (rc) return rc;
     return fdlb::download_buf(*S, instance, 1, L_host);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) {
+int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
     // n, u, T, q, P_12 come from the FP64 raw sums of the current state alone (the closure's chi
@@ -1141,9 +1138,9 @@ int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) {
                                 S->stream));
     if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, double* tau, double* n_wall2) {
+int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, double* tau, double* n_wall2) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst) return FDLB_EINVAL;
     // a right-hand-side evaluation refreshes the closure records and the wall densities
@@ -1186,9 +1183,9 @@ int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, dou
         n_wall2[1] = nw[1];
     }
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double* residual, int64_t* step) {
+int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double* residual, int64_t* step) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst) return FDLB_EINVAL;
     fdlb::launch_residual(S->sums[0], S->M.slices, S->inst_d, S->geo, S->rprev, S->rout, S->n_inst, 0, S->stream);
@@ -1203,10 +1200,10 @@ int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double
     if (errflag) return FDLB_ETIMEOUT;
     if (ro[(size_t)instance * 10 + 9] != 0.0) return FDLB_ENAN;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
 int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
-                       int64_t* steps_taken, double* residual) {
+                       int64_t* steps_taken, double* residual) try {
     Solver* S = SOL(h);
     if (!S || !(tol > 0.0) || max_steps < 1 || check_every < 1) return FDLB_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
@@ -1279,9 +1276,9 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
         if (residual) residual[q] = S->last_res[q];
     }
     return status;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) {
+int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
     const fdlb::InstanceSetup& I = S->setup[instance];
@@ -1297,11 +1294,11 @@ int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) {
     out->precision = S->precision;
     out->step = S->inst_steps[instance];
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
 static const char kMagic[8] = {'F', 'D', 'L', 'B', 'C', 'K', 'P', '2'};
 
-int fdlb_save(fdlb_handle h, const char* path) {
+int fdlb_save(fdlb_handle h, const char* path) try {
     Solver* S = SOL(h);
     if (!S || !path) return FDLB_EINVAL;
     FILE* fp = std::fopen(path, "wb");
@@ -1337,9 +1334,9 @@ int fdlb_save(fdlb_handle h, const char* path) {
     }
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? FDLB_OK : FDLB_EIO;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_load(fdlb_handle h, const char* path) {
+int fdlb_load(fdlb_handle h, const char* path) try {
     Solver* S = SOL(h);
     if (!S || !path) return FDLB_EINVAL;
     FILE* fp = std::fopen(path, "rb");
@@ -1413,7 +1410,7 @@ int fdlb_load(fdlb_handle h, const char* path) {
     else
         fdlb::launch_dens_from_sums<double>(S->sums[0], (double*)S->dens[0], nd, S->stream);
     return fdlb::cuda_status(cudaGetLastError());
-}
+} FDLB_HOST_CATCH
 
 const char* fdlb_error_string(int code) {
     switch (code) {
@@ -1430,13 +1427,13 @@ const char* fdlb_error_string(int code) {
     }
 }
 
-int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads) {
+int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads) try {
     Solver* S = SOL(h);
     if (!S || cells_per_tile < 0 || slice_k < 0 || threads < 0) return FDLB_EINVAL;
     return fdlb::configure_tiling(*S, cells_per_tile, slice_k, threads);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads) {
+int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     // candidates: tile cells x slice width x thread cap; each timed over 3 RHS evaluations
@@ -1480,18 +1477,18 @@ int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads
     if (slice_k) *slice_k = S->KS;
     if (threads) *threads = S->threads;
     return rc;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) {
+int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     S->tensor = enable ? 1 : 0;
     const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
     if (in_use) *in_use = S->mma_on;
     return rc;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use) {
+int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     if (enable < 0) {  // query only
@@ -1502,9 +1499,9 @@ int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use) {
     const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
     if (in_use) *in_use = S->fused_on;
     return rc;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra) {
+int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra) try {
     Solver* S = SOL(h);
     if (!S || tx_extra_bytes < 0 || tx_extra_bytes > 65536 || barrier_extra < 0 || barrier_extra > 65536) return FDLB_EINVAL;
     S->test_tx_extra = tx_extra_bytes;
@@ -1514,17 +1511,17 @@ int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra) {
         S->gexec = nullptr;
     }
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_clear_error(fdlb_handle h) {
+int fdlb_clear_error(fdlb_handle h) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     FDLB_CUDA(cudaMemsetAsync(S->err, 0, sizeof(int), S->stream));
     FDLB_CUDA(cudaStreamSynchronize(S->stream));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_programmatic_launch(fdlb_handle h, int enable) {
+int fdlb_set_programmatic_launch(fdlb_handle h, int enable) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     S->programmatic = enable ? 1 : 0;
@@ -1533,9 +1530,9 @@ int fdlb_set_programmatic_launch(fdlb_handle h, int enable) {
         S->gexec = nullptr;
     }
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_closure_cells(fdlb_handle h, int cells) {
+int fdlb_set_closure_cells(fdlb_handle h, int cells) try {
     Solver* S = SOL(h);
     if (!S || cells < 1 || cells > fdlb::kClosureCells) return FDLB_EINVAL;
     S->closure_cells = cells;
@@ -1544,14 +1541,14 @@ int fdlb_set_closure_cells(fdlb_handle h, int cells) {
         S->gexec = nullptr;
     }
     return fdlb::upload_items(*S);
-}
+} FDLB_HOST_CATCH
 
 int64_t fdlb_launch_count(fdlb_handle h) {
     Solver* S = SOL(h);
     return S ? S->last_launches : -1;
 }
 
-int fdlb_set_graph_steps(fdlb_handle h, int steps) {
+int fdlb_set_graph_steps(fdlb_handle h, int steps) try {
     Solver* S = SOL(h);
     if (!S || steps < 1 || steps > 1000) return FDLB_EINVAL;
     if (steps != S->graph_steps && S->gexec) {
@@ -1560,18 +1557,18 @@ int fdlb_set_graph_steps(fdlb_handle h, int steps) {
     }
     S->graph_steps = steps;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_kernel_timing(fdlb_handle h, int on) {
+int fdlb_set_kernel_timing(fdlb_handle h, int on) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     if (on && !S->tev[0])
         for (cudaEvent_t& e : S->tev) FDLB_CUDA(cudaEventCreate(&e));
     S->timing = on != 0;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, double* closure_ms, int64_t* n_closure) {
+int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, double* closure_ms, int64_t* n_closure) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     if (stream_ms) *stream_ms = S->t_stream_ms;
@@ -1581,9 +1578,9 @@ int fdlb_kernel_times(fdlb_handle h, double* stream_ms, int64_t* n_stream, doubl
     S->t_stream_ms = S->t_closure_ms = 0.0;
     S->n_stream_t = S->n_closure_t = 0;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_step_kernel_times(fdlb_handle h, double* ms, int64_t* launches, int64_t* steps) {
+int fdlb_step_kernel_times(fdlb_handle h, double* ms, int64_t* launches, int64_t* steps) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     if (ms) *ms = S->t_step_ms;
@@ -1592,16 +1589,16 @@ int fdlb_step_kernel_times(fdlb_handle h, double* ms, int64_t* launches, int64_t
     S->t_step_ms = 0.0;
     S->n_step_t = S->n_step_steps = 0;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_stream(fdlb_handle h, void** stream) {
+int fdlb_get_stream(fdlb_handle h, void** stream) try {
     Solver* S = SOL(h);
     if (!S || !stream) return FDLB_EINVAL;
     *stream = (void*)S->stream;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device) {
+int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !src) return FDLB_EINVAL;
     const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
@@ -1609,9 +1606,9 @@ int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_devi
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
     S->inst_steps[instance] = 0;
     return fdlb::launch_moments_all(*S, 0);
-}
+} FDLB_HOST_CATCH
 
-int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device) {
+int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !dst) return FDLB_EINVAL;
     const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
@@ -1619,6 +1616,6 @@ int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device) {
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
     if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
 }  // extern "C"

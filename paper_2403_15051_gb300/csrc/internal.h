@@ -10,20 +10,19 @@
 
 #include "../../include/fdlb.h"
 
+// Handlers of the function-try-blocks around the C-ABI entry points: the host side keeps its
+// tables in std::vectors, and a failed host allocation is reported as FDLB_ENOMEM, so no C++
+// exception leaves the C ABI.
+#define FDLB_HOST_CATCH                         \
+    catch (const std::bad_alloc&) {             \
+        return FDLB_ENOMEM;                     \
+    }                                           \
+    catch (const std::length_error&) {          \
+        return FDLB_ENOMEM;                     \
+    }
+
 namespace fdlb {
 
-// Runs a host step whose tables are std::vectors and reports a failed host allocation as
-// FDLB_ENOMEM: no C++ exception leaves the C ABI.
-template <class F>
-int host_guard(F&& f) {
-    try {
-        return f();
-    } catch (const std::bad_alloc&) {
-        return FDLB_ENOMEM;
-    } catch (const std::length_error&) {
-        return FDLB_ENOMEM;
-    }
-}
 
 constexpr int kMaxQ = 24;          // largest quadrature order per axis
 constexpr int kMaxN = 7;           // largest equilibrium expansion order handled on the device

@@ -317,7 +317,7 @@ using fdlb::NNet;
 extern "C" {
 
 int fdlb_nn_create(int width, int modes, int layers, int hidden, int n_points, int max_batch, void* cuda_stream,
-                   fdlb_nn_handle* out) {
+                   fdlb_nn_handle* out) try {
     if (!out || width < 1 || width > 512 || modes < 1 || 2 * modes > n_points || layers < 1 || layers > 16 ||
         hidden < 1 || n_points < 8 || n_points > 4096 || max_batch < 1 || max_batch > 4096)
         return FDLB_EINVAL;
@@ -402,7 +402,7 @@ int fdlb_nn_create(int width, int modes, int layers, int hidden, int n_points, i
     }
     *out = reinterpret_cast<fdlb_nn_handle>(n);
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
 void fdlb_nn_destroy(fdlb_nn_handle h) {
     NNet* n = reinterpret_cast<NNet*>(h);
@@ -413,14 +413,14 @@ void fdlb_nn_destroy(fdlb_nn_handle h) {
     delete n;
 }
 
-int fdlb_nn_num_params(fdlb_nn_handle h, int64_t* count) {
+int fdlb_nn_num_params(fdlb_nn_handle h, int64_t* count) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !count) return FDLB_EINVAL;
     *count = n->n_params;
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_nn_set_params(fdlb_nn_handle h, const float* theta) {
+int fdlb_nn_set_params(fdlb_nn_handle h, const float* theta) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !theta) return FDLB_EINVAL;
     if (cudaMemcpyAsync(n->w, theta, n->n_params * 4, cudaMemcpyHostToDevice, n->stream) != cudaSuccess)
@@ -430,9 +430,9 @@ int fdlb_nn_set_params(fdlb_nn_handle h, const float* theta) {
     fdlb::to_bf16_kernel<<<fdlb::grid_for(n->n_params), 256, 0, n->stream>>>(n->w, n->wb, n->n_params);
     n->step = 0;
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_nn_init_params(fdlb_nn_handle h, uint64_t seed) {
+int fdlb_nn_init_params(fdlb_nn_handle h, uint64_t seed) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n) return FDLB_EINVAL;
     // seeded initialisation (splitmix64 uniforms): weight matrices U(-1, 1)/sqrt(fan_in), spectral
@@ -459,17 +459,17 @@ int fdlb_nn_init_params(fdlb_nn_handle h, uint64_t seed) {
     fill(n->o_p1w, (long long)W * n->H, -1.0 / std::sqrt((double)W), 1.0 / std::sqrt((double)W));
     fill(n->o_p2w, (long long)n->H * fdlb::kCout, -1.0 / std::sqrt((double)n->H), 1.0 / std::sqrt((double)n->H));
     return fdlb_nn_set_params(h, t.data());
-}
+} FDLB_HOST_CATCH
 
-int fdlb_nn_get_params(fdlb_nn_handle h, float* theta) {
+int fdlb_nn_get_params(fdlb_nn_handle h, float* theta) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !theta) return FDLB_EINVAL;
     if (cudaMemcpyAsync(theta, n->w, n->n_params * 4, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess)
         return FDLB_ECUDA;
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_nn_forward(fdlb_nn_handle h, const float* raw_params, int batch, float* out_host) {
+int fdlb_nn_forward(fdlb_nn_handle h, const float* raw_params, int batch, float* out_host) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !raw_params || !out_host || batch < 1 || batch > n->Bmax) return FDLB_EINVAL;
     int rc = fdlb::upload_inputs(*n, raw_params, nullptr, batch);
@@ -479,10 +479,10 @@ int fdlb_nn_forward(fdlb_nn_handle h, const float* raw_params, int batch, float*
         cudaSuccess)
         return FDLB_ECUDA;
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
-}
+} FDLB_HOST_CATCH
 
 int fdlb_nn_loss_grad(fdlb_nn_handle h, const float* raw_params, const float* targets, int batch, float* loss,
-                      float* grad_host) {
+                      float* grad_host) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !raw_params || !targets || batch < 1 || batch > n->Bmax) return FDLB_EINVAL;
     int rc = fdlb::upload_inputs(*n, raw_params, targets, batch);
@@ -497,10 +497,10 @@ int fdlb_nn_loss_grad(fdlb_nn_handle h, const float* raw_params, const float* ta
         cudaMemcpyAsync(grad_host, n->g, n->n_params * 4, cudaMemcpyDeviceToHost, n->stream) != cudaSuccess)
         return FDLB_ECUDA;
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
-}
+} FDLB_HOST_CATCH
 
 int fdlb_nn_train_step(fdlb_nn_handle h, const float* raw_params, const float* targets, int batch, float lr,
-                       float* loss) {
+                       float* loss) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !(lr > 0.f)) return FDLB_EINVAL;
     int rc = fdlb_nn_loss_grad(h, raw_params, targets, batch, loss, nullptr);
@@ -510,9 +510,9 @@ int fdlb_nn_train_step(fdlb_nn_handle h, const float* raw_params, const float* t
     fdlb::adam_kernel<<<fdlb::grid_for(n->n_params), 256, 0, n->stream>>>(n->w, n->g, n->m1, n->m2, n->wb, n->n_params,
                                                                          lr, c1, c2);
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const float* raw_params) {
+int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const float* raw_params) try {
     NNet* n = reinterpret_cast<NNet*>(h);
     if (!n || !solver || !raw_params) return FDLB_EINVAL;
     fdlb_info info;
@@ -548,6 +548,6 @@ int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const
         qR[x] *= lam;
     }
     return fdlb_init_from_moments(solver, instance, nn.data(), u2.data(), T.data(), qR.data(), n->P);
-}
+} FDLB_HOST_CATCH
 
 }  // extern "C"

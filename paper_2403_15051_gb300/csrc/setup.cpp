@@ -535,16 +535,16 @@ int build_instance(const fdlb_params& p_in, const AxisRule& aR, InstanceSetup& o
 // ------------------------------------------------------------------------ host-only ABI
 extern "C" {
 
-int fdlb_quadrature(int kind, int Q, double* nodes, double* weights) {
+int fdlb_quadrature(int kind, int Q, double* nodes, double* weights) try {
     if (Q < 1 || Q > 128 || !nodes || !weights) return FDLB_EINVAL;
     if (kind != FDLB_QUAD_FULL && kind != FDLB_QUAD_HALF) return FDLB_EINVAL;
     fdlb::AxisRule ax = fdlb::make_axis(Q, kind == FDLB_QUAD_HALF);
     std::memcpy(nodes, ax.p.data(), ax.p.size() * sizeof(double));
     std::memcpy(weights, ax.w.data(), ax.w.size() * sizeof(double));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
-int fdlb_derivative_matrix(int kind, int Q, double* K) {
+int fdlb_derivative_matrix(int kind, int Q, double* K) try {
     if (Q < 1 || Q > 128 || !K) return FDLB_EINVAL;
     std::vector<double> M;
     if (kind == FDLB_QUAD_HALF) {
@@ -556,7 +556,7 @@ int fdlb_derivative_matrix(int kind, int Q, double* K) {
     }
     std::memcpy(K, M.data(), M.size() * sizeof(double));
     return FDLB_OK;
-}
+} FDLB_HOST_CATCH
 
 int fdlb_physical_parameters(double Kn, double eta0, double L, double* C, double* sigma, double* n0) {
     if (!(Kn > 0.0) || !(eta0 > 0.0 && eta0 < 0.5) || !(L > 0.0)) return FDLB_EINVAL;
@@ -569,33 +569,29 @@ int fdlb_physical_parameters(double Kn, double eta0, double L, double* C, double
 }
 
 int fdlb_grid(int geometry, double R_in, double R_out, double sigma, int n_cells, double beta, double* R_c,
-              double* R_f, double* V, double* kappa) {
+              double* R_f, double* V, double* kappa) try {
     if ((geometry != FDLB_CYL && geometry != FDLB_SPH) || n_cells < 8 || !(R_out - R_in > sigma) || !(sigma > 0))
         return FDLB_EINVAL;
-    return fdlb::host_guard([&] {
-        fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
-        if (R_c) std::memcpy(R_c, g.R_c.data(), n_cells * sizeof(double));
-        if (R_f) std::memcpy(R_f, g.R_f.data(), (n_cells + 1) * sizeof(double));
-        if (V) std::memcpy(V, g.V_c.data(), n_cells * sizeof(double));
-        if (kappa) std::memcpy(kappa, g.kappa.data(), n_cells * sizeof(double));
-        return FDLB_OK;
-    });
-}
+    fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
+    if (R_c) std::memcpy(R_c, g.R_c.data(), n_cells * sizeof(double));
+    if (R_f) std::memcpy(R_f, g.R_f.data(), (n_cells + 1) * sizeof(double));
+    if (V) std::memcpy(V, g.V_c.data(), n_cells * sizeof(double));
+    if (kappa) std::memcpy(kappa, g.kappa.data(), n_cells * sizeof(double));
+    return FDLB_OK;
+} FDLB_HOST_CATCH
 
-int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n_cells, double beta, double* W) {
+int fdlb_fm_weights(int geometry, double R_in, double R_out, double sigma, int n_cells, double beta, double* W) try {
     if ((geometry != FDLB_CYL && geometry != FDLB_SPH) || n_cells < 8 || !(R_out - R_in > sigma) || !(sigma > 0) || !W)
         return FDLB_EINVAL;
-    return fdlb::host_guard([&] {
-        fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
-        fdlb::FMBand b;
-        const int rc = fdlb::fm_band(geometry, g, sigma, b);
-        if (rc) return rc;
-        std::memset(W, 0, sizeof(double) * (size_t)n_cells * n_cells);
-        for (int i = 0; i < n_cells; ++i)
-            for (int k = 0; k < b.width && b.lo[i] + k < n_cells; ++k)
-                W[(size_t)i * n_cells + b.lo[i] + k] = b.W[(size_t)i * b.width + k];
-        return FDLB_OK;
-    });
-}
+    fdlb::Grid g = fdlb::make_grid(geometry, R_in, R_out, sigma, n_cells, beta);
+    fdlb::FMBand b;
+    const int rc = fdlb::fm_band(geometry, g, sigma, b);
+    if (rc) return rc;
+    std::memset(W, 0, sizeof(double) * (size_t)n_cells * n_cells);
+    for (int i = 0; i < n_cells; ++i)
+        for (int k = 0; k < b.width && b.lo[i] + k < n_cells; ++k)
+            W[(size_t)i * n_cells + b.lo[i] + k] = b.W[(size_t)i * b.width + k];
+    return FDLB_OK;
+} FDLB_HOST_CATCH
 
 }  // extern "C"
