@@ -397,3 +397,21 @@ def test_radial_gradients_converge_at_fourth_order(beta):
         return np.max(np.abs(S.d_dR(np.exp(R) * np.sin(2 * R), G) - exact))
     orders = _observed_orders([err(N) for N in (16, 32, 64, 128)])
     assert np.all(orders > 3.8), orders
+
+
+@pytest.mark.parametrize("g,horizon", [(geo.CYL, 10), (geo.SPH, 20)])
+def test_ssp_rk3_converges_at_third_order_in_time(g, horizon):
+    """The time integrator (Sec. III, SSP-RK3) on a smooth transient of the semi-discrete system:
+    halving the step divides the difference between successive solutions at a fixed time by 2^3.
+    Mass conservation and steady states do not see the stage coefficients; this does."""
+    import dataclasses
+    P0 = S.make_problem(g, 1.0, 2.0, 16, 3, 3, 3, eta0=0.1, Kn=0.3, T_wall=(1.0, 1.2),
+                        u_wall=((0.1, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    R = P0.grid.R_c
+    x = (R - R[0]) / (R[-1] - R[0])
+    uphi = 0.05 * np.sin(np.pi * x) if g == geo.CYL else np.zeros_like(x)
+    f0 = S.shakhov_seed(P0, P0.n0 * (1 + 0.05 * np.cos(np.pi * x)), uphi, 1 + 0.1 * x, 0.01 * np.sin(np.pi * x))
+    f = {k: S.run(f0, dataclasses.replace(P0, dt=P0.dt / k), horizon * k) for k in (1, 2, 4, 8)}
+    e = [np.max(np.abs(f[k] - f[2 * k])) for k in (1, 2, 4)]
+    ratios = [e[0] / e[1], e[1] / e[2]]
+    assert all(6.0 < r < 11.0 for r in ratios), ratios
