@@ -415,3 +415,25 @@ def test_ssp_rk3_converges_at_third_order_in_time(g, horizon):
     e = [np.max(np.abs(f[k] - f[2 * k])) for k in (1, 2, 4)]
     ratios = [e[0] / e[1], e[1] / e[2]]
     assert all(6.0 < r < 11.0 for r in ratios), ratios
+
+
+@pytest.mark.slow
+def test_dense_fourier_flow_radial_momentum_balance():
+    """Steady dense-gas Fourier flow between cylinders (eta0 = 0.2, RET-FM chi): the gas is at rest,
+    so the first moment of the kinetic equation reduces to dP_RR/dR + (P_RR - P_22)/R = -P_c X,
+    the kinetic pressure gradient and the curvature of the stress balanced by the momentum that J1
+    transfers (P_c = b rho chi n T, X = d ln(n^2 chi T)/dR; Eq. j1, Sec. II.B).  Away from the
+    Knudsen layers the balance holds to 3% of P_c X (discretisation); a gradient term taken
+    without the n^2, chi or T factor breaks it by 60% or more."""
+    P = S.make_problem(geo.CYL, 1.0, 2.0, 24, 4, 4, 4, eta0=0.2, Kn=0.1, T_wall=(1.2, 0.8))
+    f = S.run(S.uniform_state(P), P, int(round(12.0 / P.dt)))
+    n, u, T, _, M2 = S.macroscopic(S.raw_sums(f, P))
+    P_RR = M2[:, 0, 0] - n * u[:, 0] ** 2
+    P_22 = M2[:, 1, 1] - n * u[:, 1] ** 2
+    chi = model.chi_set(model.eta_of_n(P.W @ n, P.sigma))
+    Pc = model.b_rho(n, P.sigma) * chi * n * T
+    X = S.d_dR(np.log(n * n * chi * T), P.grid)
+    balance = S.d_dR(P_RR, P.grid) + (P_RR - P_22) / P.grid.R_c + Pc * X
+    scale = np.max(np.abs(Pc * X)[3:-3])
+    assert scale > 0.1 * np.max(np.abs(S.d_dR(P_RR, P.grid))[3:-3])
+    assert np.max(np.abs(balance[3:-3])) < 0.03 * scale
