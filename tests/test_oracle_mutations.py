@@ -17,6 +17,7 @@ from . import test_oracle_equilibrium as t_eq
 from . import test_oracle_geometry as t_geo
 from . import test_oracle_kmatrix as t_km
 from . import test_oracle_model as t_model
+from . import test_oracle_nn as t_nn
 from . import test_oracle_quadrature as t_quad
 from . import test_oracle_solver as t_solver
 
@@ -104,6 +105,15 @@ CASES = [
     # closure: the gradient of J1's momentum transfer (Eq. j1), seen by the dense-gas momentum balance
     ("J1 gradient without chi", "solver", "X = d_dR(np.log(n * n * chi * T), G)", "X = d_dR(np.log(n * n * T), G)",
      t_solver, "S", "test_dense_fourier_flow_radial_momentum_balance", ()),
+    # warm-start network (test infrastructure for the learned warm start)
+    ("GELU derivative factor", "nn", "x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)",
+     "x * np.exp(-0.5 * x * x) / math.sqrt(math.pi)", t_nn, "nn", "test_gelu_definition", ()),
+    ("spectral gradient sign", "nn",
+     'g[f"r_im{l}"] = np.einsum("bki,bko->kio", re, dyim) - np.einsum("bki,bko->kio", im, dyre)',
+     'g[f"r_im{l}"] = np.einsum("bki,bko->kio", re, dyim) + np.einsum("bki,bko->kio", im, dyre)',
+     t_nn, "nn", "test_backward_matches_central_differences", ()),
+    ("inverse DFT weight", "nn", "c = np.where(k == 0, 1.0, 2.0)", "c = np.where(k == 0, 2.0, 2.0)",
+     t_nn, "nn", "test_dft_pair_matches_numpy_fft", ()),
     # quadrature (Sec. III.A)
     ("Hermite Jacobi off-diagonal", "quadrature", "J[n, n - 1] = J[n - 1, n] = math.sqrt(n)",
      "J[n, n - 1] = J[n - 1, n] = math.sqrt(n + 1)", t_quad, "quad", "test_full_range_exact_on_gaussian_moments", (4,)),
