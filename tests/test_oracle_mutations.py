@@ -80,6 +80,8 @@ CASES = [
      t_geo, "geo", "test_grid_volumes_and_curvature", (SPH,)),
     ("lens volume coefficient", "geometry", "(dd * dd + 2 * dd * b - 3 * b * b", "(dd * dd + 2 * dd * b - 2 * b * b",
      t_geo, "geo", "test_lens_volume_special_cases", ()),
+    ("circle-circle lens term", "geometry", "- 0.5 * np.sqrt(np.maximum(k, 0.0))", "- 0.25 * np.sqrt(np.maximum(k, 0.0))",
+     t_geo, "geo", "test_ball_cylinder_volume_matches_appendix_A_formula", (0.3, 1.0, 1.1)),
     # transport model (Sec. II)
     ("Carnahan-Starling power", "model", "(2.0 - eta) / (2.0 * (1.0 - eta) ** 3)", "(2.0 - eta) / (2.0 * (1.0 - eta) ** 2)",
      t_model, "model", "test_chi_matches_carnahan_starling_equation_of_state", ()),
@@ -115,6 +117,11 @@ CASES = [
     ("inverse DFT weight", "nn", "c = np.where(k == 0, 1.0, 2.0)", "c = np.where(k == 0, 2.0, 2.0)",
      t_nn, "nn", "test_dft_pair_matches_numpy_fft", ()),
     # quadrature (Sec. III.A)
+    ("half-range weights scale", "quadrature", "lam = beta[0] * V[0, :] ** 2", "lam = V[0, :] ** 2",
+     t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),
+    ("half-range polynomial recurrence", "quadrature", "out[l + 1] = ((x - alpha[l]) * out[l] - b[l] * out[l - 1]) / b[l + 1]",
+     "out[l + 1] = ((x - alpha[l]) * out[l] + b[l] * out[l - 1]) / b[l + 1]", t_quad, "quad",
+     "test_half_polynomials_orthonormal_and_roots", (5,)),
     ("Hermite Jacobi off-diagonal", "quadrature", "J[n, n - 1] = J[n - 1, n] = math.sqrt(n)",
      "J[n, n - 1] = J[n - 1, n] = math.sqrt(n + 1)", t_quad, "quad", "test_full_range_exact_on_gaussian_moments", (4,)),
 ]
