@@ -66,6 +66,13 @@ CASES = [
      t_solver, "S", "test_weno5_flux_difference_converges_at_fifth_order", (-1,)),
     ("ghost extrapolation coefficient", "solver", "ext[1] = 4 * v[0] - 6 * v[1] + 4 * v[2] - v[3]",
      "ext[1] = 4 * v[0] - 6 * v[1] + 3 * v[2] - v[3]", t_solver, "S", "test_uniform_equilibrium_is_steady", (CYL, 0.0)),
+    # diffuse walls (Sec. IV)
+    ("wall temperatures swapped", "solver", "Tw, uw = P.T_wall[side], P.u_wall[side]",
+     "Tw, uw = P.T_wall[1 - side], P.u_wall[side]", t_solver, "S",
+     "test_diffuse_walls_pull_the_adjacent_gas_toward_their_state", (CYL,)),
+    ("wall speed dropped", "solver", "g2 = eq.g_full(P.p2, P.w2, P.N2, uw, Tw)",
+     "g2 = eq.g_full(P.p2, P.w2, P.N2, 0.0, Tw)", t_solver, "S",
+     "test_diffuse_walls_pull_the_adjacent_gas_toward_their_state", (CYL,)),
     # closure gradients
     ("one-sided stencil coefficient", "solver", "d[1] = (-3.0 * phi[0] - 10.0 * phi[1]",
      "d[1] = (-3.0 * phi[0] - 11.0 * phi[1]", t_solver, "S", "test_radial_gradients_converge_at_fourth_order", (1.5,)),

@@ -437,3 +437,20 @@ def test_dense_fourier_flow_radial_momentum_balance():
     scale = np.max(np.abs(Pc * X)[3:-3])
     assert scale > 0.1 * np.max(np.abs(S.d_dR(P_RR, P.grid))[3:-3])
     assert np.max(np.abs(balance[3:-3])) < 0.03 * scale
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+def test_diffuse_walls_pull_the_adjacent_gas_toward_their_state(g):
+    """Diffuse reflection (Sec. IV walls): particles leave each wall with the wall's Maxwellian, so
+    within 20 steps from rest at T = 1 the gas next to the hot inner wall (T = 1.2) warms and the
+    gas next to the cold outer wall (T = 0.8) cools, and next to the moving inner cylinder wall
+    (u_2 = 0.1) it is dragged along the wall's direction but not past the wall's speed, while the
+    gas at the resting outer wall is not yet moving."""
+    P = S.make_problem(g, 1.0, 2.0, 16, 4, 4, 4, eta0=0.1, Kn=0.1, T_wall=(1.2, 0.8),
+                       u_wall=((0.1, 0.0) if g == geo.CYL else (0.0, 0.0)))
+    m = S.moments(S.run(S.uniform_state(P), P, 20), P)
+    assert m["T"][0] > 1.03 and m["T"][-1] < 0.97
+    assert np.all(np.diff(m["T"]) < 0)
+    if g == geo.CYL:
+        assert 0.01 < m["u"][0, 1] < 0.1 and abs(m["u"][-1, 1]) < 1e-4
+        assert np.max(np.abs(m["u"][:, 2])) < 1e-12
