@@ -123,6 +123,8 @@ CASES = [
      t_nn, "nn", "test_backward_matches_central_differences", ()),
     ("inverse DFT weight", "nn", "c = np.where(k == 0, 1.0, 2.0)", "c = np.where(k == 0, 2.0, 2.0)",
      t_nn, "nn", "test_dft_pair_matches_numpy_fft", ()),
+    ("half-range equilibrium mirror", "equilibrium", "m = half_line_gauss_moments(half * u, T, N)",
+     "m = half_line_gauss_moments(u, T, N)", t_eq, "eq", "test_half_range_half_line_moments", (8, 7, 0.3, 1.3)),
     # quadrature (Sec. III.A)
     ("half-range weights scale", "quadrature", "lam = beta[0] * V[0, :] ** 2", "lam = V[0, :] ** 2",
      t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),
