@@ -62,3 +62,15 @@ def test_two_gloo_ranks(tmp_path):
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_hbm_view_against_measured_and_nominal_bandwidth():
+    """The HBM view of a launch: algorithmic bytes over its duration, as a fraction of the measured
+    copy bandwidth and of the nominal HBM3e bandwidth."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    v = bench.hbm_view(6.0e6, 0.01, 6000.0, "measured")  # 6 MB in 10 us = 600 GB/s
+    assert v["achieved"] == pytest.approx(600.0) and v["unit"] == "GB/s"
+    assert v["frac"] == pytest.approx(0.1) and v["peak_source"] == "measured"
+    assert v["frac_of_nominal"] == pytest.approx(600.0 / bench.HBM_NOMINAL_GBS)
