@@ -137,6 +137,12 @@ def _check(rc, where):
         raise FdlbError(rc, where)
 
 
+def _precision_code(prec) -> int:
+    if prec not in ("fp32", "fp64", FP32, FP64):
+        raise ValueError(f"precision must be 'fp32' or 'fp64', not {prec!r}")
+    return FP32 if prec in ("fp32", FP32) else FP64
+
+
 def make_params(d: dict) -> Params:
     """fdlb_params from a workload dictionary (see workloads.py)."""
     p = Params()
@@ -150,10 +156,7 @@ def make_params(d: dict) -> Params:
     p.Kn = float(d.get("Kn") or 0.0)
     p.sigma = float(d.get("sigma") or 0.0)
     p.chi_model = int(d.get("chi_model", CHI_RET_FM))
-    prec = d.get("precision", "fp64")
-    if prec not in ("fp32", "fp64", FP32, FP64):
-        raise ValueError(f"precision must be 'fp32' or 'fp64', not {prec!r}")
-    p.precision = FP32 if prec in ("fp32", FP32) else FP64
+    p.precision = _precision_code(d.get("precision", "fp64"))
     p.dt = float(d.get("dt") or 0.0)
     p.cfl = float(d.get("cfl") or 0.0)
     T = d.get("T_wall", (1.0, 1.0))
@@ -385,7 +388,7 @@ def moments_noalloc(precision, Q_R, Q_2, Q_3, n_cells, f_dev_ptr, moments_dev_pt
     L = load_library()
     nodes = np.concatenate([quadrature(QUAD_HALF, Q_R)[0], quadrature(QUAD_FULL, Q_2)[0],
                             quadrature(QUAD_FULL, Q_3)[0]])
-    prec = FP32 if precision in ("fp32", FP32) else FP64
+    prec = _precision_code(precision)
     _check(L.fdlb_moments_noalloc(prec, Q_R, Q_2, Q_3, nodes, int(n_cells), c_void_p(f_dev_ptr),
                                   c_void_p(moments_dev_ptr), c_void_p(int(stream))), "fdlb_moments_noalloc")
 

@@ -145,6 +145,8 @@ def test_params_marshalling_rejects_an_unknown_precision():
     for bad in ("bf16", "f32", "FP32", 2):
         with pytest.raises(ValueError):
             fdlb.make_params(dict(d, precision=bad))
+        with pytest.raises(ValueError):  # raised before any device pointer is used
+            fdlb.moments_noalloc(bad, 2, 2, 2, 16, 0, 0)
 
 
 def test_fm_band_beyond_32_bit_offsets_is_rejected_before_allocation(lib):
