@@ -74,3 +74,18 @@ def test_hbm_view_against_measured_and_nominal_bandwidth():
     assert v["achieved"] == pytest.approx(600.0) and v["unit"] == "GB/s"
     assert v["frac"] == pytest.approx(0.1) and v["peak_source"] == "measured"
     assert v["frac_of_nominal"] == pytest.approx(600.0 / bench.HBM_NOMINAL_GBS)
+
+
+def test_clock_samples_summary():
+    """The clock record of the JSON line: median SM clock, maximum clock and every throttle reason
+    seen active in the nvidia-smi CSV samples; malformed lines are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 2040, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 1980, 2070, 1390.2, 0x8, Active, Not Active, Not Active, Active",
+             "garbage", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    out = bench.ClockSampler.summarise(lines)
+    assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler.summarise([])["samples"] == 0
