@@ -181,10 +181,11 @@ class ClockSampler:
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                clock, clock_max = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
+            sm.append(clock)
+            mx.append(clock_max)
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)

@@ -85,7 +85,8 @@ def test_clock_samples_summary():
     lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
              "0, 2040, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
              "0, 1980, 2070, 1390.2, 0x8, Active, Not Active, Not Active, Active",
-             "garbage", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+             "garbage", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1000, [N/A], 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
     out = bench.ClockSampler.summarise(lines)
     assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
     assert bench.ClockSampler.summarise([])["samples"] == 0
