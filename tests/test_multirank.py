@@ -1,6 +1,7 @@
-"""The replica bookkeeping of bench.py on two ranks of the gloo backend (host cores): the timing
-is the maximum over the ranks, the whole-job rate counts every rank's work, and the comparison
-arm runs on rank 0 alone while the other ranks exit without work."""
+"""Host logic of bench.py.  The replica bookkeeping on two ranks of the gloo backend (host
+cores): the timing is the maximum over the ranks, the whole-job rate counts every rank's work,
+and the comparison arm runs on rank 0 alone while the other ranks exit without work.  Also the
+JSON line's helpers: the HBM view, the clock summary, the flop and unit counts."""
 import io
 import json
 import os
@@ -90,3 +91,16 @@ def test_clock_samples_summary():
     out = bench.ClockSampler.summarise(lines)
     assert out == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
     assert bench.ClockSampler.summarise([])["samples"] == 0
+
+
+def test_algorithmic_flops_and_units_of_the_benchmark_workloads():
+    """The roofline's per-update flop counts (221 on the 16 x 8 x 8 cylinder, 272 on the
+    24 x 12 x 12 sphere) and the updates per step of the two single-instance workloads."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2403_15051_gb300 import workloads as wl
+
+    assert bench.alg_flops_per_update(wl.CYL, 16, 8, 8) == 221
+    assert bench.alg_flops_per_update(wl.SPH, 24, 12, 12) == 272
+    assert bench.units_per_step([wl.fourier_cyl_1024()]) == 1024 * 1024
+    assert bench.units_per_step(bench.workload("fourier_sph_2048")) == 2048 * 3456
