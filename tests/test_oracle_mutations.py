@@ -125,6 +125,15 @@ CASES = [
      t_nn, "nn", "test_dft_pair_matches_numpy_fft", ()),
     ("half-range equilibrium mirror", "equilibrium", "m = half_line_gauss_moments(half * u, T, N)",
      "m = half_line_gauss_moments(u, T, N)", t_eq, "eq", "test_half_range_half_line_moments", (8, 7, 0.3, 1.3)),
+    # warm-start seed (Shakhov form of Sec. II) and the steady-state residual
+    ("seed Shakhov xi^2/(5T)", "solver", "(xi2 / (5.0 * e(T)) - 1.0) * p[0][None]", "(xi2 / (3.0 * e(T)) - 1.0) * p[0][None]",
+     t_solver, "S", "test_shakhov_seed_reproduces_its_moment_profiles", (CYL,)),
+    ("seed u_2 dropped from xi^2", "solver", "(p[1][None] - e(u2)) ** 2", "p[1][None] ** 2",
+     t_solver, "S", "test_shakhov_seed_reproduces_its_moment_profiles", (SPH,)),
+    ("residual without 1/K", "solver", "/ (K * max(float(np.max(np.abs(a))), s))", "/ max(float(np.max(np.abs(a))), s)",
+     t_solver, "S", "test_moment_residual_on_a_hand_computed_two_cell_case", ()),
+    ("residual scaled by the new profile", "solver", "/ (K * max(float(np.max(np.abs(a))), s))",
+     "/ (K * max(float(np.max(np.abs(b))), s))", t_solver, "S", "test_moment_residual_on_a_hand_computed_two_cell_case", ()),
     # quadrature (Sec. III.A)
     ("half-range weights scale", "quadrature", "lam = beta[0] * V[0, :] ** 2", "lam = V[0, :] ** 2",
      t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),

@@ -445,3 +445,47 @@ def test_diffuse_walls_pull_the_adjacent_gas_toward_their_state(g):
     if g == geo.CYL:
         assert 0.01 < m["u"][0, 1] < 0.1 and abs(m["u"][-1, 1]) < 1e-4
         assert np.max(np.abs(m["u"][:, 2])) < 1e-12
+
+
+@pytest.mark.parametrize("g", [geo.CYL, geo.SPH])
+def test_shakhov_seed_reproduces_its_moment_profiles(g):
+    """The warm-start seed f = n g_R(0,T) g_2(u_2,T) g_3(0,T) [1 + (xi^2/(5T) - 1) xi_R q_R/(n T^2)]
+    carries the profiles it is built from: its quadrature moments (Eq. macro_def) are n, u_2, T
+    and q_R again, with u_R = u_3 = 0, to round-off.  The Shakhov factor is odd in xi_R, so it
+    leaves n, u and T alone, and its heat flux is q_R <(xi^2/(5T) - 1) xi_R^2 xi^2>/(2T^2) =
+    q_R (35 T^3/(5T) - 5 T^2)/(2 T^2) = q_R, Gaussian moments of degree 6 in xi_R and 4 in xi_2,
+    xi_3: the expansion orders must reach them (N_R >= 6, N_2, N_3 >= 4; here 7, 5, 5)."""
+    P = S.make_problem(g, 1.0, 2.0, 12, 8, 6, 6, eta0=0.1, Kn=0.1)
+    x = (np.arange(12) + 0.5) / 12
+    n = P.n0 * (1.0 + 0.2 * np.sin(2.0 * x))
+    u2 = 0.25 * np.cos(3.0 * x)
+    T = 0.9 + 0.3 * x
+    qR = 0.03 * P.n0 * (x - 0.4)
+    m = S.moments(S.shakhov_seed(P, n, u2, T, qR), P)
+    assert np.allclose(m["n"], n, rtol=1e-13, atol=0)
+    assert np.max(np.abs(m["u"][:, 1] - u2)) < 1e-13
+    assert np.max(np.abs(m["u"][:, 0])) < 1e-13 and np.max(np.abs(m["u"][:, 2])) < 1e-13
+    assert np.allclose(m["T"], T, rtol=1e-13, atol=0)
+    assert np.max(np.abs(m["q"][:, 0] - qR)) < 1e-12 * P.n0
+    # with no heat flux and constant profiles it is the uniform equilibrium
+    f_u = S.shakhov_seed(P, np.full(12, P.n0), np.zeros(12), np.full(12, 1.1), np.zeros(12))
+    assert np.max(np.abs(f_u - S.uniform_state(P, T0=1.1))) <= 1e-13 * np.max(f_u)
+
+
+def test_moment_residual_on_a_hand_computed_two_cell_case():
+    """r = max over (n, u_2, T, q_R) of max_c |M_new - M_old| / (K max(max_c |M_old|, scale)),
+    worked by hand for two cells and K = 3 steps:
+      n:   max|dn| = |4.6 - 4.0| = 0.6, max|n_old| = 4 > scale 1      -> 0.6 / (3 * 4)   = 0.05
+      u_2: max|du| = |-0.24 + 0.3| = 0.06, max|u_old| = 0.3 < scale 1 -> 0.06 / (3 * 1)  = 0.02
+      T:   unchanged                                                   -> 0
+      q_R: max|dq| = 1e-3, max|q_old| = 0 < scale 0.005               -> 1e-3 / 0.015   = 0.0667
+    so r = 1/15 (the heat flux); with its scale raised to 0.05, r = 0.05 (the density), and with
+    the density scale raised to 10 as well, r = 0.02 (the velocity)."""
+    old = {"n": np.array([2.0, 4.0]), "u2": np.array([0.1, -0.3]), "T": np.array([1.0, 1.5]),
+           "qR": np.array([0.0, 0.0])}
+    new = {"n": np.array([2.3, 4.6]), "u2": np.array([0.1, -0.24]), "T": np.array([1.0, 1.5]),
+           "qR": np.array([1e-3, 0.0])}
+    assert S.moment_residual(old, new, 3, (1.0, 1.0, 1.0, 0.005)) == pytest.approx(1.0 / 15.0, rel=1e-14)
+    assert S.moment_residual(old, new, 3, (1.0, 1.0, 1.0, 0.05)) == pytest.approx(0.05, rel=1e-14)
+    assert S.moment_residual(old, new, 3, (10.0, 1.0, 1.0, 0.05)) == pytest.approx(0.02, rel=1e-14)
+    assert S.moment_residual(old, old, 3, (1.0, 1.0, 1.0, 1.0)) == 0.0
