@@ -50,9 +50,12 @@ KERNEL_SOURCES = ["paper_2403_15051_gb300/csrc/" + f for f in (
 
 
 def accept_kn(kn, eta0):
-    # C >= 3 with Kn = 1/(6 sqrt2 eta0 chi(eta0) C), chi the Carnahan-Starling contact value
-    chi = (2.0 - eta0) / (2.0 * (1.0 - eta0) ** 3)
-    return 1.0 / (6.0 * math.sqrt(2.0) * eta0 * chi * kn) >= 3.0
+    """C >= 3 for the confinement ratio the library derives from (Kn, eta0) (its host-only
+    parameter conversion; C does not depend on the gap width)."""
+    from paper_2403_15051_gb300 import fdlb
+
+    C, _, _ = fdlb.physical_parameters(kn, eta0, 1.0)
+    return C >= 3.0
 
 
 def workload(name):
@@ -63,7 +66,7 @@ def workload(name):
     if name == "fourier_sph_2048":
         return [wl.fourier_sph_2048(accept_kn)]
     if name == "batch_512":
-        return wl.batch_instances(lambda kn, e, r: accept_kn(kn, e) and (r - 1.0) * 0 == 0)
+        return wl.batch_instances(lambda kn, e, r: accept_kn(kn, e))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -327,7 +330,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     fbuild.build()
     ds = workload(args.workload)
+    t_create = time.perf_counter()
     S = fdlb.Solver(ds)
+    t_create = time.perf_counter() - t_create
     persistent = S.set_persistent_step(None)  # the library's default scheduling
     S.set_graph_steps(1)
     stream = torch.cuda.ExternalStream(S.stream_handle())
@@ -335,7 +340,7 @@ def run_ours(args):
     tsize = 4 if ds[0]["precision"] == "fp32" else 8
     state_bytes = units * tsize
     flush_needed = needs_flush(ds)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if flush_needed else None
 
     def l2_flush(k):
         if flush_needed:
@@ -357,6 +362,13 @@ def run_ours(args):
         l2_flush(k)
         S.step(1)
     torch.cuda.synchronize()
+    tiling = S.tiling()  # after the first step: the autotuned tiling of a batch
+    # the FP32 FMA rate the chip sustains now: the denominator of the arithmetic roofline
+    probe_sampler = ClockSampler(torch.cuda.current_device())
+    probe_sampler.start()
+    time.sleep(0.3)
+    fma_tflops, fma_ms = fdlb.fp32_fma_peak(S.stream_handle(), repeats=20)
+    probe_clocks = probe_sampler.stop()
     t_end = time.perf_counter() + 0.6
     k = 0
     sampler = ClockSampler(torch.cuda.current_device())
@@ -398,46 +410,43 @@ def run_ours(args):
     S.set_kernel_timing(False)
     clocks = sampler.stop()
 
-    # ---- hot-L2 rate (steps back to back, no flush) for context
-    torch.cuda.synchronize()
-    S.set_graph_steps(20)
-    S.step(20)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    S.step(200)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    hot_value = units * 200 / (e0.elapsed_time(e1) * 1e-3)
-    S.set_graph_steps(1)
+    hot_value = None
+    if flush_needed:
+        # hot-L2 rate (steps back to back, no flush) for context
+        torch.cuda.synchronize()
+        S.set_graph_steps(20)
+        S.step(20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hot_value = units * 200 / (e0.elapsed_time(e1) * 1e-3)
+        S.set_graph_steps(1)
 
-    # ---- end to end through the C ABI with host buffers: H2D of the state, one step,
-    # D2H of the per-cell moments, every step
-    n_inst = len(ds)
-    host_state = [torch.empty(S.raw_elements(q) * tsize, dtype=torch.uint8, pin_memory=True) for q in range(n_inst)]
-    for q in range(n_inst):
-        S.get_state_raw(host_state[q].data_ptr(), q)
-    e2e_steps = max(5, min(args.steps, 200))
+    # ---- end to end through the C ABI with host buffers: every step, H2D of the whole state from
+    # pinned memory (one copy, the raw sums recomputed), one step, D2H of every cell's moments
+    host_state = torch.empty(S.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    S.get_state_raw(host_state.data_ptr(), -1)
+    e2e_steps = max(3, min(args.steps, 100))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
     for k in range(e2e_steps):
-        for q in range(n_inst):
-            S.set_state_raw(host_state[q].data_ptr(), q)
+        S.set_state_raw(host_state.data_ptr(), -1)
         S.step(1)
-        for q in range(n_inst):
-            m = S.moments(q)
-            d2h += m["n"].size * fdlb.NMOM * 8
+        m = S.moments_all()
+        d2h += m.nbytes
     el = time.perf_counter() - t0
     el = max_over_ranks(el, world)
-    e2e = {"value": units * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+    e2e = {"value": units * e2e_steps * world / el, "unit": UNIT, "h2d_bytes_per_step": S.state_bytes(),
            "d2h_bytes_per_step": d2h // e2e_steps}
 
     # ---- roofline of the dominant kernel: the persistent step kernel (one launch per timed step:
     # three stages, each with its closure) or else the fused-stage kernel (one stage per launch).
-    # It is bound by FP32 arithmetic issue, not by HBM: achieved = algorithmic flops per launch /
-    # event-timed launch duration, against the FP32 CUDA-core peak from the unit counts and the
-    # sampled SM clock.  The HBM view (8 population passes per SSP-RK3 step, against the measured
-    # copy bandwidth) is kept for context.
+    # Two views of the same event-timed launch: arithmetic (algorithmic flops against the measured
+    # FP32 FMA rate) and HBM (8/3 population passes per stage against the measured copy
+    # bandwidth); the bound is the view with the larger fraction.
     hbm_peak, peak_kind = measured_peaks()
     d0 = ds[0]
     nR, n2, n3 = 2 * d0["Q_R"], d0["Q_2"], d0["Q_3"]
@@ -451,30 +460,39 @@ def run_ours(args):
         stages_per_launch = 1.0
         avg_ms = stream_ms / max(n_stream, 1)
     alg_flops = fpu * units * stages_per_launch
-    sm_mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
-    alu_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    achieved = alg_flops / (avg_ms * 1e-3) / 1e12
+    alu_achieved = alg_flops / (avg_ms * 1e-3) / 1e12
     alg_bytes = 8.0 / 3.0 * state_bytes * stages_per_launch
+    hv = hbm_view(alg_bytes, avg_ms, hbm_peak, peak_kind)
+    alu = {"achieved": alu_achieved, "peak": fma_tflops, "unit": "TFLOP/s", "frac": alu_achieved / fma_tflops,
+           "peak_source": "measured: FP32 FMA probe kernel (fdlb_fp32_fma_peak), best of 20 launches of "
+                          "%.2f ms at a median SM clock of %s MHz" % (fma_ms, (probe_clocks or {}).get("sm_mhz")),
+           "alg_flops_per_update": fpu, "alg_flops_per_launch": alg_flops}
+    bound = "alu" if alu["frac"] >= hv["frac"] else "hbm"
+    top = alu if bound == "alu" else hv
     traffic = recorded_traffic(args.workload, kernel)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": traffic, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz,
-                "kernel": kernel, "alg_flops_per_update": fpu, "stages_per_launch": stages_per_launch,
-                "alg_flops_per_launch": alg_flops, "avg_launch_ms": avg_ms,
-                "hbm_view": hbm_view(alg_bytes, avg_ms, hbm_peak, peak_kind)}
+    roofline = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                "frac": top["frac"], "traffic": traffic, "kernel": kernel, "stages_per_launch": stages_per_launch,
+                "avg_launch_ms": avg_ms, "alu_view": alu, "hbm_view": hv}
     if not persistent:
-        roofline["closure_avg_launch_ms"] = closure_ms / max(n_closure, 1)
+        cl_avg = closure_ms / max(n_closure, 1)
+        roofline["closure_avg_launch_ms"] = cl_avg
+        roofline["kernel_time_share"] = {"stream_kernel": stream_ms / (stream_ms + closure_ms),
+                                         "closure_kernel": closure_ms / (stream_ms + closure_ms)}
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(ds)
     if rank == 0:
-        d = ds[0]
+        cfg = bench_config(args, ds, world, flush_needed, persistent)
+        cfg["tiling"] = tiling
+        cfg["create_seconds"] = t_create
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if tsize == 4 else "f64", "data": "synthetic",
-                "config": bench_config(args, ds, world, flush_needed, persistent),
-                "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "hot_l2_value": hot_value}
+                "config": cfg, "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "fma_probe_clocks": probe_clocks}
+        if hot_value is not None:
+            line["hot_l2_value"] = hot_value
         print(json.dumps(line))
     S.close()
     if world > 1:
@@ -626,7 +644,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="fourier_cyl_1024",
+    ap.add_argument("--workload", default="batch_512",
                     choices=["fourier_cyl_1024", "couette_cyl_64", "fourier_sph_2048", "batch_512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")

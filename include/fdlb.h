@@ -178,8 +178,9 @@ int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host);
 
 /* Per-cell moments of one instance (Eq. macro_def from the quadrature sums of Eq. mom_quad):
  * out[cell][FDLB_NMOM] = n, u_1, u_2, u_3, T, q_1, q_2, q_3, P_12 (P_12 = shear stress between
- * the radial and second axis), FP64.  on_device != 0: `out` is a device pointer, written
- * asynchronously on the stream; else a host pointer (the call synchronises). */
+ * the radial and second axis), FP64.  instance -1: every instance at once, [total cells][FDLB_NMOM]
+ * with the cells of instance q after those of instances 0..q-1.  on_device != 0: `out` is a device
+ * pointer, written asynchronously on the stream; else a host pointer (the call synchronises). */
 int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device);
 
 /* Closure diagnostics of the current state of one instance, host FP64 arrays of n_cells
@@ -205,10 +206,24 @@ int fdlb_load(fdlb_handle h, const char* path);
 const char* fdlb_error_string(int code);
 
 /* Kernel-tuning knobs of the streaming kernel (cells per tile, p_3 values per momentum slice,
- * threads per block); 0 keeps the current value.  fdlb_autotune times the candidates on the
- * device and keeps the fastest (the choice is cached per momentum set and precision). */
+ * threads per block); 0 keeps the current value.  A change of the cells per tile alone regroups
+ * cells without changing any result; the slice width and the block size change the order of the
+ * moment sums (results then agree to rounding).
+ *
+ * fdlb_autotune times candidate tile shapes on the device and keeps the fastest: the cells per
+ * stream tile (2 .. 32), then the own cells per closure item (2, 4, 8, 16), each candidate over
+ * three stages written to the stage-1 scratch buffers (the state, its sums and the step count are
+ * not touched).  Only these two regrouping knobs are searched, so a tuned handle produces the same
+ * results bit for bit as an untuned one.  The choice is cached per process for the momentum set,
+ * precision, block size, slice width and size class (log2 of the handle's cells and instances);
+ * fdlb_autotune always measures and refreshes that cache.  fdlb_set_autotune selects automatic
+ * tuning at the first fdlb_step / fdlb_run_to_steady of a handle, from the cache when it holds
+ * the handle's key: 0 off, 1 batches of two or more instances (default), 2 every handle.
+ * fdlb_get_tiling reports the tiling in use (any pointer may be NULL). */
 int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads);
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
+int fdlb_set_autotune(fdlb_handle h, int mode);
+int fdlb_get_tiling(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads, int* closure_cells);
 
 /* The K^h contraction of the curvature force on the tensor cores (default off): an
  * nR x nR by nR x (n2 KS) product per cell in split TF32 (K = Kh + Kl, f = fh + fl; three
@@ -236,7 +251,11 @@ int fdlb_set_persistent_step(fdlb_handle h, int enable, int* in_use);
  * persistent step kernel waits for that many arrivals more than the grid makes, so its 1 s wait
  * runs out.  In both cases the blocks set the error flag and leave without faulting: the next
  * fdlb_get_diagnostics returns FDLB_ETIMEOUT and the state of the interrupted step is
- * undefined.  fdlb_clear_error clears the flag (the handle stays usable; set a state again). */
+ * undefined.  fdlb_clear_error clears the flag (the handle stays usable; set a state again).
+ * The same holds after a wait that runs out in use (FDLB_ETIMEOUT from fdlb_get_diagnostics
+ * without a test hook): a block that gives up leaves while a copy into its shared memory may
+ * still be in flight, so the populations, sums and records of the interrupted step are
+ * undefined; restore a checkpoint (fdlb_load) or set a new state before stepping on. */
 int fdlb_set_wait_test(fdlb_handle h, int tx_extra_bytes, int barrier_extra);
 int fdlb_clear_error(fdlb_handle h);
 
@@ -275,10 +294,14 @@ int fdlb_get_stream(fdlb_handle h, void** stream);
 
 /* Populations of one instance in the library's own layout and precision: [cell][k][i][j]
  * (k outermost inside a cell), n_cells * n_momenta elements of FP32 (FDLB_FP32) or FP64.
+ * instance -1: the whole batch as the library stores it, fdlb_state_bytes bytes (each instance's
+ * populations start on a 256-byte boundary, the gaps between them carry no data), in one copy.
  * on_device != 0: `src`/`dst` is a device pointer; else host (pinned memory gives the fastest
- * copies).  fdlb_set_state_raw also recomputes the quadrature sums of the new state. */
+ * copies).  fdlb_set_state_raw also recomputes the quadrature sums of the new state (one pass
+ * over every instance) and resets the step counts of the instances it sets. */
 int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device);
 int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device);
+int fdlb_state_bytes(fdlb_handle h, size_t* bytes);
 
 /* ----------------------------------------------------------------------- learned warm start
  * A one-dimensional Fourier neural operator that maps the five parameters of a cylindrical
@@ -321,26 +344,39 @@ int fdlb_nn_warm_start(fdlb_nn_handle h, fdlb_handle solver, int instance, const
 
 /* ----------------------------------------------------------------------- no device allocation
  * Per-cell moments of populations the caller already holds on the device, for callers that
- * cannot allocate device memory (plugins inside an application that owns the whole device
- * budget, latency-critical loops that cannot afford cudaMalloc's implicit synchronisation).
- * The paper has no counterpart: this is a library service around the moment reduction of
- * Eq. mom_quad / Eq. macro_def.
+ * cannot allocate device memory: plugins inside an application that owns the whole device
+ * budget, and latency-critical loops that cannot afford cudaMalloc's implicit synchronisation.
+ * The paper has no counterpart: this is a library service.
  *
  * f_dev: device array of n_cells * 2Q_R * Q_2 * Q_3 populations in the library's own layout
  * ([cell][k][i][j], as fdlb_get_state_raw writes it), FP32 or FP64 per `precision`.
  * nodes_host: host array [2Q_R radial nodes | Q_2 nodes | Q_3 nodes] as fdlb_quadrature returns
- * them.  moments_dev: device array [n_cells][FDLB_NMOM] (n, u_1..3, T, q_1..3, P_12), FP64.
+ * them; it is copied to the device with cudaMemcpyAsync on `cuda_stream`, in stream order: from
+ * pageable memory the call returns once the copy has been staged (the buffer may be reused at
+ * once), from pinned memory the buffer must stay valid until the copy has run on the stream.
+ * moments_dev: device array [n_cells][FDLB_NMOM] (n, u_1..3, T, q_1..3, P_12), FP64.
  * Work is issued on `cuda_stream` (a cudaStream_t; NULL = legacy stream), asynchronously.
  *
  * Allocates no device memory: the partial sums live in a fixed scratch array of this library
  * (3.4 MB, held by every GPU that loads the library until the process exits), so n_cells is
  * limited to 32768 (FDLB_EINVAL beyond).  The first call on a device looks up the scratch
- * address (cudaGetSymbolAddress) and should come before any stream capture on that device.
- * Every call shares the one scratch array, which keeps the last call's contents; calls that
- * overlap on the GPU (different streams, no ordering) race on it and must be serialised by the
- * caller.  Returns FDLB_OK, FDLB_EINVAL, FDLB_ENOGPU or FDLB_ECUDA. */
+ * address (cudaGetSymbolAddress, once per device, serialised across host threads); make that
+ * first call before any stream capture on that device.  Every call shares the one scratch
+ * array, which keeps the last call's contents; calls that overlap on the GPU (different streams,
+ * no ordering) race on it and must be serialised by the caller.  A launch error of this call is
+ * reported as FDLB_ECUDA; errors left by earlier, unrelated work are neither reported nor
+ * cleared.  Returns FDLB_OK, FDLB_EINVAL, FDLB_ENOGPU or FDLB_ECUDA. */
 int fdlb_moments_noalloc(int precision, int Q_R, int Q_2, int Q_3, const double* nodes_host, int n_cells,
                          const void* f_dev, double* moments_dev, void* cuda_stream);
+
+/* ----------------------------------------------------------------------- device probe
+ * Measured FP32 fused multiply-add rate of the current device, the denominator of the fused stage
+ * kernel's arithmetic roofline (the paper has no counterpart: a measurement service).  A kernel of
+ * independent FMA chains fills every SM; one warm-up launch, then `repeats` launches timed with
+ * CUDA events on `cuda_stream` (a cudaStream_t; NULL = legacy stream).  *tflops = the best rate
+ * (an FMA counted as two flops), *ms = that launch's duration.  Synchronises the stream.  Returns
+ * FDLB_OK, FDLB_EINVAL (repeats < 1, null outputs), FDLB_ENOGPU or FDLB_ECUDA. */
+int fdlb_fp32_fma_peak(void* cuda_stream, int repeats, double* tflops, double* ms);
 
 /* ----------------------------------------------------------------------- host-only set-up
  * These run on the host only (no GPU needed). */

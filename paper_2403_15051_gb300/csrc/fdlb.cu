@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -74,6 +76,8 @@ struct Solver {
     size_t smem_stream = 0;
     int use_bulk = 0;
     int closure_cells = 4, closure_threads = 128;  // own cells per closure item (<= kClosureCells)
+    int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
+    bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
     int closure_wst = 0;                           // staged band-row elements per closure block
     int grid_stream = 1, grid_closure = 1;
     size_t closure_smem = 0;
@@ -467,6 +471,7 @@ int upload_items(Solver& S) {
 int launch_moments_all(Solver& S, int buf);
 
 int configure_tiling(Solver& S, int B, int KS, int threads) {
+    const int old_slices = S.M.slices;
     if (B > 0) S.B = std::max(2, B);
     if (KS > 0) S.KS = KS;
     if (S.geometry == FDLB_SPH) S.KS = S.n3;  // every axis is coupled by the force term
@@ -525,8 +530,11 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     }
     int rc = upload_items(S);
     if (rc) return rc;
-    // the partial sums are stored per slice: rebuild them for the new slice count
-    return launch_moments_all(S, 0);
+    // the partial sums are stored per slice: rebuild them for a new slice count (under the same
+    // slicing they stay as the last stage wrote them, so a new tile size or block size leaves the
+    // state and its sums bit for bit as they were)
+    if (S.M.slices != old_slices) return launch_moments_all(S, 0);
+    return FDLB_OK;
 }
 
 template <typename T>
@@ -823,7 +831,125 @@ int launch_steps_fused(Solver& S, int64_t n) {
     return FDLB_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Tile shapes chosen by timing: cells per stream tile B and own cells per closure item, the two
+// knobs that regroup cells without changing any cell's arithmetic (the per-cell results and the
+// order of every sum stay those of the default, so tuning changes no result bit); the block size
+// and the momentum slicing, which do reorder the sums, stay as configured.  Each candidate is
+// timed over three stages (closure + fused stage, the second RK stage's form, written to the
+// stage-1 buffers, which every step overwrites before reading) after one warm-up stage; B is
+// tuned first at the current closure grouping, then the closure grouping at the best B.  The
+// choice is cached per process for the momentum set, precision, block size, slicing and the
+// size class of the handle (log2 of its cells and of its instances).
+struct TuneKey {
+    int geometry, precision, nR, n2, n3, KS, threads, cells_log2, inst_log2;
+    bool operator<(const TuneKey& o) const {
+        const int a[9] = {geometry, precision, nR, n2, n3, KS, threads, cells_log2, inst_log2};
+        const int b[9] = {o.geometry, o.precision, o.nR, o.n2, o.n3, o.KS, o.threads, o.cells_log2, o.inst_log2};
+        return std::lexicographical_compare(a, a + 9, b, b + 9);
+    }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mutex;
+
+int ilog2(long long x) {
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+TuneKey tune_key(const Solver& S) {
+    return TuneKey{S.geometry, S.precision, S.nR, S.n2, S.n3, S.KS, S.threads, ilog2(S.total_cells), ilog2(S.n_inst)};
+}
+
+int set_closure_grouping(Solver& S, int cells) {
+    S.closure_cells = cells;
+    if (S.gexec) {
+        cudaGraphExecDestroy(S.gexec);
+        S.gexec = nullptr;
+    }
+    return upload_items(S);
+}
+
+// Time of three stages of the current tiling (ms), or a negative value if a launch failed.
+float time_stages(Solver& S, cudaEvent_t e0, cudaEvent_t e1) {
+    if (launch_stage(S, 0, 0, 1, 0.75, 0.25, 0) != FDLB_OK) return -1.f;
+    cudaEventRecord(e0, S.stream);
+    for (int r = 0; r < 3; ++r)
+        if (launch_stage(S, 0, 0, 1, 0.75, 0.25, 0) != FDLB_OK) return -1.f;
+    cudaEventRecord(e1, S.stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
+int run_autotune(Solver& S, bool use_cache) {
+    S.tuned = true;
+    const TuneKey key = tune_key(S);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            int rc = configure_tiling(S, it->second.first, S.KS, S.threads);
+            return rc ? rc : set_closure_grouping(S, it->second.second);
+        }
+    }
+    const bool timing = S.timing;
+    S.timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FDLB_CUDA(cudaEventCreate(&e0));
+    FDLB_CUDA(cudaEventCreate(&e1));
+    const int KS = S.KS, threads = S.threads;
+    int bestB = S.B, bestC = S.closure_cells;
+    float best = time_stages(S, e0, e1);
+    if (best < 0.f) best = 1e30f;
+    const int Bs[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+    int rc = FDLB_OK;
+    for (int B : Bs) {
+        if (B == bestB) continue;
+        if (configure_tiling(S, B, KS, threads) != FDLB_OK || S.B != B) continue;
+        const float ms = time_stages(S, e0, e1);
+        if (ms >= 0.f && ms < best) {
+            best = ms;
+            bestB = B;
+        }
+    }
+    rc = configure_tiling(S, bestB, KS, threads);
+    const int Cs[] = {2, 4, 8, 16};
+    for (int C : Cs) {
+        if (rc || C == bestC) continue;
+        if (set_closure_grouping(S, C) != FDLB_OK) continue;
+        const float ms = time_stages(S, e0, e1);
+        if (ms >= 0.f && ms < best) {
+            best = ms;
+            bestC = C;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    S.timing = timing;
+    if (!rc) rc = set_closure_grouping(S, bestC);
+    if (!rc) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = {bestB, bestC};
+    }
+    return rc;
+}
+
+int maybe_autotune(Solver& S) {
+    if (S.tuned || S.autotune_mode == 0 || (S.autotune_mode == 1 && S.n_inst < 2)) return FDLB_OK;
+    return run_autotune(S, true);
+}
+
 int do_steps(Solver& S, int64_t n) {
+    if (n > 0) {
+        const int rc = maybe_autotune(S);
+        if (rc) return rc;
+    }
     const int64_t before = S.launches;
     int64_t done = 0;
     if (S.fused_on) {
@@ -1123,7 +1249,7 @@ int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) try {
 
 int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) try {
     Solver* S = SOL(h);
-    if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
+    if (!S || instance < -1 || instance >= S->n_inst || !out) return FDLB_EINVAL;
     // n, u, T, q, P_12 come from the FP64 raw sums of the current state alone (the closure's chi
     // and nbar, columns the query does not return, are not needed): the record kernel only
     if (S->precision == FDLB_FP32)
@@ -1131,8 +1257,10 @@ int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) tr
     else
         fdlb::launch_ca<double>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream);
     FDLB_CUDA(cudaGetLastError());
-    const int N = S->setup[instance].p.n_cells;
-    const double* src = S->ca + (size_t)S->cell_off[instance] * fdlb::kCA;
+    // instance -1: every instance's cells, in instance order (the cells of instance q follow those
+    // of instances 0..q-1)
+    const int N = instance < 0 ? S->total_cells : S->setup[instance].p.n_cells;
+    const double* src = S->ca + (instance < 0 ? (size_t)0 : (size_t)S->cell_off[instance] * fdlb::kCA);
     FDLB_CUDA(cudaMemcpy2DAsync(out, FDLB_NMOM * sizeof(double), src, fdlb::kCA * sizeof(double),
                                 FDLB_NMOM * sizeof(double), N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 S->stream));
@@ -1436,47 +1564,28 @@ int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads)
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
-    // candidates: tile cells x slice width x thread cap; each timed over 3 RHS evaluations
-    const int Bs[4] = {4, 8, 16, 32};
-    std::vector<int> KSs = {S->n3};
-    if (S->geometry == FDLB_CYL) {
-        KSs.clear();
-        for (int k = 1; k <= S->n3; k *= 2)
-            if (S->n3 % k == 0 && ((size_t)S->nR * S->n2 * k * S->tsize) % 16 == 0) KSs.push_back(k);
-        if (KSs.empty()) KSs.push_back(S->n3);
-    }
-    const int caps[2] = {256, 512};
-    cudaEvent_t e0, e1;
-    FDLB_CUDA(cudaEventCreate(&e0));
-    FDLB_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bB = S->B, bK = S->KS, bT = 256;
-    for (int B : Bs)
-        for (int K : KSs)
-            for (int cap : caps) {
-                if (fdlb::configure_tiling(*S, B, K, cap) != FDLB_OK) continue;
-                if (S->B != B) continue;
-                bool ok = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1) == FDLB_OK;
-                cudaEventRecord(e0, S->stream);
-                for (int r = 0; r < 3 && ok; ++r) ok = fdlb::launch_stage(*S, 0, 0, 1, 0.0, 1.0, 1) == FDLB_OK;
-                cudaEventRecord(e1, S->stream);
-                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    bB = B;
-                    bK = K;
-                    bT = cap;
-                }
-            }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    int rc = fdlb::configure_tiling(*S, bB, bK, bT);
+    const int rc = fdlb::run_autotune(*S, false);
     if (cells_per_tile) *cells_per_tile = S->B;
     if (slice_k) *slice_k = S->KS;
     if (threads) *threads = S->threads;
     return rc;
+} FDLB_HOST_CATCH
+
+int fdlb_set_autotune(fdlb_handle h, int mode) try {
+    Solver* S = SOL(h);
+    if (!S || mode < 0 || mode > 2) return FDLB_EINVAL;
+    S->autotune_mode = mode;
+    return FDLB_OK;
+} FDLB_HOST_CATCH
+
+int fdlb_get_tiling(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads, int* closure_cells) try {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (cells_per_tile) *cells_per_tile = S->B;
+    if (slice_k) *slice_k = S->KS;
+    if (threads) *threads = S->threads;
+    if (closure_cells) *closure_cells = S->closure_cells;
+    return FDLB_OK;
 } FDLB_HOST_CATCH
 
 int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) try {
@@ -1535,12 +1644,7 @@ int fdlb_set_programmatic_launch(fdlb_handle h, int enable) try {
 int fdlb_set_closure_cells(fdlb_handle h, int cells) try {
     Solver* S = SOL(h);
     if (!S || cells < 1 || cells > fdlb::kClosureCells) return FDLB_EINVAL;
-    S->closure_cells = cells;
-    if (S->gexec) {
-        cudaGraphExecDestroy(S->gexec);
-        S->gexec = nullptr;
-    }
-    return fdlb::upload_items(*S);
+    return fdlb::set_closure_grouping(*S, cells);
 } FDLB_HOST_CATCH
 
 int64_t fdlb_launch_count(fdlb_handle h) {
@@ -1600,7 +1704,15 @@ int fdlb_get_stream(fdlb_handle h, void** stream) try {
 
 int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_device) try {
     Solver* S = SOL(h);
-    if (!S || instance < 0 || instance >= S->n_inst || !src) return FDLB_EINVAL;
+    if (!S || instance < -1 || instance >= S->n_inst || !src) return FDLB_EINVAL;
+    if (instance < 0) {
+        // the whole batch as the library stores it, one copy and one pass of the raw sums
+        FDLB_CUDA(cudaMemcpyAsync(S->f[0], src, S->f_elems * S->tsize,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
+        std::fill(S->inst_steps.begin(), S->inst_steps.end(), 0);
+        S->prev_valid = false;
+        return fdlb::launch_moments_all(*S, 0);
+    }
     const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
     FDLB_CUDA(cudaMemcpyAsync((unsigned char*)S->f[0] + S->f_off[instance] * S->tsize, src, bytes,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream));
@@ -1610,11 +1722,18 @@ int fdlb_set_state_raw(fdlb_handle h, int instance, const void* src, int on_devi
 
 int fdlb_get_state_raw(fdlb_handle h, int instance, void* dst, int on_device) try {
     Solver* S = SOL(h);
-    if (!S || instance < 0 || instance >= S->n_inst || !dst) return FDLB_EINVAL;
-    const size_t bytes = (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
-    FDLB_CUDA(cudaMemcpyAsync(dst, (const unsigned char*)S->f[0] + S->f_off[instance] * S->tsize, bytes,
-                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+    if (!S || instance < -1 || instance >= S->n_inst || !dst) return FDLB_EINVAL;
+    const size_t bytes = instance < 0 ? S->f_elems * S->tsize : (size_t)S->setup[instance].p.n_cells * S->Np * S->tsize;
+    const unsigned char* src = (const unsigned char*)S->f[0] + (instance < 0 ? 0 : S->f_off[instance] * S->tsize);
+    FDLB_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
     if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    return FDLB_OK;
+} FDLB_HOST_CATCH
+
+int fdlb_state_bytes(fdlb_handle h, size_t* bytes) try {
+    Solver* S = SOL(h);
+    if (!S || !bytes) return FDLB_EINVAL;
+    *bytes = S->f_elems * S->tsize;
     return FDLB_OK;
 } FDLB_HOST_CATCH
 

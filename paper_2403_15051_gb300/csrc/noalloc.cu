@@ -12,6 +12,8 @@
 // that scratch array.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "device_common.cuh"
 #include "internal.h"
 #include "kernels.cuh"
@@ -25,8 +27,10 @@ constexpr int kNoAllocNodes = 2 * kMaxQ + 2 * kMaxQ;  // radial (2Q) + two full-
 // Scratch shared by every call on a device: the raw sums of each cell, then the momentum nodes.
 __device__ __align__(256) double g_noalloc_scratch[(size_t)kNoAllocMaxCells * kSums + kNoAllocNodes];
 
-// Device address of the scratch array, looked up once per device on the first call.
+// Device address of the scratch array, looked up once per device on the first call; the lookup is
+// serialised across host threads.
 void* g_scratch_addr[256] = {};
+std::mutex g_scratch_mutex;
 
 // Raw sums of every cell: a block per cell (grid-stride), per-thread partials and warp tree in
 // the populations' precision, FP64 across warps.  Every call overwrites the sums of its cells.
@@ -111,27 +115,42 @@ extern "C" int fdlb_moments_noalloc(int precision, int Q_R, int Q_2, int Q_3, co
     if (n_cells < 1 || n_cells > kNoAllocMaxCells || !nodes_host || !f_dev || !moments_dev) return FDLB_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return FDLB_ENOGPU;
-    if (!g_scratch_addr[dev]) {
-        // one-time set-up on this device: the device address of the scratch array
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return FDLB_ECUDA;
-        g_scratch_addr[dev] = p;
+    void* sp = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {
+            // one-time set-up on this device: the device address of the scratch array
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return FDLB_ECUDA;
+            g_scratch_addr[dev] = p;
+        }
+        sp = g_scratch_addr[dev];
     }
-    double* scratch = static_cast<double*>(g_scratch_addr[dev]);
+    double* scratch = static_cast<double*>(sp);
     const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the momentum nodes go to the tail of the scratch array, in stream order
     const int n_nodes = 2 * Q_R + Q_2 + Q_3;
     if (cudaMemcpyAsync(scratch + (size_t)kNoAllocMaxCells * kSums, nodes_host, n_nodes * sizeof(double),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FDLB_ECUDA;
+    // launches through cudaLaunchKernel return this call's own launch error, so an error left by
+    // earlier work on the thread is neither reported here nor cleared
+    int nR = 2 * Q_R, n2 = Q_2, n3 = Q_3, nc = n_cells;
     const int grid = n_cells < 4096 ? n_cells : 4096;
-    if (precision == FDLB_FP32)
-        noalloc_sums_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(f_dev), n_cells, 2 * Q_R, Q_2, Q_3,
-                                                        scratch);
-    else
-        noalloc_sums_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double*>(f_dev), n_cells, 2 * Q_R, Q_2, Q_3,
-                                                         scratch);
-    noalloc_moments_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(scratch, n_cells, moments_dev);
-    return cudaGetLastError() == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
+    cudaError_t e;
+    if (precision == FDLB_FP32) {
+        const float* fp = static_cast<const float*>(f_dev);
+        void* args[] = {&fp, &nc, &nR, &n2, &n3, &scratch};
+        e = cudaLaunchKernel((const void*)noalloc_sums_kernel<float>, dim3(grid), dim3(256), args, 0, s);
+    } else {
+        const double* fp = static_cast<const double*>(f_dev);
+        void* args[] = {&fp, &nc, &nR, &n2, &n3, &scratch};
+        e = cudaLaunchKernel((const void*)noalloc_sums_kernel<double>, dim3(grid), dim3(256), args, 0, s);
+    }
+    if (e != cudaSuccess) return FDLB_ECUDA;
+    const double* sc = scratch;
+    void* margs[] = {&sc, &nc, &moments_dev};
+    e = cudaLaunchKernel((const void*)noalloc_moments_kernel, dim3((n_cells + 255) / 256), dim3(256), margs, 0, s);
+    return e == cudaSuccess ? FDLB_OK : FDLB_ECUDA;
 }

@@ -98,6 +98,8 @@ def load_library():
         "fdlb_clear_error": (c_int, [H]),
         "fdlb_step_kernel_times": (c_int, [H, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
         "fdlb_autotune": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+        "fdlb_set_autotune": (c_int, [H, c_int]),
+        "fdlb_get_tiling": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_launch_count": (c_int64, [H]),
         "fdlb_set_graph_steps": (c_int, [H, c_int]),
         "fdlb_set_kernel_timing": (c_int, [H, c_int]),
@@ -105,7 +107,9 @@ def load_library():
         "fdlb_get_stream": (c_int, [H, POINTER(c_void_p)]),
         "fdlb_set_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
         "fdlb_get_state_raw": (c_int, [H, c_int, c_void_p, c_int]),
+        "fdlb_state_bytes": (c_int, [H, POINTER(c_size_t)]),
         "fdlb_moments_noalloc": (c_int, [c_int, c_int, c_int, c_int, _DP, c_int, c_void_p, c_void_p, c_void_p]),
+        "fdlb_fp32_fma_peak": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_double)]),
         "fdlb_nn_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, POINTER(H)]),
         "fdlb_nn_destroy": (None, [H]),
         "fdlb_nn_num_params": (c_int, [H, POINTER(c_int64)]),
@@ -336,6 +340,15 @@ class Solver:
         _check(self._L.fdlb_autotune(self._h, byref(b), byref(k), byref(t)), "fdlb_autotune")
         return b.value, k.value, t.value
 
+    def set_autotune(self, mode):
+        """0 off, 1 tune batches at their first step (default), 2 tune every handle."""
+        _check(self._L.fdlb_set_autotune(self._h, int(mode)), "fdlb_set_autotune")
+
+    def tiling(self) -> dict:
+        b, k, t, c = c_int(), c_int(), c_int(), c_int()
+        _check(self._L.fdlb_get_tiling(self._h, byref(b), byref(k), byref(t), byref(c)), "fdlb_get_tiling")
+        return {"cells_per_tile": b.value, "slice_k": k.value, "threads": t.value, "closure_cells": c.value}
+
     def launch_count(self):
         return int(self._L.fdlb_launch_count(self._h))
 
@@ -372,6 +385,20 @@ class Solver:
         n = self.shape(q)
         return n[0] * n[1] * n[2] * n[3]
 
+    def state_bytes(self):
+        """Bytes of the whole batch's populations as the library stores them (instance -1 of
+        set_state_raw / get_state_raw)."""
+        nb = c_size_t()
+        _check(self._L.fdlb_state_bytes(self._h, byref(nb)), "fdlb_state_bytes")
+        return int(nb.value)
+
+    def moments_all(self) -> np.ndarray:
+        """Moments of every instance, [total cells][NMOM] in instance order."""
+        N = sum(self.shape(q)[0] for q in range(self.n_instances))
+        out = np.empty((N, NMOM))
+        _check(self._L.fdlb_get_moments(self._h, -1, out.ctypes.data_as(c_void_p), 0), "fdlb_get_moments")
+        return out
+
 
 # ---------------------------------------------------------------------- host-only set-up
 def quadrature(kind, Q):
@@ -391,6 +418,15 @@ def moments_noalloc(precision, Q_R, Q_2, Q_3, n_cells, f_dev_ptr, moments_dev_pt
     prec = _precision_code(precision)
     _check(L.fdlb_moments_noalloc(prec, Q_R, Q_2, Q_3, nodes, int(n_cells), c_void_p(f_dev_ptr),
                                   c_void_p(moments_dev_ptr), c_void_p(int(stream))), "fdlb_moments_noalloc")
+
+
+def fp32_fma_peak(stream=0, repeats=5):
+    """Measured FP32 FMA rate of the current device in TFLOP/s and the timed launch's duration in
+    ms (fdlb_fp32_fma_peak in include/fdlb.h)."""
+    L = load_library()
+    tf, ms = c_double(), c_double()
+    _check(L.fdlb_fp32_fma_peak(c_void_p(int(stream)), int(repeats), byref(tf), byref(ms)), "fdlb_fp32_fma_peak")
+    return tf.value, ms.value
 
 
 def derivative_matrix(kind, Q):

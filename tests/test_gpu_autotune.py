@@ -1,0 +1,60 @@
+"""The autotuner of the tile shapes (fdlb_autotune, automatic tuning at a batch's first step):
+it leaves the state alone, changes no result bit, and its cached choice is reused by a handle of
+the same momentum set, precision and size class."""
+import numpy as np
+import pytest
+
+from paper_2403_15051_gb300 import build as fbuild
+from paper_2403_15051_gb300 import fdlb
+
+from .cases import small_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fbuild.build()
+
+
+def _batch(precision):
+    return [small_case(precision=precision, n_cells=n, Kn=kn, eta0=e, T_wall=(1.0, t), u_wall=(u, 0.0), R=(1.0, r),
+                       Q=(8, 8, 8))
+            for n, kn, e, t, u, r in ((133, 0.1, 0.2, 1.1, 0.1, 2.0), (64, 0.05, 0.1, 1.3, 0.0, 3.0),
+                                      (217, 0.02, 0.25, 1.0, 0.3, 1.5), (40, 0.3, 0.05, 1.2, 0.2, 4.0))]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tuned_batch_steps_bit_for_bit_like_the_untuned_one(precision):
+    ds = _batch(precision)
+    A = fdlb.Solver(ds)
+    A.set_autotune(0)
+    B = fdlb.Solver(ds)  # tunes itself at its first step (a batch)
+    A.step(12)
+    B.step(12)
+    for q in range(len(ds)):
+        assert np.array_equal(A.get_f(q), B.get_f(q)), q
+    # an explicit re-tune in the middle of the run touches neither the state nor its sums
+    f_before = [B.get_f(q) for q in range(len(ds))]
+    m_before = [B.moments(q) for q in range(len(ds))]
+    B.autotune()
+    for q in range(len(ds)):
+        assert np.array_equal(B.get_f(q), f_before[q])
+        for k, v in B.moments(q).items():
+            assert np.array_equal(v, m_before[q][k]), (q, k)
+    A.step(13)
+    B.step(13)
+    for q in range(len(ds)):
+        assert np.array_equal(A.get_f(q), B.get_f(q)), q
+    assert B.info(0)["step"] == 25
+
+
+def test_cached_choice_is_reused():
+    ds = _batch("fp32")
+    A = fdlb.Solver(ds)
+    A.autotune()
+    t = A.tiling()
+    B = fdlb.Solver(ds)
+    B.step(1)  # automatic tuning: the cached choice of A's key
+    assert B.tiling() == t
+    assert 2 <= t["cells_per_tile"] <= 32 and t["closure_cells"] in (2, 4, 8, 16)
