@@ -32,9 +32,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# the CPU legs time the oracle on one host thread: numpy's BLAS and OpenMP pools are held to one
-# thread before numpy loads them (nothing on the GPU path uses them)
-for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+# the CPU legs time the oracle on one host thread: numpy's BLAS pools are held to one thread
+# before numpy loads them (the library's host set-up keeps its OpenMP threads: the Fischer-Methfessel
+# bands of a 512-instance batch take minutes on one core)
+for _var in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ[_var] = "1"
 
 import numpy as np  # noqa: E402

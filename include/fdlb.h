@@ -69,8 +69,9 @@ typedef struct fdlb_params {
     double R_in, R_out;    /* physical wall radii, R_out > R_in > 0 (Sec. IV)              */
     int n_cells;           /* radial cells on [R_in + sigma/2, R_out - sigma/2], >= 8       */
     double stretch_beta;   /* 0: uniform cells; > 0: tanh map with this beta (finer at walls) */
-    int Q_R, Q_2, Q_3;     /* half-range order on the radial axis (2 Q_R nodes), full-range
-                              orders on the two homogeneous axes; 1 <= Q <= 24             */
+    int Q_R, Q_2, Q_3;     /* half-range order on the radial axis (2 Q_R nodes), 1 <= Q_R <= 100
+                              (the paper's runs use 20, 60 and 100, Sec. IV); full-range
+                              orders on the two homogeneous axes, 1 <= Q_2, Q_3 <= 24       */
     int N_R, N_2, N_3;     /* equilibrium expansion orders (Sec. III.C), 0 <= N < Q;
                               negative: min(Q - 1, 7)                                      */
     double eta0;           /* mean reduced density eta0 = pi sigma^3 n0 / 6, in (0, 0.5)    */
@@ -169,6 +170,24 @@ int fdlb_step(fdlb_handle h, int64_t n_steps);
  * Returns FDLB_OK, FDLB_ENOTCONVERGED, FDLB_ETIMEOUT or FDLB_ENAN. */
 int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_seconds,
                        int check_every, int64_t* steps_taken, double* residual);
+
+/* Steady state at the FP64 level of accuracy for an FP32 handle: the FP32 form runs to the
+ * residual tolerance (as fdlb_run_to_steady; its steady state sits on the FP32 rounding floor,
+ * ~1e-5 to 1e-4 of the moment scales from the FP64 one for dense, small-Kn instances), then an FP64
+ * copy of the handle (the same instances, walls and time step) continues from that state to the
+ * tolerance, and the polished state, rounded to FP32, replaces the handle's populations (its
+ * moments are the FP64 steady state's to FP32 rounding; stepping on in FP32 drifts back to the
+ * floor).  The FP64 copy lives in `fp64_workspace` (fdlb_polish_workspace_bytes bytes, 256-byte
+ * aligned) when given, else in device memory the call allocates and frees.  steps_fp32 /
+ * steps_fp64 / residual: per-instance host arrays (may be NULL); residual is the FP64 phase's.
+ * The step counts of the handle grow by the FP64 steps.  For an FP64 handle it is
+ * fdlb_run_to_steady.  Returns as fdlb_run_to_steady for the FP64 phase (an error of the FP32
+ * phase other than ENOTCONVERGED / ETIMEOUT is returned at once).  The paper's method is
+ * precision-agnostic; this two-precision schedule is a library service. */
+int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
+                             void* fp64_workspace, size_t fp64_workspace_bytes, int64_t* steps_fp32,
+                             int64_t* steps_fp64, double* residual);
+int fdlb_polish_workspace_bytes(fdlb_handle h, size_t* bytes);
 
 /* Evaluate L(f) of the current state of one instance without advancing it (Secs. II-III);
  * host FP64 [cell][i][j][k]. */

@@ -135,15 +135,23 @@ def half_range_recurrence(Q: int, prec: int | None = None):
 def half_range_rule(Q: int):
     """Positive nodes (ascending) x_1..x_Q and weights lambda (summing to 1/2) of the
     Q-point half-range rule, plus the recurrence coefficients used to build them.
+
+    Nodes: the eigenvalues of the Jacobi matrix (the roots of h_Q).  Weights: the closed form of
+    Sec. III.A, w_i = x_i a_{Q-1}^2 / (h_{Q-1}(x_i)^2 [x_i + h_Q(0)^2 / sqrt(2 pi)]) with
+    a_{Q-1} = (leading coefficient of h_Q) / (that of h_{Q-1}) = 1 / sqrt(beta_Q); it keeps its
+    relative accuracy for the smallest weights (below 1e-100 at Q = 100), which the first
+    components of the Jacobi matrix's eigenvectors do not.
     """
-    alpha, beta = half_range_recurrence(Q)
-    J = np.diag(alpha)
+    alpha, beta = half_range_recurrence(Q + 1)
+    J = np.diag(alpha[:Q])
     for k in range(1, Q):
         J[k, k - 1] = J[k - 1, k] = math.sqrt(beta[k])
-    x, V = np.linalg.eigh(J)
-    lam = beta[0] * V[0, :] ** 2
-    order = np.argsort(x)
-    return x[order].copy(), lam[order].copy(), alpha, beta
+    x = np.sort(np.linalg.eigvalsh(J))
+    H = half_poly(np.concatenate([x, [0.0]]), alpha, beta, Q)
+    hQ0 = H[Q, -1]
+    a = 1.0 / math.sqrt(beta[Q])
+    lam = x * a ** 2 / (H[Q - 1, :Q] ** 2 * (x + hQ0 ** 2 / math.sqrt(2.0 * math.pi)))
+    return x, lam, alpha[:Q].copy(), beta[:Q].copy()
 
 
 def half_range_axis(Q: int):

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libfdlb_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["fdlb.cu", "kernels_aux.cu", "stream_float_0.cu", "stream_float_1.cu", "stream_double_0.cu",
               "stream_double_1.cu", "step_float_0.cu", "step_float_1.cu", "step_double_0.cu", "step_double_1.cu",
-              "noalloc.cu", "nn.cu", "probe.cu"]
+              "noalloc.cu", "nn.cu", "probe.cu", "kr_contract.cu"]
 CPP_SOURCES = ["setup.cpp"]
 
 

@@ -21,6 +21,9 @@ namespace {
 
 constexpr double kPiH = 3.14159265358979323846;
 constexpr size_t kAlign = 256;
+// Radial node counts from which the K^h contraction runs as its own kernel (the fused stage then
+// reads K^h f; below, the stage contracts from a K^h table in shared memory).
+constexpr int kKrKernelMinNodes = 32;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -28,7 +31,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
-        rprev, rout, total;
+        rprev, rout, krf, krB, total;
 };
 
 }  // namespace
@@ -93,6 +96,10 @@ struct Solver {
     bool timing = false;
     int programmatic = 1;  // closure and stage kernels overlap their prologues with the predecessor
     int tensor = 0;        // K^h contraction on the tensor cores where available
+    void* krf = nullptr;   // K^h f of the stage input (contraction kernel), when allocated
+    int krg_on = 0;        // the contraction kernel is in use
+    float* krB = nullptr;  // K^h as TF32 pairs in the tensor-core kernel's layout (FP32 populations)
+    int kr_tc = 0;         // the contraction kernel runs on the tensor cores
     int mma_on = 0;        // ... and in use for the current tiling
     // persistent step kernel (closure + stage per tile, grid barriers between stages)
     int fused = 0;         // use it where the configuration allows (off by default: slower on GB300)
@@ -193,6 +200,43 @@ void build_tables(Solver& S) {
     M.o_h0 = put(h0);
 }
 
+// The tensor-core contraction's K^h table: per chunk of 32 values of a, the TF32 high part then the
+// low part of K^h[n][a] (n < Npad = 2Q_R rounded up to 16; zero beyond 2Q_R) in the kernel's
+// shared-memory layout, float (n / 8) * 256 + (a % 32 / 4) * 32 + (n % 8) * 4 + a % 4.
+int kr_npad(int nR) { return (nR + 15) / 16 * 16; }
+size_t kr_split_floats(int nR) {
+    const int nk = ((nR + 7) / 8 * 8 + 31) / 32;
+    return (size_t)nk * kr_npad(nR) * 64;
+}
+float tf32_round(float x) {
+    // round to the 10-bit TF32 mantissa, ties away from zero (the rule of cvt.rna.tf32.f32)
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+std::vector<float> kr_split_table(const std::vector<double>& tab, int o_KR, int nR) {
+    const int Npad = kr_npad(nR), nk = ((nR + 7) / 8 * 8 + 31) / 32;
+    std::vector<float> out(kr_split_floats(nR), 0.f);
+    for (int kc = 0; kc < nk; ++kc) {
+        float* hi = out.data() + (size_t)kc * Npad * 64;
+        float* lo = hi + (size_t)Npad * 32;
+        for (int n = 0; n < nR; ++n)
+            for (int kk = 0; kk < 32; ++kk) {
+                const int a = kc * 32 + kk;
+                if (a >= nR) continue;
+                const float k32 = (float)tab[o_KR + (size_t)n * nR + a];
+                const float h = tf32_round(k32);
+                const size_t off = (size_t)(n / 8) * 256 + (kk / 4) * 32 + (n % 8) * 4 + kk % 4;
+                hi[off] = h;
+                lo[off] = tf32_round(k32 - h);
+            }
+    }
+    return out;
+}
+
 Layout make_layout(const Solver& S) {
     Layout L{};
     size_t off = 0;
@@ -227,6 +271,10 @@ Layout make_layout(const Solver& S) {
     L.gbar = take(64);  // grid barrier counter of the persistent step kernel
     L.rprev = take((size_t)S.total_cells * 4 * sizeof(double));
     L.rout = take((size_t)S.n_inst * 10 * sizeof(double));
+    // K^h f of the stage input for the contraction kernel (large radial orders only)
+    L.krf = take(S.nR >= kKrKernelMinNodes ? S.f_elems * S.tsize : 0);
+    // K^h as TF32 pairs for the tensor-core contraction kernel (FP32 populations)
+    L.krB = take(S.nR >= kKrKernelMinNodes && S.tsize == 4 ? kr_split_floats(S.nR) * sizeof(float) : 0);
     L.total = off;
     return L;
 }
@@ -369,7 +417,7 @@ cudaError_t launch_step_dispatch(const Solver& S, const StepArgs* P, int* blocks
 int plan_step_kernel(Solver& S, int n_items) {
     S.fused_on = 0;
     S.grid_step = 0;
-    if (!S.fused || !S.scfg.spec || S.M.slices != 1 || !S.use_bulk || S.threads < 5 * 32 || S.max_tile < 1 ||
+    if (!S.fused || S.krg_on || !S.scfg.spec || S.M.slices != 1 || !S.use_bulk || S.threads < 5 * 32 || S.max_tile < 1 ||
         S.max_tile > kClosureCells || n_items < 1)
         return FDLB_OK;
     // shared memory: the stage's plan, then [staged band rows | closure tables | band-union
@@ -512,10 +560,11 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
     S.scfg = cfg;
     S.threads = nt;
-    S.mma_on = S.tensor && cfg.spec && cfg.vw == 4 && S.tsize == 4 && S.nR % 8 == 0;
+    S.mma_on = S.tensor && cfg.spec && cfg.vw == 4 && S.tsize == 4 && S.nR % 8 == 0 && !S.krg_on;
     // shrink the tile until it fits in shared memory
     for (;;) {
-        StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize, S.mma_on ? 1 : 0);
+        StreamSmem P = stream_smem_plan(S.B, Ms, S.nR, S.n2, S.n3, nt / 32, (int)S.tsize, S.mma_on ? 1 : 0,
+                                        S.krg_on ? 1 : 0);
         if ((size_t)P.total <= S.smem_optin || S.B <= 2) {
             S.smem_stream = P.total;
             break;
@@ -614,9 +663,30 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
 
 int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, int mode);
 
+// K^h f of buffer `in` by the contraction kernel (large radial orders).
+int launch_kr_buf(Solver& S, int in) {
+    const int grid = std::max(1, std::min(S.grid_stream, S.n_sm * 8));
+    cudaError_t e;
+    if (S.kr_tc)
+        e = launch_kr_contract_tc((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d, S.krB, S.M,
+                                  kr_npad(S.nR), S.err, std::max(1, std::min(S.grid_stream, S.n_sm)), S.stream);
+    else if (S.precision == FDLB_FP32)
+        e = launch_kr_contract<float>((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d,
+                                      (const float*)S.tabT + S.M.o_KR, S.M, grid, S.stream);
+    else
+        e = launch_kr_contract<double>((const double*)S.f[in], (double*)S.krf, S.sitems, S.n_sitems, S.inst_d,
+                                       (const double*)S.tabT + S.M.o_KR, S.M, grid, S.stream);
+    S.launches++;
+    return cuda_status(e);
+}
+
 // One right-hand-side evaluation and RK combination: closure launch, then the fused stage.
 // In timing mode each launch is bracketed by events and its duration accumulated.
 int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mode, int write_ca = 0) {
+    if (S.krg_on) {
+        const int rc = launch_kr_buf(S, in);
+        if (rc) return rc;
+    }
     if (S.timing) {
         FDLB_CUDA(cudaEventRecord(S.tev[0], S.stream));
         int rc = launch_closure_buf(S, in, write_ca);
@@ -670,6 +740,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.programmatic = S.programmatic;
     A.mma = S.mma_on;
     A.tx_extra = S.test_tx_extra;
+    A.krf = S.krg_on ? S.krf : nullptr;
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
@@ -966,7 +1037,7 @@ int do_steps(Solver& S, int64_t n) {
         if (rc) return rc;
         while (n - done >= S.graph_steps) {
             FDLB_CUDA(cudaGraphLaunch(S.gexec, S.stream));
-            S.launches += (int64_t)S.graph_steps * 6;
+            S.launches += (int64_t)S.graph_steps * (S.krg_on ? 9 : 6);
             done += S.graph_steps;
         }
     }
@@ -1037,6 +1108,16 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.gbar = (unsigned*)(R.ws + L.gbar);
     R.rprev = (double*)(R.ws + L.rprev);
     R.rout = (double*)(R.ws + L.rout);
+    R.krf = R.nR >= kKrKernelMinNodes ? (void*)(R.ws + L.krf) : nullptr;
+    R.krg_on = R.krf != nullptr;
+    if (R.krg_on && R.precision == FDLB_FP32) {
+        R.krB = (float*)(R.ws + L.krB);
+        const std::vector<float> kb = kr_split_table(R.tab_h, R.M.o_KR, R.nR);
+        FDLB_CUDA(cudaMemcpyAsync(R.krB, kb.data(), kb.size() * sizeof(float), cudaMemcpyHostToDevice, R.stream));
+        FDLB_CUDA(cudaStreamSynchronize(R.stream));
+        R.tensor = 1;  // the tensor-core contraction by default
+        R.kr_tc = 1;
+    }
     FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
     // tables, instances, geometry, walls, FM band
     FDLB_CUDA(cudaMemcpyAsync(R.tab, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
@@ -1406,6 +1487,94 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
     return status;
 } FDLB_HOST_CATCH
 
+// The FP64 twin of an FP32 handle: the same instances (walls as set, the time step in use) with
+// FP64 populations, in `workspace` when given.
+static int make_fp64_twin(Solver* S, void* workspace, size_t ws_bytes, fdlb_handle* out) {
+    std::vector<fdlb_params> ps(S->n_inst);
+    for (int q = 0; q < S->n_inst; ++q) {
+        ps[q] = S->setup[q].p;
+        ps[q].precision = FDLB_FP64;
+        ps[q].dt = S->setup[q].dt;
+    }
+    return fdlb::solver_create(ps.data(), S->n_inst, S->stream, workspace, ws_bytes, out);
+}
+
+int fdlb_polish_workspace_bytes(fdlb_handle h, size_t* bytes) try {
+    Solver* S = SOL(h);
+    if (!S || !bytes) return FDLB_EINVAL;
+    std::vector<fdlb_params> ps(S->n_inst);
+    for (int q = 0; q < S->n_inst; ++q) {
+        ps[q] = S->setup[q].p;
+        ps[q].precision = FDLB_FP64;
+        ps[q].dt = S->setup[q].dt;
+    }
+    return fdlb_workspace_bytes(ps.data(), S->n_inst, bytes);
+} FDLB_HOST_CATCH
+
+int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
+                             void* fp64_workspace, size_t fp64_workspace_bytes, int64_t* steps_fp32,
+                             int64_t* steps_fp64, double* residual) try {
+    Solver* S = SOL(h);
+    if (!S || !(tol > 0.0) || max_steps < 1 || check_every < 1) return FDLB_EINVAL;
+    const int n = S->n_inst;
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<int64_t> st32(n, 0), st64(n, 0);
+    std::vector<double> res(n, 0.0);
+    if (S->precision != FDLB_FP32) {
+        const int rc = fdlb_run_to_steady(h, tol, max_steps, max_seconds, check_every, st64.data(), res.data());
+        for (int q = 0; q < n; ++q) {
+            if (steps_fp32) steps_fp32[q] = 0;
+            if (steps_fp64) steps_fp64[q] = st64[q];
+            if (residual) residual[q] = res[q];
+        }
+        return rc;
+    }
+    // 1. the FP32 form to the tolerance (its residual reaches it; its steady state sits at the FP32
+    // rounding floor, ~1e-5..1e-4 of the moment scales away from the FP64 one)
+    int rc = fdlb_run_to_steady(h, tol, max_steps, max_seconds, check_every, st32.data(), res.data());
+    if (rc != FDLB_OK && rc != FDLB_ENOTCONVERGED && rc != FDLB_ETIMEOUT) return rc;
+    // 2. the FP64 polish from the FP32 steady state
+    fdlb_handle th = nullptr;
+    rc = make_fp64_twin(S, fp64_workspace, fp64_workspace_bytes, &th);
+    if (rc) return rc;
+    Solver* T = SOL(th);
+    T->autotune_mode = S->autotune_mode;
+    for (int q = 0; q < n; ++q) {
+        const long long cnt = (long long)S->setup[q].p.n_cells * S->Np;
+        fdlb::launch_convert((const float*)S->f[0] + S->f_off[q], 1, (double*)T->f[0] + T->f_off[q], 0, cnt, S->stream);
+    }
+    rc = fdlb::cuda_status(cudaGetLastError());
+    if (!rc) rc = fdlb::launch_moments_all(*T, 0);
+    double left = 0.0;
+    if (max_seconds > 0.0) {
+        left = max_seconds - std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (left <= 0.0) left = 1e-9;
+    }
+    int rc64 = rc ? rc : fdlb_run_to_steady(th, tol, max_steps, left, check_every, st64.data(), res.data());
+    // 3. the polished state, rounded to FP32, back into this handle (its moments are those of the
+    // FP64 steady state to FP32 rounding, ~1e-7 of their scales)
+    if (rc64 == FDLB_OK || rc64 == FDLB_ENOTCONVERGED || rc64 == FDLB_ETIMEOUT) {
+        for (int q = 0; q < n; ++q) {
+            const long long cnt = (long long)S->setup[q].p.n_cells * S->Np;
+            fdlb::launch_convert((const double*)T->f[0] + T->f_off[q], 0, (float*)S->f[0] + S->f_off[q], 1, cnt,
+                                 S->stream);
+            S->inst_steps[q] += st64[q];
+            S->last_res[q] = res[q];
+        }
+        rc = fdlb::cuda_status(cudaGetLastError());
+        if (!rc) rc = fdlb::launch_moments_all(*S, 0);
+        S->prev_valid = false;
+        if (rc) rc64 = rc;
+    }
+    fdlb_destroy(th);
+    for (int q = 0; q < n; ++q) {
+        if (steps_fp32) steps_fp32[q] = st32[q];
+        if (steps_fp64) steps_fp64[q] = st64[q];
+        if (residual) residual[q] = res[q];
+    }
+    return rc64;
+} FDLB_HOST_CATCH
+
 int fdlb_get_info(fdlb_handle h, int instance, fdlb_info* out) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !out) return FDLB_EINVAL;
@@ -1592,6 +1761,16 @@ int fdlb_set_tensor_contraction(fdlb_handle h, int enable, int* in_use) try {
     Solver* S = SOL(h);
     if (!S) return FDLB_EINVAL;
     S->tensor = enable ? 1 : 0;
+    if (S->krg_on) {
+        // large radial orders: the contraction kernel on the tensor cores (FP32) or the CUDA cores
+        S->kr_tc = S->tensor && S->krB ? 1 : 0;
+        if (S->gexec) {
+            cudaGraphExecDestroy(S->gexec);
+            S->gexec = nullptr;
+        }
+        if (in_use) *in_use = S->kr_tc;
+        return FDLB_OK;
+    }
     const int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
     if (in_use) *in_use = S->mma_on;
     return rc;

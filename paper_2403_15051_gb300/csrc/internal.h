@@ -24,7 +24,8 @@
 namespace fdlb {
 
 
-constexpr int kMaxQ = 24;          // largest quadrature order per axis
+constexpr int kMaxQ = 24;          // largest full-range quadrature order (the two homogeneous axes)
+constexpr int kMaxQR = 100;        // largest half-range order of the radial axis (2 kMaxQR nodes)
 constexpr int kMaxN = 7;           // largest equilibrium expansion order handled on the device
 constexpr int kNumSums = 13;       // raw quadrature sums per cell (Eq. mom_quad)
 constexpr int kCARecord = 12;      // per-cell closure record written by the closure kernel

@@ -89,6 +89,8 @@ struct StageArgs {
     int programmatic;              // launched with programmatic stream serialization
     int mma;                       // K^h contraction on the tensor cores (FP32 compile-time shapes)
     int tx_extra;                  // test hook: bytes the staged-copy barrier waits for beyond the copy
+    const void* krf;               // K^h f of f_in from the contraction kernel (T, layout of f), or
+                                   // null: the stage contracts from the K^h table in shared memory
 };
 
 struct ClosureArgs {

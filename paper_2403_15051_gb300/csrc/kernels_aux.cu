@@ -276,6 +276,26 @@ void launch_residual(const double* sums, int slices, const InstDev* inst, const 
     residual_kernel<<<n_inst < 1024 ? n_inst : 1024, 256, 0, s>>>(sums, slices, inst, geo, prev, out, n_inst, save);
 }
 
+// Populations of one precision copied into the other (rounding to nearest for FP64 -> FP32).
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ src, B* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (B)src[i];
+}
+
+void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s) {
+    const long long g = (n + 255) / 256;
+    const int grid = (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
+    if (src_fp32 && !dst_fp32)
+        convert_kernel<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)dst, n);
+    else if (!src_fp32 && dst_fp32)
+        convert_kernel<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)dst, n);
+    else if (src_fp32)
+        convert_kernel<float, float><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, n);
+    else
+        convert_kernel<double, double><<<grid, 256, 0, s>>>((const double*)src, (double*)dst, n);
+}
+
 template void launch_ca<float>(const double*, const void*, double*, int, int, cudaStream_t);
 template void launch_ca<double>(const double*, const void*, double*, int, int, cudaStream_t);
 template void launch_dens_from_sums<float>(const double*, float*, long long, cudaStream_t);

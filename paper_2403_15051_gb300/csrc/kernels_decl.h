@@ -49,7 +49,7 @@ struct StreamSmem {
 // order, then K^h with row stride kr_stride(nR), K_3 with row stride n3+1, the nodes and weights,
 // the wall Maxwellians), the cell geometry and the per-warp partial sums.
 __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize,
-                                                       int mma = 0) {
+                                                       int mma = 0, int krg = 0) {
     auto al = [](long long x) { return (int)((x + 15) & ~15LL); };
     StreamSmem s;
     int off = 16;  // mbarrier
@@ -58,7 +58,8 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
     s.rec = off;
     off += al((long long)B * record_stride(nR, n2, n3) * tsize);
     s.tabs = off;
-    off += al((long long)(2 * (nR + n2 + n3) + nR * kr_stride(nR) + kr_offset(n2, tsize) + n3 * (n3 + 1) +
+    // (no K^h table when K^h f comes from the contraction kernel: krg)
+    off += al((long long)(2 * (nR + n2 + n3) + (krg ? 0 : nR) * kr_stride(nR) + kr_offset(n2, tsize) + n3 * (n3 + 1) +
                           2 * (nR + n2 + n3)) * tsize);
     s.geo = off;
     off += al((long long)B * 3 * tsize);
@@ -112,6 +113,21 @@ FDLB_STEP_DECL(float, 1)
 FDLB_STEP_DECL(double, 0)
 FDLB_STEP_DECL(double, 1)
 #undef FDLB_STEP_DECL
+
+// K^h f of the populations of the stage items' cells (Sec. III.B half-range derivative matrix
+// applied along the radial momentum axis), written in the layout of f: the CUDA-core kernel
+// (any precision) or, for FP32 populations where available, the tensor-core kernel.
+template <typename T>
+cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int* n_items, const InstDev* inst,
+                               const T* KR, const MomSet& M, int grid, cudaStream_t s);
+
+// The tensor-core form (FP32): Bsplit holds K^h as TF32 pairs in the kernel's shared-memory layout
+// (kr_split_table), Npad = 2Q_R rounded up to 16; err is set when a bounded wait runs out.
+cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,
+                                  const float* Bsplit, const MomSet& M, int Npad, int* err, int grid, cudaStream_t s);
+size_t kr_tc_smem_bytes(int Npad);
+
+void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s);
 
 void launch_residual(const double* sums, int slices, const InstDev* inst, const double* geo, double* prev, double* out,
                      int n_inst, int save, cudaStream_t s);

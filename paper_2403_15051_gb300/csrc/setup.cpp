@@ -4,7 +4,7 @@
 // Quadrature (Sec. III.A): full-range Gauss-Hermite rules from the Jacobi matrix of the
 // probabilists' Hermite recurrence; half-range rules from recurrence coefficients obtained by
 // the discretised Stieltjes procedure on a composite Gauss-Legendre discretisation of
-// omega(x) = exp(-x^2/2)/sqrt(2 pi) on [0, 40].  Nodes are the eigenvalues of the Jacobi
+// omega(x) = exp(-x^2/2)/sqrt(2 pi) on [0, 40] (320 panels of 20 points).  Nodes are the eigenvalues of the Jacobi
 // matrix found by Sturm-sequence bisection; weights are the Christoffel numbers
 // 1 / sum_l p_l(x)^2 of the orthonormal polynomials.
 #include <algorithm>
@@ -125,10 +125,12 @@ void full_range_rule(int Q, std::vector<double>& x, std::vector<double>& w) {
 }
 
 void half_range_recurrence(int n, std::vector<double>& alpha, std::vector<double>& beta) {
-    // composite Gauss-Legendre discretisation of omega on [0, 40]: 80 panels x 20 points
+    // composite Gauss-Legendre discretisation of omega on [0, 40]: 320 panels x 20 points (panels
+    // of 1/8: the recurrence coefficients agree with a 600-digit moment-based computation to 1e-15
+    // up to order 101; 80 panels left a 1e-3 error at that order)
     std::vector<double> gx, gw;
     gauss_legendre(20, gx, gw);
-    const int panels = 80;
+    const int panels = 320;
     const double h = 40.0 / panels;
     std::vector<double> t, W;
     for (int p = 0; p < panels; ++p)
@@ -476,7 +478,7 @@ int validate_params(const fdlb_params& p) {
     const int Qs[3] = {p.Q_R, p.Q_2, p.Q_3};
     const int Ns[3] = {p.N_R, p.N_2, p.N_3};
     for (int a = 0; a < 3; ++a) {
-        if (Qs[a] < 1 || Qs[a] > kMaxQ) return FDLB_EINVAL;
+        if (Qs[a] < 1 || Qs[a] > (a == 0 ? kMaxQR : kMaxQ)) return FDLB_EINVAL;
         if (Ns[a] >= Qs[a] || Ns[a] > kMaxN) return FDLB_EINVAL;
     }
     if (!(p.eta0 > 0.0 && p.eta0 < 0.5)) return FDLB_EINVAL;

@@ -159,14 +159,15 @@ __device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
     const int rs = record_stride(nR, n2, n3);                                                                    \
     constexpr bool kMMA = sizeof(T) == 4 && NR_ > 0 && NR_ % 8 == 0 && VW == 4;                                  \
     const bool use_mma = kMMA && A.mma;                                                                          \
-    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T), use_mma ? 1 : 0);         \
+    const StreamSmem P = stream_smem_plan(A.B, Ms, nR, n2, n3, nwarps, (int)sizeof(T), use_mma ? 1 : 0,          \
+                                          A.krf ? 1 : 0);                                                        \
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                                                       \
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);                                                               \
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);                                                           \
     T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);                                                            \
     const int krs = kr_stride(nR);                                                                               \
     T* sKR = sK2 + kr_offset(n2, (int)sizeof(T));                                                                \
-    T* sK3 = sKR + nR * krs;                                                                                     \
+    T* sK3 = sKR + (A.krf ? 0 : nR) * krs;                                                                       \
     T* sp_R = sK3 + n3 * (n3 + 1);                                                                               \
     T* sp_2 = sp_R + nR;                                                                                         \
     T* sp_3 = sp_2 + n2;                                                                                         \
@@ -206,7 +207,8 @@ __device__ __forceinline__ void stream_tables(const StageArgs& A, const MomSet& 
         sp_3[e] = tab[M.o_p3 + e];
         sw_3[e] = tab[M.o_w3 + e];
     }
-    for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * krs + e % nR] = tab[M.o_KR + e];
+    if (!A.krf)
+        for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * krs + e % nR] = tab[M.o_KR + e];
     for (int e = tid; e < n2 * n2; e += NT) {
         const int j = e / n2, b = e % n2;
         sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = tab[M.o_K2 + e];
@@ -503,6 +505,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 {
                     if (kMMA && use_mma) {
                         ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
+                    } else if (A.krf) {
+                        // from the contraction kernel, in the layout of f
+                        ldg_vec<T, VW>(reinterpret_cast<const T*>(A.krf) + I.f_off + (long long)c * Np + slice_off + vb, KRf);
                     } else {
                         const T* col = fc + kk * nR * n2 + jb * VW;
                         const T* kr = sKR + i * krs;

@@ -81,6 +81,9 @@ def load_library():
         "fdlb_get_f": (c_int, [H, c_int, _DP]),
         "fdlb_step": (c_int, [H, c_int64]),
         "fdlb_run_to_steady": (c_int, [H, c_double, c_int64, c_double, c_int, POINTER(c_int64), POINTER(c_double)]),
+        "fdlb_run_to_steady_mixed": (c_int, [H, c_double, c_int64, c_double, c_int, c_void_p, c_size_t,
+                                             POINTER(c_int64), POINTER(c_int64), POINTER(c_double)]),
+        "fdlb_polish_workspace_bytes": (c_int, [H, POINTER(c_size_t)]),
         "fdlb_eval_rhs": (c_int, [H, c_int, _DP]),
         "fdlb_get_moments": (c_int, [H, c_int, c_void_p, c_int]),
         "fdlb_get_closure": (c_int, [H, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -270,6 +273,26 @@ class Solver:
         res = (c_double * n)()
         rc = self._L.fdlb_run_to_steady(self._h, tol, int(max_steps), float(max_seconds), int(check_every), st, res)
         return rc, np.array(st[:], dtype=np.int64), np.array(res[:])
+
+    def run_to_steady_mixed(self, tol=1e-8, max_steps=1_000_000, max_seconds=0.0, check_every=100):
+        """FP32 to the tolerance, then the library's FP64 polish (fdlb_run_to_steady_mixed); the
+        FP64 copy's device memory comes from torch when this handle's does.  Returns (status,
+        FP32 steps, FP64 steps, residuals)."""
+        n = self.n_instances
+        s32, s64 = (c_int64 * n)(), (c_int64 * n)()
+        res = (c_double * n)()
+        ws, nb_v = None, 0
+        torch = _torch_cuda() if self._workspace is not None else None
+        if torch is not None:
+            nb = c_size_t()
+            _check(self._L.fdlb_polish_workspace_bytes(self._h, byref(nb)), "fdlb_polish_workspace_bytes")
+            nb_v = int(nb.value)
+            ws = torch.empty(nb_v + 256, dtype=torch.uint8, device="cuda")
+        ptr = c_void_p((ws.data_ptr() + 255) // 256 * 256 if ws is not None else 0)
+        rc = self._L.fdlb_run_to_steady_mixed(self._h, tol, int(max_steps), float(max_seconds), int(check_every), ptr,
+                                              c_size_t(nb_v), s32, s64, res)
+        del ws
+        return rc, np.array(s32[:], dtype=np.int64), np.array(s64[:], dtype=np.int64), np.array(res[:])
 
     def eval_rhs(self, q=0):
         out = np.empty(self.shape(q))

@@ -31,25 +31,29 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("Q", [1, 2, 4, 8, 12, 16, 24])
+@pytest.mark.parametrize("Q", [1, 2, 4, 8, 12, 16, 24, 40, 60, 100])
 def test_quadrature_matches_oracle(lib, Q):
     x, w = fdlb.quadrature(fdlb.QUAD_HALF, Q)
     xo, wo = oquad.half_range_axis(Q)
     assert np.allclose(x, xo, rtol=0, atol=1e-13 * max(1.0, np.abs(xo).max()))
     assert np.allclose(w, wo, rtol=1e-12)
+    if Q > 24:  # the full-range axes stop at order 24
+        return
     x, w = fdlb.quadrature(fdlb.QUAD_FULL, Q)
     xo, wo = oquad.full_range_rule(Q)
     assert np.allclose(x, xo, atol=1e-13 * max(1.0, np.abs(xo).max()))
     assert np.allclose(w, wo, rtol=1e-12)
 
 
-@pytest.mark.parametrize("Q", [1, 2, 4, 8, 12, 24])
+@pytest.mark.parametrize("Q", [1, 2, 4, 8, 12, 24, 40, 100])
 def test_derivative_matrices_match_oracle(lib, Q):
     K = fdlb.derivative_matrix(fdlb.QUAD_HALF, Q)
     x, lam, a, b = oquad.half_range_rule(Q)
     p, w = np.concatenate([x, -x]), np.concatenate([lam, lam])
     Ko = okm.k1_half(p, w, a, b)
-    assert np.allclose(K * w[None, :], Ko * w[None, :], atol=1e-13)
+    assert np.allclose(K * w[None, :], Ko * w[None, :], atol=1e-13 * max(1.0, np.abs(Ko * w[None, :]).max()))
+    if Q > 24:  # the full-range axes stop at order 24
+        return
     K2 = fdlb.derivative_matrix(fdlb.QUAD_FULL, Q)
     xf, wf = oquad.full_range_rule(Q)
     K2o = okm.k2_full(xf, wf)

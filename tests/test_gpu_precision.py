@@ -1,0 +1,51 @@
+"""The precision pattern at steady state: FP32 populations reach a steady state on the FP32
+rounding floor, some 1e-5 to 1e-4 of the moment scales away from the FP64 one for dense, small-Kn
+instances; the library's two-precision schedule (fdlb_run_to_steady_mixed: FP32 to the
+tolerance, then an FP64 polish on the device) brings every moment within 1e-5 of the FP64 steady
+state.  The reference is the FP64 form run to a residual a hundred times tighter."""
+import numpy as np
+import pytest
+
+from paper_2403_15051_gb300 import build as fbuild
+from paper_2403_15051_gb300 import fdlb
+
+from .cases import compare_moments, oracle_problem, small_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fbuild.build()
+
+
+CASES = [
+    # dense, small Kn: the largest FP32 floor
+    dict(n_cells=64, Kn=0.02, eta0=0.25, T_wall=(1.0, 1.2), u_wall=(0.2, 0.0), R=(1.0, 2.0)),
+    # a batch member of the sweep distribution, moderate density
+    dict(n_cells=64, Kn=0.05, eta0=0.1, T_wall=(1.0, 1.25), u_wall=(0.25, 0.0), R=(1.0, 3.5)),
+]
+
+
+def test_fp32_with_fp64_polish_matches_fp64_steady_state():
+    ds = [small_case(precision="fp64", **c) for c in CASES]
+    R = fdlb.Solver(ds)
+    rc, _, res = R.run_to_steady(tol=1e-12, max_steps=600_000, check_every=500)
+    assert np.all(res <= 1e-11), res
+    ref = [R.moments(q) for q in range(len(ds))]
+    R.close()
+    F = fdlb.Solver([dict(d, precision="fp32") for d in ds])
+    rc32, st32, st64, res_m = F.run_to_steady_mixed(tol=1e-10, max_steps=600_000, check_every=500)
+    assert rc32 == 0 and np.all(res_m <= 1e-10), (rc32, res_m)
+    assert np.all(st32 > 0) and np.all(st64 > 0)
+    P32 = fdlb.Solver([dict(d, precision="fp32") for d in ds])
+    P32.run_to_steady(tol=1e-8, max_steps=600_000, check_every=500)
+    for q, d in enumerate(ds):
+        P = oracle_problem(d)
+        mo = {"n": ref[q]["n"], "T": ref[q]["T"], "P01": ref[q]["P12"],
+              "u": np.stack([ref[q][f"u{a + 1}"] for a in range(3)], -1),
+              "q": np.stack([ref[q][f"q{a + 1}"] for a in range(3)], -1)}
+        err_mixed = compare_moments(F.moments(q), mo, P)
+        err_fp32 = compare_moments(P32.moments(q), mo, P)
+        print("instance", q, "FP32 alone", err_fp32, "FP32 + FP64 polish", err_mixed)
+        assert max(err_mixed.values()) <= 1e-5, (q, err_mixed)

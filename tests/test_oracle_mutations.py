@@ -135,8 +135,8 @@ CASES = [
     ("residual scaled by the new profile", "solver", "/ (K * max(float(np.max(np.abs(a))), s))",
      "/ (K * max(float(np.max(np.abs(b))), s))", t_solver, "S", "test_moment_residual_on_a_hand_computed_two_cell_case", ()),
     # quadrature (Sec. III.A)
-    ("half-range weights scale", "quadrature", "lam = beta[0] * V[0, :] ** 2", "lam = V[0, :] ** 2",
-     t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),
+    ("half-range weight formula", "quadrature", "(x + hQ0 ** 2 / math.sqrt(2.0 * math.pi))",
+     "(x + hQ0 ** 2 / math.sqrt(math.pi))", t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),
     ("half-range polynomial recurrence", "quadrature", "out[l + 1] = ((x - alpha[l]) * out[l] - b[l] * out[l - 1]) / b[l + 1]",
      "out[l + 1] = ((x - alpha[l]) * out[l] + b[l] * out[l - 1]) / b[l + 1]", t_quad, "quad",
      "test_half_polynomials_orthonormal_and_roots", (5,)),
