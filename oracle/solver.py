@@ -22,6 +22,16 @@ The right-hand side L(f) = -advection - force + collision (A1 reading of the col
   cells per side (incoming: wall Maxwellian, outgoing: cubic extrapolation in the cell index).
 
 Time stepping: the three-stage TVD (SSP) Runge-Kutta scheme of Shu and Osher (Sec. III).
+
+Reduced cylinder (``reduced=True``; the p_z axis integrated out at the level of the model
+equation, Sec. III.A's remark on the trivial axes of Couette flow): the pair phi = int f dp_z,
+chi = int p_z^2 f dp_z on the (p_R, p_phi) quadrature, stored as f[c, i, j, 0] and f[c, i, j, 1].
+With f even in p_z (u_z = q_z = 0, no strain involving z), advection and the curvature force act
+on each member as on f (neither involves p_z); the moments need p_z only through
+int p_z^2 f = sum chi; the collision of each member is the p_z-integral of the full one, which
+replaces the p_z^2 carried by xi^2 with T (phi) or 3T (chi, from int p_z^4 g = 3 T^2) and weights
+chi's equilibrium by T.  The diffuse walls emit the wall Maxwellian pair (1, T_w) and balance the
+mass flux of phi alone.
 """
 from __future__ import annotations
 
@@ -69,6 +79,7 @@ class Problem:
     T_wall: tuple = (1.0, 1.0)     # (inner, outer)
     u_wall: tuple = (0.0, 0.0)     # tangential speed on axis 2 (cylinder only)
     extra: dict = field(default_factory=dict)
+    reduced: bool = False          # cylinder with p_z integrated out: f[..., 0] = phi, f[..., 1] = chi
 
     @property
     def shape(self):
@@ -86,7 +97,9 @@ def default_order(Q):
 
 def make_problem(geometry, R_in, R_out, n_cells, Q_R, Q_2, Q_3, eta0, Kn=None, sigma=None,
                  beta=0.0, N_R=None, N_2=None, N_3=None, chi_model=RET_FM,
-                 T_wall=(1.0, 1.0), u_wall=(0.0, 0.0), dt=None, cfl=0.4, n_gl=32):
+                 T_wall=(1.0, 1.0), u_wall=(0.0, 0.0), dt=None, cfl=0.4, n_gl=32, reduced=False):
+    """reduced: the cylinder with p_z integrated out (Q_3 is then ignored; the third index holds
+    the pair phi, chi)."""
     L = R_out - R_in
     if sigma is None:
         _, sigma, n0 = model.physical_parameters(Kn, eta0, L)
@@ -97,13 +110,18 @@ def make_problem(geometry, R_in, R_out, n_cells, Q_R, Q_2, Q_3, eta0, Kn=None, s
     pR = np.concatenate([xR, -xR])
     wR = np.concatenate([lamR, lamR])
     p2, w2 = quad.full_range_rule(Q_2)
-    p3, w3 = quad.full_range_rule(Q_3)
     NR = default_order(Q_R) if N_R is None else N_R
     N2 = default_order(Q_2) if N_2 is None else N_2
-    N3 = default_order(Q_3) if N_3 is None else N_3
     KR = km.k1_half(pR, wR, aR, bR)
     K2 = km.k2_full(p2, w2)
-    K3 = km.k2_full(p3, w3)
+    if reduced:
+        assert geometry == geo.CYL
+        # the pair (phi, chi): no p_z nodes; unit weights, so WENO works on phi / (w_R w_2) and chi / (w_R w_2)
+        p3, w3, N3, K3 = np.zeros(2), np.ones(2), 0, np.zeros((2, 2))
+    else:
+        p3, w3 = quad.full_range_rule(Q_3)
+        N3 = default_order(Q_3) if N_3 is None else N_3
+        K3 = km.k2_full(p3, w3)
     W = geo.fm_weights(grid, sigma, n_gl) if chi_model == RET_FM else np.zeros((0, 0))
     if dt is None:
         dr_min = float(np.min(np.diff(grid.R_f)))
@@ -112,7 +130,7 @@ def make_problem(geometry, R_in, R_out, n_cells, Q_R, Q_2, Q_3, eta0, Kn=None, s
         tau_min = float(model.relaxation_time(n0, Tmax, chi0, sigma))
         dt = min(cfl * dr_min / (float(np.max(np.abs(pR))) * math.sqrt(Tmax)), 0.5 * tau_min)
     return Problem(geometry, grid, pR, wR, aR, bR, p2, w2, p3, w3, NR, N2, N3, KR, K2, K3,
-                   sigma, eta0, n0, chi_model, W, float(dt), tuple(T_wall), tuple(u_wall))
+                   sigma, eta0, n0, chi_model, W, float(dt), tuple(T_wall), tuple(u_wall), reduced=reduced)
 
 
 # ----------------------------------------------------------------------------- moments
@@ -123,6 +141,8 @@ def momentum_axes(P: Problem):
 def raw_sums(f, P: Problem):
     """The 13 quadrature sums per cell (Eq. mom_quad): S0 = sum f, S1_a = sum f p_a,
     S2_ab = sum f p_a p_b (a <= b: 00, 11, 22, 01, 02, 12), S3_a = sum f p^2 p_a."""
+    if P.reduced:
+        return _raw_sums_reduced(f, P)
     p = momentum_axes(P)
     psq = p[0] ** 2 + p[1] ** 2 + p[2] ** 2
     ax = (1, 2, 3)
@@ -132,6 +152,21 @@ def raw_sums(f, P: Problem):
         out.append((f * (p[a] * p[b])).sum(ax))
     out += [(f * (psq * p[a])).sum(ax) for a in range(3)]
     return np.stack(out, axis=-1)  # (N, 13)
+
+
+def _raw_sums_reduced(f, P: Problem):
+    """The same 13 sums from the reduced pair: p_z enters only through sum_z p_z^2 f = sum chi
+    (S2_zz, and S3_a's p^2 p_a); with f even in p_z its odd moments (S1_z, S2_Rz, S2_phiz, S3_z)
+    vanish."""
+    phi, chi = f[..., 0], f[..., 1]
+    pR, p2 = P.pR[None, :, None], P.p2[None, None, :]
+    ax = (1, 2)
+    zero = np.zeros(f.shape[0])
+    psq = pR ** 2 + p2 ** 2
+    out = [phi.sum(ax), (phi * pR).sum(ax), (phi * p2).sum(ax), zero,
+           (phi * pR ** 2).sum(ax), (phi * p2 ** 2).sum(ax), chi.sum(ax), (phi * pR * p2).sum(ax), zero, zero,
+           (phi * psq * pR).sum(ax) + (chi * pR).sum(ax), (phi * psq * p2).sum(ax) + (chi * p2).sum(ax), zero]
+    return np.stack(out, axis=-1)
 
 
 def macroscopic(S):
@@ -235,6 +270,31 @@ def collision(f, P: Problem, cl):
     return -(f - fS) / e(cl["tau"]) + J1
 
 
+def collision_reduced(f, P: Problem, cl):
+    """The collision of the reduced pair: the p_z-integral of the full operator against 1 (phi)
+    and p_z^2 (chi) for the Gaussian p_z factor of f^MB (u_z = 0): int g_z = 1, int p_z^2 g_z = T,
+    int p_z^4 g_z = 3 T^2.  Every p_z-dependence of f^S / f^MB and J1 / f^MB is through p_z^2 in
+    xi^2 (q_z = 0, and the strain has no z component in the cylinder), so member k is the
+    full expression with p_z^2 replaced by e_k = T (phi) or 3T (chi), times m_k = 1 or T."""
+    e = lambda a: a[:, None, None]
+    n, T, u, q = cl["n"], cl["T"], cl["u"], cl["q"]
+    xi0 = P.pR[None, :, None] - e(u[:, 0])
+    xi1 = P.p2[None, None, :] - e(u[:, 1])
+    xiq = xi0 * e(q[:, 0]) + xi1 * e(q[:, 1])
+    fMB = e(n) * cl["gR"][:, :, None] * cl["g2"][:, None, :]
+    S = cl["S"]
+    strain_perp = (xi0 ** 2 * e(S[:, 0, 0]) + xi1 ** 2 * e(S[:, 1, 1]) + 2.0 * xi0 * xi1 * e(S[:, 0, 1])) / e(T)
+    out = np.empty_like(f)
+    for k, (ez, mk) in enumerate(((T, np.ones_like(T)), (3.0 * T, T))):
+        xi2 = xi0 ** 2 + xi1 ** 2 + e(ez)
+        fS = e(mk) * fMB * (1.0 + e((1.0 - cl["Pr"]) / (n * T * T)) * (xi2 / (5.0 * e(T)) - 1.0) * xiq)
+        zeta2 = xi2 / (2.0 * e(T))
+        J1 = -e(cl["br"] * cl["chi"] * mk) * fMB * (
+            xi0 * (e(cl["X"]) + 0.6 * (zeta2 - 2.5) * e(cl["Y"])) + 0.4 * (strain_perp + (zeta2 - 2.5) * e(cl["div"])))
+        out[..., k] = -(f[..., k] - fS) / e(cl["tau"]) + J1
+    return out
+
+
 # ----------------------------------------------------------------------------- advection
 def weno5(vm2, vm1, v0, vp1, vp2):
     """WENO5-JS (Jiang & Shu 1996) value at the right face of the centre cell v0, upwind
@@ -258,7 +318,8 @@ def wall_maxwellians(P: Problem):
         Tw, uw = P.T_wall[side], P.u_wall[side]
         gR = eq.g_half(P.pR, P.wR, P.alphaR, P.betaR, P.NR, 0.0, Tw)
         g2 = eq.g_full(P.p2, P.w2, P.N2, uw, Tw)
-        g3 = eq.g_full(P.p3, P.w3, P.N3, 0.0, Tw)
+        # reduced pair: (int g_z, int p_z^2 g_z) = (1, T_w)
+        g3 = np.array([1.0, Tw]) if P.reduced else eq.g_full(P.p3, P.w3, P.N3, 0.0, Tw)
         out.append(gR[:, None, None] * g2[None, :, None] * g3[None, None, :])
     return out
 
@@ -281,15 +342,17 @@ def advection(f, P: Problem, return_walls=False):
     X = lambda c: ext[c + 2]  # cell index c in [-2, N+1]
     gw = wall_maxwellians(P)
     pRb = P.pR[:, None, None]
+    # the mass flux: of every population, or of phi alone for the reduced pair
+    mass = (lambda a: a[..., :1]) if P.reduced else (lambda a: a)
     # left wall: outgoing = p_R < 0, reconstructed from the right at face 0
     vhat_L = weno5(X(2), X(1), X(0), X(-1), X(-2))
-    out_L = (np.abs(pRb) * w * vhat_L)[neg].sum()
-    in_L = (pRb * gw[0])[pos].sum()
+    out_L = mass((np.abs(pRb) * w * vhat_L)[neg]).sum()
+    in_L = mass((pRb * gw[0])[pos]).sum()
     nw_L = out_L / in_L
     # right wall: outgoing = p_R > 0, reconstructed from the left at face N
     vhat_R = weno5(X(N - 3), X(N - 2), X(N - 1), X(N), X(N + 1))
-    out_R = (pRb * w * vhat_R)[pos].sum()
-    in_R = (np.abs(pRb) * gw[1])[neg].sum()
+    out_R = mass((pRb * w * vhat_R)[pos]).sum()
+    in_R = mass((np.abs(pRb) * gw[1])[neg]).sum()
     nw_R = out_R / in_R
     # incoming ghosts: the wall Maxwellian
     for c in (-1, -2):
@@ -332,7 +395,7 @@ def rhs(f, P: Problem, details=False):
     cl = closure(f, P)
     adv, walls = advection(f, P, return_walls=True)
     frc = force(f, P)
-    col = collision(f, P, cl)
+    col = collision_reduced(f, P, cl) if P.reduced else collision(f, P, cl)
     L = -adv - frc + col
     if details:
         return L, dict(closure=cl, adv=adv, force=frc, coll=col, n_wall=walls)
@@ -361,7 +424,7 @@ def uniform_state(P: Problem, n0=None, T0=None):
     T0 = 0.5 * (P.T_wall[0] + P.T_wall[1]) if T0 is None else T0
     gR = eq.g_half(P.pR, P.wR, P.alphaR, P.betaR, P.NR, 0.0, T0)
     g2 = eq.g_full(P.p2, P.w2, P.N2, 0.0, T0)
-    g3 = eq.g_full(P.p3, P.w3, P.N3, 0.0, T0)
+    g3 = np.array([1.0, T0]) if P.reduced else eq.g_full(P.p3, P.w3, P.N3, 0.0, T0)
     f = n0 * gR[:, None, None] * g2[None, :, None] * g3[None, None, :]
     return np.broadcast_to(f, P.shape).copy()
 
@@ -373,8 +436,19 @@ def shakhov_seed(P: Problem, n, u2, T, qR):
     carried by the populations)."""
     gR = eq.g_half(P.pR, P.wR, P.alphaR, P.betaR, P.NR, np.zeros_like(T), T)
     g2 = eq.g_full(P.p2, P.w2, P.N2, u2, T)
-    g3 = eq.g_full(P.p3, P.w3, P.N3, np.zeros_like(T), T)
     e = lambda a: a[:, None, None, None]
+    if P.reduced:
+        # the p_z-integrals against 1 and p_z^2 (xi^2 carries p_z^2 -> T, 3T; chi weighted by T)
+        x0 = P.pR[None, :, None]
+        xs = x0 ** 2 + (P.p2[None, None, :] - u2[:, None, None]) ** 2
+        base = n[:, None, None] * gR[:, :, None] * g2[:, None, :]
+        f = np.empty(base.shape + (2,))
+        t = T[:, None, None]
+        qf = x0 * (qR / (n * T * T))[:, None, None]
+        f[..., 0] = base * (1.0 + ((xs + t) / (5.0 * t) - 1.0) * qf)
+        f[..., 1] = t * base * (1.0 + ((xs + 3.0 * t) / (5.0 * t) - 1.0) * qf)
+        return f
+    g3 = eq.g_full(P.p3, P.w3, P.N3, np.zeros_like(T), T)
     p = momentum_axes(P)
     xi2 = p[0][None] ** 2 + (p[1][None] - e(u2)) ** 2 + p[2][None] ** 2
     fMB = e(n) * gR[:, :, None, None] * g2[:, None, :, None] * g3[:, None, None, :]
@@ -384,7 +458,8 @@ def shakhov_seed(P: Problem, n, u2, T, qR):
 # ----------------------------------------------------------------------------- diagnostics
 def total_mass(f, P: Problem):
     """sum_c V_c n_c (per unit angle, and per unit length for the cylinder)."""
-    return float((P.grid.V_c * f.sum((1, 2, 3))).sum())
+    n = f[..., 0].sum((1, 2)) if P.reduced else f.sum((1, 2, 3))
+    return float((P.grid.V_c * n).sum())
 
 
 def moment_residual(m_old, m_new, K, scales):

@@ -19,6 +19,7 @@ from . import test_oracle_kmatrix as t_km
 from . import test_oracle_model as t_model
 from . import test_oracle_nn as t_nn
 from . import test_oracle_quadrature as t_quad
+from . import test_oracle_reduced as t_red
 from . import test_oracle_solver as t_solver
 
 
@@ -134,6 +135,15 @@ CASES = [
      t_solver, "S", "test_moment_residual_on_a_hand_computed_two_cell_case", ()),
     ("residual scaled by the new profile", "solver", "/ (K * max(float(np.max(np.abs(a))), s))",
      "/ (K * max(float(np.max(np.abs(b))), s))", t_solver, "S", "test_moment_residual_on_a_hand_computed_two_cell_case", ()),
+    # reduced cylinder (p_z integrated out)
+    ("reduced chi's p_z^2 taken as T", "solver", "(3.0 * T, T))):", "(T, T))):",
+     t_red, "S", "test_reduced_collision_is_the_projection", (FM,)),
+    ("reduced S2_zz dropped", "solver", "(phi * p2 ** 2).sum(ax), chi.sum(ax),", "(phi * p2 ** 2).sum(ax), zero,",
+     t_red, "S", "test_reduced_moments_are_the_projection", ()),
+    ("reduced wall mass flux of both members", "solver", "mass = (lambda a: a[..., :1]) if P.reduced else (lambda a: a)",
+     "mass = (lambda a: a)", t_red, "S", "test_reduced_mass_conserved_and_seed_carries_its_profiles", ()),
+    ("reduced wall pair without T_w", "solver", "g3 = np.array([1.0, Tw]) if P.reduced", "g3 = np.array([1.0, 1.0]) if P.reduced",
+     t_red, "S", "test_reduced_rhs_is_the_projection_under_linear_reconstruction", (LOCAL,)),
     # quadrature (Sec. III.A)
     ("half-range weight formula", "quadrature", "(x + hQ0 ** 2 / math.sqrt(2.0 * math.pi))",
      "(x + hQ0 ** 2 / math.sqrt(math.pi))", t_quad, "quad", "test_half_range_exact_on_half_line_moments", (4,)),
