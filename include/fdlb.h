@@ -53,6 +53,11 @@ extern "C" {
 /* ----------------------------------------------------------------------- enumerations */
 #define FDLB_CYL 0             /* coaxial cylinders, axes (R, phi, z)  (Sec. II.B)        */
 #define FDLB_SPH 1             /* concentric spheres, axes (r, theta, phi)  (Sec. II.C)   */
+#define FDLB_CYL_Z 2           /* coaxial cylinders with p_z integrated out (the trivial axis of
+                                  Sec. III.A's remark on Couette flow): per (p_R, p_phi) node the
+                                  pair phi = int f dp_z, chi = int p_z^2 f dp_z, stored as k = 0, 1
+                                  of the third index (Q_3 must be 0; n_momenta = 2 x 2Q_R x Q_2);
+                                  for states even in p_z it evolves the p_z-projection of FDLB_CYL */
 #define FDLB_FP64 0            /* populations and arithmetic in FP64                      */
 #define FDLB_FP32 1            /* FP32 populations and streaming, FP64 moment sums         */
 #define FDLB_CHI_RET_FM 0      /* chi_SET at the Fischer-Methfessel density (Eqs. chi_ret, fm) */
@@ -65,7 +70,7 @@ extern "C" {
 
 /* ----------------------------------------------------------------------- parameters */
 typedef struct fdlb_params {
-    int geometry;          /* FDLB_CYL or FDLB_SPH                                         */
+    int geometry;          /* FDLB_CYL, FDLB_SPH or FDLB_CYL_Z                             */
     double R_in, R_out;    /* physical wall radii, R_out > R_in > 0 (Sec. IV)              */
     int n_cells;           /* radial cells on [R_in + sigma/2, R_out - sigma/2], >= 8       */
     double stretch_beta;   /* 0: uniform cells; > 0: tanh map with this beta (finer at walls) */

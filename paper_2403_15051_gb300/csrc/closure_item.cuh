@@ -143,6 +143,7 @@ __device__ T wall_flux_partial(const T* wall, long long st, const MomSet& M, con
             const int k = m / (nR * n2), rem = m % (nR * n2), i = rem / n2, j = rem % n2;
             const T pr = tb.pRt[i];
             if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
+            if (M.reduced && k > 0) continue;  // the mass flux is phi's (chi = int p_z^2 f)
             const T wm = tb.wRt[i] * tb.w2t[j] * tb.w3t[k], iw = T(1) / wm;
             const T f0 = fv[u][0], f1 = fv[u][1], f2 = fv[u][2], f3 = fv[u][3];
             const T g1 = T(4) * f0 - T(6) * f1 + T(4) * f2 - f3;
@@ -526,7 +527,12 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
             dst = rec_off_g2() + j;
         } else {
             const int j = k - nR - n2;
-            for (int l = 0; l <= M.N3; ++l) acc += G3[j * kMaxE + l] * ecs[t][3][l];
+            if (M.reduced) {
+                // the pair's Gaussian factors: int g_z = 1 (phi), int p_z^2 g_z = T (chi)
+                acc = j == 0 ? T(1) : w_hi(sw_T[c0 + t - h0]);
+            } else {
+                for (int l = 0; l <= M.N3; ++l) acc += G3[j * kMaxE + l] * ecs[t][3][l];
+            }
             dst = rec_off_g3(nR, n2) + j;
         }
         recb[(long long)t * rs + dst] = acc;
@@ -552,6 +558,7 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
             for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
+        if (M.reduced) s3w[2] = w_from_t(T(1));  // the mass is phi's: its p_z factor is exactly 1
         if (lane == 0) ct[0] = w_hi(w_div(sw_n[c0 + t - h0], w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
     }
     __syncthreads();  // shared arrays are reused by the next call

@@ -38,6 +38,7 @@ struct Layout {
 
 struct Solver {
     int n_inst = 0, geometry = 0, precision = 0;
+    int reduced = 0;  // FDLB_CYL_Z: the cylinder's kernels on the pair (phi, chi) as the third index
     size_t tsize = 8;
     AxisRule aR, a2, a3;
     int NR = 0, N2 = 0, N3 = 0, nR = 0, n2 = 0, n3 = 0, Np = 0;
@@ -51,7 +52,7 @@ struct Solver {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0, n_sm = 0;
-    size_t smem_optin = 0;
+    size_t smem_optin = 0, smem_per_sm = 0;
     // device memory
     unsigned char* ws = nullptr;
     bool own_ws = false;
@@ -80,6 +81,7 @@ struct Solver {
     int use_bulk = 0;
     int closure_cells = 4, closure_threads = 128;  // own cells per closure item (<= kClosureCells)
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
+    int stage_minb = 1;     // register bound of the stage kernel (1, or 3 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
     int closure_wst = 0;                           // staged band-row elements per closure block
     int grid_stream = 1, grid_closure = 1;
@@ -299,15 +301,27 @@ int plan_solver(const fdlb_params* ps, int n, Solver& S) try {
     }());
     if (rc) return rc;
     S.n_inst = n;
-    S.geometry = p0.geometry;
+    S.reduced = p0.geometry == FDLB_CYL_Z ? 1 : 0;
+    S.geometry = S.reduced ? FDLB_CYL : p0.geometry;
     S.precision = p0.precision;
     S.tsize = p0.precision == FDLB_FP32 ? 4 : 8;
     S.aR = make_axis(p0.Q_R, true);
     S.a2 = make_axis(p0.Q_2, false);
-    S.a3 = make_axis(p0.Q_3, false);
+    if (S.reduced) {
+        // the pair (phi, chi) in the place of the p_z nodes: no p_z, unit weights (WENO then works on
+        // phi / (w_R w_2) and chi / (w_R w_2))
+        S.a3 = AxisRule();
+        S.a3.Q = 2;
+        S.a3.p = {0.0, 0.0};
+        S.a3.w = {1.0, 1.0};
+        S.a3.alpha = {0.0, 0.0, 0.0};
+        S.a3.beta = {1.0, 1.0, 2.0};
+    } else {
+        S.a3 = make_axis(p0.Q_3, false);
+    }
     S.nR = 2 * p0.Q_R;
     S.n2 = p0.Q_2;
-    S.n3 = p0.Q_3;
+    S.n3 = S.reduced ? 2 : p0.Q_3;
     S.Np = S.nR * S.n2 * S.n3;
     S.setup.resize(n);
     for (int q = 0; q < n; ++q) {
@@ -362,12 +376,18 @@ void wall_tables(const Solver& S, int q, double* out, double* den) {
         const double Tw = I.p.T_wall[side], uw = I.p.u_wall[side];
         g_half_host(S.aR, S.NR, 0.0, Tw, o);
         g_full_host(S.a2, S.N2, uw, Tw, o + S.nR);
-        g_full_host(S.a3, S.N3, 0.0, Tw, o + S.nR + S.n2);
+        if (S.reduced) {
+            // the wall's pair (int g_z, int p_z^2 g_z) = (1, T_w)
+            o[S.nR + S.n2] = 1.0;
+            o[S.nR + S.n2 + 1] = Tw;
+        } else {
+            g_full_host(S.a3, S.N3, 0.0, Tw, o + S.nR + S.n2);
+        }
         double sR = 0.0, s2 = 0.0, s3 = 0.0;
         for (int i = 0; i < S.nR; ++i)
             if (side == 0 ? S.aR.p[i] > 0 : S.aR.p[i] < 0) sR += std::fabs(S.aR.p[i]) * o[i];
         for (int j = 0; j < S.n2; ++j) s2 += o[S.nR + j];
-        for (int k = 0; k < S.n3; ++k) s3 += o[S.nR + S.n2 + k];
+        for (int k = 0; k < (S.reduced ? 1 : S.n3); ++k) s3 += o[S.nR + S.n2 + k];  // mass: phi alone
         den[side] = sR * s2 * s3;
     }
 }
@@ -380,7 +400,7 @@ void fill_inst(Solver& S, int q) {
     d.f_off = S.f_off[q];
     d.band_w = I.band.width;
     d.chi_local = I.p.chi_model == FDLB_CHI_SET_LOCAL ? 1 : 0;
-    d.geometry = I.p.geometry;
+    d.geometry = I.p.geometry == FDLB_SPH ? 1 : 0;
     d.sigma = I.sigma;
     d.bfac = 2.0 * kPiH / 3.0 * I.sigma * I.sigma * I.sigma;
     d.etafac = kPiH * I.sigma * I.sigma * I.sigma / 6.0;
@@ -509,9 +529,21 @@ int upload_items(Solver& S) {
     const size_t base = closure_smem(S.nR, S.n2, S.n3, max_union, 0, (int)S.tsize);
     if (base > S.smem_optin) return FDLB_EINVAL;
     wst = (int)std::min<size_t>((size_t)wst, (S.smem_optin - base) / S.tsize);
+    // Many more items than co-resident blocks (batches, long instances): the closure is bound by
+    // how many items are in flight, not by one item's latency, so each block keeps to the share of
+    // an SM's shared memory that lets as many blocks reside as its registers allow; the band rows
+    // of wider bands are then read from global memory (coalesced along the row) instead of being
+    // staged.
+    const bool throughput = nc > S.n_sm * 8;
+    int closure_bps = 8;
+    if (throughput && S.smem_per_sm > 0) {
+        closure_bps = std::max(1, closure_blocks_per_sm((int)S.tsize, base));
+        const size_t target = S.smem_per_sm / closure_bps;
+        wst = target > base + 1024 ? (int)std::min<size_t>((size_t)wst, (target - base - 1024) / S.tsize) : 0;
+    }
     S.closure_wst = wst;
     S.closure_smem = closure_smem(S.nR, S.n2, S.n3, max_union, wst, (int)S.tsize);
-    S.grid_closure = std::max(1, std::min(nc, S.n_sm * 8));
+    S.grid_closure = std::max(1, std::min(nc, S.n_sm * (throughput ? closure_bps : 8)));
     S.grid_stream = std::max(1, ns);
     return plan_step_kernel(S, ns);
 }
@@ -535,6 +567,7 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     S.M.KS = S.KS;
     S.M.slices = S.n3 / S.KS;
     S.M.Ms = Ms;
+    S.M.reduced = S.reduced;
     // vectors of VW consecutive j momenta; compile-time shapes for the benchmark workloads
     StreamCfg cfg{};
     if (S.tsize == 4)
@@ -558,6 +591,7 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
         if ((long long)nt * cfg.nv < Vs) nt = ((Vs + cfg.nv - 1) / cfg.nv + 31) / 32 * 32;
     }
     if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
+    cfg.minb = (S.stage_minb == 3 && cfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && nt <= 256) ? 3 : 1;
     S.scfg = cfg;
     S.threads = nt;
     S.mma_on = S.tensor && cfg.spec && cfg.vw == 4 && S.tsize == 4 && S.nR % 8 == 0 && !S.krg_on;
@@ -807,6 +841,20 @@ void seed_state(const Solver& S, int q, const std::vector<double>& n, const std:
     for (int c = 0; c < N; ++c) {
         g_half_host(S.aR, S.NR, 0.0, T[c], gR.data());
         g_full_host(S.a2, S.N2, u2[c], T[c], g2.data());
+        if (S.reduced) {
+            // the p_z-integrals of the seed against 1 (phi) and p_z^2 (chi): xi^2 carries p_z^2 as
+            // T or 3T, and chi's part is weighted by T
+            for (int i = 0; i < S.nR; ++i)
+                for (int j = 0; j < S.n2; ++j) {
+                    const double pR = S.aR.p[i], x1 = S.a2.p[j] - u2[c];
+                    const double xs = pR * pR + x1 * x1, qf = pR * qR[c] / (n[c] * T[c] * T[c]);
+                    const double base = n[c] * gR[i] * g2[j];
+                    const size_t o = (size_t)c * S.Np + ((size_t)i * S.n2 + j) * S.n3;
+                    f[o] = base * (1.0 + ((xs + T[c]) / (5.0 * T[c]) - 1.0) * qf);
+                    f[o + 1] = T[c] * base * (1.0 + ((xs + 3.0 * T[c]) / (5.0 * T[c]) - 1.0) * qf);
+                }
+            continue;
+        }
         g_full_host(S.a3, S.N3, 0.0, T[c], g3.data());
         for (int i = 0; i < S.nR; ++i)
             for (int j = 0; j < S.n2; ++j)
@@ -920,7 +968,10 @@ struct TuneKey {
         return std::lexicographical_compare(a, a + 9, b, b + 9);
     }
 };
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+struct TuneVal {
+    int B, closure_cells, minb;
+};
+std::map<TuneKey, TuneVal> g_tune_cache;
 std::mutex g_tune_mutex;
 
 int ilog2(long long x) {
@@ -965,8 +1016,9 @@ int run_autotune(Solver& S, bool use_cache) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            int rc = configure_tiling(S, it->second.first, S.KS, S.threads);
-            return rc ? rc : set_closure_grouping(S, it->second.second);
+            S.stage_minb = it->second.minb;
+            int rc = configure_tiling(S, it->second.B, S.KS, S.threads);
+            return rc ? rc : set_closure_grouping(S, it->second.closure_cells);
         }
     }
     const bool timing = S.timing;
@@ -975,20 +1027,28 @@ int run_autotune(Solver& S, bool use_cache) {
     FDLB_CUDA(cudaEventCreate(&e0));
     FDLB_CUDA(cudaEventCreate(&e1));
     const int KS = S.KS, threads = S.threads;
-    int bestB = S.B, bestC = S.closure_cells;
+    int bestB = S.B, bestC = S.closure_cells, bestM = S.stage_minb;
     float best = time_stages(S, e0, e1);
     if (best < 0.f) best = 1e30f;
     const int Bs[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+    // the register bound of the stage kernel: three blocks per SM where that variant is built
+    const bool minb_choice = S.scfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && S.threads <= 256;
     int rc = FDLB_OK;
-    for (int B : Bs) {
-        if (B == bestB) continue;
-        if (configure_tiling(S, B, KS, threads) != FDLB_OK || S.B != B) continue;
-        const float ms = time_stages(S, e0, e1);
-        if (ms >= 0.f && ms < best) {
-            best = ms;
-            bestB = B;
+    for (int mb : {1, 3}) {
+        if (mb == 3 && !minb_choice) continue;
+        S.stage_minb = mb;
+        for (int B : Bs) {
+            if (B == bestB && mb == bestM) continue;
+            if (configure_tiling(S, B, KS, threads) != FDLB_OK || S.B != B) continue;
+            const float ms = time_stages(S, e0, e1);
+            if (ms >= 0.f && ms < best) {
+                best = ms;
+                bestB = B;
+                bestM = mb;
+            }
         }
     }
+    S.stage_minb = bestM;
     rc = configure_tiling(S, bestB, KS, threads);
     const int Cs[] = {2, 4, 8, 16};
     for (int C : Cs) {
@@ -1006,7 +1066,7 @@ int run_autotune(Solver& S, bool use_cache) {
     if (!rc) rc = set_closure_grouping(S, bestC);
     if (!rc) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = {bestB, bestC};
+        g_tune_cache[key] = {bestB, bestC, bestM};
     }
     return rc;
 }
@@ -1064,6 +1124,9 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     int optin = 0;
     FDLB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device));
     S->smem_optin = (size_t)optin;
+    int per_sm = 0;
+    FDLB_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, S->device));
+    S->smem_per_sm = (size_t)per_sm;
     S->stream = (cudaStream_t)stream;
     if (!S->stream) {
         // the legacy default stream cannot be captured into a graph: use a private blocking
@@ -1129,8 +1192,6 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.inst_h.resize(n);
     std::vector<double> geo((size_t)R.total_cells * kGeo), gw((size_t)n * 2 * (R.nR + R.n2 + R.n3));
     std::vector<int> blo((size_t)R.total_cells * 2, 0);
-    std::vector<float> bandf;
-    std::vector<double> bandd;
     size_t boff = 0;
     for (int q = 0; q < n; ++q) {
         fill_inst(R, q);
@@ -1143,7 +1204,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
             o[1] = 1.0 / g.dRds_c[c];
             o[2] = g.A_f[c + 1] / g.V_c[c];
             o[3] = g.A_f[c] / g.V_c[c];
-            o[4] = I.p.geometry == FDLB_CYL ? g.kappa[c] : 0.5 * g.kappa[c];
+            o[4] = I.p.geometry == FDLB_SPH ? 0.5 * g.kappa[c] : g.kappa[c];
             o[5] = g.V_c[c];
             if (I.band.width) {
                 blo[(size_t)(R.cell_off[q] + c) * 2] = I.band.lo[c];
@@ -1152,11 +1213,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         }
         double den[2];
         wall_tables(R, q, &gw[(size_t)q * 2 * (R.nR + R.n2 + R.n3)], den);
-        for (double v : I.band.W) {
-            if (R.precision == FDLB_FP32) bandf.push_back((float)v);
-            else bandd.push_back(v);
-        }
-        boff += I.band.W.size();
+        boff += (size_t)I.p.n_cells * I.band.width;
     }
     FDLB_CUDA(cudaMemcpyAsync(R.inst_d, R.inst_h.data(), n * sizeof(InstDev), cudaMemcpyHostToDevice, R.stream));
     FDLB_CUDA(cudaMemcpyAsync(R.geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice, R.stream));
@@ -1170,10 +1227,30 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         FDLB_CUDA(cudaMemcpyAsync(R.gwT, gw.data(), gw.size() * 8, cudaMemcpyHostToDevice, R.stream));
     }
     FDLB_CUDA(cudaMemcpyAsync(R.band_lo, blo.data(), blo.size() * sizeof(int), cudaMemcpyHostToDevice, R.stream));
-    if (R.precision == FDLB_FP32 && !bandf.empty())
-        FDLB_CUDA(cudaMemcpyAsync(R.band, bandf.data(), bandf.size() * 4, cudaMemcpyHostToDevice, R.stream));
-    if (R.precision == FDLB_FP64 && !bandd.empty())
-        FDLB_CUDA(cudaMemcpyAsync(R.band, bandd.data(), bandd.size() * 8, cudaMemcpyHostToDevice, R.stream));
+    // the Fischer-Methfessel weights, computed on the device (the faces of every instance staged in
+    // the stage-1 population buffer, unused until the first step)
+    {
+        std::vector<double> faces;
+        std::vector<size_t> face_off(n);
+        for (int q = 0; q < n; ++q) {
+            face_off[q] = faces.size();
+            faces.insert(faces.end(), R.setup[q].grid.R_f.begin(), R.setup[q].grid.R_f.end());
+        }
+        if (faces.size() * sizeof(double) > L.f[2] - L.f[1]) return FDLB_ENOMEM;
+        double* dfaces = reinterpret_cast<double*>(R.f[1]);
+        FDLB_CUDA(cudaMemcpyAsync(dfaces, faces.data(), faces.size() * sizeof(double), cudaMemcpyHostToDevice, R.stream));
+        const FmRule rule = fm_rule();
+        for (int q = 0; q < n; ++q) {
+            const InstanceSetup& I = R.setup[q];
+            if (I.band.width == 0) continue;
+            const int N = I.p.n_cells;
+            FDLB_CUDA(launch_fm_band((int)R.tsize, R.geo + (size_t)R.cell_off[q] * kGeo, kGeo, dfaces + face_off[q], N,
+                                     I.p.geometry == FDLB_SPH ? 1 : 0, I.sigma, I.band.width,
+                                     reinterpret_cast<const int2*>(R.band_lo) + R.cell_off[q],
+                                     (unsigned char*)R.band + (size_t)R.inst_h[q].band_off * R.tsize, rule,
+                                     std::max(1, std::min(N, R.n_sm * 4)), R.stream));
+        }
+    }
     FDLB_CUDA(cudaStreamSynchronize(R.stream));
     // default tiling: a slice per p_3 value on the cylinder (p_3 is passive there)
     // default tiling (the fastest of a sweep on GB300; fdlb_autotune refines it per workload):

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/fdlb.h"
+#include "fm_volumes.h"
 
 // Handlers of the function-try-blocks around the C-ABI entry points: the host side keeps its
 // tables in std::vectors, and a failed host allocation is reported as FDLB_ENOMEM, so no C++
@@ -75,10 +76,14 @@ struct FMBand {
     std::vector<int> cnt;          // stored nonzero extent of each row (a multiple of 4, <= width)
     std::vector<double> W;         // [N][width], zero padded
 };
-// Fischer-Methfessel weights of every cell over the cells its ball reaches (Eq. fm, App. A).
+// Fischer-Methfessel weights of every cell over the cells its ball reaches (Eq. fm, App. A):
+// the extents (first column, stored extent, width) and, when `weights`, the weights themselves
+// (a handle fills them on the device, fill_fm_weights, with the same arithmetic).
 // FDLB_EINVAL, before the weights are allocated, when the band would hold more than 2^31 - 1
 // entries (the device tables index it with 32-bit offsets).
-int fm_band(int geometry, const Grid& g, double sigma, FMBand& b);
+int fm_band(int geometry, const Grid& g, double sigma, FMBand& b, bool weights = true);
+// The quadrature rule of the cylinder volumes.
+FmRule fm_rule();
 
 // ------------------------------------------------------------------ validated instance
 struct InstanceSetup {

@@ -58,6 +58,7 @@ struct MomSet {
     int nR, n2, n3, Np;            // axis sizes, momenta per cell
     int NR, N2, N3;                // expansion orders
     int slices, KS, Ms;            // momentum slices, k values per slice, momenta per slice
+    int reduced;                   // cylinder with p_z integrated out: k = 0 phi, k = 1 chi
     // offsets into the FP64 table buffer
     int o_pR, o_wR, o_p2, o_w2, o_p3, o_w3, o_KR, o_K2, o_K3, o_GR, o_G2, o_G3, o_ha, o_hb, o_h0;
 };

@@ -6,6 +6,7 @@
 #include "kernels.cuh"
 #include "kernels_decl.h"
 #include "closure_item.cuh"
+#include "fm_volumes.h"
 
 namespace fdlb {
 
@@ -35,6 +36,13 @@ __global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sum
                 const int k = m / (M.nR * M.n2), rem = m % (M.nR * M.n2), i = rem / M.n2, j = rem % M.n2;
                 const T p0 = (T)tab[M.o_pR + i], p1 = (T)tab[M.o_p2 + j], p2 = (T)tab[M.o_p3 + k];
                 const T v = fc[m], ps = p0 * p0 + p1 * p1 + p2 * p2;
+                if (M.reduced && k == 1) {
+                    // chi = int p_z^2 f: S2_zz and the p_z^2 p_a part of S3_a
+                    acc[6] += v;
+                    acc[10] += v * p0;
+                    acc[11] += v * p1;
+                    continue;
+                }
                 acc[0] += v;
                 acc[1] += v * p0;
                 acc[2] += v * p1;
@@ -265,6 +273,58 @@ template <typename T>
 void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {
     if (smem > 32 * 1024) cudaFuncSetAttribute(closure_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     launch_maybe_programmatic(closure_kernel<T>, grid, threads, smem, s, A.programmatic, A, M);
+}
+
+int closure_blocks_per_sm(int tsize, size_t smem) {
+    int n = 0;
+    const cudaError_t e = tsize == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, closure_kernel<float>, kClosureThreads, smem)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, closure_kernel<double>, kClosureThreads, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    return n > 0 ? n : 1;
+}
+
+// ------------------------------------------------------------------------------ FM weights
+// The Fischer-Methfessel band of one instance (Eq. fm, App. A), in FP64, stored in the
+// populations' precision: a block per cell, the volumes U_i(R_f[j]) of the cell's ball inside the
+// faces of its band into shared memory, then W_ij = norm (U_i(R_f[j+1]) - U_i(R_f[j])) over the
+// stored extent (zero beyond the domain), the rest of the row zero.  Rc: cell centres (stride
+// rc_stride), Rf: the N + 1 faces, blo: (first column, stored extent) per cell.
+template <typename T>
+__global__ void fm_band_kernel(const double* __restrict__ Rc, int rc_stride, const double* __restrict__ Rf, int N,
+                               int sphere, double sigma, int width, const int2* __restrict__ blo, T* __restrict__ W,
+                               FmRule rule) {
+    extern __shared__ double U[];  // width + 1 values
+    const double norm = 3.0 / (4.0 * kFmPi * sigma * sigma * sigma);
+    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+        const int lo = blo[i].x, cnt = blo[i].y;
+        const double d = Rc[(long long)i * rc_stride];
+        for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
+            const int j = min(lo + t, N);
+            U[t] = fm_volume_inside(sphere, sigma, d, Rf[j], rule);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < width; t += blockDim.x) {
+            const double w = (t < cnt && lo + t < N) ? norm * (U[t + 1] - U[t]) : 0.0;
+            W[(long long)i * width + t] = (T)w;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_fm_band(int tsize, const double* Rc, int rc_stride, const double* Rf, int N, int sphere, double sigma,
+                           int width, const int2* blo, void* W, const FmRule& rule, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)(width + 1) * sizeof(double);
+    if (tsize == 4) {
+        cudaFuncSetAttribute(fm_band_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fm_band_kernel<float><<<grid, 128, smem, s>>>(Rc, rc_stride, Rf, N, sphere, sigma, width, blo, (float*)W, rule);
+    } else {
+        cudaFuncSetAttribute(fm_band_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fm_band_kernel<double><<<grid, 128, smem, s>>>(Rc, rc_stride, Rf, N, sphere, sigma, width, blo, (double*)W, rule);
+    }
+    return cudaPeekAtLastError();
 }
 
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "fm_volumes.h"
 
 namespace fdlb {
 
@@ -76,6 +77,7 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
 // is used.
 struct StreamCfg {
     int vw, nv, spec;
+    int minb = 1;  // register bound of the stage kernel: 1 or 3 blocks per SM (cylinder FP32 shape)
 };
 
 template <typename T>
@@ -94,6 +96,8 @@ template <typename T>
 void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s);
 
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize);
+// Blocks of the closure kernel that fit on an SM with `smem` bytes of dynamic shared memory each.
+int closure_blocks_per_sm(int tsize, size_t smem);
 
 
 #define FDLB_STREAM_DECL(T, G)                                                                             \
@@ -126,6 +130,11 @@ cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int*
 cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,
                                   const float* Bsplit, const MomSet& M, int Npad, int* err, int grid, cudaStream_t s);
 size_t kr_tc_smem_bytes(int Npad);
+
+// The Fischer-Methfessel weights of one instance's band, computed on the device in FP64 (the host
+// set-up's arithmetic, fm_volumes.h) and stored in the populations' precision (tsize 4 or 8).
+cudaError_t launch_fm_band(int tsize, const double* Rc, int rc_stride, const double* Rf, int N, int sphere, double sigma,
+                           int width, const int2* blo, void* W, const FmRule& rule, int grid, cudaStream_t s);
 
 void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s);
 

@@ -354,81 +354,20 @@ Grid make_grid(int geometry, double R_in, double R_out, double sigma, int N, dou
 }
 
 // ------------------------------------------------------------------------ FM weights
-namespace {
-
-// Volume common to a ball of radius r centred at distance d from the origin and the ball of
-// radius Rp centred at the origin (App. A lens formula plus the nested/disjoint cases).
-double sphere_volume_inside(double r, double d, double Rp) {
-    if (Rp <= 0.0) return 0.0;
-    if (d >= r + Rp) return 0.0;
-    if (d <= std::fabs(r - Rp)) {
-        const double m = std::min(r, Rp);
-        return 4.0 / 3.0 * kPi * m * m * m;
+FmRule fm_rule() {
+    std::vector<double> x, ww;
+    gauss_legendre(kFmGL, x, ww);
+    FmRule r{};
+    for (int i = 0; i < kFmGL; ++i) {
+        // map [-1,1] -> [0,1], then u -> (1 - cos(pi u))/2 to absorb end-point singularities
+        const double s = 0.5 * (x[i] + 1.0);
+        r.u[i] = 0.5 * (1.0 - std::cos(kPi * s));
+        r.w[i] = 0.5 * ww[i] * 0.5 * kPi * std::sin(kPi * s);
     }
-    return kPi * (r + Rp - d) * (r + Rp - d) * (d * d + 2 * d * Rp - 3 * Rp * Rp + 2 * d * r + 6 * r * Rp - 3 * r * r) /
-           (12.0 * d);
+    return r;
 }
 
-// Area common to a disc of radius r at distance d from the origin and the disc of radius Rp
-// centred at the origin.
-double disc_area_inside(double r, double d, double Rp) {
-    if (r <= 0.0 || Rp <= 0.0) return 0.0;
-    if (d >= r + Rp) return 0.0;
-    if (d <= std::fabs(Rp - r)) {
-        const double m = std::min(r, Rp);
-        return kPi * m * m;
-    }
-    double c1 = (d * d + r * r - Rp * Rp) / (2.0 * d * r);
-    double c2 = (d * d + Rp * Rp - r * r) / (2.0 * d * Rp);
-    c1 = std::max(-1.0, std::min(1.0, c1));
-    c2 = std::max(-1.0, std::min(1.0, c2));
-    const double k = (-d + r + Rp) * (d + r - Rp) * (d - r + Rp) * (d + r + Rp);
-    return r * r * std::acos(c1) + Rp * Rp * std::acos(c2) - 0.5 * std::sqrt(std::max(k, 0.0));
-}
-
-struct GL01 {
-    std::vector<double> u, w;
-    explicit GL01(int m) {
-        std::vector<double> x, ww;
-        gauss_legendre(m, x, ww);
-        for (int i = 0; i < m; ++i) {
-            // map [-1,1] -> [0,1], then u -> (1 - cos(pi u))/2 to absorb end-point singularities
-            const double s = 0.5 * (x[i] + 1.0);
-            u.push_back(0.5 * (1.0 - std::cos(kPi * s)));
-            w.push_back(0.5 * ww[i] * 0.5 * kPi * std::sin(kPi * s));
-        }
-    }
-};
-
-// Volume common to a ball (radius r, centre at distance d from the axis) and the infinite
-// cylinder of radius Rp: 2 int_0^{pi/2} A(r cos t, d, Rp) r cos t dt, split where r cos t crosses
-// |Rp - d| and Rp + d.
-double cylinder_volume_inside(double r, double d, double Rp, const GL01& gl) {
-    if (Rp <= 0.0) return 0.0;
-    if (d >= r + Rp) return 0.0;
-    if (d + r <= Rp) return 4.0 / 3.0 * kPi * r * r * r;
-    double edges[4] = {0.0, 0.0, 0.0, 0.5 * kPi};
-    double b1 = std::fabs(Rp - d), b2 = Rp + d;
-    double t1 = (b1 > 0.0 && b1 < r) ? std::acos(b1 / r) : 0.0;
-    double t2 = (b2 > 0.0 && b2 < r) ? std::acos(b2 / r) : 0.0;
-    edges[1] = std::min(t1, t2);
-    edges[2] = std::max(t1, t2);
-    double total = 0.0;
-    for (int p = 0; p < 3; ++p) {
-        const double a = edges[p], L = edges[p + 1] - edges[p];
-        if (L <= 0.0) continue;
-        for (size_t i = 0; i < gl.u.size(); ++i) {
-            const double t = a + L * gl.u[i];
-            const double rc = r * std::cos(t);
-            total += 2.0 * L * gl.w[i] * disc_area_inside(rc, d, Rp) * rc;
-        }
-    }
-    return total;
-}
-
-}  // namespace
-
-int fm_band(int geometry, const Grid& g, double sigma, FMBand& b) {
+int fm_band(int geometry, const Grid& g, double sigma, FMBand& b, bool weights) {
     b = FMBand();
     const int N = g.N;
     b.lo.assign(N, 0);
@@ -447,18 +386,15 @@ int fm_band(int geometry, const Grid& g, double sigma, FMBand& b) {
     if ((long long)N * b.width > 2147483647LL) return FDLB_EINVAL;
     b.cnt.assign(N, 0);
     for (int i = 0; i < N; ++i) b.cnt[i] = std::min(b.width, (hi[i] - b.lo[i] + 1 + 3) / 4 * 4);
+    if (!weights) return FDLB_OK;  // the extents alone (a handle's weights are filled on the device)
     b.W.assign((size_t)N * b.width, 0.0);
     const double norm = 3.0 / (4.0 * kPi * sigma * sigma * sigma);
-    const double full = 4.0 / 3.0 * kPi * sigma * sigma * sigma;
-    const GL01 gl(24);
+    const FmRule gl = fm_rule();
+    const int sph = geometry == FDLB_SPH ? 1 : 0;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < N; ++i) {
         const double d = g.R_c[i];
-        auto U = [&](double Rp) {
-            if (d + sigma <= Rp) return full;
-            if (Rp <= d - sigma) return 0.0;
-            return geometry == FDLB_SPH ? sphere_volume_inside(sigma, d, Rp) : cylinder_volume_inside(sigma, d, Rp, gl);
-        };
+        auto U = [&](double Rp) { return fm_volume_inside(sph, sigma, d, Rp, gl); };
         double prev = U(g.R_f[b.lo[i]]);
         for (int j = b.lo[i]; j <= hi[i]; ++j) {
             const double next = U(g.R_f[j + 1]);
@@ -471,13 +407,18 @@ int fm_band(int geometry, const Grid& g, double sigma, FMBand& b) {
 
 // ------------------------------------------------------------------------ validation
 int validate_params(const fdlb_params& p) {
-    if (p.geometry != FDLB_CYL && p.geometry != FDLB_SPH) return FDLB_EINVAL;
+    if (p.geometry != FDLB_CYL && p.geometry != FDLB_SPH && p.geometry != FDLB_CYL_Z) return FDLB_EINVAL;
+    const bool reduced = p.geometry == FDLB_CYL_Z;  // no third momentum axis: Q_3 = 0
     if (!(p.R_in > 0.0) || !(p.R_out > p.R_in)) return FDLB_EINVAL;
     if (p.n_cells < 8) return FDLB_EINVAL;
     if (!(p.stretch_beta >= 0.0) || p.stretch_beta > 10.0) return FDLB_EINVAL;
     const int Qs[3] = {p.Q_R, p.Q_2, p.Q_3};
     const int Ns[3] = {p.N_R, p.N_2, p.N_3};
     for (int a = 0; a < 3; ++a) {
+        if (a == 2 && reduced) {
+            if (Qs[a] != 0) return FDLB_EINVAL;
+            continue;
+        }
         if (Qs[a] < 1 || Qs[a] > (a == 0 ? kMaxQR : kMaxQ)) return FDLB_EINVAL;
         if (Ns[a] >= Qs[a] || Ns[a] > kMaxN) return FDLB_EINVAL;
     }
@@ -497,7 +438,7 @@ int build_instance(const fdlb_params& p_in, const AxisRule& aR, InstanceSetup& o
     auto order = [](int N, int Q) { return N < 0 ? std::min(Q - 1, kMaxN) : N; };
     p.N_R = order(p.N_R, p.Q_R);
     p.N_2 = order(p.N_2, p.Q_2);
-    p.N_3 = order(p.N_3, p.Q_3);
+    p.N_3 = p.geometry == FDLB_CYL_Z ? 0 : order(p.N_3, p.Q_3);
     int rc = validate_params(p);
     if (rc) return rc;
     out.p = p;
@@ -515,7 +456,8 @@ int build_instance(const fdlb_params& p_in, const AxisRule& aR, InstanceSetup& o
     }
     if (!(out.C >= 3.0)) return FDLB_EINVAL;
     out.n0 = 6.0 * p.eta0 / (kPi * out.sigma * out.sigma * out.sigma);
-    out.grid = make_grid(p.geometry, p.R_in, p.R_out, out.sigma, p.n_cells, p.stretch_beta);
+    const int gbase = p.geometry == FDLB_SPH ? FDLB_SPH : FDLB_CYL;  // the reduced cylinder's grid is the cylinder's
+    out.grid = make_grid(gbase, p.R_in, p.R_out, out.sigma, p.n_cells, p.stretch_beta);
     if (p.dt > 0.0) {
         out.dt = p.dt;
     } else {
@@ -528,7 +470,7 @@ int build_instance(const fdlb_params& p_in, const AxisRule& aR, InstanceSetup& o
         const double cfl = p.cfl > 0.0 ? p.cfl : 0.4;
         out.dt = std::min(cfl * dr / (pmax * std::sqrt(Tmax)), 0.5 * tau);
     }
-    if (p.chi_model == FDLB_CHI_RET_FM) return fm_band(p.geometry, out.grid, out.sigma, out.band);
+    if (p.chi_model == FDLB_CHI_RET_FM) return fm_band(gbase, out.grid, out.sigma, out.band, false);
     return FDLB_OK;
 }
 

@@ -571,7 +571,13 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 ld_vec<T, VW>(fc + vb, fv);
                 ld_vec<T, VW>(g2c + jb * VW, g2v);
                 const T x0 = pr - u0, x2 = p3v - u2;
-                const T xsA = x0 * x0 + x2 * x2, xqA = x0 * q0 + x2 * q2;
+                T xsA = x0 * x0 + x2 * x2;
+                const T xqA = x0 * q0 + x2 * q2;
+                if (N3_ == 0 && M.reduced) {
+                    // cylinder with p_z integrated out (p_3 = u_3 = 0 here): the p_z^2 in |x|^2
+                    // becomes T for phi (k = 0), 3T for chi (k = 1); chi's T factor is in g_3
+                    xsA += (k == 0 ? T(1) : T(3)) / iT;
+                }
                 const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
                 const T fmbA = n * gRc[i] * g3c[k];
                 const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
@@ -633,6 +639,13 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 }
                 const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
                 const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
+                if (N3_ == 0 && M.reduced && k == 1) {
+                    // chi = int p_z^2 f: it enters S2_zz and the p_z^2 p_a part of S3_a only
+                    acc[6] += s0;
+                    acc[10] += prs0;
+                    acc[11] += s1;
+                    continue;
+                }
                 acc[0] += s0;
                 acc[1] += prs0;
                 acc[2] += s1;
@@ -694,7 +707,7 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 }
 
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
-__global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
+__device__ __forceinline__ void stream_body(const StageArgs& A, const MomSet& M) {
     __shared__ T snw[2];  // wall densities of the item's instance
     const int tid = threadIdx.x;
     stream_tables<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
@@ -733,10 +746,18 @@ __global__ void __launch_bounds__(512, 1) stream_kernel(StageArgs A, MomSet M) {
     }
 }
 
+// The stage kernel; MINB = the blocks per SM the register allocation is bounded for: 1 (up to 512
+// threads, 128 registers each: two blocks of 256 threads reside) or, for blocks of at most 256
+// threads, 3 (at most 85 registers each).  The arithmetic and its order are the same in both.
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_, int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) stream_kernel(StageArgs A, MomSet M) {
+    stream_body<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
+}
 
-template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_>
+
+template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_, int MINB = 1>
 cudaError_t launch_stream_t(const StageArgs& A, const MomSet& M, int grid, int threads, size_t smem, cudaStream_t s) {
-    auto kern = stream_kernel<T, GEOM, VW, NV, NR_, N2_, N3_>;
+    auto kern = stream_kernel<T, GEOM, VW, NV, NR_, N2_, N3_, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return launch_maybe_programmatic(kern, grid, threads, smem, s, A.programmatic, A, M);
@@ -752,6 +773,11 @@ cudaError_t launch_stream_dispatch(const StreamCfg& cfg, const StageArgs& A, con
     constexpr int NA = G == 0 ? 1 : 2, NB = G == 0 ? 2 : 4;
     if (cfg.spec) {
         if (cfg.vw != VS) return cudaErrorInvalidValue;
+        if constexpr (sizeof(T) == 4 && G == 0) {
+            // the cylinder's FP32 shape also bounded for three blocks of 256 threads per SM
+            if (cfg.minb == 3 && cfg.nv == NA && threads <= 256)
+                return launch_stream_t<T, G, VS, NA, SR, S2, S3, 3>(A, M, grid, threads, smem, s);
+        }
         if (cfg.nv == NA) return launch_stream_t<T, G, VS, NA, SR, S2, S3>(A, M, grid, threads, smem, s);
         if (cfg.nv == NB) return launch_stream_t<T, G, VS, NB, SR, S2, S3>(A, M, grid, threads, smem, s);
         return cudaErrorInvalidValue;

@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfdlb_gb300.so")
 
-CYL, SPH = 0, 1
+CYL, SPH, CYL_Z = 0, 1, 2  # CYL_Z: the cylinder with p_z integrated out (the pair phi, chi)
 FP64, FP32 = 0, 1
 CHI_RET_FM, CHI_SET_LOCAL = 0, 1
 QUAD_FULL, QUAD_HALF = 0, 1
@@ -234,7 +234,8 @@ class Solver:
     # ------------------------------------------------------------------ helpers
     def shape(self, q=0):
         d = self.param_dicts[q]
-        return (int(d["n_cells"]), 2 * int(d["Q_R"]), int(d["Q_2"]), int(d["Q_3"]))
+        n3 = 2 if int(d.get("geometry", CYL)) == CYL_Z else int(d["Q_3"])  # the reduced pair (phi, chi)
+        return (int(d["n_cells"]), 2 * int(d["Q_R"]), int(d["Q_2"]), n3)
 
     def info(self, q=0) -> dict:
         inf = Info()

@@ -26,6 +26,7 @@ import numpy as np
 
 CYL = 0
 SPH = 1
+CYL_Z = 2  # cylinder with p_z integrated out: the pair (phi, chi) in place of the p_z nodes
 
 
 def couette_cyl_64():
@@ -37,6 +38,15 @@ def couette_cyl_64():
 def fourier_cyl_1024():
     return dict(geometry=CYL, R_in=1.0, R_out=3.0, n_cells=1024, beta=1.5, Q_R=8, Q_2=8, Q_3=8,
                 Kn=0.05, eta0=0.2, T_wall=(1.0, 1.1), u_wall=(0.0, 0.0), dt=None, precision="fp32")
+
+
+def couette_cyl_reduced(Q_R=20, Q_2=8, eta0=0.1, C=4.0, R_L=1.0, cells_per_sigma=24, precision="fp32"):
+    """Cylindrical Couette flow on the paper's HHLB(7, Q_R) x HLB(7, 8) quadrature with p_z integrated
+    out (Sec. IV.A): sigma = 1, inner radius R_L, outer R_L + C, inner wall moving at U_w = sqrt(T_w),
+    T_w = 1 on both walls."""
+    return dict(geometry=CYL_Z, R_in=R_L, R_out=R_L + C, sigma=1.0, n_cells=int(round(C * cells_per_sigma)), beta=0.0,
+                Q_R=Q_R, Q_2=Q_2, Q_3=0, eta0=eta0, T_wall=(1.0, 1.0), u_wall=(1.0, 0.0), dt=None,
+                precision=precision, chi_model=0)
 
 
 def draw_log_uniform_kn(rng, accept, lo=0.01, hi=1.0, max_draws=10_000):

@@ -25,7 +25,9 @@ def small_case(geometry=wl.CYL, precision="fp64", n_cells=24, Q=(4, 4, 4), beta=
 
 
 def oracle_problem(d):
-    return osolver.make_problem(d["geometry"], d["R_in"], d["R_out"], d["n_cells"], d["Q_R"], d["Q_2"], d["Q_3"],
+    reduced = d["geometry"] == wl.CYL_Z
+    return osolver.make_problem(wl.CYL if reduced else d["geometry"], d["R_in"], d["R_out"], d["n_cells"], d["Q_R"],
+                                d["Q_2"], d["Q_3"], reduced=reduced,
                                 eta0=d["eta0"], Kn=d.get("Kn"), sigma=d.get("sigma"), beta=d.get("beta", 0.0) or 0.0,
                                 chi_model=d.get("chi_model", 0), T_wall=tuple(d["T_wall"]),
                                 u_wall=tuple(d["u_wall"]), dt=d.get("dt"), cfl=d.get("cfl") or 0.4)

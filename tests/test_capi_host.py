@@ -165,3 +165,18 @@ def test_fm_band_beyond_32_bit_offsets_is_rejected_before_allocation(lib):
     assert lib.fdlb_workspace_bytes(p, 1, ctypes.byref(nb)) == 1  # FDLB_EINVAL
     p = (fdlb.Params * 1)(fdlb.make_params(dict(base, chi_model=fdlb.CHI_SET_LOCAL)))
     assert lib.fdlb_workspace_bytes(p, 1, ctypes.byref(nb)) == 0 and nb.value > 0
+
+
+def test_reduced_cylinder_parameters(lib):
+    """FDLB_CYL_Z (p_z integrated out) takes Q_3 = 0 and plans a state of 2 x 2Q_R x Q_2 populations
+    per cell; a third-axis order is refused."""
+    import ctypes
+
+    from paper_2403_15051_gb300 import workloads as wl
+
+    d = wl.couette_cyl_reduced(Q_R=6, Q_2=4)
+    nb = ctypes.c_size_t()
+    arr = (fdlb.Params * 1)(fdlb.make_params(d))
+    assert lib.fdlb_workspace_bytes(arr, 1, ctypes.byref(nb)) == 0 and nb.value > 3 * d["n_cells"] * 2 * 12 * 4 * 4
+    arr = (fdlb.Params * 1)(fdlb.make_params(dict(d, Q_3=4)))
+    assert lib.fdlb_workspace_bytes(arr, 1, ctypes.byref(nb)) == 1  # FDLB_EINVAL
