@@ -556,6 +556,16 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     if (KS > 0) S.KS = KS;
     if (S.geometry == FDLB_SPH) S.KS = S.n3;  // every axis is coupled by the force term
     if (S.KS < 1 || S.n3 % S.KS) S.KS = S.n3;
+    if (S.geometry == FDLB_CYL) {
+        // a block holds at most 512 threads of at most 8 momenta: narrower slices (p_3 is passive on
+        // the cylinder) where a slice of the large radial orders would exceed that
+        const int vw_max = S.tsize == 4 ? 8 : 8;
+        while (S.KS > 1 && S.nR * S.n2 * S.KS > 512 * vw_max) {
+            int k = S.KS - 1;
+            while (k > 1 && S.n3 % k) --k;
+            S.KS = k;
+        }
+    }
     const int Ms = S.nR * S.n2 * S.KS;
     S.M.nR = S.nR;
     S.M.n2 = S.n2;
@@ -1173,7 +1183,9 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.rout = (double*)(R.ws + L.rout);
     R.krf = R.nR >= kKrKernelMinNodes ? (void*)(R.ws + L.krf) : nullptr;
     R.krg_on = R.krf != nullptr;
+    FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
     if (R.krg_on && R.precision == FDLB_FP32) {
+        // K^h as TF32 pairs for the tensor-core contraction (after the workspace is cleared)
         R.krB = (float*)(R.ws + L.krB);
         const std::vector<float> kb = kr_split_table(R.tab_h, R.M.o_KR, R.nR);
         FDLB_CUDA(cudaMemcpyAsync(R.krB, kb.data(), kb.size() * sizeof(float), cudaMemcpyHostToDevice, R.stream));
@@ -1181,7 +1193,6 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         R.tensor = 1;  // the tensor-core contraction by default
         R.kr_tc = 1;
     }
-    FDLB_CUDA(cudaMemsetAsync(R.ws, 0, L.total, R.stream));
     // tables, instances, geometry, walls, FM band
     FDLB_CUDA(cudaMemcpyAsync(R.tab, R.tab_h.data(), R.tab_h.size() * 8, cudaMemcpyHostToDevice, R.stream));
     std::vector<float> tabf(R.tab_h.begin(), R.tab_h.end());

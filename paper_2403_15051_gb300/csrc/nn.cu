@@ -8,13 +8,16 @@
 // 4 output channels (normalised n, u_2, T, q_R profiles).
 //
 // Precision: FP32 master weights (Adam), BF16 copies of every weight matrix used as GEMM
-// operands, FP32 activations and FP32 accumulation in every product.
+// operands, FP32 activations and FP32 accumulation in every product.  The products with a BF16
+// weight operand run on the tensor cores (mma.sync BF16, the activations as two BF16 parts); the
+// products of two FP32 operands (the DFT pair, the weight gradients) on the FP32 pipe.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -82,6 +85,90 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const fl
                 *c = alpha * acc[i][j] + (beta != 0.f ? beta * *c : 0.f);
             }
         }
+}
+
+// The products with a BF16 weight operand on the tensor cores: C[z] = alpha A[z] op(B[z]) + beta C[z]
+// with mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  The FP32 activations A are split into
+// two BF16 parts, a = a_hi + a_lo (a_hi = bf16(a), a_lo = bf16(a - a_hi)), and both parts multiply the
+// (exactly BF16) weights: the product keeps ~2^-17 of a's relative accuracy, as the FP32 FMA form does
+// to within that.  64 x 64 output tiles, 128 threads (four warps of 32 x 32: 2 x 4 MMA tiles of
+// 16 x 8), K in slices of 16 staged in shared memory as [row][k] BF16.
+// Fragment ownership of m16n8k16 (g = lane / 4, t = lane % 4; pairs of BF16 per 32-bit register, the
+// lower index in the low half): A a0 (g, 2t..2t+1), a1 (g+8, 2t..), a2 (g, 2t+8..), a3 (g+8, 2t+8..);
+// B b0 (k 2t..2t+1, n g), b1 (k 2t+8..2t+9, n g); D d0 (g, 2t), d1 (g, 2t+1), d2 (g+8, 2t), d3 (g+8, 2t+1).
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int lda, int tA,
+                                                        long long sA, const __nv_bfloat16* __restrict__ Bm, int ldb, int tB,
+                                                        long long sB, float* __restrict__ C, int ldc, long long sC,
+                                                        float alpha, float beta) {
+    constexpr int KP = 16 + 8;  // padded row: 48 bytes, pairs stay 4-byte aligned
+    __shared__ __align__(16) __nv_bfloat16 Ah[64][KP], Al[64][KP], Bs[64][KP];
+    const int z = blockIdx.z;
+    A += z * sA;
+    Bm += z * sB;
+    C += z * sC;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 64 * 16; e += 128) {
+            const int r = e >> 4, kk = e & 15, gk = k0 + kk;
+            const int gm = m0 + r;
+            float va = 0.f;
+            if (gm < M && gk < K) va = tA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(va);
+            Ah[r][kk] = hi;
+            Al[r][kk] = __float2bfloat16_rn(va - __bfloat162float(hi));
+            const int gn = n0 + r;
+            __nv_bfloat16 vb = __float2bfloat16_rn(0.f);
+            if (gn < N && gk < K) vb = tB ? Bm[(long long)gn * ldb + gk] : Bm[(long long)gk * ldb + gn];
+            Bs[r][kk] = vb;
+        }
+        __syncthreads();
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r = wm + mt * 16 + g;
+            ah[mt][0] = *reinterpret_cast<const uint32_t*>(&Ah[r][2 * t]);
+            ah[mt][1] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][2 * t]);
+            ah[mt][2] = *reinterpret_cast<const uint32_t*>(&Ah[r][2 * t + 8]);
+            ah[mt][3] = *reinterpret_cast<const uint32_t*>(&Ah[r + 8][2 * t + 8]);
+            al[mt][0] = *reinterpret_cast<const uint32_t*>(&Al[r][2 * t]);
+            al[mt][1] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][2 * t]);
+            al[mt][2] = *reinterpret_cast<const uint32_t*>(&Al[r][2 * t + 8]);
+            al[mt][3] = *reinterpret_cast<const uint32_t*>(&Al[r + 8][2 * t + 8]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int c = wn + nt * 8 + g;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * t]);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * t + 8]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_bf16(acc[mt][nt], al[mt], b0, b1);
+                mma_bf16(acc[mt][nt], ah[mt], b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int gm = m0 + wm + mt * 16 + g + ((q & 2) ? 8 : 0), gn = n0 + wn + nt * 8 + 2 * t + (q & 1);
+                if (gm < M && gn < N) {
+                    float* c = C + (long long)gm * ldc + gn;
+                    *c = alpha * acc[mt][nt][q] + (beta != 0.f ? beta * *c : 0.f);
+                }
+            }
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -208,7 +295,10 @@ template <typename TB>
 cudaError_t gemm(NNet& n, int M, int N, int K, const float* A, int lda, int tA, long long sA, const TB* B, int ldb,
                  int tB, long long sB, float* C, int ldc, long long sC, int batch, float alpha, float beta) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
-    gemm_kernel<TB><<<grid, 256, 0, n.stream>>>(M, N, K, A, lda, tA, sA, B, ldb, tB, sB, C, ldc, sC, alpha, beta);
+    if constexpr (std::is_same<TB, __nv_bfloat16>::value)
+        gemm_bf16_kernel<<<grid, 128, 0, n.stream>>>(M, N, K, A, lda, tA, sA, B, ldb, tB, sB, C, ldc, sC, alpha, beta);
+    else
+        gemm_kernel<TB><<<grid, 256, 0, n.stream>>>(M, N, K, A, lda, tA, sA, B, ldb, tB, sB, C, ldc, sC, alpha, beta);
     return cudaGetLastError();
 }
 

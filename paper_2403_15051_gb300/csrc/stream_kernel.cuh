@@ -416,7 +416,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const int j = jb * VW + e;
                 p2_[g][e] = sp_2[j];
                 wm_[g][e] = wik * sw_2[j];
-                iw_[g][e] = T(1) / wm_[g][e];
+                // a weight below the populations' range (FP32 at large radial orders) carries a zero
+                // population: its reconstruction and flux are zero
+                iw_[g][e] = wm_[g][e] > T(0) ? T(1) / wm_[g][e] : T(0);
             }
             if (c0 == 0 && pr > T(0)) {
                 const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
