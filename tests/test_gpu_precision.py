@@ -31,7 +31,7 @@ def test_fp32_with_fp64_polish_matches_fp64_steady_state():
     ds = [small_case(precision="fp64", **c) for c in CASES]
     R = fdlb.Solver(ds)
     rc, _, res = R.run_to_steady(tol=1e-12, max_steps=400_000, check_every=500)
-    assert np.all(res <= 1e-10), res  # a hundred times below the tolerance of the compared runs
+    assert np.all(res <= 1e-10), res  # ten times below the tolerance of the compared runs
     ref = [R.moments(q) for q in range(len(ds))]
     R.close()
     F = fdlb.Solver([dict(d, precision="fp32") for d in ds])
