@@ -503,7 +503,7 @@ def run_ours(args):
         S.close()
         # the compact form of the warm-start comparison (bench.py --time-to-steady runs the stated
         # counts): 256 training steady states, 32 held-out instances, the plain FP64 arm on 8
-        tts = time_to_steady(256, 32, 8, epochs=200)
+        tts = time_to_steady(256, 32, 8, epochs=200, ref_tol=1e-10, ref_steps=150_000)
     if rank == 0:
         cfg = bench_config(args, ds, world, flush_needed, persistent)
         cfg["tiling"] = tiling
@@ -575,18 +575,23 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
             out = {k: max(out[k], e[k]) for k in out}
         return out
 
-    # (R) FP64 references of every held-out instance, batched, to ref_tol; instances that never
-    # reach tol even in FP64 are left out
+    # (R) which held-out instances have a steady state: FP64, batched, to tol (instances that never
+    # get there even in FP64 settle on a small self-sustained oscillation; they are left out and
+    # counted); then FP64 references to ref_tol of the fixed subset the plain arm runs (the first
+    # n_plain kept, in seeded order), on which every arm's accuracy is measured
     t0 = time.perf_counter()
     R = fdlb.Solver([dict(d, precision="fp64") for d in eval_all])
+    _, _, res_tol = R.run_to_steady(tol=tol, max_steps=max_steps, check_every=ce)
+    R.close()
+    keep = [k for k in range(len(eval_all)) if float(res_tol[k]) <= tol]
+    plain_idx = keep[:n_plain]
+    R = fdlb.Solver([dict(eval_all[k], precision="fp64") for k in plain_idx])
     _, _, res_ref = R.run_to_steady(tol=ref_tol, max_steps=ref_steps, check_every=ce)
-    keep = [k for k in range(len(eval_all)) if float(res_ref[k]) <= tol]
-    ref_m = {k: R.moments(k) for k in keep}
-    n0s = {k: R.info(k)["n0"] for k in keep}
+    ref_m = {k: R.moments(j) for j, k in enumerate(plain_idx)}
+    n0s = {k: R.info(j)["n0"] for j, k in enumerate(plain_idx)}
     R.close()
     t_ref = time.perf_counter() - t0
     eval_ds = [eval_all[k] for k in keep]
-    plain_idx = keep[:n_plain]  # the fixed subset (the first kept, in seeded order)
     # (A) plain FP64, one instance after another, uniform start
     plain_steps, plain_err = [], []
     torch.cuda.synchronize()
@@ -612,13 +617,11 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
             s64 = np.zeros_like(s32)
         t = time.perf_counter() - t0
         errs = [moment_err(B.moments(j), ref_m[k], n0s[k]) for j, k in enumerate(keep) if k in plain_idx]
-        all_errs = [moment_err(B.moments(j), ref_m[k], n0s[k]) for j, k in enumerate(keep)]
         B.close()
         return {"seconds": t, "seconds_per_instance": t / len(eval_ds), "instances": len(eval_ds),
                 "steps_fp32": [int(x) for x in s32], "steps_fp64": [int(x) for x in s64],
                 "converged": int(sum(float(r) <= tol for r in res)),
-                "moment_error_vs_reference_on_plain_subset": worst(errs),
-                "moment_error_vs_reference_all": worst(all_errs)}
+                "moment_error_vs_reference_on_plain_subset": worst(errs)}
 
     arm_b = batched(True, True)
     arm_c = batched(True, False)
@@ -627,7 +630,8 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     return {"metric": "time to steady state (moment residual <= %g)" % tol, "unit": "s", "higher_is_better": False,
             "grid": {"cells": cells, "momenta": 2 * q ** 3}, "residual_check_every": ce, "max_steps": max_steps,
             "held_out": len(eval_all), "excluded_nonconvergent_fp64": len(eval_all) - len(keep),
-            "reference": {"precision": "fp64", "tol": ref_tol, "max_steps": ref_steps, "seconds": t_ref},
+            "reference": {"precision": "fp64", "tol": ref_tol, "max_steps": ref_steps, "seconds": t_ref,
+                          "instances": len(plain_idx), "residuals": [float(r) for r in res_ref]},
             "plain_fp64_sequential": {"instances": len(plain_idx), "seconds": t_plain, "seconds_per_instance": per_plain,
                                       "steps": plain_steps, "moment_error_vs_reference": worst(plain_err)},
             "batched_fp32_warm_start_fp64_polish": arm_b,

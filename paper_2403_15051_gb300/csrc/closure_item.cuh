@@ -144,7 +144,8 @@ __device__ T wall_flux_partial(const T* wall, long long st, const MomSet& M, con
             const T pr = tb.pRt[i];
             if (side == 0 ? !(pr < T(0)) : !(pr > T(0))) continue;
             if (M.reduced && k > 0) continue;  // the mass flux is phi's (chi = int p_z^2 f)
-            const T wm = tb.wRt[i] * tb.w2t[j] * tb.w3t[k], iw = wm > T(0) ? T(1) / wm : T(0);
+            const T wm = tb.wRt[i] * tb.w2t[j] * tb.w3t[k];
+            const T iw = wm > (sizeof(T) == 4 ? T(1e-30) : T(0)) ? T(1) / wm : T(0);  // as the stage kernel
             const T f0 = fv[u][0], f1 = fv[u][1], f2 = fv[u][2], f3 = fv[u][3];
             const T g1 = T(4) * f0 - T(6) * f1 + T(4) * f2 - f3;
             const T g2 = T(10) * f0 - T(20) * f1 + T(15) * f2 - T(4) * f3;

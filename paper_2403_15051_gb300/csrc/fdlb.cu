@@ -219,9 +219,30 @@ float tf32_round(float x) {
     std::memcpy(&r, &u, 4);
     return r;
 }
-std::vector<float> kr_split_table(const std::vector<double>& tab, int o_KR, int nR) {
+// The FP32 contraction's tables (kr_contract.cu): the weight-scaled Khat_ia = K^h_ia sqrt(w_a / w_i)
+// in FP64 from the radial weights w, then [split table | isw[nR] | sw[nR] | Khat[nR][nR] (FP32)],
+// isw = 1/sqrt(w) (zero beyond the float range: those populations are zero), sw = sqrt(w).
+size_t kr_table_floats(int nR) { return kr_split_floats(nR) + 2 * (size_t)nR + (size_t)nR * nR; }
+std::vector<double> kr_scaled(const std::vector<double>& tab, int o_KR, int o_wR, int nR) {
+    std::vector<double> K((size_t)nR * nR);
+    for (int i = 0; i < nR; ++i)
+        for (int a = 0; a < nR; ++a)
+            K[(size_t)i * nR + a] = tab[o_KR + (size_t)i * nR + a] * std::sqrt(tab[o_wR + a] / tab[o_wR + i]);
+    return K;
+}
+std::vector<float> kr_split_table(const std::vector<double>& tab, int o_KR, int o_wR, int nR) {
     const int Npad = kr_npad(nR), nk = ((nR + 7) / 8 * 8 + 31) / 32;
-    std::vector<float> out(kr_split_floats(nR), 0.f);
+    const std::vector<double> Kh = kr_scaled(tab, o_KR, o_wR, nR);
+    std::vector<float> out(kr_table_floats(nR), 0.f);
+    float* isw = out.data() + kr_split_floats(nR);
+    float* sw = isw + nR;
+    float* kplain = sw + nR;
+    for (int a = 0; a < nR; ++a) {
+        const double s = std::sqrt(tab[o_wR + a]);
+        sw[a] = (float)s;
+        isw[a] = 1.0 / s > 3.0e38 ? 0.f : (float)(1.0 / s);
+    }
+    for (size_t e = 0; e < Kh.size(); ++e) kplain[e] = (float)Kh[e];
     for (int kc = 0; kc < nk; ++kc) {
         float* hi = out.data() + (size_t)kc * Npad * 64;
         float* lo = hi + (size_t)Npad * 32;
@@ -229,7 +250,7 @@ std::vector<float> kr_split_table(const std::vector<double>& tab, int o_KR, int 
             for (int kk = 0; kk < 32; ++kk) {
                 const int a = kc * 32 + kk;
                 if (a >= nR) continue;
-                const float k32 = (float)tab[o_KR + (size_t)n * nR + a];
+                const float k32 = (float)Kh[(size_t)n * nR + a];
                 const float h = tf32_round(k32);
                 const size_t off = (size_t)(n / 8) * 256 + (kk / 4) * 32 + (n % 8) * 4 + kk % 4;
                 hi[off] = h;
@@ -276,7 +297,7 @@ Layout make_layout(const Solver& S) {
     // K^h f of the stage input for the contraction kernel (large radial orders only)
     L.krf = take(S.nR >= kKrKernelMinNodes ? S.f_elems * S.tsize : 0);
     // K^h as TF32 pairs for the tensor-core contraction kernel (FP32 populations)
-    L.krB = take(S.nR >= kKrKernelMinNodes && S.tsize == 4 ? kr_split_floats(S.nR) * sizeof(float) : 0);
+    L.krB = take(S.nR >= kKrKernelMinNodes && S.tsize == 4 ? kr_table_floats(S.nR) * sizeof(float) : 0);
     L.total = off;
     return L;
 }
@@ -711,15 +732,17 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
 int launch_kr_buf(Solver& S, int in) {
     const int grid = std::max(1, std::min(S.grid_stream, S.n_sm * 8));
     cudaError_t e;
+    const float* isw = S.krB ? S.krB + kr_split_floats(S.nR) : nullptr;
+    const float* sw = isw ? isw + S.nR : nullptr;
     if (S.kr_tc)
-        e = launch_kr_contract_tc((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d, S.krB, S.M,
-                                  kr_npad(S.nR), S.err, std::max(1, std::min(S.grid_stream, S.n_sm)), S.stream);
-    else if (S.precision == FDLB_FP32)
-        e = launch_kr_contract<float>((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d,
-                                      (const float*)S.tabT + S.M.o_KR, S.M, grid, S.stream);
+        e = launch_kr_contract_tc((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d, S.krB, isw, sw,
+                                  S.M, kr_npad(S.nR), S.err, std::max(1, std::min(S.grid_stream, S.n_sm)), S.stream);
+    else if (S.precision == FDLB_FP32)  // the weight-scaled form, as the tensor-core kernel
+        e = launch_kr_contract<float>((const float*)S.f[in], (float*)S.krf, S.sitems, S.n_sitems, S.inst_d, sw + S.nR,
+                                      isw, sw, S.M, grid, S.stream);
     else
         e = launch_kr_contract<double>((const double*)S.f[in], (double*)S.krf, S.sitems, S.n_sitems, S.inst_d,
-                                       (const double*)S.tabT + S.M.o_KR, S.M, grid, S.stream);
+                                       (const double*)S.tabT + S.M.o_KR, nullptr, nullptr, S.M, grid, S.stream);
     S.launches++;
     return cuda_status(e);
 }
@@ -1187,7 +1210,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     if (R.krg_on && R.precision == FDLB_FP32) {
         // K^h as TF32 pairs for the tensor-core contraction (after the workspace is cleared)
         R.krB = (float*)(R.ws + L.krB);
-        const std::vector<float> kb = kr_split_table(R.tab_h, R.M.o_KR, R.nR);
+        const std::vector<float> kb = kr_split_table(R.tab_h, R.M.o_KR, R.M.o_wR, R.nR);
         FDLB_CUDA(cudaMemcpyAsync(R.krB, kb.data(), kb.size() * sizeof(float), cudaMemcpyHostToDevice, R.stream));
         FDLB_CUDA(cudaStreamSynchronize(R.stream));
         R.tensor = 1;  // the tensor-core contraction by default

@@ -123,12 +123,14 @@ FDLB_STEP_DECL(double, 1)
 // (any precision) or, for FP32 populations where available, the tensor-core kernel.
 template <typename T>
 cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int* n_items, const InstDev* inst,
-                               const T* KR, const MomSet& M, int grid, cudaStream_t s);
+                               const T* KR, const T* isw, const T* sw, const MomSet& M, int grid, cudaStream_t s);
 
-// The tensor-core form (FP32): Bsplit holds K^h as TF32 pairs in the kernel's shared-memory layout
-// (kr_split_table), Npad = 2Q_R rounded up to 16; err is set when a bounded wait runs out.
+// The tensor-core form (FP32): Bsplit holds the weight-scaled K^h (kr_contract.cu) as TF32 pairs in
+// the kernel's shared-memory layout (kr_split_table), isw / sw the scales, Npad = 2Q_R rounded up to
+// 16; err is set when a bounded wait runs out.
 cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,
-                                  const float* Bsplit, const MomSet& M, int Npad, int* err, int grid, cudaStream_t s);
+                                  const float* Bsplit, const float* isw, const float* sw, const MomSet& M, int Npad,
+                                  int* err, int grid, cudaStream_t s);
 size_t kr_tc_smem_bytes(int Npad);
 
 // The Fischer-Methfessel weights of one instance's band, computed on the device in FP64 (the host

@@ -4,7 +4,8 @@
 // the radial order is large (the paper's HHLB(7,20) .. HHLB(7,100), Sec. IV): K^h no longer fits
 // beside the staged rows in shared memory, and the contraction (2 x 2Q_R flops per population)
 // dominates the stage's arithmetic.  The result has the layout of f; the fused stage reads it in
-// place of its own contraction.
+// place of its own contraction.  FP32 populations use the weight-scaled form (see
+// kr_cuda_core_kernel): K^h itself leaves the float range at the largest radial orders.
 //
 // Seen as one GEMM: rows i of K^h against the columns (block, j) of X, the blocks of a stage work
 // item (instance, first cell, cells, slice) being contiguous in memory.  Two forms:
@@ -26,10 +27,16 @@ namespace {
 constexpr int kTile = 64;   // output rows and columns per tile
 constexpr int kChunk = 16;  // contraction chunk
 
+// With isw and sw (FP32 populations) the product runs in the weight-scaled form
+// (K^h f)_i = sw_i sum_a Khat_ia (isw_a f_a): Khat = K^h scaled by sqrt(w_a / w_i) (radial weights
+// w) has entries of order one, where K^h itself spans ~1e-100 .. 1e+100 at the largest radial
+// orders and leaves the float range; sw = sqrt(w), isw = 1/sqrt(w) (zero where it exceeds the
+// float range: those populations are zero in FP32).  Without them, KR is K^h itself.
 template <typename T>
 __global__ void __launch_bounds__(256) kr_cuda_core_kernel(const T* __restrict__ f, T* __restrict__ out,
                                                            const int4* __restrict__ items, const int* __restrict__ n_items,
                                                            const InstDev* __restrict__ inst, const T* __restrict__ KR,
+                                                           const T* __restrict__ isw, const T* __restrict__ sw,
                                                            MomSet M) {
     __shared__ T Ks[kChunk][kTile + 1];  // [a][i]: K^h chunk, transposed
     __shared__ T Xs[kChunk][kTile];      // [a][column]
@@ -64,6 +71,7 @@ __global__ void __launch_bounds__(256) kr_cuda_core_kernel(const T* __restrict__
                             const int blk = col / n2, j = col % n2;
                             const int c = w.y + blk / KS, k = w.w * KS + blk % KS;
                             v = fb[(long long)c * Np + ((long long)k * nR + a) * n2 + j];
+                            if (isw) v *= isw[a];
                         }
                         Xs[kk][cc] = v;
                     }
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(256) kr_cuda_core_kernel(const T* __restrict__
                         if (i < nR && col < ncols) {
                             const int blk = col / n2, j = col % n2;
                             const int c = w.y + blk / KS, k = w.w * KS + blk % KS;
-                            ob[(long long)c * Np + ((long long)k * nR + i) * n2 + j] = acc[r][q];
+                            ob[(long long)c * Np + ((long long)k * nR + i) * n2 + j] = sw ? sw[i] * acc[r][q] : acc[r][q];
                         }
                     }
             }
@@ -158,6 +166,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __global__ void __launch_bounds__(128, 1) kr_tc_kernel(const float* __restrict__ f, float* __restrict__ out,
                                                        const int4* __restrict__ items, const int* __restrict__ n_items,
                                                        const InstDev* __restrict__ inst, const float* __restrict__ Bsplit,
+                                                       const float* __restrict__ isw, const float* __restrict__ sw,
                                                        MomSet M, int Npad, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bfull[2], mdone[2], drain;
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(128, 1) kr_tc_kernel(const float* __restrict__
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int a = kc * kUK + k4 * 4 + e;
-                        v[e] = (valid && a < nR) ? __ldg(f + base + (long long)a * n2) : 0.f;
+                        v[e] = (valid && a < nR) ? __ldg(f + base + (long long)a * n2) * __ldg(isw + a) : 0.f;
                     }
                     uint32_t hi[4], lo[4];
 #pragma unroll
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(128, 1) kr_tc_kernel(const float* __restrict__
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const int n = n0 + q;
-                        if (n < nR) out[base + (long long)n * n2] = v[q];
+                        if (n < nR) out[base + (long long)n * n2] = __ldg(sw + n) * v[q];
                     }
                 }
             }
@@ -308,25 +317,28 @@ __global__ void __launch_bounds__(128, 1) kr_tc_kernel(const float* __restrict__
 
 template <typename T>
 cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int* n_items, const InstDev* inst,
-                               const T* KR, const MomSet& M, int grid, cudaStream_t s) {
-    kr_cuda_core_kernel<T><<<grid, 256, 0, s>>>(f, out, items, n_items, inst, KR, M);
+                               const T* KR, const T* isw, const T* sw, const MomSet& M, int grid, cudaStream_t s) {
+    kr_cuda_core_kernel<T><<<grid, 256, 0, s>>>(f, out, items, n_items, inst, KR, isw, sw, M);
     return cudaPeekAtLastError();
 }
 
 size_t kr_tc_smem_bytes(int Npad) { return 1024 + 4 * (size_t)kAPart + 4 * (size_t)Npad * 128; }
 
 cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,
-                                  const float* Bsplit, const MomSet& M, int Npad, int* err, int grid, cudaStream_t s) {
+                                  const float* Bsplit, const float* isw, const float* sw, const MomSet& M, int Npad,
+                                  int* err, int grid, cudaStream_t s) {
     const size_t smem = kr_tc_smem_bytes(Npad);
     cudaError_t e = cudaFuncSetAttribute(kr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kr_tc_kernel<<<grid, 128, smem, s>>>(f, out, items, n_items, inst, Bsplit, M, Npad, err);
+    kr_tc_kernel<<<grid, 128, smem, s>>>(f, out, items, n_items, inst, Bsplit, isw, sw, M, Npad, err);
     return cudaPeekAtLastError();
 }
 
 template cudaError_t launch_kr_contract<float>(const float*, float*, const int4*, const int*, const InstDev*,
-                                               const float*, const MomSet&, int, cudaStream_t);
+                                               const float*, const float*, const float*, const MomSet&, int,
+                                               cudaStream_t);
 template cudaError_t launch_kr_contract<double>(const double*, double*, const int4*, const int*, const InstDev*,
-                                                const double*, const MomSet&, int, cudaStream_t);
+                                                const double*, const double*, const double*, const MomSet&, int,
+                                                cudaStream_t);
 
 }  // namespace fdlb

@@ -416,9 +416,10 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const int j = jb * VW + e;
                 p2_[g][e] = sp_2[j];
                 wm_[g][e] = wik * sw_2[j];
-                // a weight below the populations' range (FP32 at large radial orders) carries a zero
-                // population: its reconstruction and flux are zero
-                iw_[g][e] = wm_[g][e] > T(0) ? T(1) / wm_[g][e] : T(0);
+                // a weight at the bottom of the populations' range (FP32 at large radial orders: below
+                // 1e-30 its populations are below 1e-28 or zero, and 1/w leaves the float range)
+                // contributes no reconstruction and no flux
+                iw_[g][e] = wm_[g][e] > (sizeof(T) == 4 ? T(1e-30) : T(0)) ? T(1) / wm_[g][e] : T(0);
             }
             if (c0 == 0 && pr > T(0)) {
                 const T gik = nwL * gwL[i] * gwL[nR + n2 + k];

@@ -2,14 +2,17 @@
 rounding floor, some 1e-5 to 1e-4 of the moment scales away from the FP64 one for dense, small-Kn
 instances; the library's two-precision schedule (fdlb_run_to_steady_mixed: FP32 to the
 tolerance, then an FP64 polish on the device) brings every moment within 1e-5 of the FP64 steady
-state.  The reference is the FP64 form run to a residual a hundred times tighter."""
+state.  The reference is the FP64 form run ten times below the compared runs' tolerance; instances
+of the sweep distribution whose FP64 residual never gets there (a few settle on a small
+self-sustained oscillation) are left out, and at least three must remain."""
 import numpy as np
 import pytest
 
 from paper_2403_15051_gb300 import build as fbuild
 from paper_2403_15051_gb300 import fdlb
+from paper_2403_15051_gb300 import workloads as wl
 
-from .cases import compare_moments, oracle_problem, small_case
+from .cases import accept_kn, compare_moments, oracle_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -19,33 +22,30 @@ def _built():
     fbuild.build()
 
 
-CASES = [
-    # dense gas
-    dict(n_cells=64, Kn=0.1, eta0=0.2, T_wall=(1.0, 1.2), u_wall=(0.2, 0.0), R=(1.0, 2.0)),
-    # a member of the sweep distribution, moderate density
-    dict(n_cells=64, Kn=0.05, eta0=0.1, T_wall=(1.0, 1.25), u_wall=(0.25, 0.0), R=(1.0, 3.5)),
-]
-
-
 def test_fp32_with_fp64_polish_matches_fp64_steady_state():
-    ds = [small_case(precision="fp64", **c) for c in CASES]
+    # six members of the batched-sweep distribution on the reduced grid (64 cells, Q = 4)
+    ds = wl.batch_instances(lambda kn, e, r: accept_kn(kn, e), n=6, seed=3, n_lo=64, n_hi=64)
+    for d in ds:
+        d.update(Q_R=4, Q_2=4, Q_3=4, precision="fp64")
     R = fdlb.Solver(ds)
-    rc, _, res = R.run_to_steady(tol=1e-12, max_steps=400_000, check_every=500)
-    assert np.all(res <= 1e-10), res  # ten times below the tolerance of the compared runs
-    ref = [R.moments(q) for q in range(len(ds))]
+    _, _, res = R.run_to_steady(tol=1e-10, max_steps=300_000, check_every=500)
+    keep = [q for q in range(len(ds)) if res[q] <= 1e-10]
+    assert len(keep) >= 3, res
+    ref = {q: R.moments(q) for q in keep}
     R.close()
+    ds = [ds[q] for q in keep]
     F = fdlb.Solver([dict(d, precision="fp32") for d in ds])
-    rc32, st32, st64, res_m = F.run_to_steady_mixed(tol=1e-9, max_steps=400_000, check_every=500)
+    rc32, st32, st64, res_m = F.run_to_steady_mixed(tol=1e-9, max_steps=300_000, check_every=500)
     assert rc32 == 0 and np.all(res_m <= 1e-9), (rc32, res_m)
     assert np.all(st32 > 0) and np.all(st64 > 0)
     P32 = fdlb.Solver([dict(d, precision="fp32") for d in ds])
-    P32.run_to_steady(tol=1e-8, max_steps=400_000, check_every=500)
-    for q, d in enumerate(ds):
+    P32.run_to_steady(tol=1e-8, max_steps=300_000, check_every=500)
+    for j, (q, d) in enumerate(zip(keep, ds)):
         P = oracle_problem(d)
-        mo = {"n": ref[q]["n"], "T": ref[q]["T"], "P01": ref[q]["P12"],
-              "u": np.stack([ref[q][f"u{a + 1}"] for a in range(3)], -1),
-              "q": np.stack([ref[q][f"q{a + 1}"] for a in range(3)], -1)}
-        err_mixed = compare_moments(F.moments(q), mo, P)
-        err_fp32 = compare_moments(P32.moments(q), mo, P)
+        m = ref[q]
+        mo = {"n": m["n"], "T": m["T"], "P01": m["P12"], "u": np.stack([m[f"u{a + 1}"] for a in range(3)], -1),
+              "q": np.stack([m[f"q{a + 1}"] for a in range(3)], -1)}
+        err_mixed = compare_moments(F.moments(j), mo, P)
+        err_fp32 = compare_moments(P32.moments(j), mo, P)
         print("instance", q, "FP32 alone", err_fp32, "FP32 + FP64 polish", err_mixed)
         assert max(err_mixed.values()) <= 1e-5, (q, err_mixed)
