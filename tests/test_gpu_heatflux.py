@@ -38,6 +38,7 @@ def test_heat_flux_channel_constants(geom):
         spread = (c.max() - c.min()) / abs(c.mean())
         assert spread < 1e-3, (d["eta0"], d["R_in"], spread)
         const[(d["eta0"], d["R_in"])] = c.mean() / d["R_in"] ** power
+    print("geometry", geom, {k: round(v, 6) for k, v in const.items()})
     for eta0 in (0.01, 0.1, 0.2):
         v = np.array([abs(const[(eta0, rl)]) for rl in (1.0, 2.0, 5.0, 10.0, 20.0, 50.0)])
         assert np.all(np.diff(v) < 0), (eta0, v)  # toward the planar value, monotonically

@@ -43,15 +43,17 @@ LOCAL, FM = osolver.SET_LOCAL, osolver.RET_FM
 # (name, module, old, new, pin module, the pin module's name for the oracle module, pin, args)
 CASES = [
     # collision term (Eqs. shakhov, j1)
-    ("J1 div-u constant", "solver", '(zeta2 - 2.5) * e(cl["div"])', '(zeta2 - 1.5) * e(cl["div"])',
+    ("J1 div-u constant", "solver", '(strain + (zeta2 - 2.5) * e(cl["div"])', '(strain + (zeta2 - 1.5) * e(cl["div"])',
      t_solver, "S", "test_collision_momentum_and_energy_moments", (CYL, LOCAL)),
     ("J1 strain factor 2 dropped", "solver", "strain = 2.0 * strain / (2.0 * e(T))", "strain = strain / (2.0 * e(T))",
      t_solver, "S", "test_collision_momentum_and_energy_moments", (CYL, FM)),
-    ("J1 Y constant", "solver", '0.6 * (zeta2 - 2.5) * e(cl["Y"])', '0.6 * (zeta2 - 1.5) * e(cl["Y"])',
+    ("J1 Y constant", "solver", 'xi[0] * (e(cl["X"]) + 0.6 * (zeta2 - 2.5) * e(cl["Y"])',
+     'xi[0] * (e(cl["X"]) + 0.6 * (zeta2 - 1.5) * e(cl["Y"])',
      t_solver, "S", "test_collision_momentum_and_energy_moments", (CYL, LOCAL)),
     ("J1 X on the second axis", "solver", 'xi[0] * (e(cl["X"])', 'xi[1] * (e(cl["X"])',
      t_solver, "S", "test_collision_momentum_and_energy_moments", (CYL, LOCAL)),
-    ("Shakhov xi^2/(5T)", "solver", "(xi2 / (5.0 * e(T)) - 1.0) * xiq", "(xi2 / (3.0 * e(T)) - 1.0) * xiq",
+    ("Shakhov xi^2/(5T)", "solver", "fS = fMB * (1.0 + e((1.0 - cl[\"Pr\"]) / (n * T * T)) * (xi2 / (5.0 * e(T)) - 1.0) * xiq)",
+     "fS = fMB * (1.0 + e((1.0 - cl[\"Pr\"]) / (n * T * T)) * (xi2 / (3.0 * e(T)) - 1.0) * xiq)",
      t_solver, "S", "test_collision_momentum_and_energy_moments", (SPH, FM)),
     ("sphere strain S_33 dropped", "solver", "S[:, 1, 1] = S[:, 2, 2] = u[:, 0] / R", "S[:, 1, 1] = u[:, 0] / R",
      t_solver, "S", "test_collision_momentum_and_energy_moments", (SPH, LOCAL)),
@@ -142,6 +144,8 @@ CASES = [
      t_red, "S", "test_reduced_moments_are_the_projection", ()),
     ("reduced wall mass flux of both members", "solver", "mass = (lambda a: a[..., :1]) if P.reduced else (lambda a: a)",
      "mass = (lambda a: a)", t_red, "S", "test_reduced_mass_conserved_and_seed_carries_its_profiles", ()),
+    ("reduced J1 div-u constant", "solver", '(strain_perp + (zeta2 - 2.5) * e(cl["div"])',
+     '(strain_perp + (zeta2 - 1.5) * e(cl["div"])', t_red, "S", "test_reduced_collision_is_the_projection", (FM,)),
     ("reduced wall pair without T_w", "solver", "g3 = np.array([1.0, Tw]) if P.reduced", "g3 = np.array([1.0, 1.0]) if P.reduced",
      t_red, "S", "test_reduced_rhs_is_the_projection_under_linear_reconstruction", (LOCAL,)),
     # quadrature (Sec. III.A)
