@@ -289,11 +289,22 @@ int fdlb_clear_error(fdlb_handle h);
  * bit for bit either way; 0 turns it off (ordinary stream-ordered launches). */
 int fdlb_set_programmatic_launch(fdlb_handle h, int enable);
 
-/* Own cells per closure work item (1..28; default 2 on the cylinder, 4 on the sphere).  A closure item also recomputes the
- * macroscopic fields of two stencil cells on each side, so larger items repeat less work and
- * smaller items spread the latency-bound closure over more SMs.  FDLB_EINVAL outside the
- * range. */
+/* Own cells per closure work item of the chain form (1..28; default 2 on the cylinder, 4 on the
+ * sphere, 8 where items outnumber the co-resident blocks several times over).  A closure item also
+ * recomputes the macroscopic fields of two stencil cells on each side, so larger items repeat less
+ * work and smaller items spread the latency-bound closure over more SMs.  Selects the chain form.
+ * FDLB_EINVAL outside the range. */
 int fdlb_set_closure_cells(fdlb_handle h, int cells);
+
+/* Form of the closure (Eqs. fm, chi, j1, tau, prandtl and the equilibria of Sec. III.C, once per
+ * stage).  form 0, the chain: one launch, each block runs an item of a few cells through the whole
+ * closure (short, latency-bound: one instance).  form 1, the batch form: two launches over items
+ * of 28 cells, the first forming every cell's n, u, T, q and FM band sum, the second the records
+ * from them (throughput-bound: batches and long instances; the default when the items of 28 cells
+ * are more than four times the SM count).  The records are the same bit for bit either way.
+ * form -1 changes nothing.  *in_use (may be NULL) = the form in use.  FDLB_EINVAL for another
+ * form. */
+int fdlb_set_closure_form(fdlb_handle h, int form, int* in_use);
 
 /* Number of kernel launches issued by the last fdlb_step call (for launch accounting). */
 int64_t fdlb_launch_count(fdlb_handle h);

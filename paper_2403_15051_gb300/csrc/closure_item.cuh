@@ -169,6 +169,306 @@ struct NoAfterLoads {
     __device__ void operator()() const {}
 };
 
+// ---- the per-cell steps of the closure.  The item chain below (closure_cells) and the two
+// kernels of the batch form (closure_fields_kernel, closure_records_kernel) are made of these
+// functions, so a cell's record is the same whichever form computes it.
+
+// Raw sums of global cell `gc` over its slices, in the wide type: FP64, or for FP32 populations
+// the double-float pairs the stage kernel stores beside the FP64 sums (no FP64 arithmetic).
+template <typename T>
+__device__ __forceinline__ void clo_load_sums(const ClosureArgs& A, long long gc, Wide<T> (&sv)[kSums]) {
+    const int slices = A.slices;
+    if constexpr (sizeof(T) == 4) {
+        const float2* src = reinterpret_cast<const float2*>(A.sumsw) + gc * slices * kSums;
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) {
+            const float2 p = src[q];
+            sv[q] = Wide<T>{p.x, p.y};
+        }
+        for (int sl = 1; sl < slices; ++sl)
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) {
+                const float2 p = src[sl * kSums + q];
+                sv[q] = w_add(sv[q], Wide<T>{p.x, p.y});
+            }
+    } else {
+        const double* src = A.sums + gc * slices * kSums;
+#pragma unroll
+        for (int q = 0; q < kSums; ++q) sv[q] = w_from(src[q], (T*)nullptr);
+        for (int sl = 1; sl < slices; ++sl)
+#pragma unroll
+            for (int q = 0; q < kSums; ++q) sv[q] = w_add(sv[q], w_from(src[sl * kSums + q], (T*)nullptr));
+    }
+}
+
+// n, u, T of a cell (Eq. macro_def) in the wide type, and the heat flux q in the populations'
+// precision (it enters only the Shakhov factor and the diagnostics).
+template <typename T>
+__device__ __forceinline__ void clo_fields(const Wide<T> (&sv)[kSums], Wide<T>& n, Wide<T> (&u)[3], Wide<T>& Tc,
+                                           T (&q)[3]) {
+    using W = Wide<T>;
+    n = sv[0];
+    u[0] = w_div(sv[1], n);
+    u[1] = w_div(sv[2], n);
+    u[2] = w_div(sv[3], n);
+    const W tr = w_add(w_add(sv[4], sv[5]), sv[6]);
+    const W uu = w_add(w_add(w_mul(u[0], u[0]), w_mul(u[1], u[1])), w_mul(u[2], u[2]));
+    Tc = w_div(w_sub(tr, w_mul(n, uu)), w_scale(n, T(3)));
+    const T tn = w_hi(n), t0 = w_hi(u[0]), t1 = w_hi(u[1]), t2 = w_hi(u[2]), ttr = w_hi(tr), tuu = w_hi(uu);
+    const T s4 = w_hi(sv[4]), s5 = w_hi(sv[5]), s6 = w_hi(sv[6]), s7 = w_hi(sv[7]), s8 = w_hi(sv[8]), s9 = w_hi(sv[9]);
+    const T m0 = s4 * t0 + s7 * t1 + s8 * t2;
+    const T m1 = s7 * t0 + s5 * t1 + s9 * t2;
+    const T m2 = s8 * t0 + s9 * t1 + s6 * t2;
+    q[0] = T(0.5) * (w_hi(sv[10]) - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
+    q[1] = T(0.5) * (w_hi(sv[11]) - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
+    q[2] = T(0.5) * (w_hi(sv[12]) - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
+}
+
+// The FM band sum of one row (Eq. fm; a whole warp, every lane returns the sum): weights Wr[k]
+// times densities dn(k), k < kmax, lane-strided with four accumulators, then a butterfly.
+template <typename T, typename Dens>
+__device__ __forceinline__ T clo_band_row(const T* Wr, const Dens& dn, int kmax, int lane) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int k = lane;
+    for (; k + 96 < kmax; k += 128) {
+        a0 += Wr[k] * dn(k);
+        a1 += Wr[k + 32] * dn(k + 32);
+        a2 += Wr[k + 64] * dn(k + 64);
+        a3 += Wr[k + 96] * dn(k + 96);
+    }
+    for (; k < kmax; k += 32) a0 += Wr[k] * dn(k);
+    return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// chi = chi_SET(eta), eta = etafac x (Eqs. chi, chi_ret), in the wide type, rounded once: J1
+// scales with b rho chi, and near finely resolved walls J1 is large enough that a few roundings of
+// chi show in the right-hand side.
+template <typename T>
+__device__ __forceinline__ T clo_chi(T etafac, T x) {
+    using W = Wide<T>;
+    const W eta = w_scale(w_from_t(x), etafac);
+    const W om = w_sub(w_from_t(T(1)), eta);
+    const W om3 = w_mul(w_mul(om, om), om);
+    return w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
+}
+
+// The reach cells' fields as a block holds them (shared memory, reach-local index).
+template <typename T>
+struct ReachView {
+    const Wide<T>* n;
+    const Wide<T>* Tc;
+    const Wide<T>* u[3];
+    const T* chi;
+    const T* nb;
+};
+
+// Position q of the J1 gradient stencils of own cell c (reach index lt; the stencil cell has
+// reach index k, weight wq): the five gradient terms, logarithms of ratios to the own cell, exact
+// because the stencil weights sum to zero:
+//   sum_q w_q ln(n_q^2 chi_q T_q) = sum_q w_q [2 log1p(dn_q / n) + log1p(dchi_q / chi) + log1p(dT_q / T)],
+// the differences taken in the wide type; ln chi_q - ln chi_c from the packing-fraction
+// difference alone, since ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of
+// chi itself); velocity differences in the wide type.
+template <typename T>
+__device__ __forceinline__ void clo_grad_terms(const ReachView<T>& R, int k, int lt, T wq, T etaf, bool chi_local,
+                                               T (&g)[5]) {
+    const Wide<T> nw = R.n[lt], Tw = R.Tc[lt];
+    const T lT = log1p(ratio_fast(w_hi(w_sub(R.Tc[k], Tw)), w_hi(Tw)));
+    const T ln = log1p(ratio_fast(w_hi(w_sub(R.n[k], nw)), w_hi(nw)));
+    const T dnb = chi_local ? w_hi(w_sub(R.n[k], nw)) : R.nb[k] - R.nb[lt];
+    const T etac = etaf * (chi_local ? w_hi(nw) : R.nb[lt]), deta = etaf * dnb;
+    const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
+    g[0] = wq * (T(2) * ln + lchi + lT);
+    g[1] = wq * lT;
+    g[2] = wq * w_hi(w_sub(R.u[0][k], R.u[0][lt]));
+    g[3] = wq * w_hi(w_sub(R.u[1][k], R.u[1][lt]));
+    g[4] = wq * w_hi(w_sub(R.u[2][k], R.u[2][lt]));
+}
+
+// The 20 scalars of an own cell's collision record: n, u, 1/T, 1/tau (Eq. tau), the Shakhov
+// coefficient (Eq. prandtl), q, b rho chi, the J1 gradients X = d ln(n^2 chi T), Y = d ln T, the
+// velocity derivative, the covariant strain (cylinder / sphere) and its divergence (Eq. j1);
+// mu from Eq. viscosity.  gp[v][q]: the gradient terms of the cell's five stencil positions.
+template <typename T>
+__device__ __forceinline__ void clo_record_scalars(T* ct, const ReachView<T>& R, int lt, const T (&gp)[5][5], T geo0,
+                                                   T geo1, const T (&q)[3], const InstDev& I) {
+    using C = T;
+    const C cn = w_hi(R.n[lt]), cT = w_hi(R.Tc[lt]), cchi = R.chi[lt];
+    const C in = ratio_fast(C(1), cn), iT = ratio_fast(C(1), cT), ichi = ratio_fast(C(1), cchi);
+    C gsum[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) gsum[v] = (gp[v][0] + gp[v][1]) + (gp[v][2] + gp[v][3]) + gp[v][4];
+    const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
+    const C X = gsum[0] * sc, Y = gsum[1] * sc;
+    const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
+    const C iR = ratio_fast(C(1), geo0);
+    const C cu0 = w_hi(R.u[0][lt]), cu1 = w_hi(R.u[1][lt]), cu2 = w_hi(R.u[2][lt]);
+    const C sg = inst_param<C>(I.sigma, I.f_sigma);
+    const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
+    const C pi = C(3.14159265358979323846);
+    const C mu = ratio_fast(C(5), C(16) * sg * sg) * sqrt(cT * C(0.31830988618379067154)) *
+                 (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
+    const C Pr = ratio_fast(C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x),
+                            C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
+    C S11, S22, S01, S02, div;
+    if (I.geometry == 0) {
+        S11 = cu0 * iR;
+        S22 = C(0);
+        S01 = C(0.5) * (cd1 - cu1 * iR);
+        S02 = C(0.5) * cd2;
+        div = cd0 + cu0 * iR;
+    } else {
+        S11 = S22 = cu0 * iR;
+        S01 = C(0.5) * (cd1 - cu1 * iR);
+        S02 = C(0.5) * (cd2 - cu2 * iR);
+        div = cd0 + C(2) * cu0 * iR;
+    }
+    ct[0] = cn;
+    ct[1] = cu0;
+    ct[2] = cu1;
+    ct[3] = cu2;
+    ct[4] = iT;
+    ct[5] = ratio_fast(cn * cT, mu);
+    ct[6] = (C(1) - Pr) * iT * iT * in;
+    ct[7] = q[0];
+    ct[8] = q[1];
+    ct[9] = q[2];
+    ct[10] = x;
+    ct[11] = X;
+    ct[12] = Y;
+    ct[13] = cd0;
+    ct[14] = S11;
+    ct[15] = S22;
+    ct[16] = S01;
+    ct[17] = S02;
+    ct[18] = T(0);
+    ct[19] = div;
+}
+
+// Expansion coefficients of one equilibrium factor of an own cell (Sec. III.C); job 0 / 1: the
+// half-range axis on the half line of sign + / -, job 2 / 3: the full-range axes 2 / 3.  cT, tm1
+// = T - 1 (without cancellation), ur = u_R, ua = u_2 (job 2) or u_3 (job 3).
+template <typename T>
+__device__ __forceinline__ void clo_eq_coeffs(int job, T cT, T tm1, T ur, T ua, const ClosureTabs<T>& tb,
+                                              const MomSet& M, T (&ev)[kMaxE + 1]) {
+    using C = T;
+    const T *ha = tb.ha, *hb = tb.hb, *ihb = tb.ihb, *h0t = tb.h0t;
+#pragma unroll
+    for (int l = 0; l <= kMaxE; ++l) ev[l] = C(0);
+    if (job < 2) {
+        // half range, half line of sign s (job 0: +, 1: -), v = s u_R.  The recurrence of the
+        // coefficients,
+        //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
+        //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
+        //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
+        // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1: r_0 = h_0 / 2,
+        // r_l = 0 for l >= 1), where every term is small and nothing cancels: with
+        // D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) / sqrt T, z = v / sqrt(2T),
+        // and h_0(0) r_0 = 1,
+        //   d_0 = h_0 erf(z) / 2,
+        //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
+        //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
+        //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
+        const C v = job == 0 ? ur : -ur;
+        const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
+        const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
+        const C is2pi = C(0.39894228040143267794);
+        const C r0 = h0t[0] * C(0.5);
+        C d[kMaxE + 1];
+#pragma unroll
+        for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
+        d[0] = r0 * erf(z);
+        C run = C(0);  // sum_{k<l} h_k(0) d_k
+#pragma unroll
+        for (int l = 0; l < kMaxE; ++l) {
+            if (l < M.NR) {
+                C val;
+                if (l == 0) {
+                    val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
+                } else {
+                    const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
+                    val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
+                }
+                run += h0t[l] * d[l];
+                d[l + 1] = val * ihb[l + 1];
+            }
+        }
+#pragma unroll
+        for (int l = 0; l <= kMaxE; ++l) ev[l] = d[l];
+        ev[0] += r0;
+    } else {
+        // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
+        const int Nax = job == 2 ? M.N2 : M.N3;
+        ev[0] = C(1);
+        ev[1] = Nax >= 1 ? ua : C(0);
+#pragma unroll
+        for (int l = 1; l < kMaxE; ++l)
+            if (l < Nax) ev[l + 1] = ua * ev[l] + C(l) * tm1 * ev[l - 1];
+    }
+}
+
+// Entry k (of nR + n2 + n3) of an own cell's per-axis equilibrium vectors g_R, g_2, g_3 in the
+// populations' precision; ecs: the cell's coefficients [job][l]; cT its temperature (the reduced
+// pair's chi factor).  Returns the value, *dst its offset in the record.
+template <typename T>
+__device__ __forceinline__ T clo_g_entry(int k, const T (*ecs)[kMaxE], T cT, const ClosureTabs<T>& tb, const MomSet& M,
+                                         int& dst) {
+    const int nR = M.nR, n2 = M.n2, QR = nR / 2;
+    T acc = T(0);
+    if (k < nR) {
+        const T* eh = ecs[k >= QR ? 1 : 0];
+        for (int l = 0; l <= M.NR; ++l) acc += tb.GR[k * kMaxE + l] * eh[l];
+        dst = rec_off_gR(n2) + k;
+    } else if (k < nR + n2) {
+        const int j = k - nR;
+        for (int l = 0; l <= M.N2; ++l) acc += tb.G2[j * kMaxE + l] * ecs[2][l];
+        dst = rec_off_g2() + j;
+    } else {
+        const int j = k - nR - n2;
+        if (M.reduced) {
+            // the pair's Gaussian factors: int g_z = 1 (phi), int p_z^2 g_z = T (chi)
+            acc = j == 0 ? T(1) : cT;
+        } else {
+            for (int l = 0; l <= M.N3; ++l) acc += tb.G3[j * kMaxE + l] * ecs[3][l];
+        }
+        dst = rec_off_g3(nR, n2) + j;
+    }
+    return acc;
+}
+
+// Discrete mass of the stored equilibrium (a whole warp per own cell): the rounded vectors need
+// not sum to exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
+// would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is the wide n
+// divided by the wide product of the sums of the stored vectors (a butterfly of wide sums: every
+// lane ends with the same value).
+template <typename T>
+__device__ __forceinline__ void clo_mass_normalise(T* ct, Wide<T> n, const MomSet& M, int lane) {
+    using W = Wide<T>;
+    const int nR = M.nR, n2 = M.n2, ng = nR + n2 + M.n3;
+    W s3w[3] = {w_from_t(T(0)), w_from_t(T(0)), w_from_t(T(0))};
+    for (int k = lane; k < ng; k += 32) {
+        const int a = k < nR ? 0 : (k < nR + n2 ? 1 : 2);
+        const int src = a == 0 ? rec_off_gR(n2) + k : (a == 1 ? rec_off_g2() + k - nR : rec_off_g3(nR, n2) + k - nR - n2);
+        const W g = w_from_t(ct[src]);
+        s3w[0] = a == 0 ? w_add(s3w[0], g) : s3w[0];
+        s3w[1] = a == 1 ? w_add(s3w[1], g) : s3w[1];
+        s3w[2] = a == 2 ? w_add(s3w[2], g) : s3w[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
+    if (M.reduced) s3w[2] = w_from_t(T(1));  // the mass is phi's: its p_z factor is exactly 1
+    if (lane == 0) ct[0] = w_hi(w_div(n, w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
+}
+
+// Reach of an item of own cells [c0, c0 + cnt) of an instance of N cells: the own cells, two on
+// each side (the gradient stencils), and the five cells next to a wall.
+__device__ __forceinline__ void clo_reach(int c0, int cnt, int N, int& h0, int& h1) {
+    h0 = max(0, min(c0 - 2, N - 5));
+    h1 = min(N, max(c0 + cnt + 2, 5));
+}
+
 // Closure of the own cells [c0, c0 + cnt) of one instance (cnt <= kClosureCells): the collision
 // records go to `recb` (the record of cell c0, stride A.rec_stride), chi and nbar to A.cw.
 // Every thread of the block calls it (it holds block barriers); the block has at least
@@ -185,51 +485,27 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
     __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells, wide
     __shared__ T s_chi[32], snb[32];               // reach cells: chi, band density
     __shared__ int sblo[32], scnt[32];             // reach cells: first band column, stored extent
-    __shared__ T sq[4][32];                        // own cells: q1, q2, q3, P_12
+    __shared__ T sq[3][32];                        // own cells: q
     __shared__ T ecs[kClosureCells][4][kMaxE];     // own cells: expansion coefficients
-    __shared__ T sgp[5][kClosureCells][5];        // gradient terms per own cell and stencil position
+    __shared__ T sgp[kClosureCells][5][5];         // gradient terms per own cell and stencil position
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
     const T* band = reinterpret_cast<const T*>(A.band);
     const T* dens = reinterpret_cast<const T*>(A.dens);
     const T* geoT = reinterpret_cast<const T*>(A.geoT);
-    const int nR = M.nR, n2 = M.n2, n3 = M.n3, QR = nR / 2, slices = A.slices;
-    const T *ha = tb.ha, *hb = tb.hb, *ihb = tb.ihb, *h0t = tb.h0t, *GR = tb.GR, *G2 = tb.G2, *G3 = tb.G3;
+    const int slices = A.slices;
     const int N = I.n_cells;
-    // reach: the own cells, two on each side, and the five cells next to a wall
-    const int h0 = max(0, min(c0 - 2, N - 5)), h1 = min(N, max(c0 + cnt + 2, 5)), nh = h1 - h0;
-    const double* S = A.sums + (long long)I.cell_off * slices * kSums;
+    int h0, h1;
+    clo_reach(c0, cnt, N, h0, h1);
+    const int nh = h1 - h0;
     const int rs = A.rec_stride;
+    const ReachView<T> RV{sw_n, sw_T, {sw_u[0], sw_u[1], sw_u[2]}, s_chi, snb};
     // ---- 1. every global load of the item at once: the raw sums of the reach cells and the
     // geometry of the own cells (warp 0, lane per cell), the band rows of the reach cells
     // (bulk copies of their stored extents, issued by warp 0) and the densities of the union
     // of the bands (all threads)
-    // the raw sums in the wide type: FP64, or for FP32 populations the double-float pairs the
-    // stage kernel stores beside them (no FP64 arithmetic here)
     W sv[kSums];
     T geo0 = T(1), geo1 = T(0);
-    if (warp == 0 && lane < nh) {
-        if constexpr (sizeof(T) == 4) {
-            const float2* src = reinterpret_cast<const float2*>(A.sumsw) + ((long long)I.cell_off + h0 + lane) * slices * kSums;
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) {
-                const float2 p = src[q];
-                sv[q] = W{p.x, p.y};
-            }
-            for (int sl = 1; sl < slices; ++sl)
-#pragma unroll
-                for (int q = 0; q < kSums; ++q) {
-                    const float2 p = src[sl * kSums + q];
-                    sv[q] = w_add(sv[q], W{p.x, p.y});
-                }
-        } else {
-            const double* src = S + (long long)(h0 + lane) * slices * kSums;
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) sv[q] = w_from(src[q], (T*)nullptr);
-            for (int sl = 1; sl < slices; ++sl)
-#pragma unroll
-                for (int q = 0; q < kSums; ++q) sv[q] = w_add(sv[q], w_from(src[sl * kSums + q], (T*)nullptr));
-        }
-    }
+    if (warp == 0 && lane < nh) clo_load_sums<T>(A, (long long)I.cell_off + h0 + lane, sv);
     if (warp == 0 && lane < cnt) {
         const T* gc = geoT + (long long)(I.cell_off + c0 + lane) * kGeo;
         geo0 = gc[0];
@@ -294,35 +570,23 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
     } else {
         __syncthreads();  // staged: the vote above is the barrier
     }
-    // ---- 2. warp 0: n, u, T of the reach cells (wide), q and P_12 of the own cells; the other
-    // warps: FM band sums of the reach cells from shared memory
+    // ---- 2. warp 0: n, u, T of the reach cells (wide), q of the own cells; the other warps: FM
+    // band sums of the reach cells from shared memory
     if (warp == 0) {
         if (lane < nh) {
             const int c = h0 + lane;
-            const W n = sv[0];
-            const W u0 = w_div(sv[1], n);
-            const W u1 = w_div(sv[2], n);
-            const W u2 = w_div(sv[3], n);
-            const W tr = w_add(w_add(sv[4], sv[5]), sv[6]);
-            const W uu = w_add(w_add(w_mul(u0, u0), w_mul(u1, u1)), w_mul(u2, u2));
-            const W Tc = w_div(w_sub(tr, w_mul(n, uu)), w_scale(n, T(3)));
+            W n, u[3], Tc;
+            T q[3];
+            clo_fields<T>(sv, n, u, Tc, q);
             sw_n[lane] = n;
-            sw_u[0][lane] = u0;
-            sw_u[1][lane] = u1;
-            sw_u[2][lane] = u2;
+            sw_u[0][lane] = u[0];
+            sw_u[1][lane] = u[1];
+            sw_u[2][lane] = u[2];
             sw_T[lane] = Tc;
             if (c >= c0 && c < c0 + cnt) {
-                // q and P_12 in the populations' precision (they enter only the Shakhov
-                // factor and the diagnostics)
-                const T tn = w_hi(n), t0 = w_hi(u0), t1 = w_hi(u1), t2 = w_hi(u2), ttr = w_hi(tr), tuu = w_hi(uu);
-                const T s4 = w_hi(sv[4]), s5 = w_hi(sv[5]), s6 = w_hi(sv[6]), s7 = w_hi(sv[7]), s8 = w_hi(sv[8]), s9 = w_hi(sv[9]);
-                const T m0 = s4 * t0 + s7 * t1 + s8 * t2;
-                const T m1 = s7 * t0 + s5 * t1 + s9 * t2;
-                const T m2 = s8 * t0 + s9 * t1 + s6 * t2;
-                sq[0][c - c0] = T(0.5) * (w_hi(sv[10]) - T(2) * m0 - t0 * ttr + T(2) * tn * tuu * t0);
-                sq[1][c - c0] = T(0.5) * (w_hi(sv[11]) - T(2) * m1 - t1 * ttr + T(2) * tn * tuu * t1);
-                sq[2][c - c0] = T(0.5) * (w_hi(sv[12]) - T(2) * m2 - t2 * ttr + T(2) * tn * tuu * t2);
-                sq[3][c - c0] = s7 - tn * t0 * t1;
+                sq[0][c - c0] = q[0];
+                sq[1][c - c0] = q[1];
+                sq[2][c - c0] = q[2];
             }
         }
     } else if (!I.chi_local) {
@@ -333,178 +597,46 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
             const int kmax = min(min(scnt[t], N - lo), nu - (lo - jlo));
             const T* Wr = staged ? wst + (long long)t * I.band_w : band + I.band_off + (long long)c * I.band_w;
             const T* nb = nbuf + (lo - jlo);
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-            int k = lane;
-            for (; k + 96 < kmax; k += 128) {
-                a0 += Wr[k] * nb[k];
-                a1 += Wr[k + 32] * nb[k + 32];
-                a2 += Wr[k + 64] * nb[k + 64];
-                a3 += Wr[k + 96] * nb[k + 96];
-            }
-            for (; k < kmax; k += 32) a0 += Wr[k] * nb[k];
-            const T tot = warp_sum((a0 + a1) + (a2 + a3));
+            const T tot = clo_band_row<T>(Wr, [&](int k) { return nb[k]; }, kmax, lane);
             if (lane == 0) snb[t] = tot;
         }
     }
     __syncthreads();
     // ---- 3. two concurrent chains.  Warp 0: chi of the reach cells, the gradient terms (one
-    // lane per own cell and stencil position: logarithms of ratios to the own cell, differences
-    // in the wide type), then transport, strain and Shakhov coefficient (lane per own cell).
-    // Warps 1 and 2: the expansion coefficients of the equilibria (Sec. III.C), lane per
-    // (own cell, axis half): warp 1 the half-range axis (+ and -), warp 2 the axes 2 and 3.
+    // lane per own cell and stencil position), then transport, strain and Shakhov coefficient
+    // (lane per own cell).  Warps 1 and 2: the expansion coefficients of the equilibria (Sec.
+    // III.C), lane per (own cell, axis half): warp 1 the half-range axis (+ and -), warp 2 the
+    // axes 2 and 3.
     if (warp == 0) {
-        if (lane < nh) {
-            // chi in the wide type, rounded once: J1 scales with b rho chi, and near finely
-            // resolved walls J1 is large enough that a few roundings of chi show in the RHS
-            const T etafac = inst_param<T>(I.etafac, I.f_etafac);
-            const W eta = w_scale(w_from_t(I.chi_local ? w_hi(sw_n[lane]) : snb[lane]), etafac);
-            const W om = w_sub(w_from_t(T(1)), eta);
-            const W om3 = w_mul(w_mul(om, om), om);
-            s_chi[lane] = w_hi(w_div(w_sub(w_from_t(T(2)), eta), w_scale(om3, T(2))));
-        }
-        __syncwarp();
         const T etaf = inst_param<T>(I.etafac, I.f_etafac);
+        if (lane < nh) s_chi[lane] = clo_chi<T>(etaf, I.chi_local ? w_hi(sw_n[lane]) : snb[lane]);
+        __syncwarp();
         for (int e = lane; e < cnt * 5; e += 32) {
-            const int t = e / 5, q = e % 5, c = c0 + t, lt = c - h0;
+            const int t = e / 5, q = e % 5, c = c0 + t;
             int cq;
             T wq;
             stencil5_at<T>(c, N, q, cq, wq);
-            const int k = cq - h0;
-            const W nw = sw_n[lt], Tw = sw_T[lt];
-            const T lT = log1p(ratio_fast(w_hi(w_sub(sw_T[k], Tw)), w_hi(Tw)));
-            const T ln = log1p(ratio_fast(w_hi(w_sub(sw_n[k], nw)), w_hi(nw)));
-            // ln chi_q - ln chi_c from the packing-fraction difference alone, since
-            // ln chi(eta) = ln(2 - eta) - ln 2 - 3 ln(1 - eta) (no rounding noise of chi itself)
-            const T dnb = I.chi_local ? w_hi(w_sub(sw_n[k], nw)) : snb[k] - snb[lt];
-            const T etac = etaf * (I.chi_local ? w_hi(nw) : snb[lt]), deta = etaf * dnb;
-            const T lchi = log1p(ratio_fast(-deta, T(2) - etac)) - T(3) * log1p(ratio_fast(-deta, T(1) - etac));
-            sgp[0][t][q] = wq * (T(2) * ln + lchi + lT);
-            sgp[1][t][q] = wq * lT;
-            sgp[2][t][q] = wq * w_hi(w_sub(sw_u[0][k], sw_u[0][lt]));
-            sgp[3][t][q] = wq * w_hi(w_sub(sw_u[1][k], sw_u[1][lt]));
-            sgp[4][t][q] = wq * w_hi(w_sub(sw_u[2][k], sw_u[2][lt]));
+            T g[5];
+            clo_grad_terms<T>(RV, cq - h0, c - h0, wq, etaf, I.chi_local != 0, g);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sgp[t][v][q] = g[v];
         }
         __syncwarp();
         if (lane < cnt) {
-            using C = T;
-            const int t = lane, c = c0 + t, lt = c - h0;
-            const C cn = w_hi(sw_n[lt]), cT = w_hi(sw_T[lt]), cchi = s_chi[lt];
-            const C in = ratio_fast(C(1), cn), iT = ratio_fast(C(1), cT), ichi = ratio_fast(C(1), cchi);
-            C gsum[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-                gsum[v] = (sgp[v][t][0] + sgp[v][t][1]) + (sgp[v][t][2] + sgp[v][t][3]) + sgp[v][t][4];
-            const C sc = geo1 * inst_param<C>(1.0 / I.ds, I.f_ids);
-            const C X = gsum[0] * sc, Y = gsum[1] * sc;
-            const C cd0 = gsum[2] * sc, cd1 = gsum[3] * sc, cd2 = gsum[4] * sc;
-            const C iR = ratio_fast(C(1), geo0);
-            const C cu0 = w_hi(sw_u[0][lt]), cu1 = w_hi(sw_u[1][lt]), cu2 = w_hi(sw_u[2][lt]);
-            const C sg = inst_param<C>(I.sigma, I.f_sigma);
-            const C br = inst_param<C>(I.bfac, I.f_bfac) * cn, x = br * cchi;
-            const C pi = C(3.14159265358979323846);
-            const C mu = ratio_fast(C(5), C(16) * sg * sg) * sqrt(cT * C(0.31830988618379067154)) *
-                         (ichi + C(0.8) * br + C(4.0 / 25.0) * (C(1) + C(12) / pi) * br * br * cchi);
-            const C Pr = ratio_fast(C(2.0 / 3.0) * (C(1) + C(0.8) * x + C(4.0 / 25.0) * (C(1) + C(12) / pi) * x * x),
-                                    C(1) + C(1.2) * x + C(9.0 / 25.0) * (C(1) + C(32) / (C(9) * pi)) * x * x);
-            C S11, S22, S01, S02, div;
-            if (I.geometry == 0) {
-                S11 = cu0 * iR;
-                S22 = C(0);
-                S01 = C(0.5) * (cd1 - cu1 * iR);
-                S02 = C(0.5) * cd2;
-                div = cd0 + cu0 * iR;
-            } else {
-                S11 = S22 = cu0 * iR;
-                S01 = C(0.5) * (cd1 - cu1 * iR);
-                S02 = C(0.5) * (cd2 - cu2 * iR);
-                div = cd0 + C(2) * cu0 * iR;
-            }
-            T* ct = recb + (long long)t * rs;
-            ct[0] = cn;
-            ct[1] = cu0;
-            ct[2] = cu1;
-            ct[3] = cu2;
-            ct[4] = iT;
-            ct[5] = ratio_fast(cn * cT, mu);
-            ct[6] = (C(1) - Pr) * iT * iT * in;
-            ct[7] = sq[0][t];
-            ct[8] = sq[1][t];
-            ct[9] = sq[2][t];
-            ct[10] = x;
-            ct[11] = X;
-            ct[12] = Y;
-            ct[13] = cd0;
-            ct[14] = S11;
-            ct[15] = S22;
-            ct[16] = S01;
-            ct[17] = S02;
-            ct[18] = T(0);
-            ct[19] = div;
-            T* cw = reinterpret_cast<T*>(A.cw) + (long long)(I.cell_off + c) * 2;
-            cw[0] = cchi;
-            cw[1] = I.chi_local ? cn : snb[lt];
+            const int t = lane, lt = c0 + t - h0;
+            const T q[3] = {sq[0][t], sq[1][t], sq[2][t]};
+            clo_record_scalars<T>(recb + (long long)t * rs, RV, lt, sgp[t], geo0, geo1, q, I);
+            T* cw = reinterpret_cast<T*>(A.cw) + (long long)(I.cell_off + c0 + t) * 2;
+            cw[0] = s_chi[lt];
+            cw[1] = I.chi_local ? w_hi(sw_n[lt]) : snb[lt];
         }
     } else if (warp <= 2) {
-        using C = T;
         for (int e = lane; e < 2 * cnt; e += 32) {
             const int t = e % cnt, job = 2 * (warp - 1) + e / cnt, lt = c0 + t - h0;
-            C ev[kMaxE + 1];
-#pragma unroll
-            for (int l = 0; l <= kMaxE; ++l) ev[l] = C(0);
-            const C cT = w_hi(sw_T[lt]);
-            const C tm1 = w_hi(w_sub(sw_T[lt], w_from_t(C(1))));  // T - 1 without cancellation
-            if (job < 2) {
-                // half range, half line of sign s (job 0: +, 1: -), v = s u_R.  The
-                // recurrence of the coefficients,
-                //   e_0 = h_0 (1 + erf(v / sqrt(2T))) / 2,
-                //   b_{l+1} e_{l+1} = (v - a_l) e_l + (T - 1) b_l e_{l-1}
-                //                     + T h_l(0) [G_v(0) - sum_{k<l} h_k(0) e_k / sqrt(2 pi)],
-                // is run for the deviation d_l = e_l - r_l from the rest state (v = 0, T = 1:
-                // r_0 = h_0 / 2, r_l = 0 for l >= 1), where every term is small and nothing
-                // cancels: with D = sqrt(2 pi) G_v(0) - 1 = (expm1(-z^2) - (T - 1)/(1 + sqrt T)) /
-                // sqrt T, z = v / sqrt(2T), and h_0(0) r_0 = 1,
-                //   d_0 = h_0 erf(z) / 2,
-                //   b_1 d_1 = v r_0 + (v - a_0) d_0 + h_0 [(T - 1) + T D] / sqrt(2 pi),
-                //   b_{l+1} d_{l+1} = (v - a_l) d_l + (T - 1) b_l e_{l-1}
-                //                     + T h_l(0) [D - sum_{k<l} h_k(0) d_k] / sqrt(2 pi).
-                const C ur = w_hi(sw_u[0][lt]);
-                const C v = job == 0 ? ur : -ur;
-                const C sT = sqrt(cT), z = v * rsqrt(C(2) * cT);
-                const C D = (expm1(-z * z) - tm1 / (C(1) + sT)) / sT;
-                const C is2pi = C(0.39894228040143267794);
-                const C r0 = h0t[0] * C(0.5);
-                C d[kMaxE + 1];
-#pragma unroll
-                for (int l = 0; l <= kMaxE; ++l) d[l] = C(0);
-                d[0] = r0 * erf(z);
-                C run = C(0);  // sum_{k<l} h_k(0) d_k
-#pragma unroll
-                for (int l = 0; l < kMaxE; ++l) {
-                    if (l < M.NR) {
-                        C val;
-                        if (l == 0) {
-                            val = v * r0 + (v - ha[0]) * d[0] + h0t[0] * (tm1 + cT * D) * is2pi;
-                        } else {
-                            const C em1 = (l == 1 ? r0 : C(0)) + d[l > 0 ? l - 1 : 0];
-                            val = (v - ha[l]) * d[l] + tm1 * hb[l] * em1 + cT * h0t[l] * (D - run) * is2pi;
-                        }
-                        run += h0t[l] * d[l];
-                        d[l + 1] = val * ihb[l + 1];
-                    }
-                }
-#pragma unroll
-                for (int l = 0; l <= kMaxE; ++l) ev[l] = d[l];
-                ev[0] += r0;
-            } else {
-                // full range: e_l = E[He_l(X)], X ~ N(u, T): e_{l+1} = u e_l + l (T - 1) e_{l-1}
-                const C u = w_hi(sw_u[job == 2 ? 1 : 2][lt]);
-                const int Nax = job == 2 ? M.N2 : M.N3;
-                ev[0] = C(1);
-                ev[1] = Nax >= 1 ? u : C(0);
-#pragma unroll
-                for (int l = 1; l < kMaxE; ++l)
-                    if (l < Nax) ev[l + 1] = u * ev[l] + C(l) * tm1 * ev[l - 1];
-            }
+            const T cT = w_hi(sw_T[lt]);
+            const T tm1 = w_hi(w_sub(sw_T[lt], w_from_t(T(1))));  // T - 1 without cancellation
+            T ev[kMaxE + 1];
+            clo_eq_coeffs<T>(job, cT, tm1, w_hi(sw_u[0][lt]), w_hi(sw_u[job == 2 ? 1 : 2][lt]), tb, M, ev);
 #pragma unroll
             for (int l = 0; l < kMaxE; ++l) ecs[t][job][l] = ev[l];
         }
@@ -513,55 +645,16 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
     }
     __syncthreads();
     // ---- 5. per-axis equilibrium vectors of the own cells, in the populations' precision
-    const int ng = nR + n2 + n3;
+    const int ng = M.nR + M.n2 + M.n3;
     for (int e = tid; e < cnt * ng; e += NT) {
         const int t = e / ng, k = e % ng;
-        T acc = T(0);
         int dst;
-        if (k < nR) {
-            const T* eh = ecs[t][k >= QR ? 1 : 0];
-            for (int l = 0; l <= M.NR; ++l) acc += GR[k * kMaxE + l] * eh[l];
-            dst = rec_off_gR(n2) + k;
-        } else if (k < nR + n2) {
-            const int j = k - nR;
-            for (int l = 0; l <= M.N2; ++l) acc += G2[j * kMaxE + l] * ecs[t][2][l];
-            dst = rec_off_g2() + j;
-        } else {
-            const int j = k - nR - n2;
-            if (M.reduced) {
-                // the pair's Gaussian factors: int g_z = 1 (phi), int p_z^2 g_z = T (chi)
-                acc = j == 0 ? T(1) : w_hi(sw_T[c0 + t - h0]);
-            } else {
-                for (int l = 0; l <= M.N3; ++l) acc += G3[j * kMaxE + l] * ecs[t][3][l];
-            }
-            dst = rec_off_g3(nR, n2) + j;
-        }
-        recb[(long long)t * rs + dst] = acc;
+        const T g = clo_g_entry<T>(k, ecs[t], w_hi(sw_T[c0 + t - h0]), tb, M, dst);
+        recb[(long long)t * rs + dst] = g;
     }
     __syncthreads();
-    // ---- 6. discrete mass of the stored equilibrium: the rounded vectors need not sum to
-    // exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
-    // would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is
-    // divided by the wide-precision product of the sums of the stored vectors (a warp per own
-    // cell, a butterfly of wide sums: every lane ends with the same value).
-    for (int t = warp; t < cnt; t += NT / 32) {
-        T* ct = recb + (long long)t * rs;
-        W s3w[3] = {w_from_t(T(0)), w_from_t(T(0)), w_from_t(T(0))};
-        for (int k = lane; k < ng; k += 32) {
-            const int a = k < nR ? 0 : (k < nR + n2 ? 1 : 2);
-            const int src = a == 0 ? rec_off_gR(n2) + k : (a == 1 ? rec_off_g2() + k - nR : rec_off_g3(nR, n2) + k - nR - n2);
-            const W g = w_from_t(ct[src]);
-            s3w[0] = a == 0 ? w_add(s3w[0], g) : s3w[0];
-            s3w[1] = a == 1 ? w_add(s3w[1], g) : s3w[1];
-            s3w[2] = a == 2 ? w_add(s3w[2], g) : s3w[2];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
-        if (M.reduced) s3w[2] = w_from_t(T(1));  // the mass is phi's: its p_z factor is exactly 1
-        if (lane == 0) ct[0] = w_hi(w_div(sw_n[c0 + t - h0], w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
-    }
+    // ---- 6. discrete mass of the stored equilibrium (a warp per own cell)
+    for (int t = warp; t < cnt; t += NT / 32) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M, lane);
     __syncthreads();  // shared arrays are reused by the next call
     return true;
 }

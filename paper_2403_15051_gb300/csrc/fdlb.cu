@@ -31,7 +31,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
-        rprev, rout, krf, krB, total;
+        rprev, rout, krf, krB, fld, total;
 };
 
 }  // namespace
@@ -80,6 +80,10 @@ struct Solver {
     size_t smem_stream = 0;
     int use_bulk = 0;
     int closure_cells = 4, closure_threads = 128;  // own cells per closure item (<= kClosureCells)
+    int closure_batch = 0;  // the closure as two launches over all items (items of kClosureCells cells)
+    int grid_cbatch = 1;
+    size_t cbatch_smem = 0;
+    void* fld = nullptr;    // the batch closure's per-cell fields
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
     int stage_minb = 1;     // register bound of the stage kernel (1, or 3 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
@@ -298,6 +302,8 @@ Layout make_layout(const Solver& S) {
     L.krf = take(S.nR >= kKrKernelMinNodes ? S.f_elems * S.tsize : 0);
     // K^h as TF32 pairs for the tensor-core contraction kernel (FP32 populations)
     L.krB = take(S.nR >= kKrKernelMinNodes && S.tsize == 4 ? kr_table_floats(S.nR) * sizeof(float) : 0);
+    // per-cell fields of the batch form of the closure
+    L.fld = take((size_t)S.total_cells * (S.tsize == 4 ? 16 : 8) * S.tsize);
     L.total = off;
     return L;
 }
@@ -513,7 +519,8 @@ int upload_items(Solver& S) {
         // the wall densities first (their blocks read four cells of populations), then the cells
         for (int side = 0; side < 2; ++side)
             for (int part = 0; part < kWallParts; ++part) ci.push_back(make_int4(q, side ? N - 1 : 0, part, 1 + side));
-        for (int c = 0; c < N; c += S.closure_cells) ci.push_back(make_int4(q, c, std::min(S.closure_cells, N - c), 0));
+        const int cc = S.closure_batch ? kClosureCells : S.closure_cells;
+        for (int c = 0; c < N; c += cc) ci.push_back(make_int4(q, c, std::min(cc, N - c), 0));
     }
     if ((int)si.size() > S.max_sitems || (int)ci.size() > S.max_citems) return FDLB_EINVAL;
     const int ns = (int)si.size(), nc = (int)ci.size();
@@ -565,6 +572,9 @@ int upload_items(Solver& S) {
     S.closure_wst = wst;
     S.closure_smem = closure_smem(S.nR, S.n2, S.n3, max_union, wst, (int)S.tsize);
     S.grid_closure = std::max(1, std::min(nc, S.n_sm * (throughput ? closure_bps : 8)));
+    // the batch form: the tables only, as many blocks as reside
+    S.cbatch_smem = closure_smem(S.nR, S.n2, S.n3, 0, 0, (int)S.tsize);
+    S.grid_cbatch = std::max(1, std::min(nc, S.n_sm * closure_batch_blocks_per_sm((int)S.tsize, S.cbatch_smem)));
     S.grid_stream = std::max(1, ns);
     return plan_step_kernel(S, ns);
 }
@@ -710,11 +720,20 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.wst_elems = S.closure_wst;
     A.err = S.err;
     A.programmatic = S.programmatic;
-    if (S.precision == FDLB_FP32)
-        launch_closure<float>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
-    else
-        launch_closure<double>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
-    S.launches++;
+    A.fld = S.fld;
+    if (S.closure_batch) {
+        if (S.precision == FDLB_FP32)
+            launch_closure_batch<float>(A, S.M, S.grid_cbatch, S.cbatch_smem, S.stream);
+        else
+            launch_closure_batch<double>(A, S.M, S.grid_cbatch, S.cbatch_smem, S.stream);
+        S.launches += 2;
+    } else {
+        if (S.precision == FDLB_FP32)
+            launch_closure<float>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+        else
+            launch_closure<double>(A, S.M, S.grid_closure, S.closure_threads, S.closure_smem, S.stream);
+        S.launches++;
+    }
     if (write_ca) {
         // the FP64 closure record for the queries (not part of the stage)
         if (S.precision == FDLB_FP32)
@@ -1002,7 +1021,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int B, closure_cells, minb;
+    int B, closure_cells, minb, batch;
 };
 std::map<TuneKey, TuneVal> g_tune_cache;
 std::mutex g_tune_mutex;
@@ -1020,8 +1039,9 @@ TuneKey tune_key(const Solver& S) {
     return TuneKey{S.geometry, S.precision, S.nR, S.n2, S.n3, S.KS, S.threads, ilog2(S.total_cells), ilog2(S.n_inst)};
 }
 
-int set_closure_grouping(Solver& S, int cells) {
+int set_closure_grouping(Solver& S, int cells, int batch = -1) {
     S.closure_cells = cells;
+    if (batch >= 0) S.closure_batch = batch;
     if (S.gexec) {
         cudaGraphExecDestroy(S.gexec);
         S.gexec = nullptr;
@@ -1051,7 +1071,7 @@ int run_autotune(Solver& S, bool use_cache) {
         if (it != g_tune_cache.end()) {
             S.stage_minb = it->second.minb;
             int rc = configure_tiling(S, it->second.B, S.KS, S.threads);
-            return rc ? rc : set_closure_grouping(S, it->second.closure_cells);
+            return rc ? rc : set_closure_grouping(S, it->second.closure_cells, it->second.batch);
         }
     }
     const bool timing = S.timing;
@@ -1060,7 +1080,7 @@ int run_autotune(Solver& S, bool use_cache) {
     FDLB_CUDA(cudaEventCreate(&e0));
     FDLB_CUDA(cudaEventCreate(&e1));
     const int KS = S.KS, threads = S.threads;
-    int bestB = S.B, bestC = S.closure_cells, bestM = S.stage_minb;
+    int bestB = S.B, bestC = S.closure_cells, bestM = S.stage_minb, bestBatch = S.closure_batch;
     float best = time_stages(S, e0, e1);
     if (best < 0.f) best = 1e30f;
     const int Bs[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
@@ -1083,23 +1103,32 @@ int run_autotune(Solver& S, bool use_cache) {
     }
     S.stage_minb = bestM;
     rc = configure_tiling(S, bestB, KS, threads);
+    // the closure: the chain form with items of C cells, or the batch form (two launches)
     const int Cs[] = {2, 4, 8, 16};
     for (int C : Cs) {
-        if (rc || C == bestC) continue;
-        if (set_closure_grouping(S, C) != FDLB_OK) continue;
+        if (rc || (C == bestC && !bestBatch)) continue;
+        if (set_closure_grouping(S, C, 0) != FDLB_OK) continue;
         const float ms = time_stages(S, e0, e1);
         if (ms >= 0.f && ms < best) {
             best = ms;
             bestC = C;
+            bestBatch = 0;
+        }
+    }
+    if (!rc && !bestBatch && set_closure_grouping(S, bestC, 1) == FDLB_OK) {
+        const float ms = time_stages(S, e0, e1);
+        if (ms >= 0.f && ms < best) {
+            best = ms;
+            bestBatch = 1;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     S.timing = timing;
-    if (!rc) rc = set_closure_grouping(S, bestC);
+    if (!rc) rc = set_closure_grouping(S, bestC, bestBatch);
     if (!rc) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = {bestB, bestC, bestM};
+        g_tune_cache[key] = {bestB, bestC, bestM, bestBatch};
     }
     return rc;
 }
@@ -1130,7 +1159,7 @@ int do_steps(Solver& S, int64_t n) {
         if (rc) return rc;
         while (n - done >= S.graph_steps) {
             FDLB_CUDA(cudaGraphLaunch(S.gexec, S.stream));
-            S.launches += (int64_t)S.graph_steps * (S.krg_on ? 9 : 6);
+            S.launches += (int64_t)S.graph_steps * 3 * ((S.krg_on ? 1 : 0) + (S.closure_batch ? 2 : 1) + 1);
             done += S.graph_steps;
         }
     }
@@ -1198,6 +1227,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.n_citems = (int*)(R.ws + L.n_citems);
     R.nwp = (void*)(R.ws + L.nwp);
     R.cw = (void*)(R.ws + L.cw);
+    R.fld = (void*)(R.ws + L.fld);
     R.geoT = (void*)(R.ws + L.geoT);
     R.gwT = (void*)(R.ws + L.gwT);
     R.err = (int*)(R.ws + L.err);
@@ -1292,9 +1322,11 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, 256) : configure_tiling(R, 8, R.n3, 512);
     // closure items: few cells each where the whole closure is one short latency-bound launch (2 on
     // the cylinder, 4 on the sphere, with overlapped launches), 8 where items outnumber the blocks
-    // that fit on the device several times over (batches, long instances: throughput-bound)
+    // that fit on the device several times over (batches, long instances: throughput-bound); with
+    // items of the batch form (kClosureCells cells) several times the SM count, the batch form
     R.closure_cells = R.geometry == FDLB_CYL ? 2 : 4;
     if (R.total_cells / R.closure_cells > R.n_sm * 8) R.closure_cells = 8;
+    R.closure_batch = R.total_cells / kClosureCells > R.n_sm * 4 ? 1 : 0;
     if (!rc) rc = upload_items(R);
     for (int q = 0; q < n && !rc; ++q) rc = fdlb_init_uniform(reinterpret_cast<fdlb_handle>(S.get()), q, 0.0, 0.0);
     if (rc) {
@@ -1934,7 +1966,18 @@ int fdlb_set_programmatic_launch(fdlb_handle h, int enable) try {
 int fdlb_set_closure_cells(fdlb_handle h, int cells) try {
     Solver* S = SOL(h);
     if (!S || cells < 1 || cells > fdlb::kClosureCells) return FDLB_EINVAL;
-    return fdlb::set_closure_grouping(*S, cells);
+    return fdlb::set_closure_grouping(*S, cells, 0);
+} FDLB_HOST_CATCH
+
+int fdlb_set_closure_form(fdlb_handle h, int form, int* in_use) try {
+    Solver* S = SOL(h);
+    if (!S || form < -1 || form > 1) return FDLB_EINVAL;
+    if (form >= 0) {
+        const int rc = fdlb::set_closure_grouping(*S, S->closure_cells, form);
+        if (rc) return rc;
+    }
+    if (in_use) *in_use = S->closure_batch;
+    return FDLB_OK;
 } FDLB_HOST_CATCH
 
 int64_t fdlb_launch_count(fdlb_handle h) {

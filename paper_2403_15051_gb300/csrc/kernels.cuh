@@ -116,7 +116,13 @@ struct ClosureArgs {
     int wst_elems;                 // capacity of the staged band rows (elements)
     int programmatic;              // launched with programmatic stream serialization
     int* err;                      // set when a bulk copy never completes
+    void* fld;                     // batch form: per cell n, u, T (wide) and q, [cell][kFldStride]
 };
+
+// Elements per cell of the batch closure's field scratch: FP32 [n, u_R, u_2, u_3, T as (hi, lo)
+// pairs | q | pad], FP64 [n, u_R, u_2, u_3, T | q].
+template <typename T>
+__host__ __device__ constexpr int fld_stride() { return sizeof(T) == 4 ? 16 : 8; }
 
 struct StepArgs {
     StageArgs st;                  // the stage fields; buffers and coefficients set per stage

@@ -137,6 +137,240 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
     }
 }
 
+// ------------------------------------------------------------------------------ batch closure
+// The closure of a batch as two launches over all items instead of one item chain per block.  With
+// many more items than co-resident blocks the chain form is bound by how many items are in flight:
+// most of its phases run one lane per reach cell while the other lanes wait at its barriers.  Here
+// closure_fields_kernel forms per own cell the fields (n, u, T wide; q) into the scratch A.fld and,
+// from the cell's FM band sum, chi and nbar into A.cw, plus the wall items; then
+// closure_records_kernel forms each item's records from the fields of its reach, every phase
+// spread over the whole block.  Both are made of the chain's per-cell functions (closure_item.cuh),
+// so the records are the chain's.
+
+template <typename T>
+__device__ __forceinline__ void fld_store(T* o, const Wide<T>& n, const Wide<T> (&u)[3], const Wide<T>& Tc,
+                                          const T (&q)[3]) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(o)[0] = make_float4(n.hi, n.lo, u[0].hi, u[0].lo);
+        reinterpret_cast<float4*>(o)[1] = make_float4(u[1].hi, u[1].lo, u[2].hi, u[2].lo);
+        reinterpret_cast<float4*>(o)[2] = make_float4(Tc.hi, Tc.lo, q[0], q[1]);
+        o[12] = q[2];
+    } else {
+        o[0] = w_hi(n);
+        o[1] = w_hi(u[0]);
+        o[2] = w_hi(u[1]);
+        o[3] = w_hi(u[2]);
+        o[4] = w_hi(Tc);
+        o[5] = q[0];
+        o[6] = q[1];
+        o[7] = q[2];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void fld_load(const T* o, Wide<T>& n, Wide<T> (&u)[3], Wide<T>& Tc, T (&q)[3]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4*>(o)[0], b = reinterpret_cast<const float4*>(o)[1],
+                     c = reinterpret_cast<const float4*>(o)[2];
+        n = Wide<T>{a.x, a.y};
+        u[0] = Wide<T>{a.z, a.w};
+        u[1] = Wide<T>{b.x, b.y};
+        u[2] = Wide<T>{b.z, b.w};
+        Tc = Wide<T>{c.x, c.y};
+        q[0] = c.z;
+        q[1] = c.w;
+        q[2] = o[12];
+    } else {
+        n = w_from_t(o[0]);
+        u[0] = w_from_t(o[1]);
+        u[1] = w_from_t(o[2]);
+        u[2] = w_from_t(o[3]);
+        Tc = w_from_t(o[4]);
+        q[0] = o[5];
+        q[1] = o[6];
+        q[2] = o[7];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kClosureThreads, 8) closure_fields_kernel(ClosureArgs A, MomSet M) {
+    __shared__ T red[kClosureWarps];
+    __shared__ T snb[kClosureCells];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const ClosureTabs<T> tb = closure_tables<T>(reinterpret_cast<T*>(smem_raw), A.tabT, M, tid, blockDim.x);
+    __syncthreads();
+    pdl_wait();  // the raw sums, densities and populations of the previous kernel
+    pdl_trigger();
+    const T* fin_all = reinterpret_cast<const T*>(A.f_in);
+    const T* band = reinterpret_cast<const T*>(A.band);
+    const T* dens = reinterpret_cast<const T*>(A.dens);
+    T* nwp = reinterpret_cast<T*>(A.nwp);
+    T* fld = reinterpret_cast<T*>(A.fld);
+    T* cw = reinterpret_cast<T*>(A.cw);
+    const int slices = A.slices;
+    const int nit = *A.n_items;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const int4 w = A.items[it];
+        const InstDev I = A.inst[w.x];
+        if (w.w != 0) {
+            // one part of the outgoing flux through a wall, as in the chain form
+            const int side = w.w - 1, part = w.z, P = A.wall_parts;
+            const T* wall = fin_all + I.f_off + (side == 0 ? 0LL : (long long)(I.n_cells - 1) * M.Np);
+            T acc = wall_flux_partial<T>(wall, side == 0 ? (long long)M.Np : -(long long)M.Np, M, tb, side, part, P, tid);
+            acc = warp_sum(acc);
+            if (lane == 0) red[warp] = acc;
+            __syncthreads();
+            if (tid == 0) nwp[((long long)w.x * 2 + side) * P + part] = wall_part_sum(red);
+            __syncthreads();
+            continue;
+        }
+        const int c0 = w.y, cnt = w.z, N = I.n_cells;
+        const T etaf = inst_param<T>(I.etafac, I.f_etafac);
+        if (warp == 0) {
+            // lane per own cell: the fields from the raw sums
+            if (lane < cnt) {
+                const long long gc = (long long)I.cell_off + c0 + lane;
+                Wide<T> sv[kSums];
+                clo_load_sums<T>(A, gc, sv);
+                Wide<T> n, u[3], Tc;
+                T q[3];
+                clo_fields<T>(sv, n, u, Tc, q);
+                fld_store<T>(fld + gc * fld_stride<T>(), n, u, Tc, q);
+                if (I.chi_local) {
+                    cw[gc * 2] = clo_chi<T>(etaf, w_hi(n));
+                    cw[gc * 2 + 1] = w_hi(n);
+                }
+            }
+        } else if (!I.chi_local) {
+            // warp per own cell's band row (coalesced along the row)
+            const int2* bl = reinterpret_cast<const int2*>(A.band_lo) + I.cell_off;
+            for (int t = warp - 1; t < cnt; t += kClosureWarps - 1) {
+                const int c = c0 + t;
+                const int2 e = bl[c];
+                const int kmax = min(e.y, N - e.x);
+                const T* Wr = band + I.band_off + (long long)c * I.band_w;
+                const T* nd = dens + ((long long)I.cell_off + e.x) * slices;
+                const T tot = clo_band_row<T>(
+                    Wr,
+                    [&](int k) {
+                        T v = nd[(long long)k * slices];
+                        for (int sl = 1; sl < slices; ++sl) v += nd[(long long)k * slices + sl];
+                        return v;
+                    },
+                    kmax, lane);
+                if (lane == 0) snb[t] = tot;
+            }
+        }
+        if (!I.chi_local) {
+            __syncthreads();
+            if (warp == 0 && lane < cnt) {
+                const long long gc = (long long)I.cell_off + c0 + lane;
+                cw[gc * 2] = clo_chi<T>(etaf, snb[lane]);
+                cw[gc * 2 + 1] = snb[lane];
+            }
+            __syncthreads();  // snb is reused by the next item
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(ClosureArgs A, MomSet M) {
+    using W = Wide<T>;
+    __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells
+    __shared__ T s_chi[32], snb[32];
+    __shared__ T sq[kClosureCells][3], sgeo[kClosureCells][2];  // own cells
+    __shared__ T ecs[kClosureCells][4][kMaxE];
+    __shared__ T sgp[kClosureCells][5][5];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
+    const ClosureTabs<T> tb = closure_tables<T>(reinterpret_cast<T*>(smem_raw), A.tabT, M, tid, NT);
+    __syncthreads();
+    pdl_wait();  // the fields, chi and nbar of closure_fields_kernel
+    pdl_trigger();
+    const T* fld = reinterpret_cast<const T*>(A.fld);
+    const T* cw = reinterpret_cast<const T*>(A.cw);
+    const T* geoT = reinterpret_cast<const T*>(A.geoT);
+    T* rec_all = reinterpret_cast<T*>(A.rec);
+    const int rs = A.rec_stride, ng = M.nR + M.n2 + M.n3;
+    const ReachView<T> RV{sw_n, sw_T, {sw_u[0], sw_u[1], sw_u[2]}, s_chi, snb};
+    const int nit = *A.n_items;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const int4 w = A.items[it];
+        if (w.w != 0) continue;  // wall items: closure_fields_kernel
+        const InstDev I = A.inst[w.x];
+        const int c0 = w.y, cnt = w.z, N = I.n_cells;
+        int h0, h1;
+        clo_reach(c0, cnt, N, h0, h1);
+        const int nh = h1 - h0;
+        T* recb = rec_all + (long long)(I.cell_off + c0) * rs;
+        // ---- the reach's fields, chi and nbar; the own cells' q and geometry
+        for (int e = tid; e < nh; e += NT) {
+            const long long gc = (long long)I.cell_off + h0 + e;
+            W n, u[3], Tc;
+            T q[3];
+            fld_load<T>(fld + gc * fld_stride<T>(), n, u, Tc, q);
+            sw_n[e] = n;
+            sw_u[0][e] = u[0];
+            sw_u[1][e] = u[1];
+            sw_u[2][e] = u[2];
+            sw_T[e] = Tc;
+            s_chi[e] = cw[gc * 2];
+            snb[e] = cw[gc * 2 + 1];
+            const int t = h0 + e - c0;
+            if (t >= 0 && t < cnt) {
+                sq[t][0] = q[0];
+                sq[t][1] = q[1];
+                sq[t][2] = q[2];
+                const T* g = geoT + gc * kGeo;
+                sgeo[t][0] = g[0];
+                sgeo[t][1] = g[1];
+            }
+        }
+        __syncthreads();
+        // ---- gradient terms (thread per own cell and stencil position)
+        const T etaf = inst_param<T>(I.etafac, I.f_etafac);
+        for (int e = tid; e < cnt * 5; e += NT) {
+            const int t = e / 5, q = e % 5, c = c0 + t;
+            int cq;
+            T wq;
+            stencil5_at<T>(c, N, q, cq, wq);
+            T g[5];
+            clo_grad_terms<T>(RV, cq - h0, c - h0, wq, etaf, I.chi_local != 0, g);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sgp[t][v][q] = g[v];
+        }
+        __syncthreads();
+        // ---- expansion coefficients (warp = job, lane = own cell); the last warp, whose job (the
+        // third axis) is the shortest, then the record scalars
+        if (lane < cnt) {
+            const int t = lane, job = warp, lt = c0 + t - h0;
+            const T cT = w_hi(sw_T[lt]);
+            const T tm1 = w_hi(w_sub(sw_T[lt], w_from_t(T(1))));  // T - 1 without cancellation
+            T ev[kMaxE + 1];
+            clo_eq_coeffs<T>(job, cT, tm1, w_hi(sw_u[0][lt]), w_hi(sw_u[job == 2 ? 1 : 2][lt]), tb, M, ev);
+#pragma unroll
+            for (int l = 0; l < kMaxE; ++l) ecs[t][job][l] = ev[l];
+            if (warp == kClosureWarps - 1) {
+                const T q[3] = {sq[t][0], sq[t][1], sq[t][2]};
+                clo_record_scalars<T>(recb + (long long)t * rs, RV, lt, sgp[t], sgeo[t][0], sgeo[t][1], q, I);
+            }
+        }
+        __syncthreads();
+        // ---- per-axis equilibrium vectors
+        for (int e = tid; e < cnt * ng; e += NT) {
+            const int t = e / ng, k = e % ng;
+            int dst;
+            const T g = clo_g_entry<T>(k, ecs[t], w_hi(sw_T[c0 + t - h0]), tb, M, dst);
+            recb[(long long)t * rs + dst] = g;
+        }
+        __syncthreads();
+        // ---- discrete mass of the stored equilibrium (a warp per own cell)
+        for (int t = warp; t < cnt; t += NT / 32) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M, lane);
+        __syncthreads();  // shared arrays are reused by the next item
+    }
+}
+
 // ------------------------------------------------------------------------------ queries
 // The FP64 closure record of every cell of the active instances (moments and closure queries,
 // not the stage): n, u, T, q, P_12 (Eq. macro_def) from the raw sums in FP64, chi and nbar from
@@ -275,6 +509,30 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
     launch_maybe_programmatic(closure_kernel<T>, grid, threads, smem, s, A.programmatic, A, M);
 }
 
+template <typename T>
+void launch_closure_batch(const ClosureArgs& A, const MomSet& M, int grid, size_t smem, cudaStream_t s) {
+    launch_maybe_programmatic(closure_fields_kernel<T>, grid, kClosureThreads, smem, s, A.programmatic, A, M);
+    launch_maybe_programmatic(closure_records_kernel<T>, grid, kClosureThreads, smem, s, A.programmatic, A, M);
+}
+
+int closure_batch_blocks_per_sm(int tsize, size_t smem) {
+    int a = 0, b = 0;
+    cudaError_t e1, e2;
+    if (tsize == 4) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_fields_kernel<float>, kClosureThreads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, closure_records_kernel<float>, kClosureThreads, smem);
+    } else {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_fields_kernel<double>, kClosureThreads, smem);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, closure_records_kernel<double>, kClosureThreads, smem);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        return 4;
+    }
+    const int n = a < b ? a : b;
+    return n > 0 ? n : 1;
+}
+
 int closure_blocks_per_sm(int tsize, size_t smem) {
     int n = 0;
     const cudaError_t e = tsize == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, closure_kernel<float>, kClosureThreads, smem)
@@ -366,5 +624,7 @@ template void launch_moments<double>(const double*, double*, double*, void*, con
                                      const double*, const MomSet&, cudaStream_t);
 template void launch_closure<float>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
 template void launch_closure<double>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
+template void launch_closure_batch<float>(const ClosureArgs&, const MomSet&, int, size_t, cudaStream_t);
+template void launch_closure_batch<double>(const ClosureArgs&, const MomSet&, int, size_t, cudaStream_t);
 
 }  // namespace fdlb

@@ -98,6 +98,11 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize);
 // Blocks of the closure kernel that fit on an SM with `smem` bytes of dynamic shared memory each.
 int closure_blocks_per_sm(int tsize, size_t smem);
+// The batch form of the closure (closure_fields_kernel, then closure_records_kernel; items of at
+// most kClosureCells cells, A.fld set), and the blocks of either that reside on one SM.
+template <typename T>
+void launch_closure_batch(const ClosureArgs& A, const MomSet& M, int grid, size_t smem, cudaStream_t s);
+int closure_batch_blocks_per_sm(int tsize, size_t smem);
 
 
 #define FDLB_STREAM_DECL(T, G)                                                                             \

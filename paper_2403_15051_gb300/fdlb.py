@@ -94,6 +94,7 @@ def load_library():
         "fdlb_error_string": (ctypes.c_char_p, [c_int]),
         "fdlb_set_tiling": (c_int, [H, c_int, c_int, c_int]),
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
+        "fdlb_set_closure_form": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
@@ -359,6 +360,12 @@ class Solver:
     def set_closure_cells(self, cells):
         _check(self._L.fdlb_set_closure_cells(self._h, cells), "fdlb_set_closure_cells")
 
+    def closure_form(self, form=-1):
+        """0: the chain form, 1: the batch form, -1: no change; returns the form in use."""
+        u = c_int()
+        _check(self._L.fdlb_set_closure_form(self._h, int(form), byref(u)), "fdlb_set_closure_form")
+        return u.value
+
     def autotune(self):
         b, k, t = c_int(), c_int(), c_int()
         _check(self._L.fdlb_autotune(self._h, byref(b), byref(k), byref(t)), "fdlb_autotune")
@@ -371,7 +378,9 @@ class Solver:
     def tiling(self) -> dict:
         b, k, t, c = c_int(), c_int(), c_int(), c_int()
         _check(self._L.fdlb_get_tiling(self._h, byref(b), byref(k), byref(t), byref(c)), "fdlb_get_tiling")
-        return {"cells_per_tile": b.value, "slice_k": k.value, "threads": t.value, "closure_cells": c.value}
+        form = self.closure_form()
+        return {"cells_per_tile": b.value, "slice_k": k.value, "threads": t.value,
+                "closure_cells": 28 if form == 1 else c.value, "closure_form": "batch" if form == 1 else "chain"}
 
     def launch_count(self):
         return int(self._L.fdlb_launch_count(self._h))

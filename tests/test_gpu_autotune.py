@@ -1,4 +1,5 @@
-"""The autotuner of the tile shapes (fdlb_autotune, automatic tuning at a batch's first step):
+"""The autotuner of the tile shapes and the closure's form (fdlb_autotune, automatic tuning at a
+batch's first step):
 it leaves the state alone, changes no result bit, and its cached choice is reused by a handle of
 the same momentum set, precision and size class."""
 import numpy as np
@@ -57,4 +58,6 @@ def test_cached_choice_is_reused():
     B = fdlb.Solver(ds)
     B.step(1)  # automatic tuning: the cached choice of A's key
     assert B.tiling() == t
-    assert 2 <= t["cells_per_tile"] <= 32 and t["closure_cells"] in (2, 4, 8, 16)
+    assert 2 <= t["cells_per_tile"] <= 32
+    assert (t["closure_form"], t["closure_cells"]) in {("chain", 2), ("chain", 4), ("chain", 8), ("chain", 16),
+                                                       ("batch", 28)}
