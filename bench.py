@@ -441,9 +441,12 @@ def run_ours(args):
         S.set_graph_steps(1)
 
     # ---- end to end through the C ABI with host buffers: every step, H2D of the whole state from
-    # pinned memory (one copy, the raw sums recomputed), one step, D2H of every cell's moments
+    # pinned memory (one copy, the raw sums recomputed), one step, D2H of every cell's moments into
+    # pinned memory
     host_state = torch.empty(S.state_bytes(), dtype=torch.uint8, pin_memory=True)
     S.get_state_raw(host_state.data_ptr(), -1)
+    n_cells_all = sum(S.shape(q)[0] for q in range(S.n_instances))
+    host_mom = torch.empty((n_cells_all, fdlb.NMOM), dtype=torch.float64, pin_memory=True).numpy()
     e2e_steps = max(3, min(args.steps, 100))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -451,7 +454,7 @@ def run_ours(args):
     for k in range(e2e_steps):
         S.set_state_raw(host_state.data_ptr(), -1)
         S.step(1)
-        m = S.moments_all()
+        m = S.moments_all(out=host_mom)
         d2h += m.nbytes
     el = time.perf_counter() - t0
     el = max_over_ranks(el, world)

@@ -179,8 +179,10 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
 /* Steady state at the FP64 level of accuracy for an FP32 handle: the FP32 form runs to the
  * residual tolerance (as fdlb_run_to_steady; its steady state sits on the FP32 rounding floor,
  * ~1e-5 to 1e-4 of the moment scales from the FP64 one for dense, small-Kn instances), then an FP64
- * copy of the handle (the same instances, walls and time step) continues from that state to the
- * tolerance, and the polished state, rounded to FP32, replaces the handle's populations (its
+ * copy of the handle (the same instances, walls and time step) continues from that state, scaled
+ * per instance to the total mass the call started with (the walls conserve mass and the steady
+ * state depends on it; FP32 rounding walks it by up to ~1e-9 per step), to the tolerance, and
+ * the polished state, rounded to FP32, replaces the handle's populations (its
  * moments are the FP64 steady state's to FP32 rounding; stepping on in FP32 drifts back to the
  * floor).  The FP64 copy lives in `fp64_workspace` (fdlb_polish_workspace_bytes bytes, 256-byte
  * aligned) when given, else in device memory the call allocates and frees.  steps_fp32 /
@@ -299,9 +301,10 @@ int fdlb_set_closure_cells(fdlb_handle h, int cells);
 /* Form of the closure (Eqs. fm, chi, j1, tau, prandtl and the equilibria of Sec. III.C, once per
  * stage).  form 0, the chain: one launch, each block runs an item of a few cells through the whole
  * closure (short, latency-bound: one instance).  form 1, the batch form: two launches over items
- * of 28 cells, the first forming every cell's n, u, T, q and FM band sum, the second the records
- * from them (throughput-bound: batches and long instances; the default when the items of 28 cells
- * are more than four times the SM count).  The records are the same bit for bit either way.
+ * of 28 cells, the first giving every FM band row a warp of its own (the band sum, chi), the
+ * second forming the records of each item from the raw sums of its reach and the band results
+ * (throughput-bound: batches and long instances; the default when the items of 28 cells are more
+ * than four times the SM count).  The records are the same bit for bit either way.
  * form -1 changes nothing.  *in_use (may be NULL) = the form in use.  FDLB_EINVAL for another
  * form. */
 int fdlb_set_closure_form(fdlb_handle h, int form, int* in_use);

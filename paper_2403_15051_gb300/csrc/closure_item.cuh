@@ -170,7 +170,7 @@ struct NoAfterLoads {
 };
 
 // ---- the per-cell steps of the closure.  The item chain below (closure_cells) and the two
-// kernels of the batch form (closure_fields_kernel, closure_records_kernel) are made of these
+// kernels of the batch form (closure_band_kernel, closure_records_kernel) are made of these
 // functions, so a cell's record is the same whichever form computes it.
 
 // Raw sums of global cell `gc` over its slices, in the wide type: FP64, or for FP32 populations
@@ -225,11 +225,29 @@ __device__ __forceinline__ void clo_fields(const Wide<T> (&sv)[kSums], Wide<T>& 
 }
 
 // The FM band sum of one row (Eq. fm; a whole warp, every lane returns the sum): weights Wr[k]
-// times densities dn(k), k < kmax, lane-strided with four accumulators, then a butterfly.
+// times densities dn(k), k < kmax, lane-strided into four accumulators (accumulator a takes
+// k = lane + 32 a + 128 j in increasing j), then a butterfly.  The first loop takes two strides at
+// a time so that sixteen loads per lane are in flight; the order of every accumulator is the same.
 template <typename T, typename Dens>
 __device__ __forceinline__ T clo_band_row(const T* Wr, const Dens& dn, int kmax, int lane) {
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     int k = lane;
+    for (; k + 224 < kmax; k += 256) {
+        T w[8], d[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            w[u] = Wr[k + 32 * u];
+            d[u] = dn(k + 32 * u);
+        }
+        a0 += w[0] * d[0];
+        a1 += w[1] * d[1];
+        a2 += w[2] * d[2];
+        a3 += w[3] * d[3];
+        a0 += w[4] * d[4];
+        a1 += w[5] * d[5];
+        a2 += w[6] * d[6];
+        a3 += w[7] * d[7];
+    }
     for (; k + 96 < kmax; k += 128) {
         a0 += Wr[k] * dn(k);
         a1 += Wr[k + 32] * dn(k + 32);
@@ -436,30 +454,26 @@ __device__ __forceinline__ T clo_g_entry(int k, const T (*ecs)[kMaxE], T cT, con
     return acc;
 }
 
-// Discrete mass of the stored equilibrium (a whole warp per own cell): the rounded vectors need
-// not sum to exactly one per axis, and for FP32 populations that bias, times dt / tau every step,
-// would make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is the wide n
-// divided by the wide product of the sums of the stored vectors (a butterfly of wide sums: every
-// lane ends with the same value).
+// Discrete mass of the stored equilibrium (one thread per own cell): the rounded vectors need not
+// sum to exactly one per axis, and for FP32 populations that bias, times dt / tau every step, would
+// make the total mass drift.  The density stored for f^MB = n g_R g_2 g_3 is the wide n divided by
+// the wide product of the sums of the stored vectors (wide sums in the order of the entries).
 template <typename T>
-__device__ __forceinline__ void clo_mass_normalise(T* ct, Wide<T> n, const MomSet& M, int lane) {
+__device__ __forceinline__ void clo_mass_normalise(T* ct, Wide<T> n, const MomSet& M) {
     using W = Wide<T>;
-    const int nR = M.nR, n2 = M.n2, ng = nR + n2 + M.n3;
-    W s3w[3] = {w_from_t(T(0)), w_from_t(T(0)), w_from_t(T(0))};
-    for (int k = lane; k < ng; k += 32) {
-        const int a = k < nR ? 0 : (k < nR + n2 ? 1 : 2);
-        const int src = a == 0 ? rec_off_gR(n2) + k : (a == 1 ? rec_off_g2() + k - nR : rec_off_g3(nR, n2) + k - nR - n2);
-        const W g = w_from_t(ct[src]);
-        s3w[0] = a == 0 ? w_add(s3w[0], g) : s3w[0];
-        s3w[1] = a == 1 ? w_add(s3w[1], g) : s3w[1];
-        s3w[2] = a == 2 ? w_add(s3w[2], g) : s3w[2];
+    const int nR = M.nR, n2 = M.n2, n3 = M.n3;
+    W sR = w_from_t(T(0)), s2 = w_from_t(T(0)), s3 = w_from_t(T(0));
+    const T* gR = ct + rec_off_gR(n2);
+    const T* g2 = ct + rec_off_g2();
+    const T* g3 = ct + rec_off_g3(nR, n2);
+    for (int k = 0; k < nR; ++k) sR = w_add(sR, w_from_t(gR[k]));
+    for (int k = 0; k < n2; ++k) s2 = w_add(s2, w_from_t(g2[k]));
+    if (M.reduced) {
+        s3 = w_from_t(T(1));  // the mass is phi's: its p_z factor is exactly 1
+    } else {
+        for (int k = 0; k < n3; ++k) s3 = w_add(s3, w_from_t(g3[k]));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) s3w[a] = w_add(s3w[a], w_shfl_xor(s3w[a], o));
-    if (M.reduced) s3w[2] = w_from_t(T(1));  // the mass is phi's: its p_z factor is exactly 1
-    if (lane == 0) ct[0] = w_hi(w_div(n, w_mul(w_mul(s3w[0], s3w[1]), s3w[2])));
+    ct[0] = w_hi(w_div(n, w_mul(w_mul(sR, s2), s3)));
 }
 
 // Reach of an item of own cells [c0, c0 + cnt) of an instance of N cells: the own cells, two on
@@ -653,8 +667,8 @@ __device__ bool closure_cells(const ClosureArgs& A, const MomSet& M, const Closu
         recb[(long long)t * rs + dst] = g;
     }
     __syncthreads();
-    // ---- 6. discrete mass of the stored equilibrium (a warp per own cell)
-    for (int t = warp; t < cnt; t += NT / 32) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M, lane);
+    // ---- 6. discrete mass of the stored equilibrium (a thread per own cell)
+    for (int t = tid; t < cnt; t += NT) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M);
     __syncthreads();  // shared arrays are reused by the next call
     return true;
 }

@@ -228,6 +228,33 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Sums of 16 values over the 32 lanes of a warp, transposed: at every level of the butterfly a
+// lane keeps half of its values and sends the other half, so the warp needs 16 shuffles instead
+// of 16 x 5.  Lane L returns the sum of value (L >> 1).  Fixed order: deterministic.
+template <typename T>
+__device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
+    T w8[8], w4[4], w2[2];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const T send = b4 ? v[t] : v[t + 8], keep = b4 ? v[t + 8] : v[t];
+        w8[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const T send = b3 ? w8[t] : w8[t + 4], keep = b3 ? w8[t + 4] : w8[t];
+        w4[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const T send = b2 ? w4[t] : w4[t + 2], keep = b2 ? w4[t + 2] : w4[t];
+        w2[t] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const T send = b1 ? w2[0] : w2[1], keep = b1 ? w2[1] : w2[0];
+    const T w1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return w1 + __shfl_xor_sync(0xffffffffu, w1, 1);
+}
+
 // Five-point derivative stencil in the mapped coordinate (gradients of Eq. j1): fourth-order
 // central in the interior, one-sided fourth-order at the two cells next to each wall.
 template <typename R>

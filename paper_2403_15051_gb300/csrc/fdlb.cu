@@ -31,7 +31,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
-        rprev, rout, krf, krB, fld, total;
+        rprev, rout, krf, krB, mpk, total;
 };
 
 }  // namespace
@@ -64,7 +64,7 @@ struct Solver {
     void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr, *cw = nullptr;
     void* rec = nullptr;
     void* tabT = nullptr;
-    double *ca = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *rprev = nullptr,
+    double *ca = nullptr, *mpk = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *rprev = nullptr,
            *rout = nullptr;
     InstDev* inst_d = nullptr;
     void* band = nullptr;
@@ -83,7 +83,6 @@ struct Solver {
     int closure_batch = 0;  // the closure as two launches over all items (items of kClosureCells cells)
     int grid_cbatch = 1;
     size_t cbatch_smem = 0;
-    void* fld = nullptr;    // the batch closure's per-cell fields
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
     int stage_minb = 1;     // register bound of the stage kernel (1, or 3 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
@@ -278,6 +277,7 @@ Layout make_layout(const Solver& S) {
     for (int b = 0; b < 3; ++b) L.sumsw[b] = take(S.tsize == 4 ? (size_t)S.total_cells * S.n3 * kSums * 8 : 0);
     for (int b = 0; b < 3; ++b) L.dens[b] = take((size_t)S.total_cells * S.n3 * S.tsize);
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
+    L.mpk = take((size_t)S.total_cells * kNmom * sizeof(double));  // the moments query's rows
     L.cw = take((size_t)S.total_cells * 2 * S.tsize);
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
@@ -302,8 +302,6 @@ Layout make_layout(const Solver& S) {
     L.krf = take(S.nR >= kKrKernelMinNodes ? S.f_elems * S.tsize : 0);
     // K^h as TF32 pairs for the tensor-core contraction kernel (FP32 populations)
     L.krB = take(S.nR >= kKrKernelMinNodes && S.tsize == 4 ? kr_table_floats(S.nR) * sizeof(float) : 0);
-    // per-cell fields of the batch form of the closure
-    L.fld = take((size_t)S.total_cells * (S.tsize == 4 ? 16 : 8) * S.tsize);
     L.total = off;
     return L;
 }
@@ -684,14 +682,16 @@ void from_device_layout(const Solver& S, const std::vector<T>& src, double* dst,
 }
 
 int launch_moments_all(Solver& S, int buf) {
-    const int nc = S.max_citems;
+    // a warp per cell, every cell of the state
+    const long long blocks = ((long long)S.total_cells + 7) / 8;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(blocks, (long long)S.n_sm * 8));
     if (S.precision == FDLB_FP32) {
         // the FP64 sums and the double-float pairs the FP32 closure reads
-        launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.sumsw[buf], S.citems, S.n_citems,
-                              std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
+        launch_moments<float>((const float*)S.f[buf], S.sums[buf], (float*)S.dens[buf], S.sumsw[buf], S.total_cells,
+                              grid, S.tab, S.M, S.stream);
     } else {
-        launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], nullptr, S.citems, S.n_citems,
-                               std::max(1, std::min(nc, S.n_sm * 8)), S.inst_d, S.tab, S.M, S.stream);
+        launch_moments<double>((const double*)S.f[buf], S.sums[buf], (double*)S.dens[buf], nullptr, S.total_cells, grid,
+                               S.tab, S.M, S.stream);
     }
     S.launches++;
     return cuda_status(cudaGetLastError());
@@ -720,7 +720,6 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.wst_elems = S.closure_wst;
     A.err = S.err;
     A.programmatic = S.programmatic;
-    A.fld = S.fld;
     if (S.closure_batch) {
         if (S.precision == FDLB_FP32)
             launch_closure_batch<float>(A, S.M, S.grid_cbatch, S.cbatch_smem, S.stream);
@@ -1213,6 +1212,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
         R.dens[b] = (void*)(R.ws + L.dens[b]);
     }
     R.ca = (double*)(R.ws + L.ca);
+    R.mpk = (double*)(R.ws + L.mpk);
     R.rec = R.ws + L.rec;
     R.tabT = R.ws + L.tabT;
     R.tab = (double*)(R.ws + L.tab);
@@ -1227,7 +1227,6 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.n_citems = (int*)(R.ws + L.n_citems);
     R.nwp = (void*)(R.ws + L.nwp);
     R.cw = (void*)(R.ws + L.cw);
-    R.fld = (void*)(R.ws + L.fld);
     R.geoT = (void*)(R.ws + L.geoT);
     R.gwT = (void*)(R.ws + L.gwT);
     R.err = (int*)(R.ws + L.err);
@@ -1475,19 +1474,24 @@ int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device) tr
     Solver* S = SOL(h);
     if (!S || instance < -1 || instance >= S->n_inst || !out) return FDLB_EINVAL;
     // n, u, T, q, P_12 come from the FP64 raw sums of the current state alone (the closure's chi
-    // and nbar, columns the query does not return, are not needed): the record kernel only
+    // and nbar, columns the query does not return, are not needed): the record kernel only, which
+    // also writes the query's rows contiguously (into `out` itself for every instance on the device)
+    static_assert(fdlb::kNmom == FDLB_NMOM, "moments query columns");
+    const bool direct = on_device && instance < 0;
+    double* packed = direct ? out : S->mpk;
     if (S->precision == FDLB_FP32)
-        fdlb::launch_ca<float>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream);
+        fdlb::launch_ca<float>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream, packed);
     else
-        fdlb::launch_ca<double>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream);
+        fdlb::launch_ca<double>(S->sums[0], S->cw, S->ca, S->M.slices, S->total_cells, S->stream, packed);
     FDLB_CUDA(cudaGetLastError());
     // instance -1: every instance's cells, in instance order (the cells of instance q follow those
-    // of instances 0..q-1)
+    // of instances 0..q-1); one contiguous copy
     const int N = instance < 0 ? S->total_cells : S->setup[instance].p.n_cells;
-    const double* src = S->ca + (instance < 0 ? (size_t)0 : (size_t)S->cell_off[instance] * fdlb::kCA);
-    FDLB_CUDA(cudaMemcpy2DAsync(out, FDLB_NMOM * sizeof(double), src, fdlb::kCA * sizeof(double),
-                                FDLB_NMOM * sizeof(double), N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                S->stream));
+    if (!direct) {
+        const double* src = S->mpk + (instance < 0 ? (size_t)0 : (size_t)S->cell_off[instance] * FDLB_NMOM);
+        FDLB_CUDA(cudaMemcpyAsync(out, src, (size_t)N * FDLB_NMOM * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->stream));
+    }
     if (!on_device) FDLB_CUDA(cudaStreamSynchronize(S->stream));
     return FDLB_OK;
 } FDLB_HOST_CATCH
@@ -1654,6 +1658,17 @@ int fdlb_polish_workspace_bytes(fdlb_handle h, size_t* bytes) try {
     return fdlb_workspace_bytes(ps.data(), S->n_inst, bytes);
 } FDLB_HOST_CATCH
 
+// Total mass sum_c V_c n_c (FP64) of every instance's current state.
+static int instance_masses(Solver* S, std::vector<double>& m) {
+    fdlb::launch_residual(S->sums[0], S->M.slices, S->inst_d, S->geo, S->rprev, S->rout, S->n_inst, 0, S->stream);
+    std::vector<double> ro((size_t)S->n_inst * 10);
+    FDLB_CUDA(cudaMemcpyAsync(ro.data(), S->rout, ro.size() * 8, cudaMemcpyDeviceToHost, S->stream));
+    FDLB_CUDA(cudaStreamSynchronize(S->stream));
+    m.resize(S->n_inst);
+    for (int q = 0; q < S->n_inst; ++q) m[q] = ro[(size_t)q * 10 + 8];
+    return FDLB_OK;
+}
+
 int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
                              void* fp64_workspace, size_t fp64_workspace_bytes, int64_t* steps_fp32,
                              int64_t* steps_fp64, double* residual) try {
@@ -1674,8 +1689,16 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
     }
     // 1. the FP32 form to the tolerance (its residual reaches it; its steady state sits at the FP32
     // rounding floor, ~1e-5..1e-4 of the moment scales away from the FP64 one)
-    int rc = fdlb_run_to_steady(h, tol, max_steps, max_seconds, check_every, st32.data(), res.data());
+    std::vector<double> m0, m1;
+    int rc = instance_masses(S, m0);
+    if (rc) return rc;
+    rc = fdlb_run_to_steady(h, tol, max_steps, max_seconds, check_every, st32.data(), res.data());
     if (rc != FDLB_OK && rc != FDLB_ENOTCONVERGED && rc != FDLB_ETIMEOUT) return rc;
+    // the walls conserve mass and the steady state depends on it, but FP32 rounding walks the total
+    // mass away by up to ~1e-9 of it per step: the polish starts from the FP32 state scaled back to
+    // the mass this call began with
+    rc = instance_masses(S, m1);
+    if (rc) return rc;
     // 2. the FP64 polish from the FP32 steady state
     fdlb_handle th = nullptr;
     rc = make_fp64_twin(S, fp64_workspace, fp64_workspace_bytes, &th);
@@ -1684,7 +1707,9 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
     T->autotune_mode = S->autotune_mode;
     for (int q = 0; q < n; ++q) {
         const long long cnt = (long long)S->setup[q].p.n_cells * S->Np;
-        fdlb::launch_convert((const float*)S->f[0] + S->f_off[q], 1, (double*)T->f[0] + T->f_off[q], 0, cnt, S->stream);
+        const double scale = m1[q] > 0.0 && m0[q] > 0.0 ? m0[q] / m1[q] : 1.0;
+        fdlb::launch_convert((const float*)S->f[0] + S->f_off[q], 1, (double*)T->f[0] + T->f_off[q], 0, cnt, S->stream,
+                             scale);
     }
     rc = fdlb::cuda_status(cudaGetLastError());
     if (!rc) rc = fdlb::launch_moments_all(*T, 0);

@@ -31,6 +31,7 @@ namespace fdlb {
 
 constexpr int kSums = 13;
 constexpr int kCA = 12;
+constexpr int kNmom = 9;           // columns of the moments query (FDLB_NMOM)
 constexpr int kGeo = 6;            // per cell: R_c, 1/(dR/ds), A_+/V, A_-/V, force factor, V
 constexpr int kMaxE = 8;           // expansion coefficients per axis (N <= 7)
 constexpr int kMaxRed = 32;        // warps per block
@@ -116,13 +117,7 @@ struct ClosureArgs {
     int wst_elems;                 // capacity of the staged band rows (elements)
     int programmatic;              // launched with programmatic stream serialization
     int* err;                      // set when a bulk copy never completes
-    void* fld;                     // batch form: per cell n, u, T (wide) and q, [cell][kFldStride]
 };
-
-// Elements per cell of the batch closure's field scratch: FP32 [n, u_R, u_2, u_3, T as (hi, lo)
-// pairs | q | pad], FP64 [n, u_R, u_2, u_3, T | q].
-template <typename T>
-__host__ __device__ constexpr int fld_stride() { return sizeof(T) == 4 ? 16 : 8; }
 
 struct StepArgs {
     StageArgs st;                  // the stage fields; buffers and coefficients set per stage

@@ -7,82 +7,90 @@
 #include "kernels_decl.h"
 #include "closure_item.cuh"
 #include "fm_volumes.h"
+#include "internal.h"
 
 namespace fdlb {
 
 // ------------------------------------------------------------------------------ moments
-// Raw quadrature sums (Eq. mom_quad) of the populations of whole cells; written into slice 0
-// of the partial-sum array, the other slices are cleared; for FP32 populations also the
-// double-float pairs of the sums (sumsw, the closure's input).
+// Raw quadrature sums (Eq. mom_quad) of whole cells of a state, a warp per cell: a lane per
+// momentum row (k, i) of n2 contiguous values (the rows of a warp are one contiguous span of the
+// cell); per row the power sums over p_2 as in the stage kernel's epilogue, the thirteen sums in
+// the populations' precision over the lane's rows, then a transposed warp sum.  Written into slice
+// 0 of the partial-sum array in FP64 (the other slices cleared), for FP32 populations also as the
+// double-float pairs the closure reads, and the slice densities.  Every cell of the state.
+constexpr int kMomMaxNodes = 2 * kMaxQR;  // radial nodes
+
 template <typename T>
-__global__ void moments_kernel(const T* __restrict__ f, double* __restrict__ sums, T* __restrict__ dens,
-                               float2* __restrict__ sumsw, const int4* __restrict__ items,
-                               const int* __restrict__ n_items, const InstDev* __restrict__ inst,
-                               const double* __restrict__ tab, MomSet M) {
-    __shared__ double red[kMaxRed][kSums];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nit = *n_items;
-    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
-        const int4 w = items[it];
-        if (w.w != 0) continue;  // wall items of the closure list
-        const InstDev I = inst[w.x];
-        for (int cl = 0; cl < w.z; ++cl) {
-            const int c = w.y + cl;
-            const T* fc = f + I.f_off + (long long)c * M.Np;
-            T acc[kSums];
+__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ f, double* __restrict__ sums,
+                                                      T* __restrict__ dens, float2* __restrict__ sumsw,
+                                                      long long total_cells, const double* __restrict__ tab, MomSet M) {
+    __shared__ T sp_R[kMomMaxNodes], sp_2[kMaxQ], sp_3[kMaxQ];
+    const int lane = threadIdx.x & 31;
+    const int nR = M.nR, n2 = M.n2, n3 = M.n3, Np = M.Np;
+    for (int e = threadIdx.x; e < nR; e += blockDim.x) sp_R[e] = (T)tab[M.o_pR + e];
+    for (int e = threadIdx.x; e < n2; e += blockDim.x) sp_2[e] = (T)tab[M.o_p2 + e];
+    for (int e = threadIdx.x; e < n3; e += blockDim.x) sp_3[e] = (T)tab[M.o_p3 + e];
+    __syncthreads();
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int rows = nR * n3;
+    for (long long c = w0; c < total_cells; c += nw) {
+        const T* fc = f + c * Np;
+        T acc[16];
 #pragma unroll
-            for (int q = 0; q < kSums; ++q) acc[q] = T(0);
-            for (int m = threadIdx.x; m < M.Np; m += blockDim.x) {
-                const int k = m / (M.nR * M.n2), rem = m % (M.nR * M.n2), i = rem / M.n2, j = rem % M.n2;
-                const T p0 = (T)tab[M.o_pR + i], p1 = (T)tab[M.o_p2 + j], p2 = (T)tab[M.o_p3 + k];
-                const T v = fc[m], ps = p0 * p0 + p1 * p1 + p2 * p2;
-                if (M.reduced && k == 1) {
-                    // chi = int p_z^2 f: S2_zz and the p_z^2 p_a part of S3_a
-                    acc[6] += v;
-                    acc[10] += v * p0;
-                    acc[11] += v * p1;
-                    continue;
-                }
-                acc[0] += v;
-                acc[1] += v * p0;
-                acc[2] += v * p1;
-                acc[3] += v * p2;
-                acc[4] += v * p0 * p0;
-                acc[5] += v * p1 * p1;
-                acc[6] += v * p2 * p2;
-                acc[7] += v * p0 * p1;
-                acc[8] += v * p0 * p2;
-                acc[9] += v * p1 * p2;
-                acc[10] += v * ps * p0;
-                acc[11] += v * ps * p1;
-                acc[12] += v * ps * p2;
+        for (int q = 0; q < 16; ++q) acc[q] = T(0);
+        for (int r = lane; r < rows; r += 32) {
+            const int k = r / nR, i = r % nR;
+            const T* row = fc + (long long)r * n2;
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+            for (int j = 0; j < n2; ++j) {
+                const T v = row[j], p2v = sp_2[j];
+                const T o1 = v * p2v, o2 = o1 * p2v;
+                s0 += v;
+                s1 += o1;
+                s2 += o2;
+                s3 += o2 * p2v;
             }
-            // per-thread partials and warp tree in the populations' precision, FP64 across warps
-#pragma unroll
-            for (int q = 0; q < kSums; ++q) {
-                const T s = warp_sum(acc[q]);
-                if (lane == 0) red[warp][q] = (double)s;
+            const T pr = sp_R[i], p3v = sp_3[k];
+            const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
+            if (M.reduced && k == 1) {
+                // chi = int p_z^2 f: S2_zz and the p_z^2 p_a part of S3_a
+                acc[6] += s0;
+                acc[10] += prs0;
+                acc[11] += s1;
+                continue;
             }
-            __syncthreads();
-            if (threadIdx.x < kSums) {
-                double s = 0.0;
-                for (int ww = 0; ww < nw; ++ww) s += red[ww][threadIdx.x];
-                const long long base = ((long long)(I.cell_off + c) * M.slices) * kSums;
-                double* dst = sums + base;
-                dst[threadIdx.x] = s;
-                for (int sl = 1; sl < M.slices; ++sl) dst[sl * kSums + threadIdx.x] = 0.0;
-                if (sumsw) {  // the double-float pairs of the FP32 closure
-                    const float hi = __double2float_rn(s);
-                    sumsw[base + threadIdx.x] = make_float2(hi, __double2float_rn(s - (double)hi));
-                    for (int sl = 1; sl < M.slices; ++sl) sumsw[base + sl * kSums + threadIdx.x] = make_float2(0.f, 0.f);
-                }
-                if (threadIdx.x == 0) {
-                    T* dd = dens + (long long)(I.cell_off + c) * M.slices;
-                    dd[0] = (T)s;
-                    for (int sl = 1; sl < M.slices; ++sl) dd[sl] = T(0);
-                }
+            const T e10 = rr * s0 + s2;
+            acc[0] += s0;
+            acc[1] += prs0;
+            acc[2] += s1;
+            acc[3] += p3s0;
+            acc[4] += pr * prs0;
+            acc[5] += s2;
+            acc[6] += p3v * p3s0;
+            acc[7] += pr * s1;
+            acc[8] += pr * p3s0;
+            acc[9] += p3v * s1;
+            acc[10] += pr * e10;
+            acc[11] += rr * s1 + s3;
+            acc[12] += p3v * e10;
+        }
+        const T tot = warp_sum16_transposed(acc, lane);
+        const int q = lane >> 1;
+        if (!(lane & 1) && q < kSums) {
+            const double sd = (double)tot;
+            const long long base = c * M.slices * kSums;
+            sums[base + q] = sd;
+            for (int sl = 1; sl < M.slices; ++sl) sums[base + sl * kSums + q] = 0.0;
+            if (sumsw) {  // the double-float pairs of the FP32 closure
+                sumsw[base + q] = make_float2((float)tot, 0.f);
+                for (int sl = 1; sl < M.slices; ++sl) sumsw[base + sl * kSums + q] = make_float2(0.f, 0.f);
             }
-            __syncthreads();
+            if (q == 0) {
+                T* dd = dens + c * M.slices;
+                dd[0] = tot;
+                for (int sl = 1; sl < M.slices; ++sl) dd[sl] = T(0);
+            }
         }
     }
 }
@@ -140,142 +148,76 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
 // ------------------------------------------------------------------------------ batch closure
 // The closure of a batch as two launches over all items instead of one item chain per block.  With
 // many more items than co-resident blocks the chain form is bound by how many items are in flight:
-// most of its phases run one lane per reach cell while the other lanes wait at its barriers.  Here
-// closure_fields_kernel forms per own cell the fields (n, u, T wide; q) into the scratch A.fld and,
-// from the cell's FM band sum, chi and nbar into A.cw, plus the wall items; then
-// closure_records_kernel forms each item's records from the fields of its reach, every phase
-// spread over the whole block.  Both are made of the chain's per-cell functions (closure_item.cuh),
-// so the records are the chain's.
+// most of its phases run one lane per reach cell while the other lanes wait at its barriers, and
+// its FM band rows are read one item at a time.  Here closure_band_kernel gives every band row of
+// every item to a warp of its own (the band sum of Eq. fm, then chi and nbar into A.cw) and takes
+// the wall items, with no block barrier; closure_records_kernel then forms each item's records from
+// the raw sums of its reach and the band results, every phase spread over the whole block.  Both
+// are made of the chain's per-cell functions (closure_item.cuh), so the records are the chain's.
 
+// A warp per band row: the virtual row v is row v % kClosureCells of item v / kClosureCells
+// (rows beyond an item's cells, and all but the first of a wall item's, are empty).
 template <typename T>
-__device__ __forceinline__ void fld_store(T* o, const Wide<T>& n, const Wide<T> (&u)[3], const Wide<T>& Tc,
-                                          const T (&q)[3]) {
-    if constexpr (sizeof(T) == 4) {
-        reinterpret_cast<float4*>(o)[0] = make_float4(n.hi, n.lo, u[0].hi, u[0].lo);
-        reinterpret_cast<float4*>(o)[1] = make_float4(u[1].hi, u[1].lo, u[2].hi, u[2].lo);
-        reinterpret_cast<float4*>(o)[2] = make_float4(Tc.hi, Tc.lo, q[0], q[1]);
-        o[12] = q[2];
-    } else {
-        o[0] = w_hi(n);
-        o[1] = w_hi(u[0]);
-        o[2] = w_hi(u[1]);
-        o[3] = w_hi(u[2]);
-        o[4] = w_hi(Tc);
-        o[5] = q[0];
-        o[6] = q[1];
-        o[7] = q[2];
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void fld_load(const T* o, Wide<T>& n, Wide<T> (&u)[3], Wide<T>& Tc, T (&q)[3]) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 a = reinterpret_cast<const float4*>(o)[0], b = reinterpret_cast<const float4*>(o)[1],
-                     c = reinterpret_cast<const float4*>(o)[2];
-        n = Wide<T>{a.x, a.y};
-        u[0] = Wide<T>{a.z, a.w};
-        u[1] = Wide<T>{b.x, b.y};
-        u[2] = Wide<T>{b.z, b.w};
-        Tc = Wide<T>{c.x, c.y};
-        q[0] = c.z;
-        q[1] = c.w;
-        q[2] = o[12];
-    } else {
-        n = w_from_t(o[0]);
-        u[0] = w_from_t(o[1]);
-        u[1] = w_from_t(o[2]);
-        u[2] = w_from_t(o[3]);
-        Tc = w_from_t(o[4]);
-        q[0] = o[5];
-        q[1] = o[6];
-        q[2] = o[7];
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kClosureThreads, 8) closure_fields_kernel(ClosureArgs A, MomSet M) {
-    __shared__ T red[kClosureWarps];
-    __shared__ T snb[kClosureCells];
+__global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closure_band_kernel(ClosureArgs A, MomSet M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const ClosureTabs<T> tb = closure_tables<T>(reinterpret_cast<T*>(smem_raw), A.tabT, M, tid, blockDim.x);
     __syncthreads();
-    pdl_wait();  // the raw sums, densities and populations of the previous kernel
+    pdl_wait();  // the densities and populations of the previous kernel
     pdl_trigger();
     const T* fin_all = reinterpret_cast<const T*>(A.f_in);
     const T* band = reinterpret_cast<const T*>(A.band);
     const T* dens = reinterpret_cast<const T*>(A.dens);
     T* nwp = reinterpret_cast<T*>(A.nwp);
-    T* fld = reinterpret_cast<T*>(A.fld);
     T* cw = reinterpret_cast<T*>(A.cw);
     const int slices = A.slices;
-    const int nit = *A.n_items;
-    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+    const long long nv = (long long)(*A.n_items) * kClosureCells;
+    const long long gw = (long long)blockIdx.x * kClosureWarps + warp, nw = (long long)gridDim.x * kClosureWarps;
+    for (long long v = gw; v < nv; v += nw) {
+        const int it = (int)(v / kClosureCells), t = (int)(v % kClosureCells);
         const int4 w = A.items[it];
-        const InstDev I = A.inst[w.x];
         if (w.w != 0) {
-            // one part of the outgoing flux through a wall, as in the chain form
+            if (t != 0) continue;
+            // one part of the outgoing flux through a wall, by one warp in the order of the chain
+            // form's block of kClosureThreads threads: lane L takes the momenta of its threads
+            // L, L + 32, L + 64, L + 96 and the four warp sums are combined as there
+            const InstDev I = A.inst[w.x];
             const int side = w.w - 1, part = w.z, P = A.wall_parts;
             const T* wall = fin_all + I.f_off + (side == 0 ? 0LL : (long long)(I.n_cells - 1) * M.Np);
-            T acc = wall_flux_partial<T>(wall, side == 0 ? (long long)M.Np : -(long long)M.Np, M, tb, side, part, P, tid);
-            acc = warp_sum(acc);
-            if (lane == 0) red[warp] = acc;
-            __syncthreads();
-            if (tid == 0) nwp[((long long)w.x * 2 + side) * P + part] = wall_part_sum(red);
-            __syncthreads();
+            T r[kClosureWarps];
+#pragma unroll
+            for (int vw = 0; vw < kClosureWarps; ++vw)
+                r[vw] = warp_sum(wall_flux_partial<T>(wall, side == 0 ? (long long)M.Np : -(long long)M.Np, M, tb, side,
+                                                      part, P, 32 * vw + lane));
+            if (lane == 0) nwp[((long long)w.x * 2 + side) * P + part] = wall_part_sum(r);
             continue;
         }
-        const int c0 = w.y, cnt = w.z, N = I.n_cells;
-        const T etaf = inst_param<T>(I.etafac, I.f_etafac);
-        if (warp == 0) {
-            // lane per own cell: the fields from the raw sums
-            if (lane < cnt) {
-                const long long gc = (long long)I.cell_off + c0 + lane;
-                Wide<T> sv[kSums];
-                clo_load_sums<T>(A, gc, sv);
-                Wide<T> n, u[3], Tc;
-                T q[3];
-                clo_fields<T>(sv, n, u, Tc, q);
-                fld_store<T>(fld + gc * fld_stride<T>(), n, u, Tc, q);
-                if (I.chi_local) {
-                    cw[gc * 2] = clo_chi<T>(etaf, w_hi(n));
-                    cw[gc * 2 + 1] = w_hi(n);
-                }
-            }
-        } else if (!I.chi_local) {
-            // warp per own cell's band row (coalesced along the row)
-            const int2* bl = reinterpret_cast<const int2*>(A.band_lo) + I.cell_off;
-            for (int t = warp - 1; t < cnt; t += kClosureWarps - 1) {
-                const int c = c0 + t;
-                const int2 e = bl[c];
-                const int kmax = min(e.y, N - e.x);
-                const T* Wr = band + I.band_off + (long long)c * I.band_w;
-                const T* nd = dens + ((long long)I.cell_off + e.x) * slices;
-                const T tot = clo_band_row<T>(
-                    Wr,
-                    [&](int k) {
-                        T v = nd[(long long)k * slices];
-                        for (int sl = 1; sl < slices; ++sl) v += nd[(long long)k * slices + sl];
-                        return v;
-                    },
-                    kmax, lane);
-                if (lane == 0) snb[t] = tot;
-            }
-        }
-        if (!I.chi_local) {
-            __syncthreads();
-            if (warp == 0 && lane < cnt) {
-                const long long gc = (long long)I.cell_off + c0 + lane;
-                cw[gc * 2] = clo_chi<T>(etaf, snb[lane]);
-                cw[gc * 2 + 1] = snb[lane];
-            }
-            __syncthreads();  // snb is reused by the next item
+        if (t >= w.z) continue;
+        const InstDev I = A.inst[w.x];
+        if (I.chi_local) continue;  // chi at the local density: closure_records_kernel
+        const int N = I.n_cells, c = w.y + t;
+        const int2 e = reinterpret_cast<const int2*>(A.band_lo)[I.cell_off + c];
+        const int kmax = min(e.y, N - e.x);
+        const T* Wr = band + I.band_off + (long long)c * I.band_w;
+        const T* nd = dens + ((long long)I.cell_off + e.x) * slices;
+        const T tot = clo_band_row<T>(
+            Wr,
+            [&](int k) {
+                T x = nd[(long long)k * slices];
+                for (int sl = 1; sl < slices; ++sl) x += nd[(long long)k * slices + sl];
+                return x;
+            },
+            kmax, lane);
+        if (lane == 0) {
+            const long long gc = (long long)I.cell_off + c;
+            cw[gc * 2] = clo_chi<T>(inst_param<T>(I.etafac, I.f_etafac), tot);
+            cw[gc * 2 + 1] = tot;
         }
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(ClosureArgs A, MomSet M) {
+__global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closure_records_kernel(ClosureArgs A, MomSet M) {
     using W = Wide<T>;
     __shared__ W sw_n[32], sw_T[32], sw_u[3][32];  // reach cells
     __shared__ T s_chi[32], snb[32];
@@ -286,10 +228,9 @@ __global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(Clo
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
     const ClosureTabs<T> tb = closure_tables<T>(reinterpret_cast<T*>(smem_raw), A.tabT, M, tid, NT);
     __syncthreads();
-    pdl_wait();  // the fields, chi and nbar of closure_fields_kernel
+    pdl_wait();  // the band results of closure_band_kernel
     pdl_trigger();
-    const T* fld = reinterpret_cast<const T*>(A.fld);
-    const T* cw = reinterpret_cast<const T*>(A.cw);
+    T* cw = reinterpret_cast<T*>(A.cw);
     const T* geoT = reinterpret_cast<const T*>(A.geoT);
     T* rec_all = reinterpret_cast<T*>(A.rec);
     const int rs = A.rec_stride, ng = M.nR + M.n2 + M.n3;
@@ -297,27 +238,40 @@ __global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(Clo
     const int nit = *A.n_items;
     for (int it = blockIdx.x; it < nit; it += gridDim.x) {
         const int4 w = A.items[it];
-        if (w.w != 0) continue;  // wall items: closure_fields_kernel
+        if (w.w != 0) continue;  // wall items: closure_band_kernel
         const InstDev I = A.inst[w.x];
         const int c0 = w.y, cnt = w.z, N = I.n_cells;
         int h0, h1;
         clo_reach(c0, cnt, N, h0, h1);
         const int nh = h1 - h0;
         T* recb = rec_all + (long long)(I.cell_off + c0) * rs;
-        // ---- the reach's fields, chi and nbar; the own cells' q and geometry
+        const T etaf = inst_param<T>(I.etafac, I.f_etafac);
+        // ---- the reach's n, u, T from the raw sums (thread per reach cell), chi and nbar from the
+        // band kernel or, for chi at the local density, here; the own cells' q and geometry
         for (int e = tid; e < nh; e += NT) {
             const long long gc = (long long)I.cell_off + h0 + e;
+            W sv[kSums];
+            clo_load_sums<T>(A, gc, sv);
             W n, u[3], Tc;
             T q[3];
-            fld_load<T>(fld + gc * fld_stride<T>(), n, u, Tc, q);
+            clo_fields<T>(sv, n, u, Tc, q);
             sw_n[e] = n;
             sw_u[0][e] = u[0];
             sw_u[1][e] = u[1];
             sw_u[2][e] = u[2];
             sw_T[e] = Tc;
-            s_chi[e] = cw[gc * 2];
-            snb[e] = cw[gc * 2 + 1];
             const int t = h0 + e - c0;
+            if (I.chi_local) {
+                s_chi[e] = clo_chi<T>(etaf, w_hi(n));
+                snb[e] = w_hi(n);
+                if (t >= 0 && t < cnt) {
+                    cw[gc * 2] = s_chi[e];
+                    cw[gc * 2 + 1] = snb[e];
+                }
+            } else {
+                s_chi[e] = cw[gc * 2];
+                snb[e] = cw[gc * 2 + 1];
+            }
             if (t >= 0 && t < cnt) {
                 sq[t][0] = q[0];
                 sq[t][1] = q[1];
@@ -329,7 +283,6 @@ __global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(Clo
         }
         __syncthreads();
         // ---- gradient terms (thread per own cell and stencil position)
-        const T etaf = inst_param<T>(I.etafac, I.f_etafac);
         for (int e = tid; e < cnt * 5; e += NT) {
             const int t = e / 5, q = e % 5, c = c0 + t;
             int cq;
@@ -365,8 +318,8 @@ __global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(Clo
             recb[(long long)t * rs + dst] = g;
         }
         __syncthreads();
-        // ---- discrete mass of the stored equilibrium (a warp per own cell)
-        for (int t = warp; t < cnt; t += NT / 32) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M, lane);
+        // ---- discrete mass of the stored equilibrium (a thread per own cell)
+        for (int t = tid; t < cnt; t += NT) clo_mass_normalise<T>(recb + (long long)t * rs, sw_n[c0 + t - h0], M);
         __syncthreads();  // shared arrays are reused by the next item
     }
 }
@@ -377,7 +330,7 @@ __global__ void __launch_bounds__(kClosureThreads, 8) closure_records_kernel(Clo
 // the closure's side buffer.
 template <typename T>
 __global__ void ca_kernel(const double* __restrict__ sums, const void* cwv, double* __restrict__ ca, int slices,
-                          int total_cells) {
+                          int total_cells, double* __restrict__ packed) {
     const T* cw = reinterpret_cast<const T*>(cwv);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < total_cells; c += gridDim.x * blockDim.x) {
         double s[kSums];
@@ -405,13 +358,16 @@ __global__ void ca_kernel(const double* __restrict__ sums, const void* cwv, doub
         r[9] = (double)cw[2 * (long long)c];
         r[10] = (double)cw[2 * (long long)c + 1];
         r[11] = 0.0;
+        if (packed)  // the moments query's rows: the first kNmom columns, contiguous
+            for (int e = 0; e < kNmom; ++e) packed[(long long)c * kNmom + e] = r[e];
     }
 }
 
 template <typename T>
-void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s) {
+void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s,
+               double* packed) {
     const int g = (total_cells + 255) / 256;
-    ca_kernel<T><<<g < 2048 ? (g > 0 ? g : 1) : 2048, 256, 0, s>>>(sums, cw, ca, slices, total_cells);
+    ca_kernel<T><<<g < 2048 ? (g > 0 ? g : 1) : 2048, 256, 0, s>>>(sums, cw, ca, slices, total_cells, packed);
 }
 
 // ------------------------------------------------------------------------------ stream
@@ -470,9 +426,9 @@ __global__ void residual_kernel(const double* __restrict__ sums, int slices, con
 
 // ------------------------------------------------------------------------------ launchers
 template <typename T>
-void launch_moments(const T* f, double* sums, T* dens, void* sumsw, const int4* items, const int* n_items, int grid,
-                    const InstDev* inst, const double* tab, const MomSet& M, cudaStream_t s) {
-    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, dens, reinterpret_cast<float2*>(sumsw), items, n_items, inst, tab, M);
+void launch_moments(const T* f, double* sums, T* dens, void* sumsw, long long total_cells, int grid, const double* tab,
+                    const MomSet& M, cudaStream_t s) {
+    moments_kernel<T><<<grid, 256, 0, s>>>(f, sums, dens, reinterpret_cast<float2*>(sumsw), total_cells, tab, M);
 }
 
 // Slice densities from restored raw sums.
@@ -511,7 +467,7 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
 
 template <typename T>
 void launch_closure_batch(const ClosureArgs& A, const MomSet& M, int grid, size_t smem, cudaStream_t s) {
-    launch_maybe_programmatic(closure_fields_kernel<T>, grid, kClosureThreads, smem, s, A.programmatic, A, M);
+    launch_maybe_programmatic(closure_band_kernel<T>, grid, kClosureThreads, smem, s, A.programmatic, A, M);
     launch_maybe_programmatic(closure_records_kernel<T>, grid, kClosureThreads, smem, s, A.programmatic, A, M);
 }
 
@@ -519,10 +475,10 @@ int closure_batch_blocks_per_sm(int tsize, size_t smem) {
     int a = 0, b = 0;
     cudaError_t e1, e2;
     if (tsize == 4) {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_fields_kernel<float>, kClosureThreads, smem);
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_band_kernel<float>, kClosureThreads, smem);
         e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, closure_records_kernel<float>, kClosureThreads, smem);
     } else {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_fields_kernel<double>, kClosureThreads, smem);
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, closure_band_kernel<double>, kClosureThreads, smem);
         e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, closure_records_kernel<double>, kClosureThreads, smem);
     }
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -596,32 +552,32 @@ void launch_residual(const double* sums, int slices, const InstDev* inst, const 
 
 // Populations of one precision copied into the other (rounding to nearest for FP64 -> FP32).
 template <typename A, typename B>
-__global__ void convert_kernel(const A* __restrict__ src, B* __restrict__ dst, long long n) {
+__global__ void convert_kernel(const A* __restrict__ src, B* __restrict__ dst, long long n, double scale) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = (B)src[i];
+        dst[i] = (B)((double)src[i] * scale);
 }
 
-void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s) {
+void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s, double scale) {
     const long long g = (n + 255) / 256;
     const int grid = (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
     if (src_fp32 && !dst_fp32)
-        convert_kernel<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)dst, n);
+        convert_kernel<float, double><<<grid, 256, 0, s>>>((const float*)src, (double*)dst, n, scale);
     else if (!src_fp32 && dst_fp32)
-        convert_kernel<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)dst, n);
+        convert_kernel<double, float><<<grid, 256, 0, s>>>((const double*)src, (float*)dst, n, scale);
     else if (src_fp32)
-        convert_kernel<float, float><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, n);
+        convert_kernel<float, float><<<grid, 256, 0, s>>>((const float*)src, (float*)dst, n, scale);
     else
-        convert_kernel<double, double><<<grid, 256, 0, s>>>((const double*)src, (double*)dst, n);
+        convert_kernel<double, double><<<grid, 256, 0, s>>>((const double*)src, (double*)dst, n, scale);
 }
 
-template void launch_ca<float>(const double*, const void*, double*, int, int, cudaStream_t);
-template void launch_ca<double>(const double*, const void*, double*, int, int, cudaStream_t);
+template void launch_ca<float>(const double*, const void*, double*, int, int, cudaStream_t, double*);
+template void launch_ca<double>(const double*, const void*, double*, int, int, cudaStream_t, double*);
 template void launch_dens_from_sums<float>(const double*, float*, long long, cudaStream_t);
 template void launch_dens_from_sums<double>(const double*, double*, long long, cudaStream_t);
-template void launch_moments<float>(const float*, double*, float*, void*, const int4*, const int*, int, const InstDev*,
-                                    const double*, const MomSet&, cudaStream_t);
-template void launch_moments<double>(const double*, double*, double*, void*, const int4*, const int*, int, const InstDev*,
-                                     const double*, const MomSet&, cudaStream_t);
+template void launch_moments<float>(const float*, double*, float*, void*, long long, int, const double*, const MomSet&,
+                                    cudaStream_t);
+template void launch_moments<double>(const double*, double*, double*, void*, long long, int, const double*,
+                                     const MomSet&, cudaStream_t);
 template void launch_closure<float>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
 template void launch_closure<double>(const ClosureArgs&, const MomSet&, int, int, size_t, cudaStream_t);
 template void launch_closure_batch<float>(const ClosureArgs&, const MomSet&, int, size_t, cudaStream_t);

@@ -80,12 +80,17 @@ struct StreamCfg {
     int minb = 1;  // register bound of the stage kernel: 1 or 3 blocks per SM (cylinder FP32 shape)
 };
 
+// Raw sums (FP64, slice 0), double-float pairs (FP32 populations) and densities of every cell of a
+// state of total_cells cells.
 template <typename T>
-void launch_moments(const T* f, double* sums, T* dens, void* sumsw, const int4* items, const int* n_items, int grid, const InstDev* inst,
-                    const double* tab, const MomSet& M, cudaStream_t s);
+void launch_moments(const T* f, double* sums, T* dens, void* sumsw, long long total_cells, int grid, const double* tab,
+                    const MomSet& M, cudaStream_t s);
 
 template <typename T>
-void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s);
+// The FP64 closure record of every cell (kCA columns); with `packed`, also the moments query's rows
+// (the first kNmom columns) contiguous, [cell][kNmom].
+void launch_ca(const double* sums, const void* cw, double* ca, int slices, int total_cells, cudaStream_t s,
+               double* packed = nullptr);
 
 void launch_sums_pairs(const double* sums, void* sw, long long n, cudaStream_t s);
 
@@ -98,8 +103,8 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize);
 // Blocks of the closure kernel that fit on an SM with `smem` bytes of dynamic shared memory each.
 int closure_blocks_per_sm(int tsize, size_t smem);
-// The batch form of the closure (closure_fields_kernel, then closure_records_kernel; items of at
-// most kClosureCells cells, A.fld set), and the blocks of either that reside on one SM.
+// The batch form of the closure (closure_band_kernel, then closure_records_kernel; items of at
+// most kClosureCells cells), and the blocks of either that reside on one SM.
 template <typename T>
 void launch_closure_batch(const ClosureArgs& A, const MomSet& M, int grid, size_t smem, cudaStream_t s);
 int closure_batch_blocks_per_sm(int tsize, size_t smem);
@@ -143,7 +148,9 @@ size_t kr_tc_smem_bytes(int Npad);
 cudaError_t launch_fm_band(int tsize, const double* Rc, int rc_stride, const double* Rf, int N, int sphere, double sigma,
                            int width, const int2* blo, void* W, const FmRule& rule, int grid, cudaStream_t s);
 
-void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s);
+// dst = src x scale, the product formed in FP64 and rounded once to the destination's precision.
+void launch_convert(const void* src, int src_fp32, void* dst, int dst_fp32, long long n, cudaStream_t s,
+                    double scale = 1.0);
 
 void launch_residual(const double* sums, int slices, const InstDev* inst, const double* geo, double* prev, double* out,
                      int n_inst, int save, cudaStream_t s);

@@ -113,33 +113,6 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
     }
 }
 
-// Sums of 16 values over the 32 lanes of a warp, transposed: at every level of the butterfly a
-// lane keeps half of its values and sends the other half, so the warp needs 16 shuffles instead
-// of 16 x 5.  Lane L returns the sum of value (L >> 1).  Fixed order: deterministic.
-template <typename T>
-__device__ __forceinline__ T warp_sum16_transposed(const T (&v)[16], int lane) {
-    T w8[8], w4[4], w2[2];
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const T send = b4 ? v[t] : v[t + 8], keep = b4 ? v[t + 8] : v[t];
-        w8[t] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const T send = b3 ? w8[t] : w8[t + 4], keep = b3 ? w8[t + 4] : w8[t];
-        w4[t] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const T send = b2 ? w4[t] : w4[t + 2], keep = b2 ? w4[t + 2] : w4[t];
-        w2[t] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    const T send = b1 ? w2[0] : w2[1], keep = b1 ? w2[1] : w2[0];
-    const T w1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    return w1 + __shfl_xor_sync(0xffffffffu, w1, 1);
-}
-
 // Local names of the stage's dimensions and of its shared-memory plan (StreamSmem): fs the
 // staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sK2 K_2 in the vector-swizzled
 // order [e][b / VW][j / VW][b % VW] (first: aligned vector loads), sKR K^h with row stride krs,

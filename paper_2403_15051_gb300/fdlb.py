@@ -425,10 +425,14 @@ class Solver:
         _check(self._L.fdlb_state_bytes(self._h, byref(nb)), "fdlb_state_bytes")
         return int(nb.value)
 
-    def moments_all(self) -> np.ndarray:
-        """Moments of every instance, [total cells][NMOM] in instance order."""
+    def moments_all(self, out=None) -> np.ndarray:
+        """Moments of every instance, [total cells][NMOM] in instance order.  `out`: an FP64 host
+        array of that shape to fill (page-locked memory copies at the full link rate)."""
         N = sum(self.shape(q)[0] for q in range(self.n_instances))
-        out = np.empty((N, NMOM))
+        if out is None:
+            out = np.empty((N, NMOM))
+        if out.shape != (N, NMOM) or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array of shape (%d, %d)" % (N, NMOM))
         _check(self._L.fdlb_get_moments(self._h, -1, out.ctypes.data_as(c_void_p), 0), "fdlb_get_moments")
         return out
 
