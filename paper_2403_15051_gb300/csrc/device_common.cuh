@@ -126,13 +126,15 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
 // difference and t_k the first-difference part of its indicator, so the value is
 // w2 + sum_k a_k X_k / (12 sum_k a_k), X_k = D_k +- 3 sigma t_k.  The linear weights follow the
 // direction: (dL, dC, dR) = (0.1, 0.6, 0.3) or (0.3, 0.6, 0.1); s3 = 3 sigma.  Indicators are
-// taken four times over (4 eps + 13/3 D^2 + t^2): the normalised weights are unchanged.
+// taken four times over (e4 + 13/3 D^2 + t^2, e4 = 4 eps): the normalised weights are unchanged.
+// The reconstruction is homogeneous of degree one in the window once eps scales with its square:
+// the value for c w0..c w4 with c^2 e4 is c times the value for w0..w4 with e4.
 template <typename T>
-__device__ __forceinline__ T weno5_sym(T w0, T w1, T w2, T w3, T w4, T s3, T dL, T dR) {
+__device__ __forceinline__ T weno5_sym(T w0, T w1, T w2, T w3, T w4, T s3, T dL, T dR, T e4) {
     const T d0 = w1 - w0, d1 = w2 - w1, d2 = w3 - w2, d3 = w4 - w3;
     const T D1 = d1 - d0, D2 = d2 - d1, D3 = d3 - d2;
     const T tL = T(3) * d1 - d0, tC = -(d1 + d2), tR = d3 - T(3) * d2;
-    const T c = T(13.0 / 3.0), e4 = T(4e-6);
+    const T c = T(13.0 / 3.0);
     const T EL = tL * tL + (c * D1 * D1 + e4);
     const T EC = tC * tC + (c * D2 * D2 + e4);
     const T ER = tR * tR + (c * D3 * D3 + e4);

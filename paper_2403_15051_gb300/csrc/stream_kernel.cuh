@@ -368,14 +368,14 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
     // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
     int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
     T pr_[NV], p3_[NV];
-    T wm_[NV][VW], iw_[NV][VW], p2_[NV][VW], vl_[NV][VW];
+    T e4w_[NV][VW], p2_[NV][VW], p2q_[NV][VW], vl_[NV][VW];
 #pragma unroll
     for (int g = 0; g < NV; ++g) {
         const int v = tid + g * NT;
         vcode[g] = -1;
         pr_[g] = p3_[g] = T(0);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) wm_[g][e] = iw_[g][e] = p2_[g][e] = vl_[g][e] = T(0);
+        for (int e = 0; e < VW; ++e) e4w_[g][e] = p2_[g][e] = p2q_[g][e] = vl_[g][e] = T(0);
         if (v < Vs) {
             const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
             const int k = sl * KS + kk;
@@ -388,16 +388,18 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
             for (int e = 0; e < VW; ++e) {
                 const int j = jb * VW + e;
                 p2_[g][e] = sp_2[j];
-                wm_[g][e] = wik * sw_2[j];
-                // a weight at the bottom of the populations' range (FP32 at large radial orders: below
-                // 1e-30 its populations are below 1e-28 or zero, and 1/w leaves the float range)
-                // contributes no reconstruction and no flux
-                iw_[g][e] = wm_[g][e] > (sizeof(T) == 4 ? T(1e-30) : T(0)) ? T(1) / wm_[g][e] : T(0);
+                p2q_[g][e] = sp_2[j] * sp_2[j];
+                // WENO5 of f / w (Sec. II.C) taken on f itself: with eps scaled by w^2 the face value
+                // of f is w times that of f / w, and the flux needs no division by the weight.  In
+                // FP32 eps w^2 is kept above the float range's floor (weights below ~1e-16 at large
+                // radial orders, whose populations are negligible, reconstruct with linear weights)
+                const T wm = wik * sw_2[j];
+                e4w_[g][e] = sizeof(T) == 4 ? fmax(T(4e-6) * wm * wm, T(1e-37)) : T(4e-6) * wm * wm;
             }
             if (c0 == 0 && pr > T(0)) {
                 const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e] * iw_[g][e];
+                for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e];
             } else {
                 // rows of cells c0-3..c0+1 (p_R > 0) or c0-2..c0+2 (p_R < 0), ascending
                 const T* b = fs + (long long)(pr > T(0) ? 0 : 1) * Ms + v * VW;
@@ -409,10 +411,7 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 ld_vec<T, VW>(b + 3 * Ms, r3);
                 ld_vec<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const T iw = iw_[g][e];
-                    vl_[g][e] = weno5_sym(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw, s3, dL, dR);
-                }
+                for (int e = 0; e < VW; ++e) vl_[g][e] = weno5_sym(r0[e], r1[e], r2[e], r3[e], r4[e], s3, dL, dR, e4w_[g][e]);
             }
         }
     }
@@ -456,7 +455,7 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 if (c == N - 1 && pr < T(0)) {
                     const T gik = nwR * gwR[i] * gwR[nR + n2 + k];
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e] * iw_[g][e];
+                    for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e];
                 } else {
                     // rows of cells c-2..c+2 (p_R > 0) or c-1..c+3 (p_R < 0), ascending
                     const T* b = fc + (pr > T(0) ? -2 * Ms : -Ms) + vb;
@@ -469,10 +468,7 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                     ld_vec<T, VW>(b + 3 * Ms, r3);
                     ld_vec<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) {
-                        const T iw = iw_[g][e];
-                        vr[e] = weno5_sym(r0[e] * iw, r1[e] * iw, r2[e] * iw, r3[e] * iw, r4[e] * iw, s3, dL, dR);
-                    }
+                    for (int e = 0; e < VW; ++e) vr[e] = weno5_sym(r0[e], r1[e], r2[e], r3[e], r4[e], s3, dL, dR, e4w_[g][e]);
                 }
                 // curvature force: K^h along i (one column shared by the vector), K_2 along j
                 T KRf[VW], K2f[VW], K3f[VW];
@@ -563,17 +559,18 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const T J2 = nbr * (Yd * hiT + J2c);
                 const T b0 = fiT * xsA - T(1), cb0 = cS * b0;
                 const T F0 = T(1) + cb0 * xqA, F1 = cb0 * q1, F2 = cS * fiT * xqA;
+                const T pAp = pr * Ap, pAm = pr * Am;  // face values are of f: p_R A+/V, p_R A-/V
                 T out[VW];
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
                     const T p2v = p2_[g][e];
-                    const T adv = pr * wm_[g][e] * (Ap * vr[e] - Am * vl_[g][e]);
+                    const T adv = pAp * vr[e] - pAm * vl_[g][e];
                     vl_[g][e] = vr[e];
                     T frc;
                     if (GEOM == 0) {
-                        frc = kf * (p2v * p2v * KRf[e] - pr * K2f[e]);
+                        frc = kf * (p2q_[g][e] * KRf[e] - pr * K2f[e]);
                     } else {
-                        frc = (kf * p2v * p2v + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
+                        frc = (kf * p2q_[g][e] + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
                     }
                     const T x1 = p2v - u1;
                     const T fmb = fmbA * g2v[e];
@@ -606,12 +603,11 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
 #pragma unroll
                 for (int e = 0; e < VW; ++e) {
-                    const T p2v = p2_[g][e];
-                    const T o1 = out[e] * p2v, o2 = o1 * p2v;
+                    const T o1 = out[e] * p2_[g][e];
                     s0 += out[e];
                     s1 += o1;
-                    s2 += o2;
-                    s3 += o2 * p2v;
+                    s2 += out[e] * p2q_[g][e];
+                    s3 += o1 * p2q_[g][e];
                 }
                 const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
                 const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
