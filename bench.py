@@ -530,7 +530,7 @@ def run_ours(args):
 
 
 def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.01, max_steps=150_000, epochs=300,
-                   ref_tol=1e-11, ref_steps=300_000, check_every=200):
+                   ref_tol=1e-11, ref_steps=300_000, check_every=200, stall_checks=50):
     """Time to steady state (moment residual <= tol) on held-out sweep instances (the batched-sweep
     parameter distribution at a reduced grid: `cells` cells, Q = q on every axis):
     (A) the plain form - FP64, one instance at a time, uniform start - on a fixed seeded subset of
@@ -542,7 +542,11 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     plus, for what they show, (C) the batched FP32 form alone and (D) the batched FP32 form from the
     uniform start (the network's gain).  Accuracy: the largest moment error of each arm's steady
     state against an FP64 reference run to ref_tol, on the n_plain subset.  Instances whose FP64
-    residual never reaches tol (a small self-sustained oscillation) are left out and counted."""
+    residual never reaches tol (a small self-sustained oscillation) are left out and counted.  Every
+    run but the references uses the library's stall rule (an instance whose residual has not halved
+    its lowest value for stall_checks checks stops stepping, unconverged), so that an instance that
+    settles on such an oscillation does not hold a batch to max_steps; training data are the
+    instances with finite profiles."""
     import torch
 
     from paper_2403_15051_gb300 import fdlb
@@ -559,7 +563,10 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     ce = check_every
     t0 = time.perf_counter()
     train_ds = instances(n_train, 1)
-    raw, tg, st_train, _, rc_data = wsm.steady_states(train_ds, n_points=P, tol=tol, max_steps=max_steps)
+    raw, tg, st_train, res_train, rc_data = wsm.steady_states(train_ds, n_points=P, tol=tol, max_steps=max_steps,
+                                                              stall_checks=stall_checks)
+    finite = np.isfinite(res_train) & np.all(np.isfinite(tg), axis=(1, 2))
+    raw, tg = raw[finite], tg[finite]
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     net, losses = wsm.train(raw, tg, epochs=epochs, batch=32, lr=2e-3)
@@ -584,6 +591,7 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     # n_plain kept, in seeded order), on which every arm's accuracy is measured
     t0 = time.perf_counter()
     R = fdlb.Solver([dict(d, precision="fp64") for d in eval_all])
+    R.set_stall_checks(stall_checks)
     _, _, res_tol = R.run_to_steady(tol=tol, max_steps=max_steps, check_every=ce)
     R.close()
     keep = [k for k in range(len(eval_all)) if float(res_tol[k]) <= tol]
@@ -601,6 +609,7 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     t0 = time.perf_counter()
     for k in plain_idx:
         S = fdlb.Solver(dict(eval_all[k], precision="fp64"))
+        S.set_stall_checks(stall_checks)
         _, st, res = S.run_to_steady(tol=tol, max_steps=max_steps, check_every=ce)
         plain_steps.append(int(st[0]))
         plain_err.append(moment_err(S.moments(), ref_m[k], n0s[k]))
@@ -610,6 +619,7 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     def batched(warm, polish):
         t0 = time.perf_counter()
         B = fdlb.Solver([dict(d, precision="fp32") for d in eval_ds])
+        B.set_stall_checks(stall_checks)
         if warm:
             for j, d in enumerate(eval_ds):
                 net.warm_start(B, j, wsm.raw_parameters(d))
@@ -632,6 +642,7 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
     per_plain = t_plain / max(len(plain_idx), 1)
     return {"metric": "time to steady state (moment residual <= %g)" % tol, "unit": "s", "higher_is_better": False,
             "grid": {"cells": cells, "momenta": 2 * q ** 3}, "residual_check_every": ce, "max_steps": max_steps,
+            "stall_checks": stall_checks,
             "held_out": len(eval_all), "excluded_nonconvergent_fp64": len(eval_all) - len(keep),
             "reference": {"precision": "fp64", "tol": ref_tol, "max_steps": ref_steps, "seconds": t_ref,
                           "instances": len(plain_idx), "residuals": [float(r) for r in res_ref]},
@@ -641,7 +652,7 @@ def time_to_steady(n_train, n_eval, n_plain, cells=64, q=4, tol=1e-8, min_kn=0.0
             "batched_fp32_warm_start": arm_c,
             "batched_fp32_uniform_start": arm_d,
             "speedup_per_instance_same_accuracy": per_plain / arm_b["seconds_per_instance"],
-            "training": {"instances": len(train_ds), "data_seconds": t_data, "train_seconds": t_train,
+            "training": {"instances": int(len(raw)), "generated": len(train_ds), "data_seconds": t_data, "train_seconds": t_train,
                          "epochs": epochs, "first_loss": losses[0], "final_loss": losses[-1], "data_status": rc_data,
                          "data_steps_max": int(np.max(st_train))}}
 

@@ -170,11 +170,21 @@ int fdlb_step(fdlb_handle h, int64_t n_steps);
 /* Step until the moment residual r <= tol for every instance (checked every `check_every`
  * steps; r = max over n, u_2, T, q_R of max_cells |M(t+K dt) - M(t)| / (K max(max|M(t)|,
  * scale)), scales n0, 1, T0, n0 T0^1.5), or max_steps / max_seconds is reached.  In a batch,
- * converged instances stop stepping.  steps_taken (per instance, may be NULL) and residual
- * (per instance, may be NULL) are host arrays of length n_instances.
- * Returns FDLB_OK, FDLB_ENOTCONVERGED, FDLB_ETIMEOUT or FDLB_ENAN. */
+ * converged instances stop stepping; so do instances whose moments become non-finite (residual
+ * +inf; the others run on) and, with fdlb_set_stall_checks, instances whose residual has stopped
+ * falling.  steps_taken (per instance, may be NULL) and residual (per instance, may be NULL) are
+ * host arrays of length n_instances.  Returns FDLB_OK (every instance converged), else FDLB_ENAN
+ * if an instance became non-finite, else FDLB_ETIMEOUT or FDLB_ENOTCONVERGED. */
 int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_seconds,
                        int check_every, int64_t* steps_taken, double* residual);
+
+/* Stall rule of fdlb_run_to_steady (and of both phases of fdlb_run_to_steady_mixed): an instance
+ * whose residual has not fallen below half of its lowest value for `checks` consecutive checks
+ * stops stepping, unconverged (it has settled on a small self-sustained oscillation of the
+ * residual instead of a steady state, as some instances of the discretised problem do; in a batch
+ * it would otherwise keep the whole run going to max_steps).  0 (default): never.  FDLB_EINVAL
+ * for checks < 0. */
+int fdlb_set_stall_checks(fdlb_handle h, int checks);
 
 /* Steady state at the FP64 level of accuracy for an FP32 handle: the FP32 form runs to the
  * residual tolerance (as fdlb_run_to_steady; its steady state sits on the FP32 rounding floor,
@@ -188,8 +198,9 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
  * aligned) when given, else in device memory the call allocates and frees.  steps_fp32 /
  * steps_fp64 / residual: per-instance host arrays (may be NULL); residual is the FP64 phase's.
  * The step counts of the handle grow by the FP64 steps.  For an FP64 handle it is
- * fdlb_run_to_steady.  Returns as fdlb_run_to_steady for the FP64 phase (an error of the FP32
- * phase other than ENOTCONVERGED / ETIMEOUT is returned at once).  The paper's method is
+ * fdlb_run_to_steady.  Returns as fdlb_run_to_steady for the FP64 phase, FDLB_ENAN if either
+ * phase met non-finite moments (an error of the FP32 phase other than ENOTCONVERGED / ETIMEOUT /
+ * ENAN is returned at once).  The paper's method is
  * precision-agnostic; this two-precision schedule is a library service. */
 int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, double max_seconds, int check_every,
                              void* fp64_workspace, size_t fp64_workspace_bytes, int64_t* steps_fp32,

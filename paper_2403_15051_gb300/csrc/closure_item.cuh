@@ -258,6 +258,51 @@ __device__ __forceinline__ T clo_band_row(const T* Wr, const Dens& dn, int kmax,
     return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Two band rows at once by one warp, each summed exactly as clo_band_row sums it, with the loads
+// of both rows in flight together.  clo_band_row's eight-wide pass is two of its four-wide passes
+// in the same order, so strides of 128 alone reproduce it; a row that has left a pass adds zeros
+// there, which leaves its accumulators unchanged.
+template <typename T, typename DensA, typename DensB>
+__device__ __forceinline__ void clo_band_row2(const T* WrA, const DensA& dnA, int kmaxA, const T* WrB, const DensB& dnB,
+                                              int kmaxB, int lane, T& totA, T& totB) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), b0 = T(0), b1 = T(0), b2 = T(0), b3 = T(0);
+    int ka = lane, kb = lane;
+    for (;;) {
+        const bool pa = ka + 96 < kmaxA, pb = kb + 96 < kmaxB;
+        if (!pa && !pb) break;
+        T wa[4], da[4], wb[4], db[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wa[u] = pa ? WrA[ka + 32 * u] : T(0);
+            da[u] = pa ? dnA(ka + 32 * u) : T(0);
+            wb[u] = pb ? WrB[kb + 32 * u] : T(0);
+            db[u] = pb ? dnB(kb + 32 * u) : T(0);
+        }
+        a0 += wa[0] * da[0];
+        a1 += wa[1] * da[1];
+        a2 += wa[2] * da[2];
+        a3 += wa[3] * da[3];
+        b0 += wb[0] * db[0];
+        b1 += wb[1] * db[1];
+        b2 += wb[2] * db[2];
+        b3 += wb[3] * db[3];
+        ka += pa ? 128 : 0;
+        kb += pb ? 128 : 0;
+    }
+    for (;;) {
+        const bool pa = ka < kmaxA, pb = kb < kmaxB;
+        if (!pa && !pb) break;
+        const T wa = pa ? WrA[ka] : T(0), da = pa ? dnA(ka) : T(0);
+        const T wb = pb ? WrB[kb] : T(0), db = pb ? dnB(kb) : T(0);
+        a0 += wa * da;
+        b0 += wb * db;
+        ka += pa ? 32 : 0;
+        kb += pb ? 32 : 0;
+    }
+    totA = warp_sum((a0 + a1) + (a2 + a3));
+    totB = warp_sum((b0 + b1) + (b2 + b3));
+}
+
 // chi = chi_SET(eta), eta = etafac x (Eqs. chi, chi_ret), in the wide type, rounded once: J1
 // scales with b rho chi, and near finely resolved walls J1 is large enough that a few roundings of
 // chi show in the right-hand side.
@@ -433,13 +478,18 @@ __device__ __forceinline__ T clo_g_entry(int k, const T (*ecs)[kMaxE], T cT, con
                                          int& dst) {
     const int nR = M.nR, n2 = M.n2, QR = nR / 2;
     T acc = T(0);
+    // (the expansion orders are at most kMaxE - 1: every loop runs unrolled, predicated)
     if (k < nR) {
         const T* eh = ecs[k >= QR ? 1 : 0];
-        for (int l = 0; l <= M.NR; ++l) acc += tb.GR[k * kMaxE + l] * eh[l];
+#pragma unroll
+        for (int l = 0; l < kMaxE; ++l)
+            if (l <= M.NR) acc += tb.GR[k * kMaxE + l] * eh[l];
         dst = rec_off_gR(n2) + k;
     } else if (k < nR + n2) {
         const int j = k - nR;
-        for (int l = 0; l <= M.N2; ++l) acc += tb.G2[j * kMaxE + l] * ecs[2][l];
+#pragma unroll
+        for (int l = 0; l < kMaxE; ++l)
+            if (l <= M.N2) acc += tb.G2[j * kMaxE + l] * ecs[2][l];
         dst = rec_off_g2() + j;
     } else {
         const int j = k - nR - n2;
@@ -447,7 +497,9 @@ __device__ __forceinline__ T clo_g_entry(int k, const T (*ecs)[kMaxE], T cT, con
             // the pair's Gaussian factors: int g_z = 1 (phi), int p_z^2 g_z = T (chi)
             acc = j == 0 ? T(1) : cT;
         } else {
-            for (int l = 0; l <= M.N3; ++l) acc += tb.G3[j * kMaxE + l] * ecs[3][l];
+#pragma unroll
+            for (int l = 0; l < kMaxE; ++l)
+                if (l <= M.N3) acc += tb.G3[j * kMaxE + l] * ecs[3][l];
         }
         dst = rec_off_g3(nR, n2) + j;
     }

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -84,6 +85,7 @@ struct Solver {
     int grid_cbatch = 1;
     size_t cbatch_smem = 0;
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
+    int stall_checks = 0;   // run_to_steady: checks without halving the best residual before an instance stops
     int stage_minb = 1;     // register bound of the stage kernel (1, or 3 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
     int closure_wst = 0;                           // staged band-row elements per closure block
@@ -1578,6 +1580,9 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
     rc = fdlb::upload_items(*S);
     if (rc) return rc;
     int status = FDLB_ENOTCONVERGED;
+    bool nan_seen = false;
+    std::vector<double> best(n, std::numeric_limits<double>::infinity());
+    std::vector<int> since(n, 0);
     int64_t done = 0;
     while (done < max_steps) {
         const int64_t k = std::min<int64_t>(check_every, max_steps - done);
@@ -1588,30 +1593,40 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
             if (S->active[q]) taken[q] += k;
         rc = check(1);
         if (rc) return rc;
-        bool any_active = false, changed = false, nan = false;
+        bool any_active = false, changed = false;
         for (int q = 0; q < n; ++q) {
             if (!S->active[q]) continue;
             const double* r = &ro[(size_t)q * 10];
-            if (r[9] != 0.0) nan = true;
+            if (r[9] != 0.0) {
+                // non-finite moments: this instance stops, the others run on
+                S->last_res[q] = std::numeric_limits<double>::infinity();
+                S->active[q] = 0;
+                changed = nan_seen = true;
+                continue;
+            }
             const fdlb::InstanceSetup& I = S->setup[q];
             const double T0 = 0.5 * (I.p.T_wall[0] + I.p.T_wall[1]);
             const double scale[4] = {I.n0, 1.0, T0, I.n0 * T0 * std::sqrt(T0)};
             double res = 0.0;
             for (int e = 0; e < 4; ++e) res = std::max(res, r[e] / ((double)k * std::max(r[4 + e], scale[e])));
             S->last_res[q] = res;
-            if (res <= tol) {
+            if (res < 0.5 * best[q]) {
+                best[q] = res;
+                since[q] = 0;
+            } else {
+                ++since[q];
+            }
+            if (res <= tol || (S->stall_checks > 0 && since[q] >= S->stall_checks)) {
                 S->active[q] = 0;
                 changed = true;
             } else {
                 any_active = true;
             }
         }
-        if (nan) {
-            status = FDLB_ENAN;
-            break;
-        }
         if (!any_active) {
-            status = FDLB_OK;
+            bool all = true;
+            for (int q = 0; q < n; ++q) all = all && S->last_res[q] <= tol;
+            status = nan_seen ? FDLB_ENAN : (all ? FDLB_OK : FDLB_ENOTCONVERGED);
             break;
         }
         if (changed) {
@@ -1620,10 +1635,11 @@ int fdlb_run_to_steady(fdlb_handle h, double tol, int64_t max_steps, double max_
         }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (max_seconds > 0.0 && el > max_seconds) {
-            status = FDLB_ETIMEOUT;
+            status = nan_seen ? FDLB_ENAN : FDLB_ETIMEOUT;
             break;
         }
     }
+    if (done >= max_steps && status == FDLB_ENOTCONVERGED && nan_seen) status = FDLB_ENAN;
     std::fill(S->active.begin(), S->active.end(), 1);
     rc = fdlb::upload_items(*S);
     if (rc) return rc;
@@ -1693,7 +1709,8 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
     int rc = instance_masses(S, m0);
     if (rc) return rc;
     rc = fdlb_run_to_steady(h, tol, max_steps, max_seconds, check_every, st32.data(), res.data());
-    if (rc != FDLB_OK && rc != FDLB_ENOTCONVERGED && rc != FDLB_ETIMEOUT) return rc;
+    if (rc != FDLB_OK && rc != FDLB_ENOTCONVERGED && rc != FDLB_ETIMEOUT && rc != FDLB_ENAN) return rc;
+    const bool nan32 = rc == FDLB_ENAN;  // those instances stop at once in the FP64 phase too
     // the walls conserve mass and the steady state depends on it, but FP32 rounding walks the total
     // mass away by up to ~1e-9 of it per step: the polish starts from the FP32 state scaled back to
     // the mass this call began with
@@ -1705,6 +1722,7 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
     if (rc) return rc;
     Solver* T = SOL(th);
     T->autotune_mode = S->autotune_mode;
+    T->stall_checks = S->stall_checks;
     for (int q = 0; q < n; ++q) {
         const long long cnt = (long long)S->setup[q].p.n_cells * S->Np;
         const double scale = m1[q] > 0.0 && m0[q] > 0.0 ? m0[q] / m1[q] : 1.0;
@@ -1721,7 +1739,7 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
     int rc64 = rc ? rc : fdlb_run_to_steady(th, tol, max_steps, left, check_every, st64.data(), res.data());
     // 3. the polished state, rounded to FP32, back into this handle (its moments are those of the
     // FP64 steady state to FP32 rounding, ~1e-7 of their scales)
-    if (rc64 == FDLB_OK || rc64 == FDLB_ENOTCONVERGED || rc64 == FDLB_ETIMEOUT) {
+    if (rc64 == FDLB_OK || rc64 == FDLB_ENOTCONVERGED || rc64 == FDLB_ETIMEOUT || rc64 == FDLB_ENAN) {
         for (int q = 0; q < n; ++q) {
             const long long cnt = (long long)S->setup[q].p.n_cells * S->Np;
             fdlb::launch_convert((const double*)T->f[0] + T->f_off[q], 0, (float*)S->f[0] + S->f_off[q], 1, cnt,
@@ -1740,6 +1758,7 @@ int fdlb_run_to_steady_mixed(fdlb_handle h, double tol, int64_t max_steps, doubl
         if (steps_fp64) steps_fp64[q] = st64[q];
         if (residual) residual[q] = res[q];
     }
+    if (nan32 && (rc64 == FDLB_OK || rc64 == FDLB_ENOTCONVERGED || rc64 == FDLB_ETIMEOUT)) rc64 = FDLB_ENAN;
     return rc64;
 } FDLB_HOST_CATCH
 
@@ -1992,6 +2011,13 @@ int fdlb_set_closure_cells(fdlb_handle h, int cells) try {
     Solver* S = SOL(h);
     if (!S || cells < 1 || cells > fdlb::kClosureCells) return FDLB_EINVAL;
     return fdlb::set_closure_grouping(*S, cells, 0);
+} FDLB_HOST_CATCH
+
+int fdlb_set_stall_checks(fdlb_handle h, int checks) try {
+    Solver* S = SOL(h);
+    if (!S || checks < 0) return FDLB_EINVAL;
+    S->stall_checks = checks;
+    return FDLB_OK;
 } FDLB_HOST_CATCH
 
 int fdlb_set_closure_form(fdlb_handle h, int form, int* in_use) try {

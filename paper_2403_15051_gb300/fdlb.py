@@ -95,6 +95,7 @@ def load_library():
         "fdlb_set_tiling": (c_int, [H, c_int, c_int, c_int]),
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
         "fdlb_set_closure_form": (c_int, [H, c_int, POINTER(c_int)]),
+        "fdlb_set_stall_checks": (c_int, [H, c_int]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
@@ -359,6 +360,11 @@ class Solver:
 
     def set_closure_cells(self, cells):
         _check(self._L.fdlb_set_closure_cells(self._h, cells), "fdlb_set_closure_cells")
+
+    def set_stall_checks(self, checks):
+        """Instances whose residual has not halved its best value for `checks` consecutive checks
+        stop stepping in run_to_steady (0: never)."""
+        _check(self._L.fdlb_set_stall_checks(self._h, int(checks)), "fdlb_set_stall_checks")
 
     def closure_form(self, form=-1):
         """0: the chain form, 1: the batch form, -1: no change; returns the form in use."""

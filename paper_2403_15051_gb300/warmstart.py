@@ -40,10 +40,12 @@ def encode_profiles(S, q, n_points):
     return np.stack(ch, axis=-1).astype(np.float32)
 
 
-def steady_states(ds, n_points=256, tol=1e-8, max_steps=400_000, check_every=200):
+def steady_states(ds, n_points=256, tol=1e-8, max_steps=400_000, check_every=200, stall_checks=0):
     """Run every instance to steady state in one batched handle; returns (raw [M][5],
-    targets [M][P][4], steps [M], residuals [M], status)."""
+    targets [M][P][4], steps [M], residuals [M], status).  stall_checks: the library's stall rule
+    (instances whose residual has stopped falling stop stepping; 0: off)."""
     S = fdlb.Solver(ds)
+    S.set_stall_checks(stall_checks)
     rc, steps, res = S.run_to_steady(tol=tol, max_steps=max_steps, check_every=check_every)
     raw = np.stack([raw_parameters(d) for d in ds])
     tg = np.stack([encode_profiles(S, q, n_points) for q in range(len(ds))])
@@ -70,10 +72,11 @@ def train(raw, targets, epochs=400, batch=32, lr=1e-3, seed=0, width=64, modes=6
     return net, losses
 
 
-def steps_to_steady(ds, net=None, tol=1e-8, max_steps=400_000, check_every=200):
+def steps_to_steady(ds, net=None, tol=1e-8, max_steps=400_000, check_every=200, stall_checks=0):
     """SSP-RK3 steps to the residual tolerance, from the uniform equilibrium (net None) or from
     the network's predicted profiles."""
     S = fdlb.Solver(ds)
+    S.set_stall_checks(stall_checks)
     if net is not None:
         for q, d in enumerate(ds):
             net.warm_start(S, q, raw_parameters(d))
