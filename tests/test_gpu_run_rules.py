@@ -44,13 +44,18 @@ def test_a_non_finite_instance_stops_alone(precision):
 
 
 def test_stalled_instances_stop_before_max_steps():
-    ds = _batch("fp32")
+    ds = _batch("fp64")
     S = fdlb.Solver(ds)
+    S.step(500)  # past the fast relaxation of q: the residual now falls on the flow's slow scale
+    # checks ten steps apart: a relaxing residual does not halve between them, so with a stall
+    # window of five checks every instance stops after six checks (sixty steps), unconverged
     S.set_stall_checks(5)
-    # a tolerance below the FP32 rounding floor: every residual stops falling on that floor
-    rc, steps, res = S.run_to_steady(tol=1e-30, max_steps=2_000_000, check_every=200)
+    rc, steps, res = S.run_to_steady(tol=1e-30, max_steps=10_000, check_every=10)
     assert rc == 4  # FDLB_ENOTCONVERGED
-    assert np.all(steps < 2_000_000) and np.all(res > 1e-30), (steps, res)
+    assert np.all(steps == 60) and np.all(res > 1e-30), (steps, res)
+    S.set_stall_checks(0)
+    rc, steps, _ = S.run_to_steady(tol=1e-30, max_steps=100, check_every=10)
+    assert rc == 4 and np.all(steps == 100)
     with pytest.raises(fdlb.FdlbError):
         S.set_stall_checks(-1)
 
