@@ -1,5 +1,6 @@
 """The exact rewritings the kernels use, restated in numpy and checked against the direct forms of
 the formulas on random FP64 inputs (CPU): the ascending-window WENO5 for both upwind directions,
+the reconstruction of f itself with epsilon scaled by the squared weight,
 the Shakhov factor and J1 as polynomials in x1 = p_2 - u_2 along a vector of momenta, and the
 double-float split of an FP64 sum.  The kernels themselves are checked against the oracle by the
 GPU tests; these pin the algebra the kernels were derived from."""
@@ -18,11 +19,11 @@ def weno5_direct(a, b, c, d, e):
     return sum(x * y for x, y in zip(al, r)) / sum(al)
 
 
-def weno5_ascending(w0, w1, w2, w3, w4, sigma):
+def weno5_ascending(w0, w1, w2, w3, w4, sigma, e4=4e-6):
     d0, d1, d2, d3 = w1 - w0, w2 - w1, w3 - w2, w4 - w3
     D1, D2, D3 = d1 - d0, d2 - d1, d3 - d2
     tL, tC, tR = 3 * d1 - d0, -(d1 + d2), d3 - 3 * d2
-    E = [tL ** 2 + 13 / 3 * D1 ** 2 + 4e-6, tC ** 2 + 13 / 3 * D2 ** 2 + 4e-6, tR ** 2 + 13 / 3 * D3 ** 2 + 4e-6]
+    E = [tL ** 2 + 13 / 3 * D1 ** 2 + e4, tC ** 2 + 13 / 3 * D2 ** 2 + e4, tR ** 2 + 13 / 3 * D3 ** 2 + e4]
     m = np.minimum(E[0], np.minimum(E[1], E[2]))
     dL, dR = (0.1, 0.3) if sigma > 0 else (0.3, 0.1)
     a = [dL * (m / E[0]) ** 2, 0.6 * (m / E[1]) ** 2, dR * (m / E[2]) ** 2]
@@ -39,6 +40,18 @@ def test_ascending_weno5_equals_the_direct_form_both_directions():
     scale = np.max(np.abs(w), axis=0)
     assert np.max(np.abs(weno5_ascending(*w, +1) - fwd) / scale) < 1e-12
     assert np.max(np.abs(weno5_ascending(*w, -1) - rev) / scale) < 1e-12
+
+
+def test_weno5_of_f_with_scaled_epsilon_is_w_times_weno5_of_f_over_w():
+    # the stage kernel reconstructs f = w g with 4 eps w^2; the method reconstructs g = f / w with
+    # 4 eps: the face value of f is w times that of g (weights spanning the half-range rules' range)
+    rng = np.random.default_rng(7)
+    g = np.exp(rng.normal(size=(5, 20000))) * (1.0 + 0.3 * rng.normal(size=(5, 20000)))
+    wt = 10.0 ** rng.uniform(-12, 0, size=20000)
+    for sigma in (+1, -1):
+        ref = wt * (weno5_direct(*g) if sigma > 0 else weno5_direct(g[4], g[3], g[2], g[1], g[0]))
+        got = weno5_ascending(*(wt * g), sigma, e4=4e-6 * wt ** 2)
+        assert np.max(np.abs(got - ref) / (wt * np.max(np.abs(g), axis=0))) < 1e-12
 
 
 def test_collision_polynomials_equal_the_direct_form():
