@@ -215,13 +215,16 @@ __global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closu
             };
             T totA, totB;
             clo_band_row2<T>(WrA, dA, kmaxA, WrB, dB, kmaxB, lane, totA, totB);
+            // lane 0's sums: every lane ends the butterfly with the total, but each in an order of
+            // its own, and the chain form takes lane 0's
             const long long gc = (long long)I.cell_off + c0 + t;
             if (lane == 0) {
                 cw[gc * 2] = clo_chi<T>(etaf, totA);
                 cw[gc * 2 + 1] = totA;
-            } else if (lane == 1 && hasB) {
-                cw[gc * 2 + 2] = clo_chi<T>(etaf, totB);
-                cw[gc * 2 + 3] = totB;
+                if (hasB) {
+                    cw[gc * 2 + 2] = clo_chi<T>(etaf, totB);
+                    cw[gc * 2 + 3] = totB;
+                }
             }
         }
     }
