@@ -228,6 +228,8 @@ __device__ __forceinline__ void clo_fields(const Wide<T> (&sv)[kSums], Wide<T>& 
 // times densities dn(k), k < kmax, lane-strided into four accumulators (accumulator a takes
 // k = lane + 32 a + 128 j in increasing j), then a butterfly.  The first loop takes two strides at
 // a time so that sixteen loads per lane are in flight; the order of every accumulator is the same.
+// Every term is an explicit fused multiply-add, so the sum does not depend on how the compiler
+// contracts the expression in a given caller (clo_band_row2 must reproduce it bit for bit).
 template <typename T, typename Dens>
 __device__ __forceinline__ T clo_band_row(const T* Wr, const Dens& dn, int kmax, int lane) {
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
@@ -239,22 +241,22 @@ __device__ __forceinline__ T clo_band_row(const T* Wr, const Dens& dn, int kmax,
             w[u] = Wr[k + 32 * u];
             d[u] = dn(k + 32 * u);
         }
-        a0 += w[0] * d[0];
-        a1 += w[1] * d[1];
-        a2 += w[2] * d[2];
-        a3 += w[3] * d[3];
-        a0 += w[4] * d[4];
-        a1 += w[5] * d[5];
-        a2 += w[6] * d[6];
-        a3 += w[7] * d[7];
+        a0 = fma(w[0], d[0], a0);
+        a1 = fma(w[1], d[1], a1);
+        a2 = fma(w[2], d[2], a2);
+        a3 = fma(w[3], d[3], a3);
+        a0 = fma(w[4], d[4], a0);
+        a1 = fma(w[5], d[5], a1);
+        a2 = fma(w[6], d[6], a2);
+        a3 = fma(w[7], d[7], a3);
     }
     for (; k + 96 < kmax; k += 128) {
-        a0 += Wr[k] * dn(k);
-        a1 += Wr[k + 32] * dn(k + 32);
-        a2 += Wr[k + 64] * dn(k + 64);
-        a3 += Wr[k + 96] * dn(k + 96);
+        a0 = fma(Wr[k], dn(k), a0);
+        a1 = fma(Wr[k + 32], dn(k + 32), a1);
+        a2 = fma(Wr[k + 64], dn(k + 64), a2);
+        a3 = fma(Wr[k + 96], dn(k + 96), a3);
     }
-    for (; k < kmax; k += 32) a0 += Wr[k] * dn(k);
+    for (; k < kmax; k += 32) a0 = fma(Wr[k], dn(k), a0);
     return warp_sum((a0 + a1) + (a2 + a3));
 }
 
@@ -278,14 +280,14 @@ __device__ __forceinline__ void clo_band_row2(const T* WrA, const DensA& dnA, in
             wb[u] = pb ? WrB[kb + 32 * u] : T(0);
             db[u] = pb ? dnB(kb + 32 * u) : T(0);
         }
-        a0 += wa[0] * da[0];
-        a1 += wa[1] * da[1];
-        a2 += wa[2] * da[2];
-        a3 += wa[3] * da[3];
-        b0 += wb[0] * db[0];
-        b1 += wb[1] * db[1];
-        b2 += wb[2] * db[2];
-        b3 += wb[3] * db[3];
+        a0 = fma(wa[0], da[0], a0);
+        a1 = fma(wa[1], da[1], a1);
+        a2 = fma(wa[2], da[2], a2);
+        a3 = fma(wa[3], da[3], a3);
+        b0 = fma(wb[0], db[0], b0);
+        b1 = fma(wb[1], db[1], b1);
+        b2 = fma(wb[2], db[2], b2);
+        b3 = fma(wb[3], db[3], b3);
         ka += pa ? 128 : 0;
         kb += pb ? 128 : 0;
     }
@@ -294,8 +296,8 @@ __device__ __forceinline__ void clo_band_row2(const T* WrA, const DensA& dnA, in
         if (!pa && !pb) break;
         const T wa = pa ? WrA[ka] : T(0), da = pa ? dnA(ka) : T(0);
         const T wb = pb ? WrB[kb] : T(0), db = pb ? dnB(kb) : T(0);
-        a0 += wa * da;
-        b0 += wb * db;
+        a0 = fma(wa, da, a0);
+        b0 = fma(wb, db, b0);
         ka += pa ? 32 : 0;
         kb += pb ? 32 : 0;
     }
