@@ -351,9 +351,11 @@ __device__ __forceinline__ void clo_grad_terms(const ReachView<T>& R, int k, int
 }
 
 // The 20 scalars of an own cell's collision record: n, u, 1/T, 1/tau (Eq. tau), the Shakhov
-// coefficient (Eq. prandtl), q, b rho chi, the J1 gradients X = d ln(n^2 chi T), Y = d ln T, the
+// coefficient (Eq. prandtl), q, -b rho chi, the J1 gradients X = d ln(n^2 chi T), Y = d ln T, the
 // velocity derivative, the covariant strain (cylinder / sphere) and its divergence (Eq. j1);
-// mu from Eq. viscosity.  gp[v][q]: the gradient terms of the cell's five stencil positions.
+// mu from Eq. viscosity.  Products the stage kernel would otherwise form per cell and thread are
+// stored in place of their factors that it uses nowhere else: 0.4 S_11 / T in place of S_11,
+// 2 S_01 / T in place of S_01, 1 / (2T) in the spare slot 18.  gp[v][q]: the gradient terms of the cell's five stencil positions.
 template <typename T>
 __device__ __forceinline__ void clo_record_scalars(T* ct, const ReachView<T>& R, int lt, const T (&gp)[5][5], T geo0,
                                                    T geo1, const T (&q)[3], const InstDev& I) {
@@ -398,15 +400,15 @@ __device__ __forceinline__ void clo_record_scalars(T* ct, const ReachView<T>& R,
     ct[7] = q[0];
     ct[8] = q[1];
     ct[9] = q[2];
-    ct[10] = x;
+    ct[10] = -x;
     ct[11] = X;
     ct[12] = Y;
     ct[13] = cd0;
-    ct[14] = S11;
+    ct[14] = T(0.4) * iT * S11;
     ct[15] = S22;
-    ct[16] = S01;
+    ct[16] = T(2) * iT * S01;
     ct[17] = S02;
-    ct[18] = T(0);
+    ct[18] = T(0.5) * iT;
     ct[19] = div;
 }
 

@@ -429,11 +429,11 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
             sc[q] = t4[0]; sc[q + 1] = t4[1]; sc[q + 2] = t4[2]; sc[q + 3] = t4[3];
         }
         const T n = sc[0], u0 = sc[1], u1 = sc[2], u2 = sc[3], iT = sc[4], itau = sc[5], cS = sc[6];
-        const T q0 = sc[7], q1 = sc[8], q2 = sc[9], brchi = sc[10], X = sc[11], Y = sc[12];
-        const T S00 = sc[13], S11 = sc[14], S22 = sc[15], S01 = sc[16], S02 = sc[17], dv = sc[19];
-        // collision terms of the cell that do not depend on the momentum (see below)
-        const T hiT = T(0.5) * iT, fiT = T(0.2) * iT, nbr = -brchi;
-        const T g1c = T(2) * iT * S01, J2c = T(0.4) * iT * S11, F3 = cS * fiT * q1;
+        const T q0 = sc[7], q1 = sc[8], q2 = sc[9], nbr = sc[10], X = sc[11], Y = sc[12];
+        const T S00 = sc[13], J2c = sc[14], S22 = sc[15], g1c = sc[16], S02 = sc[17], hiT = sc[18], dv = sc[19];
+        // collision terms of the cell that do not depend on the momentum (see below; the closure
+        // stores -b rho chi, 0.4 S_11 / T, 2 S_01 / T and 1 / (2T) as they are used here)
+        const T fiT = T(0.2) * iT, F3 = cS * fiT * q1;
         const T* g2c = ct + rec_off_g2();
         const T* gRc = ct + rec_off_gR(n2);
         const T* g3c = ct + rec_off_g3(nR, n2);
