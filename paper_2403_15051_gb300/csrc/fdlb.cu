@@ -618,10 +618,16 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     cfg.spec = ((S.geometry == FDLB_CYL && S.nR == 16 && S.n2 == 8 && S.n3 == 8) ||
                 (S.geometry == FDLB_SPH && S.nR == 24 && S.n2 == 12 && S.n3 == 12)) &&
                cfg.vw == (S.tsize == 4 ? 4 : 2);
-    const int Vs = Ms / cfg.vw;
     const int cap = threads > 0 ? threads : 256;
+    // the cylinder's FP32 shape in blocks of at most 128 threads: a thread per whole p_2 row (8
+    // momenta; per-vector and per-cell work spread over twice the momenta, half the warps per cell)
+    if (cfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && cap <= 128 && Ms / 8 <= 128) cfg.vw = 8;
+    const int Vs = Ms / cfg.vw;
     int nt = 0;
-    if (cfg.spec) {
+    if (cfg.vw == 8) {
+        cfg.nv = 1;
+        nt = (Vs + 31) / 32 * 32;
+    } else if (cfg.spec) {
         // vectors per thread fixed by the instantiation: the smaller count whose block fits the cap
         const int na = S.geometry == FDLB_CYL ? 1 : 2, nb = 2 * na;
         cfg.nv = ((Vs + na - 1) / na + 31) / 32 * 32 <= std::max(cap, 32) ? na : nb;
@@ -1319,8 +1325,12 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     FDLB_CUDA(cudaStreamSynchronize(R.stream));
     // default tiling: a slice per p_3 value on the cylinder (p_3 is passive there)
     // default tiling (the fastest of a sweep on GB300; fdlb_autotune refines it per workload):
-    // whole cells per block, 4 cells per tile (cylinder, 256 threads) or 8 (sphere, 512 threads)
-    rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, 256) : configure_tiling(R, 8, R.n3, 512);
+    // whole cells per block, 4 cells per tile (cylinder, 256 threads) or 8 (sphere, 512 threads).
+    // The cylinder's 16 x 8 x 8 FP32 shape over many cells (batches) in blocks of 128 threads of
+    // whole p_2 rows: 12% less time per stage on the 512-instance sweep, 30% more on one
+    // 1024-cell instance, whose few tiles are bound by latency
+    const bool cyl_rows = R.tsize == 4 && R.nR == 16 && R.n2 == 8 && R.n3 == 8 && R.total_cells > R.n_sm * 64;
+    rc = R.geometry == FDLB_CYL ? configure_tiling(R, 4, R.n3, cyl_rows ? 128 : 256) : configure_tiling(R, 8, R.n3, 512);
     // closure items: few cells each where the whole closure is one short latency-bound launch (2 on
     // the cylinder, 4 on the sphere, with overlapped launches), 8 where items outnumber the blocks
     // that fit on the device several times over (batches, long instances: throughput-bound); with

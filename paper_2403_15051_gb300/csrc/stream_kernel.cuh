@@ -42,6 +42,9 @@ __device__ __forceinline__ void ld_vec(const T* p, T (&o)[VW]) {
     if constexpr (sizeof(T) == 4 && VW == 4) {
         const float4 x = *reinterpret_cast<const float4*>(p);
         o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 8) {
+        const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
     } else if constexpr (sizeof(T) == 4 && VW == 2) {
         const float2 x = *reinterpret_cast<const float2*>(p);
         o[0] = x.x; o[1] = x.y;
@@ -62,6 +65,9 @@ __device__ __forceinline__ void ldg_vec(const T* p, T (&o)[VW]) {
     if constexpr (sizeof(T) == 4 && VW == 4) {
         const float4 x = __ldg(reinterpret_cast<const float4*>(p));
         o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 8) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p)), y = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
     } else if constexpr (sizeof(T) == 4 && VW == 2) {
         const float2 x = __ldg(reinterpret_cast<const float2*>(p));
         o[0] = x.x; o[1] = x.y;
@@ -83,6 +89,9 @@ __device__ __forceinline__ void ldcg_vec(const T* p, T (&o)[VW]) {
     if constexpr (sizeof(T) == 4 && VW == 4) {
         const float4 x = __ldcg(reinterpret_cast<const float4*>(p));
         o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+    } else if constexpr (sizeof(T) == 4 && VW == 8) {
+        const float4 x = __ldcg(reinterpret_cast<const float4*>(p)), y = __ldcg(reinterpret_cast<const float4*>(p) + 1);
+        o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; o[4] = y.x; o[5] = y.y; o[6] = y.z; o[7] = y.w;
     } else if constexpr (sizeof(T) == 4 && VW == 2) {
         const float2 x = __ldcg(reinterpret_cast<const float2*>(p));
         o[0] = x.x; o[1] = x.y;
@@ -102,6 +111,9 @@ template <typename T, int VW>
 __device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
     if constexpr (sizeof(T) == 4 && VW == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 4 && VW == 8) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(o[4], o[5], o[6], o[7]);
     } else if constexpr (sizeof(T) == 4 && VW == 2) {
         *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
     } else if constexpr (sizeof(T) == 8 && VW >= 2) {
@@ -744,6 +756,10 @@ cudaError_t launch_stream_dispatch(const StreamCfg& cfg, const StageArgs& A, con
     constexpr int SR = G == 0 ? 16 : 24, S2 = G == 0 ? 8 : 12, S3 = G == 0 ? 8 : 12;
     constexpr int NA = G == 0 ? 1 : 2, NB = G == 0 ? 2 : 4;
     if (cfg.spec) {
+        if constexpr (sizeof(T) == 4 && G == 0) {
+            // the cylinder's FP32 shape also as one vector of a whole p_2 row (8 momenta) per thread
+            if (cfg.vw == 8 && cfg.nv == 1) return launch_stream_t<T, G, 8, 1, SR, S2, S3>(A, M, grid, threads, smem, s);
+        }
         if (cfg.vw != VS) return cudaErrorInvalidValue;
         if constexpr (sizeof(T) == 4 && G == 0) {
             // the cylinder's FP32 shape also bounded for three blocks of 256 threads per SM

@@ -268,3 +268,21 @@ def test_tensor_core_contraction_matches_oracle():
     f_or = osolver.run(f0, P, 10)
     errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
     assert max(errs.values()) <= TOL["fp32"], errs
+
+
+@pytest.mark.parametrize("threads", [256, 128])
+def test_cylinder_fp32_shape_both_vector_widths_match_oracle(threads):
+    # the 16 x 8 x 8 cylinder in FP32 has two compile-time kernels: four momenta per thread (blocks
+    # of 256) and a whole p_2 row of eight per thread (blocks of at most 128)
+    d = small_case(precision="fp32", n_cells=45, Q=(8, 8, 8), u_wall=(0.2, 0.0), T_wall=(1.0, 1.15))
+    P, f0, S = _pair(d, seed=4)
+    S.set_autotune(0)
+    S.set_tiling(6, 8, threads)
+    assert S.tiling()["threads"] == threads
+    L_or = osolver.rhs(f0, P)
+    L = S.eval_rhs()
+    assert np.max(np.abs(L - L_or)) / np.max(np.abs(L_or)) <= RHS_TOL["fp32"]
+    S.step(20)
+    f_or = osolver.run(f0, P, 20)
+    errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
+    assert max(errs.values()) <= TOL["fp32"], errs
