@@ -245,13 +245,16 @@ const char* fdlb_error_string(int code);
 /* Kernel-tuning knobs of the streaming kernel (cells per tile, p_3 values per momentum slice,
  * threads per block); 0 keeps the current value.  A change of the cells per tile alone regroups
  * cells without changing any result; the slice width and the block size change the order of the
- * moment sums (results then agree to rounding).
+ * moment sums (results then agree to rounding).  For the 16 x 8 x 8 FP32 cylinder a block of at
+ * most 128 threads selects the row kernel (a whole p_2 row of 8 momenta per thread), the default
+ * for handles of more than 64 cells per SM.
  *
  * fdlb_autotune times candidate tile shapes on the device and keeps the fastest: the cells per
- * stream tile (2 .. 32), then the own cells per closure item (2, 4, 8, 16), each candidate over
- * three stages written to the stage-1 scratch buffers (the state, its sums and the step count are
- * not touched).  Only these two regrouping knobs are searched, so a tuned handle produces the same
- * results bit for bit as an untuned one.  The choice is cached per process for the momentum set,
+ * stream tile (2 .. 32) under each register bound of the stage kernel that is built for the shape
+ * (the compiled arithmetic is the same), then the closure's form and its own cells per item (2, 4,
+ * 8, 16), each candidate over three stages written to the stage-1 scratch buffers (the state, its
+ * sums and the step count are not touched).  Only these regrouping knobs are searched, so a tuned
+ * handle produces the same results bit for bit as an untuned one.  The choice is cached per process for the momentum set,
  * precision, block size, slice width and size class (log2 of the handle's cells and instances);
  * fdlb_autotune always measures and refreshes that cache.  fdlb_set_autotune selects automatic
  * tuning at the first fdlb_step / fdlb_run_to_steady of a handle, from the cache when it holds
@@ -261,6 +264,11 @@ int fdlb_set_tiling(fdlb_handle h, int cells_per_tile, int slice_k, int threads)
 int fdlb_autotune(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads);
 int fdlb_set_autotune(fdlb_handle h, int mode);
 int fdlb_get_tiling(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threads, int* closure_cells);
+
+/* The stage kernel in use: momenta per thread vector (vector_width), vectors per thread, and the
+ * blocks per SM its register allocation is bounded for (1: none beyond the 512-thread bound).  Any
+ * pointer may be NULL. */
+int fdlb_get_stage_kernel(fdlb_handle h, int* vector_width, int* vectors_per_thread, int* min_blocks);
 
 /* The K^h contraction of the curvature force on the tensor cores (default off): an
  * nR x nR by nR x (n2 KS) product per cell in split TF32 (K = Kh + Kl, f = fh + fl; three

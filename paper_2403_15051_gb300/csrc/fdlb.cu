@@ -86,7 +86,7 @@ struct Solver {
     size_t cbatch_smem = 0;
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
     int stall_checks = 0;   // run_to_steady: checks without halving the best residual before an instance stops
-    int stage_minb = 1;     // register bound of the stage kernel (1, or 3 blocks per SM where built)
+    int stage_minb = 1;     // register bound of the stage kernel (1; 3 or 2 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
     int closure_wst = 0;                           // staged band-row elements per closure block
     int grid_stream = 1, grid_closure = 1;
@@ -638,7 +638,10 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
         if ((long long)nt * cfg.nv < Vs) nt = ((Vs + cfg.nv - 1) / cfg.nv + 31) / 32 * 32;
     }
     if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
-    cfg.minb = (S.stage_minb == 3 && cfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && nt <= 256) ? 3 : 1;
+    if (cfg.vw == 8)
+        cfg.minb = (S.stage_minb == 2 || S.stage_minb == 3) ? S.stage_minb : 1;
+    else
+        cfg.minb = (S.stage_minb == 3 && cfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && nt <= 256) ? 3 : 1;
     S.scfg = cfg;
     S.threads = nt;
     S.mma_on = S.tensor && cfg.spec && cfg.vw == 4 && S.tsize == 4 && S.nR % 8 == 0 && !S.krg_on;
@@ -1091,11 +1094,14 @@ int run_autotune(Solver& S, bool use_cache) {
     float best = time_stages(S, e0, e1);
     if (best < 0.f) best = 1e30f;
     const int Bs[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
-    // the register bound of the stage kernel: three blocks per SM where that variant is built
+    // the register bound of the stage kernel: three blocks per SM where that variant is built, and
+    // for the row kernel also two
     const bool minb_choice = S.scfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && S.threads <= 256;
+    const bool rows = S.scfg.vw == 8;
     int rc = FDLB_OK;
-    for (int mb : {1, 3}) {
+    for (int mb : {1, 3, 2}) {
         if (mb == 3 && !minb_choice) continue;
+        if (mb == 2 && !rows) continue;
         S.stage_minb = mb;
         for (int B : Bs) {
             if (B == bestB && mb == bestM) continue;
@@ -1941,6 +1947,15 @@ int fdlb_set_autotune(fdlb_handle h, int mode) try {
     Solver* S = SOL(h);
     if (!S || mode < 0 || mode > 2) return FDLB_EINVAL;
     S->autotune_mode = mode;
+    return FDLB_OK;
+} FDLB_HOST_CATCH
+
+int fdlb_get_stage_kernel(fdlb_handle h, int* vector_width, int* vectors_per_thread, int* min_blocks) try {
+    Solver* S = SOL(h);
+    if (!S) return FDLB_EINVAL;
+    if (vector_width) *vector_width = S->scfg.vw;
+    if (vectors_per_thread) *vectors_per_thread = S->scfg.nv;
+    if (min_blocks) *min_blocks = S->scfg.minb;
     return FDLB_OK;
 } FDLB_HOST_CATCH
 

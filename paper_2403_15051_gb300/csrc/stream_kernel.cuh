@@ -732,9 +732,11 @@ __device__ __forceinline__ void stream_body(const StageArgs& A, const MomSet& M)
 
 // The stage kernel; MINB = the blocks per SM the register allocation is bounded for: 1 (up to 512
 // threads, 128 registers each: two blocks of 256 threads reside) or, for blocks of at most 256
-// threads, 3 (at most 85 registers each).  The arithmetic and its order are the same in both.
+// threads, 3 (at most 85 registers each); for the row kernel (VW = 8, blocks of at most 128
+// threads) 3 or 2 (at most 170 or 255 registers each).  The arithmetic and its order are the same
+// in all.
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_, int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) stream_kernel(StageArgs A, MomSet M) {
+__global__ void __launch_bounds__(MINB == 1 ? 512 : (VW == 8 ? 128 : 256), MINB) stream_kernel(StageArgs A, MomSet M) {
     stream_body<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
 }
 
@@ -758,7 +760,12 @@ cudaError_t launch_stream_dispatch(const StreamCfg& cfg, const StageArgs& A, con
     if (cfg.spec) {
         if constexpr (sizeof(T) == 4 && G == 0) {
             // the cylinder's FP32 shape also as one vector of a whole p_2 row (8 momenta) per thread
-            if (cfg.vw == 8 && cfg.nv == 1) return launch_stream_t<T, G, 8, 1, SR, S2, S3>(A, M, grid, threads, smem, s);
+            if (cfg.vw == 8 && cfg.nv == 1) {
+                if (threads > 128 && cfg.minb != 1) return cudaErrorInvalidValue;
+                if (cfg.minb == 3) return launch_stream_t<T, G, 8, 1, SR, S2, S3, 3>(A, M, grid, threads, smem, s);
+                if (cfg.minb == 2) return launch_stream_t<T, G, 8, 1, SR, S2, S3, 2>(A, M, grid, threads, smem, s);
+                return launch_stream_t<T, G, 8, 1, SR, S2, S3>(A, M, grid, threads, smem, s);
+            }
         }
         if (cfg.vw != VS) return cudaErrorInvalidValue;
         if constexpr (sizeof(T) == 4 && G == 0) {

@@ -96,6 +96,7 @@ def load_library():
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
         "fdlb_set_closure_form": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_stall_checks": (c_int, [H, c_int]),
+        "fdlb_get_stage_kernel": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
@@ -385,8 +386,12 @@ class Solver:
         b, k, t, c = c_int(), c_int(), c_int(), c_int()
         _check(self._L.fdlb_get_tiling(self._h, byref(b), byref(k), byref(t), byref(c)), "fdlb_get_tiling")
         form = self.closure_form()
+        vw, nv, mb = c_int(), c_int(), c_int()
+        _check(self._L.fdlb_get_stage_kernel(self._h, byref(vw), byref(nv), byref(mb)), "fdlb_get_stage_kernel")
         return {"cells_per_tile": b.value, "slice_k": k.value, "threads": t.value,
-                "closure_cells": 28 if form == 1 else c.value, "closure_form": "batch" if form == 1 else "chain"}
+                "closure_cells": 28 if form == 1 else c.value, "closure_form": "batch" if form == 1 else "chain",
+                "stage_vector_width": vw.value, "stage_vectors_per_thread": nv.value,
+                "stage_min_blocks_per_sm": mb.value}
 
     def launch_count(self):
         return int(self._L.fdlb_launch_count(self._h))

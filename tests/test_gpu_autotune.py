@@ -61,3 +61,21 @@ def test_cached_choice_is_reused():
     assert 2 <= t["cells_per_tile"] <= 32
     assert (t["closure_form"], t["closure_cells"]) in {("chain", 2), ("chain", 4), ("chain", 8), ("chain", 16),
                                                        ("batch", 28)}
+
+
+def test_tuned_row_kernel_steps_bit_for_bit_like_the_untuned_one():
+    # the 16 x 8 x 8 FP32 cylinder in blocks of 128 threads (a whole p_2 row per thread): the tuner
+    # also tries the register bounds of 3 and 2 blocks per SM, which change no result bit
+    ds = _batch("fp32")
+    A = fdlb.Solver(ds)
+    A.set_autotune(0)
+    A.set_tiling(0, 0, 128)
+    B = fdlb.Solver(ds)
+    B.set_autotune(0)
+    B.set_tiling(0, 0, 128)
+    B.autotune()
+    assert A.tiling()["threads"] == 128 and B.tiling()["threads"] == 128
+    A.step(12)
+    B.step(12)
+    for q in range(len(ds)):
+        assert np.array_equal(A.get_f(q), B.get_f(q)), q
