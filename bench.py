@@ -349,6 +349,13 @@ def run_ours(args):
     t_create = time.perf_counter()
     S = fdlb.Solver(ds)
     t_create = time.perf_counter() - t_create
+    if args.tiling:
+        # a pinned tiling instead of the tuner's choice (profiling: a profiler's serialisation of the
+        # launches would steer the tuner's timings)
+        cells, threads, form = args.tiling.split(",")
+        S.set_autotune(0)
+        S.set_tiling(int(cells), 0, int(threads))
+        S.closure_form(1 if form == "batch" else 0)
     persistent = S.set_persistent_step(None)  # the library's default scheduling
     S.set_graph_steps(1)
     stream = torch.cuda.ExternalStream(S.stream_handle())
@@ -364,11 +371,19 @@ def run_ours(args):
                 flush.fill_(float(k % 7))
 
     if args.profile:
-        # lean run for launch lists under a profiler: warm-up and K steps, nothing else
-        for k in range(args.warmup + args.steps):
+        # lean run for launch lists under a profiler: warm-up and K steps, nothing else; the K steps
+        # inside the NVTX range "fdlb_timed" (a profiler can capture from them alone, past the
+        # tuner's candidate launches)
+        for k in range(args.warmup):
             l2_flush(k)
             S.step(1)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("fdlb_timed")
+        for k in range(args.warmup, args.warmup + args.steps):
+            l2_flush(k)
+            S.step(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile_run": args.workload, "steps": args.steps, "warmup": args.warmup}))
         S.close()
         return 0
@@ -708,6 +723,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="leave out the compact time-to-steady comparison")
     ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")
+    ap.add_argument("--tiling", default="", help="CELLS,THREADS,chain|batch: a pinned tiling, tuner off")
     ap.add_argument("--time-to-steady", action="store_true",
                     help="time-to-steady comparison: plain FP64 sequential vs batched warm-started FP32")
     ap.add_argument("--tts-train", type=int, default=4096)
