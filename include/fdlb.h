@@ -226,6 +226,14 @@ int fdlb_get_moments(fdlb_handle h, int instance, double* out, int on_device);
 int fdlb_get_closure(fdlb_handle h, int instance, double* nbar, double* chi, double* tau,
                      double* n_wall2);
 
+/* One SSP-RK3 step of every active instance, reporting per instance the relative L2 change of the
+ * populations, rel_change[q] = ||f^{n+1} - f^n||_2 / ||f^n||_2 summed in FP64 (a host array of
+ * n_instances; inactive instances report 0): the per-step change of f itself, beside the moment
+ * residual of fdlb_run_to_steady.  Keeps a copy of the state in device memory it allocates and frees
+ * (the size of the populations); synchronises the stream.  Returns FDLB_OK, FDLB_EINVAL, FDLB_ENOMEM
+ * or FDLB_ECUDA. */
+int fdlb_step_change(fdlb_handle h, double* rel_change);
+
 /* Total mass sum_c V_c n_c (FP64), the last residual and the step count of one instance. */
 int fdlb_get_diagnostics(fdlb_handle h, int instance, double* total_mass, double* residual,
                          int64_t* step);

@@ -1480,6 +1480,54 @@ int fdlb_step(fdlb_handle h, int64_t n_steps) try {
     return fdlb::do_steps(*S, n_steps);
 } FDLB_HOST_CATCH
 
+int fdlb_step_change(fdlb_handle h, double* rel_change) try {
+    Solver* S = SOL(h);
+    if (!S || !rel_change) return FDLB_EINVAL;
+    const int n = S->n_inst;
+    const long long C = 1LL << 16;
+    long long maxc = 0;
+    std::vector<long long> off(n), cnt(n);
+    for (int q = 0; q < n; ++q) {
+        off[q] = S->f_off[q];
+        cnt[q] = (long long)S->setup[q].p.n_cells * S->Np;
+        maxc = std::max(maxc, cnt[q]);
+    }
+    const int chunks = (int)std::max<long long>(1, (maxc + C - 1) / C);
+    const size_t fbytes = S->f_elems * S->tsize;
+    const size_t meta = (size_t)2 * n * sizeof(long long), pbytes = (size_t)n * chunks * 2 * sizeof(double);
+    unsigned char* scratch = nullptr;
+    if (cudaMalloc(&scratch, fbytes + meta + pbytes + 512) != cudaSuccess) {
+        cudaGetLastError();
+        return FDLB_ENOMEM;
+    }
+    long long* doff = reinterpret_cast<long long*>(scratch + (fbytes + 255) / 256 * 256);
+    long long* dcnt = doff + n;
+    double* part = reinterpret_cast<double*>(dcnt + n);
+    std::vector<double> hp((size_t)n * chunks * 2);
+    int rc = FDLB_OK;
+    if (cudaMemcpyAsync(scratch, S->f[0], fbytes, cudaMemcpyDeviceToDevice, S->stream) != cudaSuccess ||
+        cudaMemcpyAsync(doff, off.data(), n * sizeof(long long), cudaMemcpyHostToDevice, S->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dcnt, cnt.data(), n * sizeof(long long), cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+        rc = FDLB_ECUDA;
+    if (!rc) rc = fdlb::do_steps(*S, 1);
+    if (!rc) rc = fdlb::cuda_status(fdlb::launch_change_sums((int)S->tsize, S->f[0], scratch, doff, dcnt, n, chunks, C, part,
+                                                              S->stream));
+    if (!rc && (cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+                cudaStreamSynchronize(S->stream) != cudaSuccess))
+        rc = FDLB_ECUDA;
+    cudaFree(scratch);
+    if (rc) return rc;
+    for (int q = 0; q < n; ++q) {
+        double d2 = 0.0, b2 = 0.0;
+        for (int k = 0; k < chunks; ++k) {
+            d2 += hp[((size_t)q * chunks + k) * 2];
+            b2 += hp[((size_t)q * chunks + k) * 2 + 1];
+        }
+        rel_change[q] = (S->active[q] && b2 > 0.0) ? std::sqrt(d2 / b2) : 0.0;
+    }
+    return FDLB_OK;
+} FDLB_HOST_CATCH
+
 int fdlb_eval_rhs(fdlb_handle h, int instance, double* L_host) try {
     Solver* S = SOL(h);
     if (!S || instance < 0 || instance >= S->n_inst || !L_host) return FDLB_EINVAL;

@@ -344,6 +344,47 @@ __global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closu
     }
 }
 
+// ------------------------------------------------------------------------------ state change
+// Sums over one chunk of an instance's populations of (a - b)^2 and b^2 in FP64 (a the state after
+// a step, b before it): chunk k of instance q covers elements [k C, (k + 1) C) of the instance; the
+// block's sums go to part[(q * chunks + k) * 2 + {0, 1}] in a fixed tree order.
+template <typename T>
+__global__ void change_sums_kernel(const T* __restrict__ a, const T* __restrict__ b, const long long* __restrict__ off,
+                                   const long long* __restrict__ cnt, int chunks, long long C, double* __restrict__ part) {
+    __shared__ double red[2][32];
+    const int q = blockIdx.x / chunks, k = blockIdx.x % chunks;
+    const long long lo = k * C, hi = min(cnt[q], lo + C);
+    double d2 = 0.0, b2 = 0.0;
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const double x = (double)a[off[q] + e], y = (double)b[off[q] + e];
+        d2 += (x - y) * (x - y);
+        b2 += y * y;
+    }
+    d2 = warp_sum(d2);
+    b2 = warp_sum(b2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = d2;
+        red[1][warp] = b2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        part[((long long)q * chunks + k) * 2 + threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_change_sums(int tsize, const void* a, const void* b, const long long* off, const long long* cnt,
+                               int n_inst, int chunks, long long C, double* part, cudaStream_t s) {
+    const int grid = n_inst * chunks;
+    if (tsize == 4)
+        change_sums_kernel<float><<<grid, 256, 0, s>>>((const float*)a, (const float*)b, off, cnt, chunks, C, part);
+    else
+        change_sums_kernel<double><<<grid, 256, 0, s>>>((const double*)a, (const double*)b, off, cnt, chunks, C, part);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------ queries
 // The FP64 closure record of every cell of the active instances (moments and closure queries,
 // not the stage): n, u, T, q, P_12 (Eq. macro_def) from the raw sums in FP64, chi and nbar from

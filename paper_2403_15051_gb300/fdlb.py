@@ -96,6 +96,7 @@ def load_library():
         "fdlb_set_closure_cells": (c_int, [H, c_int]),
         "fdlb_set_closure_form": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_stall_checks": (c_int, [H, c_int]),
+        "fdlb_step_change": (c_int, [H, POINTER(c_double)]),
         "fdlb_get_stage_kernel": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
@@ -361,6 +362,12 @@ class Solver:
 
     def set_closure_cells(self, cells):
         _check(self._L.fdlb_set_closure_cells(self._h, cells), "fdlb_set_closure_cells")
+
+    def step_change(self):
+        """One step; per instance the relative L2 change ||f^{n+1} - f^n|| / ||f^n|| (FP64 sums)."""
+        out = (c_double * self.n_instances)()
+        _check(self._L.fdlb_step_change(self._h, out), "fdlb_step_change")
+        return np.array(out[:])
 
     def set_stall_checks(self, checks):
         """Instances whose residual has not halved its best value for `checks` consecutive checks
