@@ -1362,6 +1362,14 @@ using fdlb::Solver;
 
 static Solver* SOL(fdlb_handle h) { return reinterpret_cast<Solver*>(h); }
 
+namespace fdlb {
+// Per instance and chunk of C elements, the FP64 sums of (a - b)^2 and b^2 over populations (tsize 4
+// or 8) at offsets off[q], counts cnt[q] (device arrays); part: n_inst * chunks * 2 doubles
+// (kernels_aux.cu).
+cudaError_t launch_change_sums(int tsize, const void* a, const void* b, const long long* off, const long long* cnt,
+                               int n_inst, int chunks, long long C, double* part, cudaStream_t s);
+}  // namespace fdlb
+
 extern "C" {
 
 int fdlb_create(const fdlb_params* p, void* cuda_stream, fdlb_handle* out) try {

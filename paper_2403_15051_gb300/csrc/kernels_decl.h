@@ -103,10 +103,6 @@ void launch_closure(const ClosureArgs& A, const MomSet& M, int grid, int threads
 size_t closure_smem(int nR, int n2, int n3, int max_union, int wst_elems, int tsize);
 // Blocks of the closure kernel that fit on an SM with `smem` bytes of dynamic shared memory each.
 int closure_blocks_per_sm(int tsize, size_t smem);
-// Per instance and chunk of C elements, the FP64 sums of (a - b)^2 and b^2 over populations (tsize 4
-// or 8) at offsets off[q], counts cnt[q] (device arrays); part: n_inst * chunks * 2 doubles.
-cudaError_t launch_change_sums(int tsize, const void* a, const void* b, const long long* off, const long long* cnt,
-                               int n_inst, int chunks, long long C, double* part, cudaStream_t s);
 // The batch form of the closure (closure_band_kernel, then closure_records_kernel; items of at
 // most kClosureCells cells), and the blocks of either that reside on one SM.
 template <typename T>

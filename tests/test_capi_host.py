@@ -31,6 +31,21 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_library_leaves_no_symbol_of_its_own_unresolved(lib):
+    # every undefined symbol of the shared library is a versioned one of the system libraries (an
+    # internal function declared with the wrong linkage would show here, unversioned)
+    import shutil
+    import subprocess
+
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    so = os.path.join(ROOT, "paper_2403_15051_gb300", "libfdlb_gb300.so")
+    out = subprocess.run([nm, "-D", "--undefined-only", so], capture_output=True, text=True, check=True).stdout
+    own = [ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-2:-1] == ["U"] and "@" not in ln]
+    assert own == [], own
+
+
 @pytest.mark.parametrize("Q", [1, 2, 4, 8, 12, 16, 24, 40, 60, 100])
 def test_quadrature_matches_oracle(lib, Q):
     x, w = fdlb.quadrature(fdlb.QUAD_HALF, Q)
