@@ -32,7 +32,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
-        rprev, rout, krf, krB, mpk, total;
+        rprev, rout, krf, krB, mpk, bpairs, n_bpairs, total;
 };
 
 }  // namespace
@@ -65,6 +65,8 @@ struct Solver {
     void *geoT = nullptr, *gwT = nullptr, *nwp = nullptr, *cw = nullptr;
     void* rec = nullptr;
     void* tabT = nullptr;
+    BandPair* bpairs = nullptr;  // the batch closure's band jobs (per work list)
+    int* n_bpairs = nullptr;
     double *ca = nullptr, *mpk = nullptr, *tab = nullptr, *geo = nullptr, *gw = nullptr, *rprev = nullptr,
            *rout = nullptr;
     InstDev* inst_d = nullptr;
@@ -280,6 +282,8 @@ Layout make_layout(const Solver& S) {
     for (int b = 0; b < 3; ++b) L.dens[b] = take((size_t)S.total_cells * S.n3 * S.tsize);
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
     L.mpk = take((size_t)S.total_cells * kNmom * sizeof(double));  // the moments query's rows
+    L.bpairs = take((size_t)S.max_citems * sizeof(BandPair));   // the batch closure's band jobs
+    L.n_bpairs = take(sizeof(int));
     L.cw = take((size_t)S.total_cells * 2 * S.tsize);
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
     L.tab = take(S.tab_h.size() * sizeof(double));
@@ -523,6 +527,39 @@ int upload_items(Solver& S) {
         for (int c = 0; c < N; c += cc) ci.push_back(make_int4(q, c, std::min(cc, N - c), 0));
     }
     if ((int)si.size() > S.max_sitems || (int)ci.size() > S.max_citems) return FDLB_EINVAL;
+    // the batch closure's band jobs: two band rows of an item at a time (instances with chi at the
+    // local density have none), or a wall part; geometry only, so formed here once per work list
+    std::vector<BandPair> bp;
+    if (S.closure_batch) {
+        for (const int4& w : ci) {
+            const InstanceSetup& I = S.setup[w.x];
+            const InstDev& D = S.inst_h[w.x];
+            if (w.w != 0) {
+                bp.push_back(BandPair{0, 0, 0, 0, -w.w, w.z, 0, w.x});
+                continue;
+            }
+            if (D.chi_local || I.band.width == 0) continue;
+            const int N = I.p.n_cells;
+            for (int t = 0; t < w.z; t += 2) {
+                const int a = w.y + t, b = a + 1;
+                const bool hasB = t + 1 < w.z;
+                BandPair p{};
+                p.wA = (long long)D.band_off + (long long)a * D.band_w;
+                p.wB = p.wA + D.band_w;
+                p.dA = (long long)D.cell_off + I.band.lo[a];
+                p.dB = hasB ? (long long)D.cell_off + I.band.lo[b] : p.dA;
+                p.kmaxA = std::min(I.band.cnt[a], N - I.band.lo[a]);
+                p.kmaxB = hasB ? std::min(I.band.cnt[b], N - I.band.lo[b]) : 0;
+                p.gc = D.cell_off + a;
+                p.q = w.x;
+                bp.push_back(p);
+            }
+        }
+        if ((int)bp.size() > S.max_citems) return FDLB_EINVAL;
+    }
+    const int nbp = (int)bp.size();
+    if (nbp) FDLB_CUDA(cudaMemcpyAsync(S.bpairs, bp.data(), nbp * sizeof(BandPair), cudaMemcpyHostToDevice, S.stream));
+    FDLB_CUDA(cudaMemcpyAsync(S.n_bpairs, &nbp, sizeof(int), cudaMemcpyHostToDevice, S.stream));
     const int ns = (int)si.size(), nc = (int)ci.size();
     if (ns) FDLB_CUDA(cudaMemcpyAsync(S.sitems, si.data(), ns * sizeof(int4), cudaMemcpyHostToDevice, S.stream));
     if (nc) FDLB_CUDA(cudaMemcpyAsync(S.citems, ci.data(), nc * sizeof(int4), cudaMemcpyHostToDevice, S.stream));
@@ -731,6 +768,8 @@ int launch_closure_buf(Solver& S, int buf, int write_ca) {
     A.wst_elems = S.closure_wst;
     A.err = S.err;
     A.programmatic = S.programmatic;
+    A.pairs = S.bpairs;
+    A.n_pairs = S.n_bpairs;
     if (S.closure_batch) {
         if (S.precision == FDLB_FP32)
             launch_closure_batch<float>(A, S.M, S.grid_cbatch, S.cbatch_smem, S.stream);
@@ -1227,6 +1266,8 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     }
     R.ca = (double*)(R.ws + L.ca);
     R.mpk = (double*)(R.ws + L.mpk);
+    R.bpairs = (BandPair*)(R.ws + L.bpairs);
+    R.n_bpairs = (int*)(R.ws + L.n_bpairs);
     R.rec = R.ws + L.rec;
     R.tabT = R.ws + L.tabT;
     R.tab = (double*)(R.ws + L.tab);

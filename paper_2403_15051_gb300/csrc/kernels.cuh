@@ -95,6 +95,15 @@ struct StageArgs {
                                    // null: the stage contracts from the K^h table in shared memory
 };
 
+// A warp's job in the batch closure's band kernel, formed once per work list on the host: two
+// band rows (A, B) of one instance, or (kmaxA < 0) part kmaxB of the outgoing flux through wall
+// -1 - kmaxA of instance q.  wA, wB: first band element of each row; dA, dB: global cell of each
+// row's first column; kmaxA, kmaxB: the rows' summed extents (0: no row B); gc: global cell of A.
+struct BandPair {
+    long long wA, wB, dA, dB;
+    int kmaxA, kmaxB, gc, q;
+};
+
 struct ClosureArgs {
     const double* sums;
     const void* sumsw;             // the raw sums as double-float pairs (FP32 populations)
@@ -117,6 +126,8 @@ struct ClosureArgs {
     int wst_elems;                 // capacity of the staged band rows (elements)
     int programmatic;              // launched with programmatic stream serialization
     int* err;                      // set when a bulk copy never completes
+    const BandPair* pairs;         // batch form: the band kernel's jobs
+    const int* n_pairs;
 };
 
 struct StepArgs {

@@ -155,10 +155,10 @@ __global__ void __launch_bounds__(kClosureThreads) closure_kernel(ClosureArgs A,
 // the raw sums of its reach and the band results, every phase spread over the whole block.  Both
 // are made of the chain's per-cell functions (closure_item.cuh), so the records are the chain's.
 
-// A warp per pair of band rows: the virtual pair v is rows 2 (v mod P), 2 (v mod P) + 1 of item
-// v div P, P = kClosureCells / 2 (pairs beyond an item's cells are empty; a wall item's first pair
-// is its part of the outgoing flux), summed together by clo_band_row2 with the loads of both rows
-// in flight, then chi and nbar of the two cells.
+// A warp per job of the host-formed list A.pairs: two band rows summed together by clo_band_row2
+// with the loads of both in flight, then chi and nbar of the two cells; or one part of the
+// outgoing flux through a wall.  A job's description is one 48-byte load, so the weights and
+// densities follow it after a single dependent load.
 template <typename T>
 __global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closure_band_kernel(ClosureArgs A, MomSet M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,42 +173,27 @@ __global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closu
     T* nwp = reinterpret_cast<T*>(A.nwp);
     T* cw = reinterpret_cast<T*>(A.cw);
     const int slices = A.slices;
-    static_assert(kClosureCells % 2 == 0, "band rows are taken in pairs");
-    constexpr int kPairs = kClosureCells / 2;
-    const long long nv = (long long)(*A.n_items) * kPairs;
-    const long long gw = (long long)blockIdx.x * kClosureWarps + warp, nw = (long long)gridDim.x * kClosureWarps;
-    for (long long v = gw; v < nv; v += nw) {
-        const int it = (int)(v / kPairs), t = 2 * (int)(v % kPairs);
-        const int4 w = A.items[it];
-        if (w.w != 0) {
-            if (t != 0) continue;
+    const int np = *A.n_pairs;
+    const int gw = blockIdx.x * kClosureWarps + warp, nw = gridDim.x * kClosureWarps;
+    for (int v = gw; v < np; v += nw) {
+        const BandPair P = A.pairs[v];
+        if (P.kmaxA < 0) {
             // one part of the outgoing flux through a wall, by one warp in the order of the chain
             // form's block of kClosureThreads threads: lane L takes the momenta of its threads
             // L, L + 32, L + 64, L + 96 and the four warp sums are combined as there
-            const InstDev I = A.inst[w.x];
-            const int side = w.w - 1, part = w.z, P = A.wall_parts;
+            const InstDev I = A.inst[P.q];
+            const int side = -1 - P.kmaxA, part = P.kmaxB, WP = A.wall_parts;
             const T* wall = fin_all + I.f_off + (side == 0 ? 0LL : (long long)(I.n_cells - 1) * M.Np);
             T r[kClosureWarps];
 #pragma unroll
             for (int vw = 0; vw < kClosureWarps; ++vw)
                 r[vw] = warp_sum(wall_flux_partial<T>(wall, side == 0 ? (long long)M.Np : -(long long)M.Np, M, tb, side,
-                                                      part, P, 32 * vw + lane));
-            if (lane == 0) nwp[((long long)w.x * 2 + side) * P + part] = wall_part_sum(r);
+                                                      part, WP, 32 * vw + lane));
+            if (lane == 0) nwp[((long long)P.q * 2 + side) * WP + part] = wall_part_sum(r);
             continue;
         }
-        const int c0 = w.y, cnt = w.z;
-        if (t >= cnt) continue;
-        const InstDev I = A.inst[w.x];
-        if (I.chi_local) continue;  // chi at the local density: closure_records_kernel
-        const int N = I.n_cells;
-        const bool hasB = t + 1 < cnt;
-        const int2* bl = reinterpret_cast<const int2*>(A.band_lo) + I.cell_off + c0 + t;
-        const int2 eA = bl[0], eB = hasB ? bl[1] : make_int2(0, 0);
-        const int kmaxA = min(eA.y, N - eA.x), kmaxB = hasB ? min(eB.y, N - eB.x) : 0;
-        const T* WrA = band + I.band_off + (long long)(c0 + t) * I.band_w;
-        const T* WrB = WrA + I.band_w;
-        const T* ndA = dens + ((long long)I.cell_off + eA.x) * slices;
-        const T* ndB = dens + ((long long)I.cell_off + eB.x) * slices;
+        const T* ndA = dens + P.dA * slices;
+        const T* ndB = dens + P.dB * slices;
         auto dA = [&](int k) {
             T x = ndA[(long long)k * slices];
             for (int sl = 1; sl < slices; ++sl) x += ndA[(long long)k * slices + sl];
@@ -220,15 +205,16 @@ __global__ void __launch_bounds__(kClosureThreads, sizeof(T) == 4 ? 8 : 4) closu
             return x;
         };
         T totA, totB;
-        clo_band_row2<T>(WrA, dA, kmaxA, WrB, dB, kmaxB, lane, totA, totB);
+        clo_band_row2<T>(band + P.wA, dA, P.kmaxA, band + P.wB, dB, P.kmaxB, lane, totA, totB);
         // lane 0's sums: every lane ends the butterfly with the total, but each in an order of its
         // own, and the chain form takes lane 0's
         if (lane == 0) {
+            const InstDev& I = A.inst[P.q];
             const T etaf = inst_param<T>(I.etafac, I.f_etafac);
-            const long long gc = (long long)I.cell_off + c0 + t;
+            const long long gc = P.gc;
             cw[gc * 2] = clo_chi<T>(etaf, totA);
             cw[gc * 2 + 1] = totA;
-            if (hasB) {
+            if (P.kmaxB > 0) {
                 cw[gc * 2 + 2] = clo_chi<T>(etaf, totB);
                 cw[gc * 2 + 3] = totB;
             }
