@@ -23,6 +23,8 @@
 // vector share p_R and hence the upwind direction.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "kernels_decl.h"
 
@@ -656,10 +658,11 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
         // sums over the warps in a fixed pairwise tree, to FP64.  FP32 partials: a double-float
         // tree (error-free first level, ~44 bits after), converted once (exact); the FP64 pipe is
         // slow on this part and the sums are the tail of every item.  FP64 partials: FP64.
-        for (int e = tid; e < Be * kSums; e += NT) {
-            const int cl = e / kSums, q = e % kSums;
-            constexpr int kW = 16;  // at most 512 threads
-            double s;
+        // The tree over 16 slots (at most 512 threads), the slots beyond the block's warps zero; it
+        // is taken over the smallest power of two of slots that holds the warps, since the levels
+        // above add exact zeros (the same sums bit for bit, without their instructions).
+        auto tree = [&](auto kWc, int cl, int q) -> double {
+            constexpr int kW = decltype(kWc)::value;
             if constexpr (sizeof(T) == 4) {
                 Wide<float> v[kW];
 #pragma unroll
@@ -668,10 +671,10 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 for (int h = kW / 2; h > 0; h >>= 1)
 #pragma unroll
                     for (int ww = 0; ww < h; ++ww) v[ww] = w_add(v[ww], v[ww + h]);
-                s = (double)v[0].hi + (double)v[0].lo;
-                // the pair itself for the closure (its split of s: hi = fl(s), lo = s - hi)
+                // the pair itself for the closure (its split of the sum: hi = fl(s), lo = s - hi)
                 const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
                 reinterpret_cast<float2*>(A.sumsw_out)[cs * kSums + q] = make_float2(v[0].hi, v[0].lo);
+                return (double)v[0].hi + (double)v[0].lo;
             } else {
                 double v[kW];
 #pragma unroll
@@ -680,8 +683,18 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 for (int h = kW / 2; h > 0; h >>= 1)
 #pragma unroll
                     for (int ww = 0; ww < h; ++ww) v[ww] = v[ww] + v[ww + h];
-                s = v[0];
+                return v[0];
             }
+        };
+        for (int e = tid; e < Be * kSums; e += NT) {
+            const int cl = e / kSums, q = e % kSums;
+            double s;
+            if (nwarps <= 4)
+                s = tree(std::integral_constant<int, 4>{}, cl, q);
+            else if (nwarps <= 8)
+                s = tree(std::integral_constant<int, 8>{}, cl, q);
+            else
+                s = tree(std::integral_constant<int, 16>{}, cl, q);
             const long long cs = (long long)(I.cell_off + c0 + cl) * M.slices + sl;
             A.sums_out[cs * kSums + q] = s;
             if (q == 0) reinterpret_cast<T*>(A.dens_out)[cs] = (T)s;
