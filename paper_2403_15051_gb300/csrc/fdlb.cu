@@ -32,7 +32,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     size_t f[3], sums[3], sumsw[3], dens[3], ca, cw, rec, tab, tabT, inst, geo, geoT, gw, gwT, band, band_lo, sitems, n_sitems, citems,
         n_citems, nwp, err, gbar,
-        rprev, rout, krf, krB, mpk, bpairs, n_bpairs, total;
+        rprev, rout, krf, krB, mpk, bpairs, n_bpairs, k3f, total;
 };
 
 }  // namespace
@@ -107,6 +107,8 @@ struct Solver {
     int tensor = 0;        // K^h contraction on the tensor cores where available
     void* krf = nullptr;   // K^h f of the stage input (contraction kernel), when allocated
     int krg_on = 0;        // the contraction kernel is in use
+    void* k3f = nullptr;   // sphere: K_3 f of the stage input, when the momenta are sliced along p_3
+    int k3_on = 0;         // ... and in use (slices narrower than the p_3 axis)
     float* krB = nullptr;  // K^h as TF32 pairs in the tensor-core kernel's layout (FP32 populations)
     int kr_tc = 0;         // the contraction kernel runs on the tensor cores
     int mma_on = 0;        // ... and in use for the current tiling
@@ -283,6 +285,7 @@ Layout make_layout(const Solver& S) {
     L.ca = take((size_t)S.total_cells * kCA * sizeof(double));
     L.mpk = take((size_t)S.total_cells * kNmom * sizeof(double));  // the moments query's rows
     L.bpairs = take((size_t)S.max_citems * sizeof(BandPair));   // the batch closure's band jobs
+    L.k3f = take(S.geometry == FDLB_SPH ? S.f_elems * S.tsize : 0);  // sphere: K_3 f of the stage input
     L.n_bpairs = take(sizeof(int));
     L.cw = take((size_t)S.total_cells * 2 * S.tsize);
     L.rec = take((size_t)S.total_cells * record_stride(S.nR, S.n2, S.n3) * S.tsize);
@@ -468,7 +471,7 @@ cudaError_t launch_step_dispatch(const Solver& S, const StepArgs* P, int* blocks
 int plan_step_kernel(Solver& S, int n_items) {
     S.fused_on = 0;
     S.grid_step = 0;
-    if (!S.fused || S.krg_on || !S.scfg.spec || S.M.slices != 1 || !S.use_bulk || S.threads < 5 * 32 || S.max_tile < 1 ||
+    if (!S.fused || S.krg_on || S.k3_on || !S.scfg.spec || S.M.slices != 1 || !S.use_bulk || S.threads < 5 * 32 || S.max_tile < 1 ||
         S.max_tile > kClosureCells || n_items < 1)
         return FDLB_OK;
     // shared memory: the stage's plan, then [staged band rows | closure tables | band-union
@@ -622,8 +625,11 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     const int old_slices = S.M.slices;
     if (B > 0) S.B = std::max(2, B);
     if (KS > 0) S.KS = KS;
-    if (S.geometry == FDLB_SPH) S.KS = S.n3;  // every axis is coupled by the force term
+    // the sphere's force couples every axis: slices narrower than the p_3 axis take K_3 f from its
+    // own contraction kernel
+    if (S.geometry == FDLB_SPH && !S.k3f) S.KS = S.n3;
     if (S.KS < 1 || S.n3 % S.KS) S.KS = S.n3;
+    S.k3_on = S.geometry == FDLB_SPH && S.KS < S.n3 ? 1 : 0;
     if (S.geometry == FDLB_CYL) {
         // a block holds at most 512 threads of at most 8 momenta: narrower slices (p_3 is passive on
         // the cylinder) where a slice of the large radial orders would exceed that
@@ -815,11 +821,29 @@ int launch_kr_buf(Solver& S, int in) {
     return cuda_status(e);
 }
 
+// Sphere with momenta sliced along p_3: K_3 f of buffer `in` by its contraction kernel.
+int launch_k3_buf(Solver& S, int in) {
+    const int grid = std::max(1, std::min(S.grid_stream, S.n_sm * 8));
+    cudaError_t e;
+    if (S.precision == FDLB_FP32)
+        e = launch_k3_contract<float>((const float*)S.f[in], (float*)S.k3f, S.sitems, S.n_sitems, S.inst_d,
+                                      (const float*)S.tabT + S.M.o_K3, S.M, grid, S.stream);
+    else
+        e = launch_k3_contract<double>((const double*)S.f[in], (double*)S.k3f, S.sitems, S.n_sitems, S.inst_d,
+                                       (const double*)S.tabT + S.M.o_K3, S.M, grid, S.stream);
+    S.launches++;
+    return cuda_status(e);
+}
+
 // One right-hand-side evaluation and RK combination: closure launch, then the fused stage.
 // In timing mode each launch is bracketed by events and its duration accumulated.
 int launch_stage(Solver& S, int in, int fn, int out, double a, double b, int mode, int write_ca = 0) {
     if (S.krg_on) {
         const int rc = launch_kr_buf(S, in);
+        if (rc) return rc;
+    }
+    if (S.k3_on) {
+        const int rc = launch_k3_buf(S, in);
         if (rc) return rc;
     }
     if (S.timing) {
@@ -876,6 +900,7 @@ int launch_stream_only(Solver& S, int in, int fn, int out, double a, double b, i
     A.mma = S.mma_on;
     A.tx_extra = S.test_tx_extra;
     A.krf = S.krg_on ? S.krf : nullptr;
+    A.k3f = S.k3_on ? S.k3f : nullptr;
     cudaError_t e;
     const int g = S.geometry;
     if (S.precision == FDLB_FP32)
@@ -1211,7 +1236,7 @@ int do_steps(Solver& S, int64_t n) {
         if (rc) return rc;
         while (n - done >= S.graph_steps) {
             FDLB_CUDA(cudaGraphLaunch(S.gexec, S.stream));
-            S.launches += (int64_t)S.graph_steps * 3 * ((S.krg_on ? 1 : 0) + (S.closure_batch ? 2 : 1) + 1);
+            S.launches += (int64_t)S.graph_steps * 3 * ((S.krg_on ? 1 : 0) + (S.k3_on ? 1 : 0) + (S.closure_batch ? 2 : 1) + 1);
             done += S.graph_steps;
         }
     }
@@ -1267,6 +1292,7 @@ int solver_create(const fdlb_params* ps, int n, void* stream, void* workspace, s
     R.ca = (double*)(R.ws + L.ca);
     R.mpk = (double*)(R.ws + L.mpk);
     R.bpairs = (BandPair*)(R.ws + L.bpairs);
+    R.k3f = R.geometry == FDLB_SPH ? (void*)(R.ws + L.k3f) : nullptr;
     R.n_bpairs = (int*)(R.ws + L.n_bpairs);
     R.rec = R.ws + L.rec;
     R.tabT = R.ws + L.tabT;

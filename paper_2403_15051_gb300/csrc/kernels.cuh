@@ -93,6 +93,8 @@ struct StageArgs {
     int tx_extra;                  // test hook: bytes the staged-copy barrier waits for beyond the copy
     const void* krf;               // K^h f of f_in from the contraction kernel (T, layout of f), or
                                    // null: the stage contracts from the K^h table in shared memory
+    const void* k3f;               // sphere: K_3 f of f_in (T, layout of f) when the momenta are
+                                   // sliced along p_3, or null: contracted from the staged rows
 };
 
 // A warp's job in the batch closure's band kernel, formed once per work list on the host: two

@@ -138,6 +138,11 @@ cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int*
 // The tensor-core form (FP32): Bsplit holds the weight-scaled K^h (kr_contract.cu) as TF32 pairs in
 // the kernel's shared-memory layout (kr_split_table), isw / sw the scales, Npad = 2Q_R rounded up to
 // 16; err is set when a bounded wait runs out.
+// Sphere: out = K_3 f along the third momentum axis, per cell (each cell once: the items of slice 0
+// of the stream work list), in the order the stage kernel contracts it (the same values).
+template <typename T>
+cudaError_t launch_k3_contract(const T* f, T* out, const int4* items, const int* n_items, const InstDev* inst,
+                               const T* K3, const MomSet& M, int grid, cudaStream_t s);
 cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,
                                   const float* Bsplit, const float* isw, const float* sw, const MomSet& M, int Npad,
                                   int* err, int grid, cudaStream_t s);

@@ -322,6 +322,68 @@ cudaError_t launch_kr_contract(const T* f, T* out, const int4* items, const int*
     return cudaPeekAtLastError();
 }
 
+// ------------------------------------------------------------------------------ K_3 (sphere)
+// The third axis's derivative matrix of the sphere's curvature force (Sec. III.B, full range) as
+// its own pass: out[c][k][i][j] = sum_b K_3[k][b] f[c][b][i][j], b in increasing order as the fused
+// stage sums it (the same values).  Taken out of the stage so that the stage can slice the momenta
+// along p_3 (the sphere's force otherwise couples every axis and one slice must hold all of a
+// cell's momenta).  A block per work item of slice 0 (each cell once), a thread per (i, j) column:
+// the n3 inputs of a column are read coalesced across the threads, its n3 outputs written so.
+// N3: the compile-time axis size, 0 for any size up to kMaxQ3.
+constexpr int kMaxQ3 = 24;
+
+template <typename T, int N3>
+__global__ void __launch_bounds__(256) k3_contract_kernel(const T* __restrict__ f, T* __restrict__ out,
+                                                          const int4* __restrict__ items, const int* __restrict__ n_items,
+                                                          const InstDev* __restrict__ inst, const T* __restrict__ K3,
+                                                          MomSet M) {
+    constexpr int NB = N3 ? N3 : kMaxQ3;
+    __shared__ T sK[NB * NB];
+    const int n3 = N3 ? N3 : M.n3;
+    for (int e = threadIdx.x; e < n3 * n3; e += blockDim.x) sK[(e / n3) * NB + e % n3] = K3[e];
+    __syncthreads();
+    const int cols = M.nR * M.n2;
+    const int nit = *n_items;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const int4 w = items[it];
+        if (w.w != 0) continue;  // slice 0 covers the item's cells once
+        const InstDev& I = inst[w.x];
+        for (int cl = 0; cl < w.z; ++cl) {
+            const long long base = I.f_off + (long long)(w.y + cl) * M.Np;
+            for (int col = threadIdx.x; col < cols; col += blockDim.x) {
+                T v[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) v[b] = b < n3 ? f[base + (long long)b * cols + col] : T(0);
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    if (k >= n3) break;
+                    T acc = T(0);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        if (b < n3) acc += sK[k * NB + b] * v[b];
+                    out[base + (long long)k * cols + col] = acc;
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_k3_contract(const T* f, T* out, const int4* items, const int* n_items, const InstDev* inst,
+                               const T* K3, const MomSet& M, int grid, cudaStream_t s) {
+    if (M.n3 > kMaxQ3) return cudaErrorInvalidValue;
+    if (M.n3 == 12)
+        k3_contract_kernel<T, 12><<<grid, 256, 0, s>>>(f, out, items, n_items, inst, K3, M);
+    else
+        k3_contract_kernel<T, 0><<<grid, 256, 0, s>>>(f, out, items, n_items, inst, K3, M);
+    return cudaPeekAtLastError();
+}
+
+template cudaError_t launch_k3_contract<float>(const float*, float*, const int4*, const int*, const InstDev*,
+                                               const float*, const MomSet&, int, cudaStream_t);
+template cudaError_t launch_k3_contract<double>(const double*, double*, const int4*, const int*, const InstDev*,
+                                                const double*, const MomSet&, int, cudaStream_t);
+
 size_t kr_tc_smem_bytes(int Npad) { return 1024 + 4 * (size_t)kAPart + 4 * (size_t)Npad * 128; }
 
 cudaError_t launch_kr_contract_tc(const float* f, float* out, const int4* items, const int* n_items, const InstDev* inst,

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(512, 1) step_kernel(StepArgs S, MomSet M) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31;
     const int nR = NR_ ? NR_ : M.nR, n2 = N2_ ? N2_ : M.n2, n3 = N3_ ? N3_ : M.n3;
-    const int KS = GEOM == 1 ? n3 : M.KS;
+    const int KS = M.KS;  // the sphere runs here with one slice (KS = n3)
     const StreamSmem P = stream_smem_plan(S.st.B, nR * n2 * KS, nR, n2, n3, (int)(blockDim.x >> 5), (int)sizeof(T),
                                           (sizeof(T) == 4 && S.st.mma) ? 1 : 0);
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);

@@ -133,13 +133,14 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
 // sK3 K_3 with row stride n3+1, nodes and weights, sgw the inner and outer wall Maxwellians per
 // axis [2][nR + n2 + n3], sgeo the tile's geometry, red the per-warp sums [cell][warp][16], skrf
 // K^h f of the own cells (tensor-core path).  NR_, N2_, N3_: compile-time axis sizes (0: taken
-// from M at run time).  The sphere couples every axis: one slice (KS = n3).
+// from M at run time).  The sphere couples every axis: one slice (KS = n3), unless K_3 f comes from
+// its own contraction kernel (A.k3f).
 #define FDLB_STREAM_LAYOUT                                                                                       \
     extern __shared__ __align__(16) unsigned char smem_raw[];                                                    \
     const int NT = blockDim.x;                                                                                   \
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;                             \
     const int nR = NR_ ? NR_ : M.nR, n2 = N2_ ? N2_ : M.n2, n3 = N3_ ? N3_ : M.n3;                               \
-    const int KS = GEOM == 1 ? n3 : M.KS;                                                                        \
+    const int KS = M.KS;                                                                                         \
     const int Ms = nR * n2 * KS, Np = nR * n2 * n3;                                                              \
     const int n2v = n2 / VW;                                                                                     \
     const int Vs = Ms / VW;                                                                                      \
@@ -535,7 +536,10 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                             for (int t = 0; t < VW; ++t) K2f[e] += kq[t] * rv[t];
                         }
                     }
-                    if (GEOM == 1) {
+                    if (GEOM == 1 && A.k3f) {
+                        // sliced along p_3: from the contraction kernel, in the layout of f
+                        ldg_vec<T, VW>(reinterpret_cast<const T*>(A.k3f) + I.f_off + (long long)c * Np + slice_off + vb, K3f);
+                    } else if (GEOM == 1) {
                         const T* k3 = sK3 + k * (n3 + 1);
                         const T* c3 = fc + i * n2 + jb * VW;
 #pragma unroll 4

@@ -286,3 +286,22 @@ def test_cylinder_fp32_shape_both_vector_widths_match_oracle(threads):
     f_or = osolver.run(f0, P, 20)
     errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
     assert max(errs.values()) <= TOL["fp32"], errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("slice_k", [1, 2])
+def test_sphere_sliced_along_p3_matches_oracle(precision, slice_k):
+    # slices narrower than the p_3 axis: K_3 f from its own contraction kernel, the rest of the
+    # sphere's stage per slice
+    d = small_case(geometry=wl.SPH, precision=precision, n_cells=33, beta=1.2)
+    P, f0, S = _pair(d, seed=6)
+    S.set_autotune(0)
+    S.set_tiling(4, slice_k, 0)
+    assert S.tiling()["slice_k"] == slice_k
+    L_or = osolver.rhs(f0, P)
+    L = S.eval_rhs()
+    assert np.max(np.abs(L - L_or)) / np.max(np.abs(L_or)) <= RHS_TOL[precision]
+    S.step(20)
+    f_or = osolver.run(f0, P, 20)
+    errs = compare_moments(S.moments(), osolver.moments(f_or, P), P)
+    assert max(errs.values()) <= TOL[precision], errs
