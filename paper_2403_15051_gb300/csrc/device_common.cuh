@@ -118,6 +118,55 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
     return ratio_fast(a0 * r0 + a1 * r1 + a2 * r2, T(6) * (a0 + a1 + a2));
 }
 
+// ---- pairs of lanes: two momenta of a vector per instruction.  FP32 pairs use the packed FP32x2
+// operations of the sm_100 family (__ffma2_rn, __fadd2_rn, __fmul2_rn: one issue slot for two
+// FP32 operations, each lane rounded like the scalar operation); FP64 pairs are two scalar
+// operations.  Every operation is written out (nothing is left to the compiler's contraction),
+// so a lane's result is the same whichever pair it travels in.
+template <typename T>
+struct PairT;
+template <>
+struct PairT<float> {
+    using type = float2;
+};
+template <>
+struct PairT<double> {
+    using type = double2;
+};
+template <typename T>
+using Pair = typename PairT<T>::type;
+
+__device__ __forceinline__ float2 p_make(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 p_make(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 p_splat(double a) { return make_double2(a, a); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) { return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)); }
+// a - b: b times -1 is exact, so the fused form rounds once, like a subtraction
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 p_sub(double2 a, double2 b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 p_min(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ double2 p_min(double2 a, double2 b) { return make_double2(fmin(a.x, b.x), fmin(a.y, b.y)); }
+// Approximate FP32 reciprocal (the PTX rcp.approx instruction: at most one unit in the last place
+// off, subnormals flushed to zero).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// a / b lane by lane: for FP32 the product with the approximate reciprocal (the operands here are
+// normal numbers well inside the range); for FP64 the correctly rounded quotient.
+__device__ __forceinline__ float2 p_ratio(float2 a, float2 b) {
+    return __fmul2_rn(a, make_float2(rcp_approx(b.x), rcp_approx(b.y)));
+}
+__device__ __forceinline__ double2 p_ratio(double2 a, double2 b) { return make_double2(a.x / b.x, a.y / b.y); }
+
 // The same reconstruction written on the window in ascending cell order, w0..w4, for either
 // upwind direction: sigma = +1 gives weno5(w0, .., w4) (value at the right face of w2's cell,
 // from the left), sigma = -1 gives weno5(w4, .., w0) (left face, from the right).  The three
@@ -129,20 +178,31 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e) {
 // taken four times over (e4 + 13/3 D^2 + t^2, e4 = 4 eps): the normalised weights are unchanged.
 // The reconstruction is homogeneous of degree one in the window once eps scales with its square:
 // the value for c w0..c w4 with c^2 e4 is c times the value for w0..w4 with e4.
+// Written for a pair of momenta (one packed operation per step for FP32 pairs).  The window's
+// first difference enters negated (w0 - w1), and so does the centre stencil's first-difference
+// part (-tC = d1 + d2), which the indicators square and the candidate values take with the
+// opposite sign: no negation is ever formed.  s3, ns3 = 3 sigma and its negative; dL, dR the
+// linear weights of the outer stencils; e4 = 4 eps (w^2 for the reconstruction of f, below).
 template <typename T>
-__device__ __forceinline__ T weno5_sym(T w0, T w1, T w2, T w3, T w4, T s3, T dL, T dR, T e4) {
-    const T d0 = w1 - w0, d1 = w2 - w1, d2 = w3 - w2, d3 = w4 - w3;
-    const T D1 = d1 - d0, D2 = d2 - d1, D3 = d3 - d2;
-    const T tL = T(3) * d1 - d0, tC = -(d1 + d2), tR = d3 - T(3) * d2;
-    const T c = T(13.0 / 3.0);
-    const T EL = tL * tL + (c * D1 * D1 + e4);
-    const T EC = tC * tC + (c * D2 * D2 + e4);
-    const T ER = tR * tR + (c * D3 * D3 + e4);
-    const T m = fmin(EL, fmin(EC, ER));
-    const T sL = ratio_fast(m, EL), sC = ratio_fast(m, EC), sR = ratio_fast(m, ER);
-    const T aL = dL * sL * sL, aC = T(0.6) * sC * sC, aR = dR * sR * sR;
-    const T XL = D1 + s3 * tL, XC = D2 - s3 * tC, XR = D3 - s3 * tR;
-    return w2 + ratio_fast(aL * XL + aC * XC + aR * XR, T(12) * (aL + aC + aR));
+__device__ __forceinline__ Pair<T> weno5_pair(Pair<T> w0, Pair<T> w1, Pair<T> w2, Pair<T> w3, Pair<T> w4, Pair<T> s3,
+                                              Pair<T> ns3, Pair<T> dL, Pair<T> dR, Pair<T> e4) {
+    using P = Pair<T>;
+    const P nd0 = p_sub(w0, w1), d1 = p_sub(w2, w1), d2 = p_sub(w3, w2), d3 = p_sub(w4, w3);
+    const P D1 = p_add(d1, nd0), D2 = p_sub(d2, d1), D3 = p_sub(d3, d2);
+    const P tL = p_fma(p_splat(T(3)), d1, nd0);    // 3 d1 - d0
+    const P ntC = p_add(d1, d2);                    // -tC
+    const P tR = p_fma(p_splat(T(-3)), d2, d3);     // d3 - 3 d2
+    const P c = p_splat(T(13.0 / 3.0));
+    const P EL = p_fma(tL, tL, p_fma(p_mul(c, D1), D1, e4));
+    const P EC = p_fma(ntC, ntC, p_fma(p_mul(c, D2), D2, e4));
+    const P ER = p_fma(tR, tR, p_fma(p_mul(c, D3), D3, e4));
+    const P m = p_min(EL, p_min(EC, ER));
+    const P sL = p_ratio(m, EL), sC = p_ratio(m, EC), sR = p_ratio(m, ER);
+    const P aL = p_mul(dL, p_mul(sL, sL)), aC = p_mul(p_splat(T(0.6)), p_mul(sC, sC)), aR = p_mul(dR, p_mul(sR, sR));
+    const P XL = p_fma(s3, tL, D1), XC = p_fma(s3, ntC, D2), XR = p_fma(ns3, tR, D3);
+    const P num = p_fma(aR, XR, p_fma(aC, XC, p_mul(aL, XL)));
+    const P den = p_mul(p_splat(T(12)), p_add(p_add(aL, aC), aR));
+    return p_add(w2, p_ratio(num, den));
 }
 
 // ---- wide accumulators: plain FP64 for FP64 populations; for FP32 populations a double-float

@@ -127,9 +127,47 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[VW]) {
     }
 }
 
+// A vector as (VW + 1) / 2 pairs of lanes: (e0, e1), (e2, e3), ...; for VW = 1 one pair whose
+// second lane repeats the first (computed alongside and never stored).  The loads go through the
+// VW-wide forms above, whose registers the pairs then name without a move.
+template <typename T, int VW>
+__device__ __forceinline__ void pairs_of(const T (&v)[VW], Pair<T> (&o)[(VW + 1) / 2]) {
+#pragma unroll
+    for (int h = 0; h < (VW + 1) / 2; ++h) o[h] = p_make(v[2 * h], v[VW == 1 ? 0 : 2 * h + 1]);
+}
+template <typename T, int VW>
+__device__ __forceinline__ void ld_pairs(const T* p, Pair<T> (&o)[(VW + 1) / 2]) {
+    T v[VW];
+    ld_vec<T, VW>(p, v);
+    pairs_of<T, VW>(v, o);
+}
+template <typename T, int VW>
+__device__ __forceinline__ void ldg_pairs(const T* p, Pair<T> (&o)[(VW + 1) / 2]) {
+    T v[VW];
+    ldg_vec<T, VW>(p, v);
+    pairs_of<T, VW>(v, o);
+}
+template <typename T, int VW>
+__device__ __forceinline__ void ldcg_pairs(const T* p, Pair<T> (&o)[(VW + 1) / 2]) {
+    T v[VW];
+    ldcg_vec<T, VW>(p, v);
+    pairs_of<T, VW>(v, o);
+}
+template <typename T, int VW>
+__device__ __forceinline__ void st_pairs(T* p, const Pair<T> (&o)[(VW + 1) / 2]) {
+    T v[VW];
+#pragma unroll
+    for (int h = 0; h < (VW + 1) / 2; ++h) {
+        v[2 * h] = o[h].x;
+        if (2 * h + 1 < VW) v[2 * h + 1] = o[h].y;
+    }
+    st_vec<T, VW>(p, v);
+}
+
 // Local names of the stage's dimensions and of its shared-memory plan (StreamSmem): fs the
 // staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sK2 K_2 in the vector-swizzled
-// order [e][b / VW][j / VW][b % VW] (first: aligned vector loads), sKR K^h with row stride krs,
+// transposed, [b][j] (the coefficients of input b for a vector's outputs: one aligned vector load),
+// sKR K^h with row stride krs,
 // sK3 K_3 with row stride n3+1, nodes and weights, sgw the inner and outer wall Maxwellians per
 // axis [2][nR + n2 + n3], sgeo the tile's geometry, red the per-warp sums [cell][warp][16], skrf
 // K^h f of the own cells (tensor-core path).  NR_, N2_, N3_: compile-time axis sizes (0: taken
@@ -197,10 +235,7 @@ __device__ __forceinline__ void stream_tables(const StageArgs& A, const MomSet& 
     }
     if (!A.krf)
         for (int e = tid; e < nR * nR; e += NT) sKR[(e / nR) * krs + e % nR] = tab[M.o_KR + e];
-    for (int e = tid; e < n2 * n2; e += NT) {
-        const int j = e / n2, b = e % n2;
-        sK2[(((j % VW) * n2v + b / VW) * n2v + j / VW) * VW + b % VW] = tab[M.o_K2 + e];
-    }
+    for (int e = tid; e < n2 * n2; e += NT) sK2[(e % n2) * n2 + e / n2] = tab[M.o_K2 + e];  // transposed
     if (GEOM == 1)
         for (int e = tid; e < n3 * n3; e += NT) sK3[(e / n3) * (n3 + 1) + e % n3] = tab[M.o_K3 + e];
 }
@@ -380,17 +415,20 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
       }
     }
 
-    // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0
+    // ---- 4. the thread's vectors in this slice; WENO value at the left face of c0.  A vector's
+    // momenta are processed in pairs of lanes (packed FP32x2 operations for FP32 populations).
+    using V2 = Pair<T>;
+    constexpr int NP = (VW + 1) / 2;
     int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
     T pr_[NV], p3_[NV];
-    T e4w_[NV][VW], p2_[NV][VW], p2q_[NV][VW], vl_[NV][VW];
+    V2 e4w_[NV][NP], p2_[NV][NP], p2q_[NV][NP], vl_[NV][NP];
 #pragma unroll
     for (int g = 0; g < NV; ++g) {
         const int v = tid + g * NT;
         vcode[g] = -1;
         pr_[g] = p3_[g] = T(0);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) e4w_[g][e] = p2_[g][e] = p2q_[g][e] = vl_[g][e] = T(0);
+        for (int h = 0; h < NP; ++h) e4w_[g][h] = p2_[g][h] = p2q_[g][h] = vl_[g][h] = p_splat(T(0));
         if (v < Vs) {
             const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
             const int k = sl * KS + kk;
@@ -400,33 +438,39 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
             p3_[g] = sp_3[k];
             const T wik = sw_R[i] * sw_3[k];
 #pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const int j = jb * VW + e;
-                p2_[g][e] = sp_2[j];
-                p2q_[g][e] = sp_2[j] * sp_2[j];
+            for (int h = 0; h < NP; ++h) {
+                const int ja = jb * VW + 2 * h, jc = VW == 1 ? ja : ja + 1;
+                p2_[g][h] = p_make(sp_2[ja], sp_2[jc]);
+                p2q_[g][h] = p_mul(p2_[g][h], p2_[g][h]);
                 // WENO5 of f / w (Sec. II.C) taken on f itself: with eps scaled by w^2 the face value
                 // of f is w times that of f / w, and the flux needs no division by the weight.  In
                 // FP32 eps w^2 is kept above the float range's floor (weights below ~1e-16 at large
                 // radial orders, whose populations are negligible, reconstruct with linear weights)
-                const T wm = wik * sw_2[j];
-                e4w_[g][e] = sizeof(T) == 4 ? fmax(T(4e-6) * wm * wm, T(1e-37)) : T(4e-6) * wm * wm;
+                const T wa = wik * sw_2[ja], wc = wik * sw_2[jc];
+                e4w_[g][h] = sizeof(T) == 4 ? p_make(fmax(T(4e-6) * wa * wa, T(1e-37)), fmax(T(4e-6) * wc * wc, T(1e-37)))
+                                            : p_make(T(4e-6) * wa * wa, T(4e-6) * wc * wc);
             }
             if (c0 == 0 && pr > T(0)) {
-                const T gik = nwL * gwL[i] * gwL[nR + n2 + k];
+                const V2 gik = p_splat(nwL * gwL[i] * gwL[nR + n2 + k]);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) vl_[g][e] = gik * gwL[nR + jb * VW + e];
+                for (int h = 0; h < NP; ++h) {
+                    const int ja = jb * VW + 2 * h, jc = VW == 1 ? ja : ja + 1;
+                    vl_[g][h] = p_mul(gik, p_make(gwL[nR + ja], gwL[nR + jc]));
+                }
             } else {
                 // rows of cells c0-3..c0+1 (p_R > 0) or c0-2..c0+2 (p_R < 0), ascending
                 const T* b = fs + (long long)(pr > T(0) ? 0 : 1) * Ms + v * VW;
-                const T s3 = pr > T(0) ? T(3) : T(-3), dL = pr > T(0) ? T(0.1) : T(0.3), dR = pr > T(0) ? T(0.3) : T(0.1);
-                T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
-                ld_vec<T, VW>(b, r0);
-                ld_vec<T, VW>(b + Ms, r1);
-                ld_vec<T, VW>(b + 2 * Ms, r2);
-                ld_vec<T, VW>(b + 3 * Ms, r3);
-                ld_vec<T, VW>(b + 4 * Ms, r4);
+                const V2 s3 = p_splat(pr > T(0) ? T(3) : T(-3)), ns3 = p_splat(pr > T(0) ? T(-3) : T(3));
+                const V2 dL = p_splat(pr > T(0) ? T(0.1) : T(0.3)), dR = p_splat(pr > T(0) ? T(0.3) : T(0.1));
+                V2 r0[NP], r1[NP], r2[NP], r3[NP], r4[NP];
+                ld_pairs<T, VW>(b, r0);
+                ld_pairs<T, VW>(b + Ms, r1);
+                ld_pairs<T, VW>(b + 2 * Ms, r2);
+                ld_pairs<T, VW>(b + 3 * Ms, r3);
+                ld_pairs<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) vl_[g][e] = weno5_sym(r0[e], r1[e], r2[e], r3[e], r4[e], s3, dL, dR, e4w_[g][e]);
+                for (int h = 0; h < NP; ++h)
+                    vl_[g][h] = weno5_pair<T>(r0[h], r1[h], r2[h], r3[h], r4[h], s3, ns3, dL, dR, e4w_[g][h]);
             }
         }
     }
@@ -466,35 +510,40 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const int vb = ((kk * nR + i) * n2v + jb) * VW;  // element offset in the slice
                 const T pr = pr_[g], p3v = p3_[g];
                 // advection: WENO5 value at the right face, upwind by sign(p_R)
-                T vr[VW];
+                V2 vr[NP];
                 if (c == N - 1 && pr < T(0)) {
-                    const T gik = nwR * gwR[i] * gwR[nR + n2 + k];
+                    const V2 gik = p_splat(nwR * gwR[i] * gwR[nR + n2 + k]);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) vr[e] = gik * gwR[nR + jb * VW + e];
+                    for (int h = 0; h < NP; ++h) {
+                        const int ja = jb * VW + 2 * h, jc = VW == 1 ? ja : ja + 1;
+                        vr[h] = p_mul(gik, p_make(gwR[nR + ja], gwR[nR + jc]));
+                    }
                 } else {
                     // rows of cells c-2..c+2 (p_R > 0) or c-1..c+3 (p_R < 0), ascending
                     const T* b = fc + (pr > T(0) ? -2 * Ms : -Ms) + vb;
-                    const T s3 = pr > T(0) ? T(3) : T(-3), dL = pr > T(0) ? T(0.1) : T(0.3);
-                    const T dR = pr > T(0) ? T(0.3) : T(0.1);
-                    T r0[VW], r1[VW], r2[VW], r3[VW], r4[VW];
-                    ld_vec<T, VW>(b, r0);
-                    ld_vec<T, VW>(b + Ms, r1);
-                    ld_vec<T, VW>(b + 2 * Ms, r2);
-                    ld_vec<T, VW>(b + 3 * Ms, r3);
-                    ld_vec<T, VW>(b + 4 * Ms, r4);
+                    const V2 s3 = p_splat(pr > T(0) ? T(3) : T(-3)), ns3 = p_splat(pr > T(0) ? T(-3) : T(3));
+                    const V2 dL = p_splat(pr > T(0) ? T(0.1) : T(0.3)), dR = p_splat(pr > T(0) ? T(0.3) : T(0.1));
+                    V2 r0[NP], r1[NP], r2[NP], r3[NP], r4[NP];
+                    ld_pairs<T, VW>(b, r0);
+                    ld_pairs<T, VW>(b + Ms, r1);
+                    ld_pairs<T, VW>(b + 2 * Ms, r2);
+                    ld_pairs<T, VW>(b + 3 * Ms, r3);
+                    ld_pairs<T, VW>(b + 4 * Ms, r4);
 #pragma unroll
-                    for (int e = 0; e < VW; ++e) vr[e] = weno5_sym(r0[e], r1[e], r2[e], r3[e], r4[e], s3, dL, dR, e4w_[g][e]);
+                    for (int h = 0; h < NP; ++h)
+                        vr[h] = weno5_pair<T>(r0[h], r1[h], r2[h], r3[h], r4[h], s3, ns3, dL, dR, e4w_[g][h]);
                 }
-                // curvature force: K^h along i (one column shared by the vector), K_2 along j
-                T KRf[VW], K2f[VW], K3f[VW];
+                // curvature force: K^h along i (one column shared by the vector), K_2 along j; each
+                // output sums its terms in the order of the contracted index
+                V2 KRf[NP], K2f[NP], K3f[NP];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) KRf[e] = K2f[e] = K3f[e] = T(0);
+                for (int h = 0; h < NP; ++h) KRf[h] = K2f[h] = K3f[h] = p_splat(T(0));
                 {
                     if (kMMA && use_mma) {
-                        ld_vec<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
+                        ld_pairs<T, VW>(skrf + (long long)cl * Ms + vb, KRf);
                     } else if (A.krf) {
                         // from the contraction kernel, in the layout of f
-                        ldg_vec<T, VW>(reinterpret_cast<const T*>(A.krf) + I.f_off + (long long)c * Np + slice_off + vb, KRf);
+                        ldg_pairs<T, VW>(reinterpret_cast<const T*>(A.krf) + I.f_off + (long long)c * Np + slice_off + vb, KRf);
                     } else {
                         const T* col = fc + kk * nR * n2 + jb * VW;
                         const T* kr = sKR + i * krs;
@@ -506,49 +555,53 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                                 ld_vec<T, 4>(kr + a4, kq);
 #pragma unroll
                                 for (int t = 0; t < 4; ++t) {
-                                    T cv[VW];
-                                    ld_vec<T, VW>(col + (a4 + t) * n2, cv);
+                                    V2 cv[NP];
+                                    ld_pairs<T, VW>(col + (a4 + t) * n2, cv);
+                                    const V2 kv = p_splat(kq[t]);
 #pragma unroll
-                                    for (int e = 0; e < VW; ++e) KRf[e] += kq[t] * cv[e];
+                                    for (int h = 0; h < NP; ++h) KRf[h] = p_fma(kv, cv[h], KRf[h]);
                                 }
                             }
                         } else {
 #pragma unroll 8
                             for (int a = 0; a < nR; ++a) {
-                                T cv[VW];
-                                ld_vec<T, VW>(col + a * n2, cv);
-                                const T kv = kr[a];
+                                V2 cv[NP];
+                                ld_pairs<T, VW>(col + a * n2, cv);
+                                const V2 kv = p_splat(kr[a]);
 #pragma unroll
-                                for (int e = 0; e < VW; ++e) KRf[e] += kv * cv[e];
+                                for (int h = 0; h < NP; ++h) KRf[h] = p_fma(kv, cv[h], KRf[h]);
                             }
                         }
                     }
+                    // K_2 from its transpose: input b's coefficients for the vector's outputs
                     const T* row = fc + (kk * nR + i) * n2;
-#pragma unroll 4
+                    const T* k2 = sK2 + jb * VW;
+#pragma unroll 2
                     for (int b4 = 0; b4 < n2v; ++b4) {
                         T rv[VW];
                         ld_vec<T, VW>(row + b4 * VW, rv);
 #pragma unroll
-                        for (int e = 0; e < VW; ++e) {
-                            T kq[VW];
-                            ld_vec<T, VW>(sK2 + ((e * n2v + b4) * n2v + jb) * VW, kq);
+                        for (int t = 0; t < VW; ++t) {
+                            V2 kq[NP];
+                            ld_pairs<T, VW>(k2 + (b4 * VW + t) * n2, kq);
+                            const V2 fv1 = p_splat(rv[t]);
 #pragma unroll
-                            for (int t = 0; t < VW; ++t) K2f[e] += kq[t] * rv[t];
+                            for (int h = 0; h < NP; ++h) K2f[h] = p_fma(kq[h], fv1, K2f[h]);
                         }
                     }
                     if (GEOM == 1 && A.k3f) {
                         // sliced along p_3: from the contraction kernel, in the layout of f
-                        ldg_vec<T, VW>(reinterpret_cast<const T*>(A.k3f) + I.f_off + (long long)c * Np + slice_off + vb, K3f);
+                        ldg_pairs<T, VW>(reinterpret_cast<const T*>(A.k3f) + I.f_off + (long long)c * Np + slice_off + vb, K3f);
                     } else if (GEOM == 1) {
                         const T* k3 = sK3 + k * (n3 + 1);
                         const T* c3 = fc + i * n2 + jb * VW;
 #pragma unroll 4
                         for (int b = 0; b < n3; ++b) {
-                            T cv[VW];
-                            ld_vec<T, VW>(c3 + b * nR * n2, cv);
-                            const T kv = k3[b];
+                            V2 cv[NP];
+                            ld_pairs<T, VW>(c3 + b * nR * n2, cv);
+                            const V2 kv = p_splat(k3[b]);
 #pragma unroll
-                            for (int e = 0; e < VW; ++e) K3f[e] += kv * cv[e];
+                            for (int h = 0; h < NP; ++h) K3f[h] = p_fma(kv, cv[h], K3f[h]);
                         }
                     }
                 }
@@ -557,9 +610,9 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 // factor f^S / f^MB = 1 + c_S (|x|^2 / (5 T) - 1) x.q is a cubic in x1 and J1 / f^MB
                 // (which holds |x|^2 / (2T) - 5/2 and the strain x.S.x / T) a quadratic: their
                 // coefficients are formed once per vector, then two Horner evaluations per momentum.
-                T fv[VW], g2v[VW];
-                ld_vec<T, VW>(fc + vb, fv);
-                ld_vec<T, VW>(g2c + jb * VW, g2v);
+                V2 fv[NP], g2v[NP];
+                ld_pairs<T, VW>(fc + vb, fv);
+                ld_pairs<T, VW>(g2c + jb * VW, g2v);
                 const T x0 = pr - u0, x2 = p3v - u2;
                 T xsA = x0 * x0 + x2 * x2;
                 const T xqA = x0 * q0 + x2 * q2;
@@ -570,63 +623,75 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 }
                 const T stA = x0 * x0 * S00 + x2 * x2 * S22 + T(2) * x0 * x2 * S02;
                 const T fmbA = n * gRc[i] * g3c[k];
-                const T frcA = GEOM == 0 ? T(0) : kf * p3v * p3v;  // sphere: the p_3^2 part
                 const T Yd = T(0.6) * x0 * Y + T(0.4) * dv;
                 const T J0 = nbr * (x0 * X + Yd * (hiT * xsA - T(2.5)) + T(0.4) * iT * stA);
                 const T J1 = nbr * T(0.4) * g1c * x0;
                 const T J2 = nbr * (Yd * hiT + J2c);
                 const T b0 = fiT * xsA - T(1), cb0 = cS * b0;
                 const T F0 = T(1) + cb0 * xqA, F1 = cb0 * q1, F2 = cS * fiT * xqA;
-                const T pAp = pr * Ap, pAm = pr * Am;  // face values are of f: p_R A+/V, p_R A-/V
-                T out[VW];
+                // the advection and force terms enter negated: -(p_R A+/V vr - p_R A-/V vl) (face
+                // values are of f) and -frc, each formed with one rounding like its positive
+                const V2 npAp = p_splat(-(pr * Ap)), pAm = p_splat(pr * Am);
+                const V2 pu1 = p_splat(u1), pfmbA = p_splat(fmbA), pitau = p_splat(itau);
+                const V2 pF0 = p_splat(F0), pF1 = p_splat(F1), pF2 = p_splat(F2), pF3 = p_splat(F3);
+                const V2 pJ0 = p_splat(J0), pJ1 = p_splat(J1), pJ2 = p_splat(J2);
+                V2 out[NP];
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const T p2v = p2_[g][e];
-                    const T adv = pAp * vr[e] - pAm * vl_[g][e];
-                    vl_[g][e] = vr[e];
-                    T frc;
+                for (int h = 0; h < NP; ++h) {
+                    const V2 nadv = p_fma(npAp, vr[h], p_mul(pAm, vl_[g][h]));
+                    vl_[g][h] = vr[h];
+                    V2 nfrc;
                     if (GEOM == 0) {
-                        frc = kf * (p2q_[g][e] * KRf[e] - pr * K2f[e]);
+                        // -kf (p_2^2 K^h f - p_R K_2 f)
+                        nfrc = p_mul(p_splat(-kf), p_fma(p2q_[g][h], KRf[h], p_mul(p_splat(-pr), K2f[h])));
                     } else {
-                        frc = (kf * p2q_[g][e] + frcA) * KRf[e] - kf * pr * (K2f[e] + K3f[e]);
+                        // -((kf p_2^2 + kf p_3^2) K^h f - kf p_R (K_2 f + K_3 f))
+                        const V2 na = p_fma(p_splat(-kf), p2q_[g][h], p_splat(-(kf * p3v * p3v)));
+                        nfrc = p_fma(na, KRf[h], p_mul(p_splat(kf * pr), p_add(K2f[h], K3f[h])));
                     }
-                    const T x1 = p2v - u1;
-                    const T fmb = fmbA * g2v[e];
-                    const T fS = fmb * (((F3 * x1 + F2) * x1 + F1) * x1 + F0);
-                    const T j1 = (J2 * x1 + J1) * x1 + J0;
-                    out[e] = -adv - frc - (fv[e] - fS) * itau + fmb * j1;
+                    const V2 x1 = p_sub(p2_[g][h], pu1);
+                    const V2 fmb = p_mul(pfmbA, g2v[h]);
+                    const V2 fS = p_mul(fmb, p_fma(p_fma(p_fma(pF3, x1, pF2), x1, pF1), x1, pF0));
+                    const V2 j1 = p_fma(p_fma(pJ2, x1, pJ1), x1, pJ0);
+                    out[h] = p_fma(fmb, j1, p_fma(p_sub(fS, fv[h]), pitau, p_add(nadv, nfrc)));
                 }
                 const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
                 if (A.mode == 0) {
                     // a f_n + b (f + dt L) with a = 1 - b, written as f_n + b ((f - f_n) + dt L):
                     // exactly affine whatever the rounding of b (in FP32, fl(1/3) + fl(2/3)
                     // exceeds one by 3e-8, which would scale the state by that much every step)
+                    const V2 pdt = p_splat(dt);
                     if (ca_ != T(0)) {
-                        T fnv[VW];
-                        // f_n: read-only for the stage kernel; written earlier in the same launch for the
-                // persistent step kernel, which reads it coherently (L2)
-                if constexpr (kCoherent)
-                    ldcg_vec<T, VW>(f_n + gidx, fnv);
-                else
-                    ldg_vec<T, VW>(f_n + gidx, fnv);
+                        V2 fnv[NP];
+                        // f_n: read-only for the stage kernel; written earlier in the same launch for
+                        // the persistent step kernel, which reads it coherently (L2)
+                        if constexpr (kCoherent)
+                            ldcg_pairs<T, VW>(f_n + gidx, fnv);
+                        else
+                            ldg_pairs<T, VW>(f_n + gidx, fnv);
+                        const V2 pcb = p_splat(cb_);
 #pragma unroll
-                        for (int e = 0; e < VW; ++e) out[e] = fnv[e] + cb_ * ((fv[e] - fnv[e]) + dt * out[e]);
+                        for (int h = 0; h < NP; ++h) out[h] = p_fma(pcb, p_fma(pdt, out[h], p_sub(fv[h], fnv[h])), fnv[h]);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < VW; ++e) out[e] = fv[e] + dt * out[e];
+                        for (int h = 0; h < NP; ++h) out[h] = p_fma(pdt, out[h], fv[h]);
                     }
                 }
-                st_vec<T, VW>(f_out + gidx, out);
-                // raw sums: power sums over the vector's p_2, then the 13 moments
-                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+                st_pairs<T, VW>(f_out + gidx, out);
+                // raw sums: power sums over the vector's p_2 (per lane of the pairs, then the two
+                // lanes), then the 13 moments
+                V2 ps1 = p_mul(out[0], p2_[g][0]);
+                V2 ps0 = out[0], ps2 = p_mul(out[0], p2q_[g][0]), ps3 = p_mul(ps1, p2q_[g][0]);
 #pragma unroll
-                for (int e = 0; e < VW; ++e) {
-                    const T o1 = out[e] * p2_[g][e];
-                    s0 += out[e];
-                    s1 += o1;
-                    s2 += out[e] * p2q_[g][e];
-                    s3 += o1 * p2q_[g][e];
+                for (int h = 1; h < NP; ++h) {
+                    const V2 o1 = p_mul(out[h], p2_[g][h]);
+                    ps0 = p_add(ps0, out[h]);
+                    ps1 = p_add(ps1, o1);
+                    ps2 = p_fma(out[h], p2q_[g][h], ps2);
+                    ps3 = p_fma(o1, p2q_[g][h], ps3);
                 }
+                const T s0 = VW == 1 ? ps0.x : ps0.x + ps0.y, s1 = VW == 1 ? ps1.x : ps1.x + ps1.y;
+                const T s2 = VW == 1 ? ps2.x : ps2.x + ps2.y, s3 = VW == 1 ? ps3.x : ps3.x + ps3.y;
                 const T prs0 = pr * s0, p3s0 = p3v * s0, rr = pr * pr + p3v * p3v;
                 const T e10 = rr * s0 + s2;  // sum out (p_R^2 + p_2^2 + p_3^2)
                 if (N3_ == 0 && M.reduced && k == 1) {

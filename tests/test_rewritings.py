@@ -1,5 +1,6 @@
 """The exact rewritings the kernels use, restated in numpy and checked against the direct forms of
-the formulas on random FP64 inputs (CPU): the ascending-window WENO5 for both upwind directions,
+the formulas on random FP64 inputs (CPU): the ascending-window WENO5 for both upwind directions
+(and its negation-free arrangement, evaluated on pairs of momenta),
 the reconstruction of f itself with epsilon scaled by the squared weight,
 the Shakhov factor and J1 as polynomials in x1 = p_2 - u_2 along a vector of momenta, and the
 double-float split of an FP64 sum.  The kernels themselves are checked against the oracle by the
@@ -32,6 +33,23 @@ def weno5_ascending(w0, w1, w2, w3, w4, sigma, e4=4e-6):
     return w2 + sum(x * y for x, y in zip(a, X)) / (12 * sum(a))
 
 
+def weno5_negation_free(w0, w1, w2, w3, w4, sigma, e4=4e-6):
+    # the arrangement the stage kernel evaluates on pairs of momenta: -d0 and -tC enter instead of
+    # d0 and tC, so that every step is one fused multiply-add, add or product
+    nd0, d1, d2, d3 = w0 - w1, w2 - w1, w3 - w2, w4 - w3
+    D1, D2, D3 = d1 + nd0, d2 - d1, d3 - d2
+    tL, ntC, tR = 3 * d1 + nd0, d1 + d2, -3 * d2 + d3
+    E = [tL * tL + (13 / 3 * D1) * D1 + e4, ntC * ntC + (13 / 3 * D2) * D2 + e4, tR * tR + (13 / 3 * D3) * D3 + e4]
+    m = np.minimum(E[0], np.minimum(E[1], E[2]))
+    dL, dR = (0.1, 0.3) if sigma > 0 else (0.3, 0.1)
+    s = [m / E[0], m / E[1], m / E[2]]
+    a = [dL * (s[0] * s[0]), 0.6 * (s[1] * s[1]), dR * (s[2] * s[2])]
+    s3, ns3 = 3.0 * sigma, -3.0 * sigma
+    X = [s3 * tL + D1, s3 * ntC + D2, ns3 * tR + D3]
+    num = a[2] * X[2] + (a[1] * X[1] + a[0] * X[0])
+    return w2 + num / (12 * ((a[0] + a[1]) + a[2]))
+
+
 def test_ascending_weno5_equals_the_direct_form_both_directions():
     rng = np.random.default_rng(3)
     w = rng.normal(size=(5, 20000)) * np.exp(rng.normal(size=(5, 20000)))
@@ -40,6 +58,8 @@ def test_ascending_weno5_equals_the_direct_form_both_directions():
     scale = np.max(np.abs(w), axis=0)
     assert np.max(np.abs(weno5_ascending(*w, +1) - fwd) / scale) < 1e-12
     assert np.max(np.abs(weno5_ascending(*w, -1) - rev) / scale) < 1e-12
+    assert np.max(np.abs(weno5_negation_free(*w, +1) - fwd) / scale) < 1e-12
+    assert np.max(np.abs(weno5_negation_free(*w, -1) - rev) / scale) < 1e-12
 
 
 def test_weno5_of_f_with_scaled_epsilon_is_w_times_weno5_of_f_over_w():
