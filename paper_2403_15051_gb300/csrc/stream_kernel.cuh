@@ -270,6 +270,15 @@ __device__ __forceinline__ void stream_issue(const StageArgs& A, const MomSet& M
                 }
             }
             if (records && (part & 2)) bulk_g2s(cellT, rsrc, (uint32_t)(Be * rs * sizeof(T)), bar);
+            // the tile's f_n (read once per population at the end of its update, from HBM) into L2
+            // while the item is staged and computed
+            if ((part & 1) && A.mode == 0 && (sizeof(T) == 4 ? A.fa : (float)A.a) != 0.f) {
+                const T* fn = f_n + I.f_off + (long long)c0 * Np;
+                if (M.slices == 1)
+                    bulk_prefetch_l2(fn, (uint32_t)(Be * Np * sizeof(T)));
+                else
+                    for (int cl = 0; cl < Be; ++cl) bulk_prefetch_l2(fn + (long long)cl * Np + slice_off, (uint32_t)(Ms * sizeof(T)));
+            }
         }
     } else {
         for (int cc = lo; cc < hi; ++cc)
