@@ -517,7 +517,19 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 const int kk = cd >> 20, i = (cd >> 10) & 1023, jb = cd & 1023;
                 const int k = sl * KS + kk;
                 const int vb = ((kk * nR + i) * n2v + jb) * VW;  // element offset in the slice
+                const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
                 const T pr = pr_[g], p3v = p3_[g];
+                // f_n for the RK combination, requested first so that its latency overlaps the update.
+                // f_n: read-only for the stage kernel; written earlier in the same launch for the
+                // persistent step kernel, which reads it coherently (L2)
+                V2 fnv[NP];
+                const bool use_fn = A.mode == 0 && ca_ != T(0);
+                if (use_fn) {
+                    if constexpr (kCoherent)
+                        ldcg_pairs<T, VW>(f_n + gidx, fnv);
+                    else
+                        ldg_pairs<T, VW>(f_n + gidx, fnv);
+                }
                 // advection: WENO5 value at the right face, upwind by sign(p_R)
                 V2 vr[NP];
                 if (c == N - 1 && pr < T(0)) {
@@ -664,20 +676,12 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                     const V2 j1 = p_fma(p_fma(pJ2, x1, pJ1), x1, pJ0);
                     out[h] = p_fma(fmb, j1, p_fma(p_sub(fS, fv[h]), pitau, p_add(nadv, nfrc)));
                 }
-                const long long gidx = I.f_off + (long long)c * Np + slice_off + vb;
                 if (A.mode == 0) {
                     // a f_n + b (f + dt L) with a = 1 - b, written as f_n + b ((f - f_n) + dt L):
                     // exactly affine whatever the rounding of b (in FP32, fl(1/3) + fl(2/3)
                     // exceeds one by 3e-8, which would scale the state by that much every step)
                     const V2 pdt = p_splat(dt);
-                    if (ca_ != T(0)) {
-                        V2 fnv[NP];
-                        // f_n: read-only for the stage kernel; written earlier in the same launch for
-                        // the persistent step kernel, which reads it coherently (L2)
-                        if constexpr (kCoherent)
-                            ldcg_pairs<T, VW>(f_n + gidx, fnv);
-                        else
-                            ldg_pairs<T, VW>(f_n + gidx, fnv);
+                    if (use_fn) {
                         const V2 pcb = p_splat(cb_);
 #pragma unroll
                         for (int h = 0; h < NP; ++h) out[h] = p_fma(pcb, p_fma(pdt, out[h], p_sub(fv[h], fnv[h])), fnv[h]);
