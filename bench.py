@@ -352,10 +352,13 @@ def run_ours(args):
     if args.tiling:
         # a pinned tiling instead of the tuner's choice (profiling: a profiler's serialisation of the
         # launches would steer the tuner's timings)
-        cells, threads, form = args.tiling.split(",")
+        parts = args.tiling.split(",")
+        cells, threads, form = parts[:3]
         S.set_autotune(0)
         S.set_tiling(int(cells), 0, int(threads))
         S.closure_form(1 if form == "batch" else 0)
+        if len(parts) > 3:
+            S.stage_min_blocks(int(parts[3]))
     persistent = S.set_persistent_step(None)  # the library's default scheduling
     S.set_graph_steps(1)
     stream = torch.cuda.ExternalStream(S.stream_handle())
@@ -729,7 +732,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="leave out the compact time-to-steady comparison")
     ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")
-    ap.add_argument("--tiling", default="", help="CELLS,THREADS,chain|batch: a pinned tiling, tuner off")
+    ap.add_argument("--tiling", default="",
+                    help="CELLS,THREADS,chain|batch[,MIN_BLOCKS]: a pinned tiling (and stage register bound), tuner off")
     ap.add_argument("--time-to-steady", action="store_true",
                     help="time-to-steady comparison: plain FP64 sequential vs batched warm-started FP32")
     ap.add_argument("--tts-train", type=int, default=4096)

@@ -278,6 +278,14 @@ int fdlb_get_tiling(fdlb_handle h, int* cells_per_tile, int* slice_k, int* threa
  * pointer may be NULL. */
 int fdlb_get_stage_kernel(fdlb_handle h, int* vector_width, int* vectors_per_thread, int* min_blocks);
 
+/* Pins the register bound of the stage kernel (the choice fdlb_autotune makes among the variants
+ * built for the shape): min_blocks 1 (none beyond the 512-thread bound), or 2, 3, 5 where built
+ * (the 16 x 8 x 8 FP32 cylinder: 3 for blocks of up to 256 threads, 2, 3 and 5 for the row
+ * kernel).  The arithmetic and its order are the same in all, so results do not change by a bit.
+ * min_blocks -1 changes nothing.  *in_use (may be NULL) = the bound in use.  FDLB_EINVAL for a
+ * bound not built for the handle's shape (the handle keeps its previous one). */
+int fdlb_set_stage_min_blocks(fdlb_handle h, int min_blocks, int* in_use);
+
 /* The K^h contraction of the curvature force on the tensor cores (default off): an
  * nR x nR by nR x (n2 KS) product per cell in split TF32 (K = Kh + Kl, f = fh + fl; three
  * TF32 products with FP32 accumulation, FP32-level accuracy) with mma.sync m16n8k8, for FP32

@@ -88,7 +88,7 @@ struct Solver {
     size_t cbatch_smem = 0;
     int autotune_mode = 1;  // 0 off; 1 tune on the first step of a batch; 2 also of a single instance
     int stall_checks = 0;   // run_to_steady: checks without halving the best residual before an instance stops
-    int stage_minb = 1;     // register bound of the stage kernel (1; 3 or 2 blocks per SM where built)
+    int stage_minb = 1;     // register bound of the stage kernel (1; 3, 2 or 5 blocks per SM where built)
     bool tuned = false;     // the tuner has run (or its cached choice was applied) for this handle
     int closure_wst = 0;                           // staged band-row elements per closure block
     int grid_stream = 1, grid_closure = 1;
@@ -682,7 +682,7 @@ int configure_tiling(Solver& S, int B, int KS, int threads) {
     }
     if (nt > 512 || (long long)nt * cfg.nv < Vs) return FDLB_EINVAL;
     if (cfg.vw == 8)
-        cfg.minb = (S.stage_minb == 2 || S.stage_minb == 3) ? S.stage_minb : 1;
+        cfg.minb = (S.stage_minb == 2 || S.stage_minb == 3 || S.stage_minb == 5) ? S.stage_minb : 1;
     else
         cfg.minb = (S.stage_minb == 3 && cfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && nt <= 256) ? 3 : 1;
     S.scfg = cfg;
@@ -1159,13 +1159,13 @@ int run_autotune(Solver& S, bool use_cache) {
     if (best < 0.f) best = 1e30f;
     const int Bs[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
     // the register bound of the stage kernel: three blocks per SM where that variant is built, and
-    // for the row kernel also two
+    // for the row kernel also two and five
     const bool minb_choice = S.scfg.spec && S.tsize == 4 && S.geometry == FDLB_CYL && S.threads <= 256;
     const bool rows = S.scfg.vw == 8;
     int rc = FDLB_OK;
-    for (int mb : {1, 3, 2}) {
+    for (int mb : {1, 3, 2, 5}) {
         if (mb == 3 && !minb_choice) continue;
-        if (mb == 2 && !rows) continue;
+        if ((mb == 2 || mb == 5) && !rows) continue;
         S.stage_minb = mb;
         for (int B : Bs) {
             if (B == bestB && mb == bestM) continue;
@@ -2176,6 +2176,24 @@ int fdlb_set_closure_form(fdlb_handle h, int form, int* in_use) try {
         if (rc) return rc;
     }
     if (in_use) *in_use = S->closure_batch;
+    return FDLB_OK;
+} FDLB_HOST_CATCH
+
+int fdlb_set_stage_min_blocks(fdlb_handle h, int min_blocks, int* in_use) try {
+    Solver* S = SOL(h);
+    if (!S || min_blocks < -1 || min_blocks == 0 || min_blocks > 5) return FDLB_EINVAL;
+    if (min_blocks > 0) {
+        const int old = S->stage_minb;
+        S->stage_minb = min_blocks;
+        int rc = fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
+        if (rc == FDLB_OK && S->scfg.minb != min_blocks) rc = FDLB_EINVAL;  // not built for this shape
+        if (rc) {
+            S->stage_minb = old;
+            fdlb::configure_tiling(*S, S->B, S->KS, S->threads);
+            return rc;
+        }
+    }
+    if (in_use) *in_use = S->scfg.minb;
     return FDLB_OK;
 } FDLB_HOST_CATCH
 

@@ -38,7 +38,9 @@ inline cudaError_t launch_maybe_programmatic(void (*kern)(Args...), int grid, in
 // Row stride of K^h in the stage kernel's shared memory: a multiple of four elements (16-byte
 // vector loads of a row) whose rows fall on distinct banks for the rows a quarter warp reads.
 inline __host__ __device__ int kr_stride(int nR) { return (nR + 3) / 4 * 4 + 4; }
-// Elements from the start of the tables to K^h: K_2, padded to 16 bytes.
+// Elements of the p_2 nodes at the start of the tables, padded to 16 bytes (four elements).
+inline __host__ __device__ int p2_span(int n2) { return (n2 + 3) / 4 * 4; }
+// Elements from K_2 to K^h: K_2, padded to 16 bytes.
 inline __host__ __device__ int kr_offset(int n2, int tsize) { return (n2 * n2 * tsize + 15) / 16 * 16 / tsize; }
 
 struct StreamSmem {
@@ -46,9 +48,9 @@ struct StreamSmem {
 };
 
 // Shared-memory plan of the stream kernel (byte offsets), shared with the host: the staged rows
-// of cells c0-3 .. c0+B+2, the tile's collision records, the tables (K_2 in the vector-swizzled
-// order, then K^h with row stride kr_stride(nR), K_3 with row stride n3+1, the nodes and weights,
-// the wall Maxwellians), the cell geometry and the per-warp partial sums.
+// of cells c0-3 .. c0+B+2, the tile's collision records, the tables (the p_2 nodes, K_2
+// transposed, then K^h with row stride kr_stride(nR), K_3 with row stride n3+1, the other nodes
+// and the weights, the wall Maxwellians), the cell geometry and the per-warp partial sums.
 __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, int n2, int n3, int nwarps, int tsize,
                                                        int mma = 0, int krg = 0) {
     auto al = [](long long x) { return (int)((x + 15) & ~15LL); };
@@ -60,8 +62,8 @@ __host__ __device__ inline StreamSmem stream_smem_plan(int B, int Ms, int nR, in
     off += al((long long)B * record_stride(nR, n2, n3) * tsize);
     s.tabs = off;
     // (no K^h table when K^h f comes from the contraction kernel: krg)
-    off += al((long long)(2 * (nR + n2 + n3) + (krg ? 0 : nR) * kr_stride(nR) + kr_offset(n2, tsize) + n3 * (n3 + 1) +
-                          2 * (nR + n2 + n3)) * tsize);
+    off += al((long long)(p2_span(n2) + 2 * (nR + n3) + n2 + (krg ? 0 : nR) * kr_stride(nR) + kr_offset(n2, tsize) +
+                          n3 * (n3 + 1) + 2 * (nR + n2 + n3)) * tsize);
     s.geo = off;
     off += al((long long)B * 3 * tsize);
     s.red = off;

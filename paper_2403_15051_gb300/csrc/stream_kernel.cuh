@@ -165,7 +165,8 @@ __device__ __forceinline__ void st_pairs(T* p, const Pair<T> (&o)[(VW + 1) / 2])
 }
 
 // Local names of the stage's dimensions and of its shared-memory plan (StreamSmem): fs the
-// staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sK2 K_2 in the vector-swizzled
+// staged rows of cells c0-3 .. c0+B+2, cellT the tile's records, sp_2 the p_2 nodes (first in the
+// tables: aligned vector loads), sK2 K_2 in the vector-swizzled
 // transposed, [b][j] (the coefficients of input b for a vector's outputs: one aligned vector load),
 // sKR K^h with row stride krs,
 // sK3 K_3 with row stride n3+1, nodes and weights, sgw the inner and outer wall Maxwellians per
@@ -190,13 +191,13 @@ __device__ __forceinline__ void st_pairs(T* p, const Pair<T> (&o)[(VW + 1) / 2])
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                                                       \
     T* fs = reinterpret_cast<T*>(smem_raw + P.fs);                                                               \
     T* cellT = reinterpret_cast<T*>(smem_raw + P.rec);                                                           \
-    T* sK2 = reinterpret_cast<T*>(smem_raw + P.tabs);                                                            \
+    T* sp_2 = reinterpret_cast<T*>(smem_raw + P.tabs);                                                           \
+    T* sK2 = sp_2 + p2_span(n2);                                                                                 \
     const int krs = kr_stride(nR);                                                                               \
     T* sKR = sK2 + kr_offset(n2, (int)sizeof(T));                                                                \
     T* sK3 = sKR + (A.krf ? 0 : nR) * krs;                                                                       \
     T* sp_R = sK3 + n3 * (n3 + 1);                                                                               \
-    T* sp_2 = sp_R + nR;                                                                                         \
-    T* sp_3 = sp_2 + n2;                                                                                         \
+    T* sp_3 = sp_R + nR;                                                                                         \
     T* sw_R = sp_3 + n3;                                                                                         \
     T* sw_2 = sw_R + nR;                                                                                         \
     T* sw_3 = sw_2 + n2;                                                                                         \
@@ -430,14 +431,14 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
     constexpr int NP = (VW + 1) / 2;
     int vcode[NV];  // (kk << 20) | (i << 10) | jb, -1 if none
     T pr_[NV], p3_[NV];
-    V2 e4w_[NV][NP], p2_[NV][NP], p2q_[NV][NP], vl_[NV][NP];
+    V2 e4w_[NV][NP], vl_[NV][NP];
 #pragma unroll
     for (int g = 0; g < NV; ++g) {
         const int v = tid + g * NT;
         vcode[g] = -1;
         pr_[g] = p3_[g] = T(0);
 #pragma unroll
-        for (int h = 0; h < NP; ++h) e4w_[g][h] = p2_[g][h] = p2q_[g][h] = vl_[g][h] = p_splat(T(0));
+        for (int h = 0; h < NP; ++h) e4w_[g][h] = vl_[g][h] = p_splat(T(0));
         if (v < Vs) {
             const int kk = v / (nR * n2v), rem = v % (nR * n2v), i = rem / n2v, jb = rem % n2v;
             const int k = sl * KS + kk;
@@ -449,8 +450,6 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
 #pragma unroll
             for (int h = 0; h < NP; ++h) {
                 const int ja = jb * VW + 2 * h, jc = VW == 1 ? ja : ja + 1;
-                p2_[g][h] = p_make(sp_2[ja], sp_2[jc]);
-                p2q_[g][h] = p_mul(p2_[g][h], p2_[g][h]);
                 // WENO5 of f / w (Sec. II.C) taken on f itself: with eps scaled by w^2 the face value
                 // of f is w times that of f / w, and the flux needs no division by the weight.  In
                 // FP32 eps w^2 is kept above the float range's floor (weights below ~1e-16 at large
@@ -631,9 +630,12 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 // factor f^S / f^MB = 1 + c_S (|x|^2 / (5 T) - 1) x.q is a cubic in x1 and J1 / f^MB
                 // (which holds |x|^2 / (2T) - 5/2 and the strain x.S.x / T) a quadratic: their
                 // coefficients are formed once per vector, then two Horner evaluations per momentum.
-                V2 fv[NP], g2v[NP];
+                V2 fv[NP], g2v[NP], p2v[NP], p2q[NP];
                 ld_pairs<T, VW>(fc + vb, fv);
                 ld_pairs<T, VW>(g2c + jb * VW, g2v);
+                ld_pairs<T, VW>(sp_2 + jb * VW, p2v);
+#pragma unroll
+                for (int h = 0; h < NP; ++h) p2q[h] = p_mul(p2v[h], p2v[h]);
                 const T x0 = pr - u0, x2 = p3v - u2;
                 T xsA = x0 * x0 + x2 * x2;
                 const T xqA = x0 * q0 + x2 * q2;
@@ -664,13 +666,13 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                     V2 nfrc;
                     if (GEOM == 0) {
                         // -kf (p_2^2 K^h f - p_R K_2 f)
-                        nfrc = p_mul(p_splat(-kf), p_fma(p2q_[g][h], KRf[h], p_mul(p_splat(-pr), K2f[h])));
+                        nfrc = p_mul(p_splat(-kf), p_fma(p2q[h], KRf[h], p_mul(p_splat(-pr), K2f[h])));
                     } else {
                         // -((kf p_2^2 + kf p_3^2) K^h f - kf p_R (K_2 f + K_3 f))
-                        const V2 na = p_fma(p_splat(-kf), p2q_[g][h], p_splat(-(kf * p3v * p3v)));
+                        const V2 na = p_fma(p_splat(-kf), p2q[h], p_splat(-(kf * p3v * p3v)));
                         nfrc = p_fma(na, KRf[h], p_mul(p_splat(kf * pr), p_add(K2f[h], K3f[h])));
                     }
-                    const V2 x1 = p_sub(p2_[g][h], pu1);
+                    const V2 x1 = p_sub(p2v[h], pu1);
                     const V2 fmb = p_mul(pfmbA, g2v[h]);
                     const V2 fS = p_mul(fmb, p_fma(p_fma(p_fma(pF3, x1, pF2), x1, pF1), x1, pF0));
                     const V2 j1 = p_fma(p_fma(pJ2, x1, pJ1), x1, pJ0);
@@ -693,15 +695,15 @@ __device__ __forceinline__ void stream_compute(const StageArgs& A, const MomSet&
                 st_pairs<T, VW>(f_out + gidx, out);
                 // raw sums: power sums over the vector's p_2 (per lane of the pairs, then the two
                 // lanes), then the 13 moments
-                V2 ps1 = p_mul(out[0], p2_[g][0]);
-                V2 ps0 = out[0], ps2 = p_mul(out[0], p2q_[g][0]), ps3 = p_mul(ps1, p2q_[g][0]);
+                V2 ps1 = p_mul(out[0], p2v[0]);
+                V2 ps0 = out[0], ps2 = p_mul(out[0], p2q[0]), ps3 = p_mul(ps1, p2q[0]);
 #pragma unroll
                 for (int h = 1; h < NP; ++h) {
-                    const V2 o1 = p_mul(out[h], p2_[g][h]);
+                    const V2 o1 = p_mul(out[h], p2v[h]);
                     ps0 = p_add(ps0, out[h]);
                     ps1 = p_add(ps1, o1);
-                    ps2 = p_fma(out[h], p2q_[g][h], ps2);
-                    ps3 = p_fma(o1, p2q_[g][h], ps3);
+                    ps2 = p_fma(out[h], p2q[h], ps2);
+                    ps3 = p_fma(o1, p2q[h], ps3);
                 }
                 const T s0 = VW == 1 ? ps0.x : ps0.x + ps0.y, s1 = VW == 1 ? ps1.x : ps1.x + ps1.y;
                 const T s2 = VW == 1 ? ps2.x : ps2.x + ps2.y, s3 = VW == 1 ? ps3.x : ps3.x + ps3.y;
@@ -828,8 +830,8 @@ __device__ __forceinline__ void stream_body(const StageArgs& A, const MomSet& M)
 // The stage kernel; MINB = the blocks per SM the register allocation is bounded for: 1 (up to 512
 // threads, 128 registers each: two blocks of 256 threads reside) or, for blocks of at most 256
 // threads, 3 (at most 85 registers each); for the row kernel (VW = 8, blocks of at most 128
-// threads) 3 or 2 (at most 170 or 255 registers each).  The arithmetic and its order are the same
-// in all.
+// threads) 5, 3 or 2 (at most 102, 170 or 255 registers each; five blocks fit in shared memory
+// with tiles of up to three cells).  The arithmetic and its order are the same in all.
 template <typename T, int GEOM, int VW, int NV, int NR_, int N2_, int N3_, int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? 512 : (VW == 8 ? 128 : 256), MINB) stream_kernel(StageArgs A, MomSet M) {
     stream_body<T, GEOM, VW, NV, NR_, N2_, N3_>(A, M);
@@ -857,6 +859,7 @@ cudaError_t launch_stream_dispatch(const StreamCfg& cfg, const StageArgs& A, con
             // the cylinder's FP32 shape also as one vector of a whole p_2 row (8 momenta) per thread
             if (cfg.vw == 8 && cfg.nv == 1) {
                 if (threads > 128 && cfg.minb != 1) return cudaErrorInvalidValue;
+                if (cfg.minb == 5) return launch_stream_t<T, G, 8, 1, SR, S2, S3, 5>(A, M, grid, threads, smem, s);
                 if (cfg.minb == 3) return launch_stream_t<T, G, 8, 1, SR, S2, S3, 3>(A, M, grid, threads, smem, s);
                 if (cfg.minb == 2) return launch_stream_t<T, G, 8, 1, SR, S2, S3, 2>(A, M, grid, threads, smem, s);
                 return launch_stream_t<T, G, 8, 1, SR, S2, S3>(A, M, grid, threads, smem, s);

@@ -98,6 +98,7 @@ def load_library():
         "fdlb_set_stall_checks": (c_int, [H, c_int]),
         "fdlb_step_change": (c_int, [H, POINTER(c_double)]),
         "fdlb_get_stage_kernel": (c_int, [H, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+        "fdlb_set_stage_min_blocks": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_programmatic_launch": (c_int, [H, c_int]),
         "fdlb_set_tensor_contraction": (c_int, [H, c_int, POINTER(c_int)]),
         "fdlb_set_persistent_step": (c_int, [H, c_int, POINTER(c_int)]),
@@ -378,6 +379,13 @@ class Solver:
         """0: the chain form, 1: the batch form, -1: no change; returns the form in use."""
         u = c_int()
         _check(self._L.fdlb_set_closure_form(self._h, int(form), byref(u)), "fdlb_set_closure_form")
+        return u.value
+
+    def stage_min_blocks(self, min_blocks=-1):
+        """Pins the stage kernel's register bound (1, or 2, 3, 5 where built; -1: no change);
+        returns the bound in use (fdlb_set_stage_min_blocks in include/fdlb.h)."""
+        u = c_int()
+        _check(self._L.fdlb_set_stage_min_blocks(self._h, int(min_blocks), byref(u)), "fdlb_set_stage_min_blocks")
         return u.value
 
     def autotune(self):

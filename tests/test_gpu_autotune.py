@@ -65,7 +65,7 @@ def test_cached_choice_is_reused():
 
 def test_tuned_row_kernel_steps_bit_for_bit_like_the_untuned_one():
     # the 16 x 8 x 8 FP32 cylinder in blocks of 128 threads (a whole p_2 row per thread): the tuner
-    # also tries the register bounds of 3 and 2 blocks per SM, which change no result bit
+    # also tries the register bounds of 5, 3 and 2 blocks per SM, which change no result bit
     ds = _batch("fp32")
     A = fdlb.Solver(ds)
     A.set_autotune(0)
@@ -79,3 +79,38 @@ def test_tuned_row_kernel_steps_bit_for_bit_like_the_untuned_one():
     B.step(12)
     for q in range(len(ds)):
         assert np.array_equal(A.get_f(q), B.get_f(q)), q
+
+
+def test_every_register_bound_of_the_row_kernel_steps_bit_for_bit_alike():
+    # the row kernel's variants bounded for 1, 2, 3 and 5 blocks per SM, pinned one by one (tiles of
+    # three cells, which five blocks fit): the same populations and moments bit for bit
+    ds = _batch("fp32")
+    out = {}
+    for mb in (1, 2, 3, 5):
+        S = fdlb.Solver(ds)
+        S.set_autotune(0)
+        S.set_tiling(3, 0, 128)
+        assert S.stage_min_blocks(mb) == mb
+        t = S.tiling()
+        assert t["stage_vector_width"] == 8 and t["stage_min_blocks_per_sm"] == mb
+        S.step(9)
+        out[mb] = ([S.get_f(q) for q in range(len(ds))], S.moments_all())
+    for mb in (2, 3, 5):
+        for q in range(len(ds)):
+            assert np.array_equal(out[mb][0][q], out[1][0][q]), (mb, q)
+        assert np.array_equal(out[mb][1], out[1][1]), mb
+
+
+def test_a_register_bound_not_built_for_the_shape_is_refused():
+    S = fdlb.Solver(_batch("fp32"))
+    S.set_autotune(0)
+    S.set_tiling(3, 0, 128)
+    before = S.tiling()
+    with pytest.raises(fdlb.FdlbError):
+        S.stage_min_blocks(4)
+    assert S.tiling() == before
+    D = fdlb.Solver(_batch("fp64"))
+    D.set_autotune(0)
+    with pytest.raises(fdlb.FdlbError):
+        D.stage_min_blocks(5)
+    assert D.stage_min_blocks(1) == 1
