@@ -490,7 +490,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": sum(H.state_bytes() for H in handles), "d2h_bytes_per_step": d2h // steps}
 
     e2e_seq = e2e_run([S], e2e_steps)
-    G = 4 if len(ds) >= 8 else 1
+    G = args.e2e_handles if len(ds) >= 2 * args.e2e_handles else 1
     if G > 1:
         order = sorted(range(len(ds)), key=lambda q: -ds[q]["n_cells"])
         streams = [torch.cuda.Stream() for _ in range(G)]
@@ -731,6 +731,8 @@ def main():
                              "couette_cyl_reduced_q20"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="leave out the compact time-to-steady comparison")
+    ap.add_argument("--e2e-handles", type=int, default=4,
+                    help="handles (one stream each) the end-to-end pipeline deals a batch's instances over")
     ap.add_argument("--profile", action="store_true", help="warm-up + K steps only (for ncu launch lists)")
     ap.add_argument("--tiling", default="",
                     help="CELLS,THREADS,chain|batch[,MIN_BLOCKS]: a pinned tiling (and stage register bound), tuner off")
