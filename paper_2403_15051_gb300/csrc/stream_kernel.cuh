@@ -19,8 +19,11 @@
 // Thread mapping: a "vector" is VW momenta with the same (k, i) and consecutive j, which are
 // contiguous in the [k][i][j] layout.  A thread owns up to NV vectors for the whole kernel, so
 // every shared-memory access is a VW-wide load: the five WENO rows, the column of the K^h
-// contraction (shared by the VW momenta), the row of the K_2 contraction.  All momenta of a
-// vector share p_R and hence the upwind direction.
+// contraction (shared by the VW momenta), the row of the K_2 contraction and, from K_2 stored
+// transposed, each input's coefficients for the vector's outputs.  All momenta of a vector share
+// p_R and hence the upwind direction.  A vector's momenta are processed in pairs of lanes (packed
+// FP32x2 operations for FP32 populations), every operation written out, so that a lane's result
+// does not depend on the pairing.
 #pragma once
 
 #include <type_traits>
