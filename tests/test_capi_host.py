@@ -155,6 +155,8 @@ def test_handle_calls_reject_a_null_handle(lib):
     assert lib.fdlb_set_wait_test(null, 0, 0) == 1
     assert lib.fdlb_clear_error(null) == 1
     assert lib.fdlb_step_kernel_times(null, ctypes.byref(d), ctypes.byref(n1), ctypes.byref(n2)) == 1
+    assert lib.fdlb_set_stage_min_blocks(null, 1, ctypes.byref(used)) == 1
+    assert lib.fdlb_set_closure_form(null, 0, ctypes.byref(used)) == 1
 
 
 def test_params_marshalling_rejects_an_unknown_precision():

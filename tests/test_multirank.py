@@ -104,3 +104,28 @@ def test_algorithmic_flops_and_units_of_the_benchmark_workloads():
     assert bench.alg_flops_per_update(wl.SPH, 24, 12, 12) == 272
     assert bench.units_per_step([wl.fourier_cyl_1024()]) == 1024 * 1024
     assert bench.units_per_step(bench.workload("fourier_sph_2048")) == 2048 * 3456
+
+
+def test_recorded_traffic_follows_the_kernel_code_not_its_comments(tmp_path, monkeypatch):
+    """The roofline's traffic comes from the committed ncu record only while the timed kernels' code
+    is the code it was taken on: the source hash ignores comments and spacing and changes with any
+    change of code."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = tmp_path / "k.cuh"
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["k.cuh"])
+    src.write_text("// the stage\n__global__ void k(float* a) { a[0] = 1.f; }  /* one store */\n")
+    h0 = bench.kernel_source_hash()
+    rec = {"batch_512:stream_kernel": {"source_hash": h0, "dram_bytes_per_launch": 6.0e9}}
+    (tmp_path / "profiles" / "roofline_traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("batch_512", "stream_kernel") == 6.0e9
+    assert bench.recorded_traffic("batch_64", "stream_kernel") is None
+    src.write_text("// the fused stage\n__global__ void k(float* a)\n{\n    a[0] = 1.f;  // a store\n}\n")
+    assert bench.kernel_source_hash() == h0
+    assert bench.recorded_traffic("batch_512", "stream_kernel") == 6.0e9
+    src.write_text("__global__ void k(float* a) { a[0] = 2.f; }\n")
+    assert bench.kernel_source_hash() != h0
+    assert bench.recorded_traffic("batch_512", "stream_kernel") is None
